@@ -1,0 +1,57 @@
+"""Write workloads/critical_masses.json: near-critical masses of the benchmark
+gauge configurations, computed by the oracle's critical-mass finder only.
+
+Test infrastructure (see ``oracle/__init__.py``): the stored masses are inputs
+of the workloads; every value in the file comes from ``oracle.critical``.
+Each entry also records the mean plaquette and Q of the configuration so that
+a regenerated configuration can be checked against it.
+
+    python -m oracle.find_critical_masses [name ...]
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W                       # noqa: E402
+from oracle import critical                 # noqa: E402
+
+OUT = os.path.join(ROOT, "workloads", "critical_masses.json")
+
+# name -> (L, beta, sweeps, seed)
+CONFIGS = {
+    "L128_b6_s1": (128, 6.0, 200, 1),
+    "L128_b6_s2": (128, 6.0, 200, 2),
+    "L256_b10_s1": (256, 10.0, 500, 1),
+}
+
+
+def main(names):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names:
+        L, beta, sweeps, seed = CONFIGS[name]
+        tried = []
+        while True:
+            t0 = time.time()
+            th = W.quenched_u1_angles(L, L, beta, sweeps, seed)
+            res = critical.near_critical_mass(W.links_from_angles(th))
+            tried.append(seed)
+            if res is not None:
+                break
+            seed += 1000                    # no real mode near the physical branch
+        res.update({"L": L, "beta": beta, "sweeps": sweeps, "seed": seed, "seeds_tried": tried,
+                    "plaquette": W.mean_plaquette(th), "Q": round(W.topological_charge(th)),
+                    "finder_seconds": round(time.time() - t0, 1)})
+        data[name] = res
+        print(name, res, flush=True)
+        json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(CONFIGS))

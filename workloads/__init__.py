@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module holds no arithmetic of the multigrid method.  It produces:
+
+* quenched U(1) gauge fields from the Wilson plaquette action of the
+  paper's Results section (S = -beta * sum_p Re U_p; the printed sign is
+  garbled, the weight used here is exp(-S) with that S, so that beta > 0
+  orders the links), by Metropolis sweeps from a cold start;
+* complex Gaussian source vectors chi (E|z|^2 = 1);
+* the random starting vectors the adaptive setup draws (Eq. "relax" starts,
+  the power-iteration start and the minimum-residual start of the smoother),
+  passed to both sides as an input so that no side re-implements a generator;
+* gauge diagnostics: the mean plaquette and the topological charge Q.
+
+Array conventions (both sides): a lattice field is indexed [t][x] with the
+site index x + Lx * t.  Links are ``U[mu][t][x]`` with mu = 0 the x
+direction and mu = 1 the t direction; a spinor is ``psi[t][x][spin]``.
+All random numbers come from ``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "quenched_u1_angles",
+    "links_from_angles",
+    "quenched_u1",
+    "plaquette_angles",
+    "mean_plaquette",
+    "topological_charge",
+    "gaussian_field",
+    "level_shapes",
+    "setup_noise",
+    "setup_noise_len",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def plaquette_angles(theta: np.ndarray) -> np.ndarray:
+    """Angle of U_p(x) = U_x^0 U_{x+0}^1 U_{x+1}^{0*} U_x^{1*}, shape [Lt, Lx].
+
+    theta[0] holds the x-links and theta[1] the t-links, both [Lt, Lx].
+    """
+    th0, th1 = theta[0], theta[1]
+    return (th0 + np.roll(th1, -1, axis=1) - np.roll(th0, -1, axis=0) - th1)
+
+
+def mean_plaquette(theta: np.ndarray) -> float:
+    """Volume average of Re U_p."""
+    return float(np.mean(np.cos(plaquette_angles(theta))))
+
+
+def topological_charge(theta: np.ndarray) -> float:
+    """Q = (1/2pi) sum_x arg U_p(x) with arg in (-pi, pi]; an integer on a torus."""
+    ph = plaquette_angles(theta)
+    arg = np.angle(np.exp(1j * ph))
+    arg = np.where(arg <= -math.pi, arg + 2 * math.pi, arg)
+    return float(np.sum(arg) / (2 * math.pi))
+
+
+def _metropolis_half(theta, mu, parity, beta, eps, rng):
+    """Update every link of direction mu whose other coordinate has the given
+    parity.  Such links share no plaquette, so they are updated at once."""
+    Lt, Lx = theta.shape[1:]
+    th0, th1 = theta[0], theta[1]
+    if mu == 0:
+        # link theta0(x,t) enters p(x,t) with + and p(x,t-1) with -.
+        a = np.roll(th1, -1, axis=1) - np.roll(th0, -1, axis=0) - th1           # p(x,t) = th0 + a
+        b = (np.roll(th0, 1, axis=0) + np.roll(np.roll(th1, -1, axis=1), 1, axis=0)
+             - np.roll(th1, 1, axis=0))                                           # p(x,t-1) = b - th0
+        mask = (np.arange(Lt)[:, None] % 2 == parity) & np.ones((1, Lx), bool)
+        cur = th0
+    else:
+        # link theta1(x,t) enters p(x,t) with - and p(x-1,t) with +.
+        a = th0 - np.roll(th0, -1, axis=0) + np.roll(th1, -1, axis=1)           # p(x,t) = a - th1
+        b = (np.roll(th0, 1, axis=1) - np.roll(np.roll(th0, -1, axis=0), 1, axis=1)
+             - np.roll(th1, 1, axis=1))                                           # p(x-1,t) = b + th1
+        mask = (np.arange(Lx)[None, :] % 2 == parity) & np.ones((Lt, 1), bool)
+        cur = th1
+    u_prop = rng.random((Lt, Lx))
+    u_acc = rng.random((Lt, Lx))
+    new = cur + eps * (2.0 * u_prop - 1.0)
+    if mu == 0:
+        s_old = np.cos(cur + a) + np.cos(b - cur)
+        s_new = np.cos(new + a) + np.cos(b - new)
+    else:
+        s_old = np.cos(a - cur) + np.cos(b + cur)
+        s_new = np.cos(a - new) + np.cos(b + new)
+    d_s = -beta * (s_new - s_old)                      # S = -beta sum Re U_p
+    accept = mask & (u_acc < np.exp(np.minimum(-d_s, 0.0)))
+    cur[accept] = np.mod(new[accept] + math.pi, 2 * math.pi) - math.pi
+    return int(np.count_nonzero(accept))
+
+
+def quenched_u1_angles(Lx: int, Lt: int, beta: float, sweeps: int, seed: int,
+                       eps: float = 1.0) -> np.ndarray:
+    """Link angles theta[2][Lt][Lx] after `sweeps` Metropolis sweeps from theta = 0.
+
+    One sweep visits every link once, direction by direction, each direction
+    in two halves by the parity of the other coordinate.  Proposal
+    theta' = theta + eps * (2u - 1); accept if u2 < exp(-dS).  Lx and Lt must
+    be even so that the two halves share no plaquette across the boundary.
+    """
+    if Lx % 2 or Lt % 2:
+        raise ValueError("Lx and Lt must be even")
+    rng = _rng(seed)
+    theta = np.zeros((2, Lt, Lx), dtype=np.float64)
+    for _ in range(int(sweeps)):
+        for mu in (0, 1):
+            for parity in (0, 1):
+                _metropolis_half(theta, mu, parity, float(beta), float(eps), rng)
+    return theta
+
+
+def links_from_angles(theta: np.ndarray) -> np.ndarray:
+    """U = exp(i theta) as complex128 [2][Lt][Lx] (gauge links, no fermion sign)."""
+    return np.exp(1j * theta).astype(np.complex128)
+
+
+def quenched_u1(Lx: int, Lt: int, beta: float, sweeps: int, seed: int) -> np.ndarray:
+    return links_from_angles(quenched_u1_angles(Lx, Lt, beta, sweeps, seed))
+
+
+def gaussian_field(shape, seed: int) -> np.ndarray:
+    """i.i.d. complex Gaussian entries with Re, Im ~ N(0, 1/2)."""
+    rng = _rng(seed)
+    z = rng.standard_normal(tuple(shape) + (2,))
+    return ((z[..., 0] + 1j * z[..., 1]) * math.sqrt(0.5)).astype(np.complex128)
+
+
+def level_shapes(Lx: int, Lt: int, blocks, Nv):
+    """(Lx_l, Lt_l, ndof_l) for every level l = 1..L of a blocking schedule.
+
+    Level 1 has 2 spin components per site; level l+1 has 2*Nv_l (Nv_l
+    vectors per chirality).  Pure shape bookkeeping.
+    """
+    shapes = [(Lx, Lt, 2)]
+    for (bx, bt), nv in zip(blocks, Nv):
+        lx, lt, _ = shapes[-1]
+        if lx % bx or lt % bt:
+            raise ValueError("lattice extent not divisible by block")
+        shapes.append((lx // bx, lt // bt, 2 * nv))
+    return shapes
+
+
+def setup_noise_len(Lx: int, Lt: int, blocks, Nv) -> int:
+    """Number of complex entries of the setup noise buffer (see setup_noise)."""
+    shapes = level_shapes(Lx, Lt, blocks, Nv)
+    return sum((nv + 2) * lx * lt * n for (lx, lt, n), nv in zip(shapes[:-1], Nv))
+
+
+def setup_noise(Lx: int, Lt: int, blocks, Nv, seed: int) -> np.ndarray:
+    """Random vectors drawn by the adaptive setup, flattened complex128.
+
+    For each non-coarsest level l (finest first) the buffer holds, in order,
+    Nv_l starting vectors for the null-space relaxation, one start for the
+    power iteration that sets the relaxation step, and one start for the two
+    minimum-residual steps that fix the smoother; each is a level-l vector in
+    [t][x][dof] order.
+    """
+    return gaussian_field((setup_noise_len(Lx, Lt, blocks, Nv),), seed)
