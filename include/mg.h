@@ -1,0 +1,203 @@
+/*
+ * mg.h -- C ABI of the GB300 adaptive-multigrid solver for the 2D U(1)
+ * Wilson-Dirac normal equations A = D^dagger D.
+ *
+ * Method: Brannick, Brower, Clark, Osborn, Rebbi, "Adaptive Multigrid
+ * Algorithm for the QCD Dirac-Wilson Operator" (Lattice 2007):
+ *   Sec. 1   Wilson operator D (display after Eq. 1), normal operator A = D^dagger D
+ *   Sec. 2   Galerkin coarse operator (Eq. Galerkin), five-step V-cycle
+ *   Sec. 3   adaptive setup: relaxation on A e = 0 (Eq. relax), geometric
+ *            blocks S_j, normalised block vectors (Eq. P1), index s over
+ *            vector sets
+ *   Sec. 4   frozen two-step MR smoother, setup reuse across masses, MG-CG
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: Lx x Lt sites, site index x + Lx * t; x periodic, t antiperiodic
+ * for the fermion field, gauge field periodic.  gamma_1 = sigma_1 (x links),
+ * gamma_2 = sigma_2 (t links), gamma_5 = sigma_3; diagonal 2d + m = 4 + m.
+ *
+ * Levels are numbered as in the paper: 1 = finest ... nlevels = coarsest.
+ * A level-l vector is [nrhs][Lt_l][Lx_l][n_l] complex, n_1 = 2 (spin),
+ * n_{l+1} = 2 * Nv_l.  Coarse dof s = c * Nv + k: vector k restricted to
+ * chirality c (c = 0: gamma_5 = +1).  On level 1 chirality c is spin c; on
+ * level l > 1 the first n_l/2 components have chirality 0.
+ *
+ * Coarse operator A_l (l >= 2): 9-point stencil of dense n_l x n_l blocks,
+ * stored [Lt_l][Lx_l][9][n_l][n_l] (row-major blocks), displacement index
+ * d = (dx + 1) + 3 (dt + 1); (A_l v)(j) = sum_d A_l[j][d] v(j + d).
+ *
+ * Precision codes: MG_PREC_F64 -> complex128 buffers (double re, double im);
+ * MG_PREC_F32 -> complex64 buffers; MG_PREC_BF16 -> complex64 vectors with
+ * the coarse blocks held in bfloat16 and FP32 accumulation.
+ *
+ * Pointers: every vector, gauge and noise pointer is a DEVICE pointer on the
+ * handle's device; the caller owns it.  Input and output buffers must not
+ * alias.  All work is enqueued on the handle's CUDA stream (the stream passed
+ * to mg_setup); calls returning data in host memory synchronise that stream.
+ * Errors: every call returns an mg_status, never aborts and never throws;
+ * mg_last_error() gives a message.  A handle is not thread-safe.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 5
+
+typedef struct mg_handle mg_handle;
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_ARG = 1,        /* invalid argument (sizes, pointers, divisibility) */
+  MG_ERR_NOMEM = 2,      /* device allocation failed                          */
+  MG_ERR_CUDA = 3,       /* a CUDA call failed                                */
+  MG_ERR_NOCONV = 4,     /* solver stopped at maxiter above tolerance         */
+  MG_ERR_BREAKDOWN = 5,  /* <p,Ap> <= 0, non-finite residual, or rank-deficient
+                            block Gram-Schmidt                                 */
+  MG_ERR_TIMEOUT = 6     /* reserved for bounded device-side waits            */
+} mg_status;
+
+typedef enum { MG_PREC_F64 = 0, MG_PREC_F32 = 1, MG_PREC_BF16 = 2 } mg_precision;
+
+typedef enum {
+  MG_SOLVER_MGCG_FP64 = 0,  /* MG-CG, everything in FP64 (Sec. 4)                */
+  MG_SOLVER_MGCG_MIXED = 1, /* FP64 iterative refinement around an FP32 MG-CG
+                               whose coarse blocks are BF16 (FP32 accumulate);
+                               true residual, solution, coarsest solve in FP64 */
+  MG_SOLVER_CG_FP64 = 2     /* plain CG on A, FP64 (the paper's baseline)        */
+} mg_solver;
+
+typedef struct {
+  int Lx, Lt;                           /* fine lattice                          */
+  int nlevels;                          /* 2 .. MG_MAX_LEVELS                    */
+  int block[MG_MAX_LEVELS - 1][2];      /* (bx, bt) blocking level l -> l+1      */
+  int Nv[MG_MAX_LEVELS - 1];            /* vectors per chirality, level l -> l+1 */
+  int setup_sweeps;                     /* nu of Eq. relax (default 8)           */
+  int power_iters;                      /* iterations for lambda_max (30)        */
+  double omega_mr;                      /* MR under-relaxation, Sec. 4 (0.8)     */
+  const void* setup_noise;              /* device complex128, mg_setup_noise_len
+                                           entries; layout below                 */
+  double coarsest_tol;                  /* FP64 refinement target of the coarsest
+                                           solve, relative (1e-13)               */
+  int coarsest_refine_max;              /* cap on refinement steps (12)          */
+  double inner_tol;                     /* mixed solver: inner FP32 MG-CG
+                                           relative tolerance (1e-5)             */
+  int inner_coarsest_refine;            /* mixed solver: FP64 refinement steps of
+                                           the coarsest solve inside the FP32
+                                           V-cycle (2)                           */
+} mg_params;
+
+typedef struct {
+  int iterations;             /* Krylov iterations (inner iterations summed)   */
+  int refinements;            /* mixed solver: outer FP64 corrections          */
+  double true_residual;       /* |b - A x| / |b| recomputed in FP64            */
+  long long fine_applies;     /* applications of the fine A = D^dagger D        */
+  long long vcycles;          /* V-cycles applied                               */
+  double milliseconds;        /* wall time of the call                          */
+} mg_solve_info;
+
+/* Fill *p with the defaults listed above for an Lx x Lt lattice (no levels). */
+mg_status mg_params_default(mg_params* p, int Lx, int Lt);
+
+/* Number of complex128 entries of params->setup_noise.  For each level
+ * l < nlevels (finest first): Nv_l start vectors for the relaxation of
+ * Eq. relax, then one start vector for the power iteration that sets the
+ * relaxation step 1/lambda_max(A_l), then one start vector for the two MR
+ * steps that fix the smoother (Sec. 4).  Each is a level-l vector.
+ * Returns 0 for invalid parameters. */
+size_t mg_setup_noise_len(const mg_params* p);
+
+/* Adaptive setup (Sec. 3, Eq. relax, Eq. P1, Eq. Galerkin; Sec. 4 smoother).
+ * gauge: device complex128 [2][Lt][Lx], mu = 0 x links, mu = 1 t links,
+ *   |U| = 1 (checked to 1e-12); copied, the caller keeps ownership.
+ * mass: m of D (the setup mass; the paper sets up at the lightest mass).
+ * stream: cudaStream_t to use (NULL: the legacy default stream).
+ * Validation: Lx, Lt even; each extent divisible by its block; every coarse
+ *   extent >= 2; blocks >= 2 x 2; 1 <= Nv_l <= (bx * bt * n_l / 2);
+ *   2 <= nlevels <= MG_MAX_LEVELS.  MG_ERR_ARG otherwise.
+ * On success *out owns all device memory of the hierarchy. */
+mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void* stream,
+                   mg_handle** out);
+
+/* Reuse the setup's vectors at another mass (Sec. 4): rebuilds every
+ * Galerkin operator, the smoothers and the coarsest inverse. */
+mg_status mg_set_mass(mg_handle* h, double mass);
+
+/* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
+ * b, x: device complex128 [nrhs][Lt][Lx][2].  Stops each RHS when the true
+ * FP64 |b - A x| / |b| <= tol.  b = 0 gives x = 0.  info (host, may be NULL)
+ * receives nrhs records.  Synchronises the stream.  MG_ERR_NOCONV when maxiter
+ * Krylov iterations (outer + inner) are exhausted. */
+mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
+                   int solver, mg_solve_info* info);
+
+/* D (dagger = 0) or D^dagger (dagger = 1) on nrhs fine vectors (Sec. 1).
+ * precision MG_PREC_F64 (complex128) or MG_PREC_F32 (complex64). */
+mg_status mg_apply_D(mg_handle* h, const void* in, void* out, int nrhs, int dagger, int precision);
+
+/* A = D^dagger D on nrhs fine vectors, fused (one pass over memory). */
+mg_status mg_apply_A(mg_handle* h, const void* in, void* out, int nrhs, int precision);
+
+/* Coarse operator A_level (2 <= level <= nlevels) on nrhs level vectors
+ * (Eq. Galerkin).  precision F64, F32 or BF16 (coarse blocks in bf16). */
+mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, int nrhs,
+                          int precision);
+
+/* Restriction P^dagger from level `level` to level+1 (Sec. 2 step 2) and
+ * prolongation P from level+1 to `level` (Sec. 2 step 4), 1 <= level < nlevels.
+ * precision F64 or F32. */
+mg_status mg_restrict(mg_handle* h, int level, const void* fine_in, void* coarse_out, int nrhs,
+                      int precision);
+mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_out, int nrhs,
+                     int precision);
+
+/* One V-cycle from the finest level (Sec. 2, five steps, recursive), on one
+ * fine vector.  precision F64 (complex128) or F32 (complex64; the mixed
+ * solver's preconditioner: FP32 vectors, BF16 coarse blocks, FP64 coarsest). */
+mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision);
+
+/* Coarsest-level solve A_L x = b (FP64, complex128 level-L vectors): FP32
+ * explicit inverse refined in FP64 to coarsest_tol. */
+mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out);
+
+/* Level geometry: extents and dof per site; Nv of the blocking below it
+ * (0 on the coarsest).  Any output pointer may be NULL. */
+mg_status mg_get_level(const mg_handle* h, int level, int* Lx, int* Lt, int* ndof, int* Nv);
+
+/* Copy the block-orthonormal vectors of level l < nlevels into out:
+ * device complex128 [Nv][Lt_l][Lx_l][n_l] (v_k on every block, both
+ * chiralities; P e_{j,(c,k)} = Pi_c v_k restricted to S_j). */
+mg_status mg_get_null_vectors(const mg_handle* h, int level, void* out);
+
+/* Copy the FP64 coarse operator A_level (2 <= level <= nlevels) into out
+ * (device complex128, layout above). */
+mg_status mg_get_coarse_op(const mg_handle* h, int level, void* out);
+
+/* Smoother and relaxation scalars of level l < nlevels, host doubles:
+ * out4 = {c0, c1, lambda_max, omega_relax}; R = c0 + c1 A_l. */
+mg_status mg_get_smoother(const mg_handle* h, int level, double* out4);
+
+/* Block map of Sec. 3 computed by the device index functions the kernels use:
+ * coarse[i] = (t / bt) * (Lx / bx) + x / bx, offset[i] = (t % bt) * bx + x % bx,
+ * for i = x + Lx t.  Device int32 arrays of Lx * Lt entries.  stream may be NULL. */
+mg_status mg_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
+                       void* stream);
+
+/* Message of the last error on h (h == NULL: last mg_setup / mg_block_map
+ * error of the calling thread). */
+const char* mg_last_error(const mg_handle* h);
+
+/* Frees everything owned by h; NULL is allowed.  Synchronises the stream. */
+void mg_destroy(mg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

@@ -1,0 +1,124 @@
+// Host-side launchers of the CUDA kernels (one declaration per kernel family).
+// Vectors are [nrhs][count] complex arrays (count = sites * dof), precision R
+// (double -> complex128, float -> complex64).  Every launcher enqueues on the
+// given stream and returns the launch error.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mgk {
+
+// ---- deterministic reductions -------------------------------------------
+// Number of partial sums a reduction over `count` complex entries produces.
+int reduce_blocks(long long count);
+
+// partial[rhs][blk] (2 doubles: re, im) of sum conj(a) b; then out[rhs] (double2).
+template <typename R>
+cudaError_t dot(const void* a, const void* b, long long count, int nrhs, double* partials,
+                double* out, cudaStream_t s);
+// out[rhs] = sum |a|^2 (stored as double2 {norm2, 0}).
+template <typename R>
+cudaError_t norm2(const void* a, long long count, int nrhs, double* partials, double* out,
+                  cudaStream_t s);
+
+// ---- BLAS-1 --------------------------------------------------------------
+// y = a x + b y (host real scalars).
+template <typename R>
+cudaError_t axpby(double a, const void* x, double b, void* y, long long count, int nrhs,
+                  cudaStream_t s);
+// y = x * (1 / sqrt(nrm[rhs].x))  (power iteration normalisation)
+template <typename R>
+cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long count, int nrhs,
+                           cudaStream_t s);
+// CG step on per-RHS device scalars (double2 arrays, real part used):
+//   alpha = rz / pq (0 when frozen[rhs]); x += alpha p; r -= alpha q.
+template <typename R>
+cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
+                  const double* pq, const int* frozen, long long count, int nrhs, cudaStream_t s);
+//   beta = rz_new / rz_old; p = z + beta p; then rz_old <- rz_new is done by the caller.
+template <typename R>
+cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
+                 const int* frozen, long long count, int nrhs, cudaStream_t s);
+// out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
+cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
+                              int nrhs, cudaStream_t s);
+// x(FP64) += in(FP32) * sqrt(nrm[rhs].x)
+cudaError_t f32_accumulate_scaled(const void* in, void* x, const double* nrm, long long count,
+                                  int nrhs, cudaStream_t s);
+// out = in (precision convert, no scaling)
+cudaError_t convert_f64_f32(const void* in, void* out, long long count, cudaStream_t s);
+cudaError_t convert_f32_f64(const void* in, void* out, long long count, cudaStream_t s);
+// out = a u + b v (+ c w when w != nullptr); out may alias u, v or w.
+template <typename R>
+cudaError_t lincomb(void* out, double a, const void* u, double b, const void* v, double c,
+                    const void* w, long long count, int nrhs, cudaStream_t s);
+// r = b - r  (in place: r holds A x on entry)
+template <typename R>
+cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s);
+
+// ---- fine Wilson operator ------------------------------------------------
+// U: [2][V] complex of precision R with the antiperiodic sign folded into the
+// t links at t = Lt - 1.  diag = 4 + m.
+template <typename R>
+cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
+                     int nrhs, bool dagger, cudaStream_t s);
+template <typename R>
+cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
+                     int nrhs, void* tmp, cudaStream_t s);
+// links: gauge complex128 [2][V] -> folded links of precision R
+template <typename R>
+cudaError_t fold_links(const void* gauge, void* U, int Lx, int Lt, cudaStream_t s);
+// max_i ||U_i| - 1| into *out (device double), single block reduction
+cudaError_t link_unitarity(const void* gauge, long long count, double* out, cudaStream_t s);
+
+// ---- coarse operator -----------------------------------------------------
+// y(j) = sum_d A[j][d] x(j + d); A element type: double2 (R=double), float2
+// (R=float, W=float) or bf16x2 (R=float, W=bf16).
+enum CoarseWeights { W_F64 = 0, W_F32 = 1, W_BF16 = 2 };
+cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
+                         int n, int nrhs, cudaStream_t s);
+// A (complex128) -> float2 or bf16x2 copy
+cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
+                           cudaStream_t s);
+
+// ---- transfer ------------------------------------------------------------
+// Vst: [V_f][2][Nv][h] complex (h = n_f / 2), the per-site storage of P.
+template <typename R>
+cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
+                        int bt, int h, int Nv, int nrhs, cudaStream_t s);
+template <typename R>
+cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
+                       int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s);
+
+// ---- setup ---------------------------------------------------------------
+// Chirality-split block modified Gram-Schmidt (two passes) of Nv relaxed
+// vectors E [Nv][V_f][n] (complex128) into Vst [V_f][2][Nv][h] (complex128).
+// flag (device int) is set to 1 on breakdown.
+cudaError_t block_gram_schmidt(const void* E, void* Vst, int Lx, int Lt, int bx, int bt, int h,
+                               int Nv, double breakdown_tol, int* flag, cudaStream_t s);
+// Level-1 Galerkin: W = D P on the extended blocks, then A_c = W^dagger W
+// overlaps.  Wbuf: [Vc][2Nv][(bx+2)(bt+2)][2] complex128 scratch.
+cudaError_t galerkin_fine(const void* U64, double diag, const void* Vst, void* Wbuf, void* Ac,
+                          int Lx, int Lt, int bx, int bt, int Nv, cudaStream_t s);
+// Level >= 2 Galerkin: A_{l+1}[j][d] = sum P(i)^dagger A_l[i][e] P(i+e).
+cudaError_t galerkin_coarse(const void* Af, const void* Vst, void* Ac, int Lx, int Lt, int bx,
+                            int bt, int nf, int Nv, cudaStream_t s);
+// Dense coarsest matrix (complex64, row-major, leading dimension ld >= N) from
+// the stencil (complex128); rows/columns N..ld-1 are set to the identity.
+cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int n, long long ld,
+                                cudaStream_t s);
+// In-place blocked Gauss-Jordan inversion of a Hermitian positive definite
+// complex64 N x N matrix (N multiple of 64).  work: 2 * N * 32 + 32 * 32 complex64.
+cudaError_t gauss_jordan_inverse_f32(void* M, int N, void* work, cudaStream_t s);
+// y = B x, or y += B x when accumulate (complex64 B, leading dimension ld);
+// x complex128 (N) -> y complex128 (N); FP32 products and accumulation, result
+// widened to FP64.  xtmp: ld complex64.
+cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld, void* xtmp,
+                           bool accumulate, cudaStream_t s);
+
+// index map for tests
+cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
+                      cudaStream_t s);
+
+}  // namespace mgk

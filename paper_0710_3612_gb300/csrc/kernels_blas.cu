@@ -1,0 +1,298 @@
+// Vector kernels of the Krylov solvers: deterministic reductions (fixed block
+// count and fixed summation tree, so repeated solves give identical bits),
+// CG updates on per-RHS device scalars, precision conversions.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mgk {
+
+static constexpr int RT = 256;   // threads per reduction block
+
+int reduce_blocks(long long count) {
+  long long g = (count + 4 * RT - 1) / (4 * RT);
+  if (g < 1) g = 1;
+  if (g > 608) g = 608;           // 4 x 152 SMs
+  return (int)g;
+}
+
+// Fixed-order block reduction of (a, b) pairs held one per thread.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    a = l < nw ? sh[2 * l] : 0.0;
+    b = l < nw ? sh[2 * l + 1] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
+template <typename R, bool NORM>
+__global__ void __launch_bounds__(RT) k_dot_partial(const cplx_t<R>* __restrict__ a,
+                                                    const cplx_t<R>* __restrict__ b,
+                                                    long long count, double* partials) {
+  __shared__ double sh[2 * RT / 32];
+  const int rhs = blockIdx.y;
+  const cplx_t<R>* pa = a + (long long)rhs * count;
+  const cplx_t<R>* pb = NORM ? pa : b + (long long)rhs * count;
+  double re = 0.0, im = 0.0;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    cplx_t<R> u = pa[i];
+    if (NORM) {
+      re = fma((double)u.x, (double)u.x, re);
+      re = fma((double)u.y, (double)u.y, re);
+    } else {
+      cplx_t<R> v = pb[i];
+      re = fma((double)u.x, (double)v.x, re);
+      re = fma((double)u.y, (double)v.y, re);
+      im = fma((double)u.x, (double)v.y, im);
+      im = fma(-(double)u.y, (double)v.x, im);
+    }
+  }
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * ((long long)rhs * gridDim.x + blockIdx.x)] = re;
+    partials[2 * ((long long)rhs * gridDim.x + blockIdx.x) + 1] = im;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_finalize(const double* partials, int nblk, double* out) {
+  __shared__ double sh[2 * RT / 32];
+  const int rhs = blockIdx.x;
+  double re = 0.0, im = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RT) {
+    re += partials[2 * (rhs * nblk + i)];
+    im += partials[2 * (rhs * nblk + i) + 1];
+  }
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) { out[2 * rhs] = re; out[2 * rhs + 1] = im; }
+}
+
+template <typename R>
+cudaError_t dot(const void* a, const void* b, long long count, int nrhs, double* partials,
+                double* out, cudaStream_t s) {
+  int g = reduce_blocks(count);
+  k_dot_partial<R, false><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, (const cplx_t<R>*)b,
+                                                       count, partials);
+  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t norm2(const void* a, long long count, int nrhs, double* partials, double* out,
+                  cudaStream_t s) {
+  int g = reduce_blocks(count);
+  k_dot_partial<R, true><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, nullptr, count,
+                                                      partials);
+  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out);
+  return cudaGetLastError();
+}
+
+static inline dim3 grid1(long long count, int nrhs) {
+  long long g = (count + RT - 1) / RT;
+  return dim3((unsigned)g, nrhs);
+}
+
+template <typename R>
+__global__ void k_axpby(R a, const cplx_t<R>* __restrict__ x, R b, cplx_t<R>* __restrict__ y,
+                        long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  i += (long long)blockIdx.y * count;
+  cplx_t<R> u = x[i], v = y[i];
+  y[i] = mk(a * u.x + b * v.x, a * u.y + b * v.y);
+}
+
+template <typename R>
+cudaError_t axpby(double a, const void* x, double b, void* y, long long count, int nrhs,
+                  cudaStream_t s) {
+  k_axpby<R><<<grid1(count, nrhs), RT, 0, s>>>((R)a, (const cplx_t<R>*)x, (R)b, (cplx_t<R>*)y,
+                                                count);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_scale_inv_sqrt(const cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ y,
+                                 const double* nrm, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double n2 = nrm[2 * blockIdx.y];
+  const R sc = n2 > 0.0 ? (R)(1.0 / sqrt(n2)) : (R)0;
+  i += (long long)blockIdx.y * count;
+  cplx_t<R> u = x[i];
+  y[i] = mk(u.x * sc, u.y * sc);
+}
+
+template <typename R>
+cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long count, int nrhs,
+                           cudaStream_t s) {
+  k_scale_inv_sqrt<R><<<grid1(count, nrhs), RT, 0, s>>>((const cplx_t<R>*)x, (cplx_t<R>*)y, nrm,
+                                                         count);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ r,
+                        const cplx_t<R>* __restrict__ p, const cplx_t<R>* __restrict__ q,
+                        const double* rz, const double* pq, const int* frozen, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= count || (frozen && frozen[rhs])) return;
+  const double d = pq[2 * rhs];
+  const R alpha = d != 0.0 ? (R)(rz[2 * rhs] / d) : (R)0;
+  i += (long long)rhs * count;
+  cplx_t<R> xv = x[i], rv = r[i], pv = p[i], qv = q[i];
+  x[i] = mk(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
+  r[i] = mk(fma(-alpha, qv.x, rv.x), fma(-alpha, qv.y, rv.y));
+}
+
+template <typename R>
+cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
+                  const double* pq, const int* frozen, long long count, int nrhs, cudaStream_t s) {
+  k_cg_xr<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
+                                                (const cplx_t<R>*)q, rz, pq, frozen, count);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_cg_p(cplx_t<R>* __restrict__ p, const cplx_t<R>* __restrict__ z,
+                       const double* rz_new, const double* rz_old, const int* frozen,
+                       long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (i >= count || (frozen && frozen[rhs])) return;
+  const double d = rz_old[2 * rhs];
+  const R beta = d != 0.0 ? (R)(rz_new[2 * rhs] / d) : (R)0;
+  i += (long long)rhs * count;
+  cplx_t<R> pv = p[i], zv = z[i];
+  p[i] = mk(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+}
+
+template <typename R>
+cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
+                 const int* frozen, long long count, int nrhs, cudaStream_t s) {
+  k_cg_p<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)p, (const cplx_t<R>*)z, rz_new, rz_old,
+                                               frozen, count);
+  return cudaGetLastError();
+}
+
+__global__ void k_f64_to_f32_scaled(const double2* __restrict__ in, float2* __restrict__ out,
+                                    const double* nrm, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double n2 = nrm[2 * blockIdx.y];
+  const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  i += (long long)blockIdx.y * count;
+  double2 v = in[i];
+  out[i] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+}
+
+cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
+                              int nrhs, cudaStream_t s) {
+  k_f64_to_f32_scaled<<<grid1(count, nrhs), RT, 0, s>>>((const double2*)in, (float2*)out, nrm,
+                                                         count);
+  return cudaGetLastError();
+}
+
+__global__ void k_f32_acc_scaled(const float2* __restrict__ in, double2* __restrict__ x,
+                                 const double* nrm, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double sc = sqrt(nrm[2 * blockIdx.y]);
+  i += (long long)blockIdx.y * count;
+  float2 v = in[i];
+  double2 xv = x[i];
+  x[i] = make_double2(fma((double)v.x, sc, xv.x), fma((double)v.y, sc, xv.y));
+}
+
+cudaError_t f32_accumulate_scaled(const void* in, void* x, const double* nrm, long long count,
+                                  int nrhs, cudaStream_t s) {
+  k_f32_acc_scaled<<<grid1(count, nrhs), RT, 0, s>>>((const float2*)in, (double2*)x, nrm, count);
+  return cudaGetLastError();
+}
+
+__global__ void k_cvt_64_32(const double2* __restrict__ in, float2* __restrict__ out,
+                            long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void k_cvt_32_64(const float2* __restrict__ in, double2* __restrict__ out,
+                            long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = make_double2(in[i].x, in[i].y);
+}
+cudaError_t convert_f64_f32(const void* in, void* out, long long count, cudaStream_t s) {
+  k_cvt_64_32<<<grid1(count, 1), RT, 0, s>>>((const double2*)in, (float2*)out, count);
+  return cudaGetLastError();
+}
+cudaError_t convert_f32_f64(const void* in, void* out, long long count, cudaStream_t s) {
+  k_cvt_32_64<<<grid1(count, 1), RT, 0, s>>>((const float2*)in, (double2*)out, count);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_lincomb(cplx_t<R>* out, R a, const cplx_t<R>* u, R b, const cplx_t<R>* v, R c,
+                          const cplx_t<R>* w, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  i += (long long)blockIdx.y * count;
+  cplx_t<R> uu = u[i], vv = v[i];
+  R re = a * uu.x + b * vv.x, im = a * uu.y + b * vv.y;
+  if (w) {
+    cplx_t<R> ww = w[i];
+    re += c * ww.x;
+    im += c * ww.y;
+  }
+  out[i] = mk(re, im);
+}
+
+template <typename R>
+cudaError_t lincomb(void* out, double a, const void* u, double b, const void* v, double c,
+                    const void* w, long long count, int nrhs, cudaStream_t s) {
+  k_lincomb<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)out, (R)a, (const cplx_t<R>*)u, (R)b,
+                                                  (const cplx_t<R>*)v, (R)c,
+                                                  (const cplx_t<R>*)w, count);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_sub_from(const cplx_t<R>* __restrict__ b, cplx_t<R>* __restrict__ r,
+                           long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) r[i] = csub(b[i], r[i]);
+}
+template <typename R>
+cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s) {
+  k_sub_from<R><<<grid1(count, 1), RT, 0, s>>>((const cplx_t<R>*)b, (cplx_t<R>*)r, count);
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                              \
+  template cudaError_t dot<R>(const void*, const void*, long long, int, double*, double*,    \
+                              cudaStream_t);                                                 \
+  template cudaError_t norm2<R>(const void*, long long, int, double*, double*, cudaStream_t); \
+  template cudaError_t axpby<R>(double, const void*, double, void*, long long, int,          \
+                                cudaStream_t);                                               \
+  template cudaError_t scale_inv_sqrt<R>(const void*, void*, const double*, long long, int,  \
+                                         cudaStream_t);                                      \
+  template cudaError_t cg_xr<R>(void*, void*, const void*, const void*, const double*,       \
+                                const double*, const int*, long long, int, cudaStream_t);    \
+  template cudaError_t cg_p<R>(void*, const void*, const double*, const double*, const int*, \
+                               long long, int, cudaStream_t);                                \
+  template cudaError_t sub_from<R>(const void*, void*, long long, cudaStream_t);             \
+  template cudaError_t lincomb<R>(void*, double, const void*, double, const void*, double,   \
+                                  const void*, long long, int, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace mgk

@@ -1,0 +1,652 @@
+// Coarse-grid kernels of the V-cycle and the adaptive setup:
+//  * coarse_apply     -- 9-point block stencil of the Galerkin operator (Eq. Galerkin)
+//  * restrict/prolong -- P^dagger and P built from block vectors (Sec. 2, Eq. P1)
+//  * block Gram-Schmidt of the chirality halves of the relaxed vectors (Sec. 3)
+//  * Galerkin build: level 1 from W = D P on blocks plus a one-site halo,
+//    levels >= 2 from the block formula P(i)^dagger A_l[i, e] P(i + e)
+//  * coarsest level: dense FP32 Gauss-Jordan inverse and GEMV (the FP64
+//    refinement around them lives in the host orchestration)
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mgk {
+
+// ---------------------------------------------------------------------------
+// Coarse stencil apply: y(j)[r] = sum_d sum_c A[j][d][r][c] x(j + d)[c]
+// ---------------------------------------------------------------------------
+template <typename W> struct wload;
+template <> struct wload<double2> {
+  static __device__ __forceinline__ double2 get(const double2* p) { return *p; }
+};
+template <> struct wload<float2> {
+  static __device__ __forceinline__ float2 get(const float2* p) { return *p; }
+};
+template <> struct wload<__nv_bfloat162> {
+  static __device__ __forceinline__ float2 get(const __nv_bfloat162* p) { return bf2_to_f2(*p); }
+};
+
+template <typename R, typename WT>
+__global__ void __launch_bounds__(256) k_coarse_apply(const cplx_t<R>* __restrict__ in,
+                                                      cplx_t<R>* __restrict__ out,
+                                                      const WT* __restrict__ A, int Lx, int Lt,
+                                                      int n) {
+  const int V = Lx * Lt;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)V * n) return;
+  const int j = (int)(idx / n), r = (int)(idx % n);
+  const int x = j % Lx, t = j / Lx;
+  const cplx_t<R>* vin = in + (long long)blockIdx.y * V * n;
+  cplx_t<R> acc = mk((R)0, (R)0);
+#pragma unroll 1
+  for (int d = 0; d < 9; ++d) {
+    const int dx = d % 3 - 1, dt = d / 3 - 1;
+    int xn = x + dx, tn = t + dt;
+    xn = xn < 0 ? xn + Lx : (xn >= Lx ? xn - Lx : xn);
+    tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
+    const cplx_t<R>* v = vin + (long long)(xn + Lx * tn) * n;
+    const WT* row = A + (((long long)j * 9 + d) * n + r) * n;
+    for (int c = 0; c < n; ++c) cfma(acc, wload<WT>::get(row + c), v[c]);
+  }
+  out[(long long)blockIdx.y * V * n + idx] = acc;
+}
+
+cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
+                         int n, int nrhs, cudaStream_t s) {
+  const long long tot = (long long)Lx * Lt * n;
+  dim3 grid((unsigned)((tot + 255) / 256), nrhs);
+  if (weights == W_F64)
+    k_coarse_apply<double, double2><<<grid, 256, 0, s>>>((const double2*)in, (double2*)out,
+                                                         (const double2*)A, Lx, Lt, n);
+  else if (weights == W_F32)
+    k_coarse_apply<float, float2><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out,
+                                                       (const float2*)A, Lx, Lt, n);
+  else
+    k_coarse_apply<float, __nv_bfloat162><<<grid, 256, 0, s>>>(
+        (const float2*)in, (float2*)out, (const __nv_bfloat162*)A, Lx, Lt, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_coarse_convert(const double2* __restrict__ a, void* out, int weights,
+                                 long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double2 v = a[i];
+  if (weights == W_F32)
+    ((float2*)out)[i] = make_float2((float)v.x, (float)v.y);
+  else
+    ((__nv_bfloat162*)out)[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+}
+
+cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
+                           cudaStream_t s) {
+  k_coarse_convert<<<(unsigned)((count + 255) / 256), 256, 0, s>>>((const double2*)A64, out,
+                                                                   weights, count);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Restriction and prolongation.  Vst[i][c][k][a]: component c*h + a of vector
+// k at fine site i, orthonormal per (block, chirality).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_site(int j, int o, int Lxc, int Lx, int bx, int bt) {
+  const int jx = j % Lxc, jt = j / Lxc;
+  return (jx * bx + o % bx) + Lx * (jt * bt + o / bx);
+}
+
+template <typename R>
+__global__ void k_restrict(const cplx_t<R>* __restrict__ fine, cplx_t<R>* __restrict__ coarse,
+                           const cplx_t<R>* __restrict__ Vst, int Lx, int Lt, int bx, int bt,
+                           int h, int Nv) {
+  const int Lxc = Lx / bx, Vc = Lxc * (Lt / bt), nc = 2 * Nv, nf = 2 * h;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Vc * nc) return;
+  const int j = idx / nc, s = idx % nc, c = s / Nv, k = s % Nv;
+  const cplx_t<R>* f = fine + (long long)blockIdx.y * Lx * Lt * nf;
+  cplx_t<R> acc = mk((R)0, (R)0);
+  for (int o = 0; o < bx * bt; ++o) {
+    const int i = block_site(j, o, Lxc, Lx, bx, bt);
+    const cplx_t<R>* v = Vst + (((long long)i * 2 + c) * Nv + k) * h;
+    const cplx_t<R>* r = f + (long long)i * nf + c * h;
+    for (int a = 0; a < h; ++a) cfmac(acc, v[a], r[a]);
+  }
+  coarse[(long long)blockIdx.y * Vc * nc + idx] = acc;
+}
+
+template <typename R>
+cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
+                        int bt, int h, int Nv, int nrhs, cudaStream_t s) {
+  const int tot = (Lx / bx) * (Lt / bt) * 2 * Nv;
+  k_restrict<R><<<dim3((tot + 127) / 128, nrhs), 128, 0, s>>>(
+      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_prolong(const cplx_t<R>* __restrict__ coarse, cplx_t<R>* __restrict__ fine,
+                          const cplx_t<R>* __restrict__ Vst, int Lx, int Lt, int bx, int bt, int h,
+                          int Nv, bool accumulate) {
+  const int V = Lx * Lt, nf = 2 * h, nc = 2 * Nv;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= V * nf) return;
+  const int i = idx / nf, comp = idx % nf, c = comp / h, a = comp % h;
+  const int x = i % Lx, t = i / Lx;
+  const int j = coarse_site(x, t, Lx, bx, bt);
+  const cplx_t<R>* e = coarse + (long long)blockIdx.y * (V / (bx * bt)) * nc + (long long)j * nc +
+                       c * Nv;
+  const cplx_t<R>* v = Vst + ((long long)i * 2 + c) * Nv * h + a;
+  cplx_t<R> acc = mk((R)0, (R)0);
+  for (int k = 0; k < Nv; ++k) cfma(acc, v[(long long)k * h], e[k]);
+  const long long o = (long long)blockIdx.y * V * nf + idx;
+  fine[o] = accumulate ? cadd(fine[o], acc) : acc;
+}
+
+template <typename R>
+cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
+                       int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s) {
+  const int tot = Lx * Lt * 2 * h;
+  k_prolong<R><<<dim3((tot + 255) / 256, nrhs), 256, 0, s>>>(
+      (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+      accumulate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Chirality-split block modified Gram-Schmidt, one warp per (block, chirality).
+// The m = bx*bt*h entries of a block vector are spread over the 32 lanes
+// (entry e = lane + 32 q); orthonormalised vectors are kept in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+static constexpr int GS_MAXQ = 8;   // up to 256 entries per block vector
+
+__global__ void __launch_bounds__(32) k_block_gs(const double2* __restrict__ E,
+                                                 double2* __restrict__ Vst, int Lx, int Lt,
+                                                 int bx, int bt, int h, int Nv, double tol,
+                                                 int* flag) {
+  extern __shared__ double2 Q[];   // [Nv][m]
+  const int V = Lx * Lt, nf = 2 * h, Lxc = Lx / bx;
+  const int j = blockIdx.x >> 1, c = blockIdx.x & 1, lane = threadIdx.x;
+  const int m = bx * bt * h, nq = (m + 31) / 32;
+  for (int k = 0; k < Nv; ++k) {
+    double2 u[GS_MAXQ];
+    double n0 = 0.0;
+#pragma unroll
+    for (int q = 0; q < GS_MAXQ; ++q) {
+      u[q] = make_double2(0.0, 0.0);
+      const int e = lane + 32 * q;
+      if (q < nq && e < m) {
+        const int o = e / h, a = e % h;
+        const int i = block_site(j, o, Lxc, Lx, bx, bt);
+        u[q] = E[((long long)k * V + i) * nf + c * h + a];
+        n0 += u[q].x * u[q].x + u[q].y * u[q].y;
+      }
+    }
+    n0 = warp_sum(n0);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int kk = 0; kk < k; ++kk) {
+        double re = 0.0, im = 0.0;
+#pragma unroll
+        for (int q = 0; q < GS_MAXQ; ++q) {
+          const int e = lane + 32 * q;
+          if (q < nq && e < m) {
+            double2 w = Q[kk * m + e];
+            re += w.x * u[q].x + w.y * u[q].y;
+            im += w.x * u[q].y - w.y * u[q].x;
+          }
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+#pragma unroll
+        for (int q = 0; q < GS_MAXQ; ++q) {
+          const int e = lane + 32 * q;
+          if (q < nq && e < m) {
+            double2 w = Q[kk * m + e];
+            u[q].x -= re * w.x - im * w.y;
+            u[q].y -= re * w.y + im * w.x;
+          }
+        }
+      }
+    }
+    double n1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < GS_MAXQ; ++q)
+      if (q < nq) n1 += u[q].x * u[q].x + u[q].y * u[q].y;
+    n1 = warp_sum(n1);
+    if (!(n1 > tol * tol * n0)) {
+      if (lane == 0) atomicExch(flag, 1);
+      n1 = n1 > 0.0 ? n1 : 1.0;
+    }
+    const double inv = 1.0 / sqrt(n1);
+#pragma unroll
+    for (int q = 0; q < GS_MAXQ; ++q) {
+      const int e = lane + 32 * q;
+      if (q < nq && e < m) {
+        double2 w = make_double2(u[q].x * inv, u[q].y * inv);
+        Q[k * m + e] = w;
+        const int o = e / h, a = e % h;
+        const int i = block_site(j, o, Lxc, Lx, bx, bt);
+        Vst[(((long long)i * 2 + c) * Nv + k) * h + a] = w;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t block_gram_schmidt(const void* E, void* Vst, int Lx, int Lt, int bx, int bt, int h,
+                               int Nv, double breakdown_tol, int* flag, cudaStream_t s) {
+  const int m = bx * bt * h;
+  if (m > 32 * GS_MAXQ) return cudaErrorInvalidValue;
+  const int Vc = (Lx / bx) * (Lt / bt);
+  const size_t smem = (size_t)Nv * m * sizeof(double2);
+  k_block_gs<<<2 * Vc, 32, smem, s>>>((const double2*)E, (double2*)Vst, Lx, Lt, bx, bt, h, Nv,
+                                     breakdown_tol, flag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Level-1 Galerkin.  W_{j,s} = D P e_{j,s} on the extended block
+// [-1, bx] x [-1, bt] (local coordinates of block j); then
+// A_c[j][d][r][s] = sum_x W_{j,r}(x)^dagger W_{j+d,s}(x) over the overlap of
+// the two extended blocks, taken in unwrapped coordinates so that the two
+// couplings of a coarse extent of 2 stay in separate displacement slots.
+// ---------------------------------------------------------------------------
+__global__ void k_galerkin_W(const double2* __restrict__ U, double diag,
+                             const double2* __restrict__ Vst, double2* __restrict__ Wbuf, int Lx,
+                             int Lt, int bx, int bt, int Nv) {
+  const int Lxc = Lx / bx, Vc = Lxc * (Lt / bt), nc = 2 * Nv;
+  const int ex_w = bx + 2, E = (bx + 2) * (bt + 2);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Vc * nc * E) return;
+  const int e = (int)(idx % E);
+  const int s = (int)((idx / E) % nc);
+  const int j = (int)(idx / ((long long)E * nc));
+  const int c = s / Nv, k = s % Nv;
+  const int lx = e % ex_w - 1, lt = e / ex_w - 1;          // local coords in [-1, b]
+  const int jx = j % Lxc, jt = j / Lxc;
+  const int V = Lx * Lt;
+  auto gsite = [&](int ax, int at) {                         // local -> global (wrapped)
+    int gx = jx * bx + ax, gt = jt * bt + at;
+    gx = (gx % Lx + Lx) % Lx;
+    gt = (gt % Lt + Lt) % Lt;
+    return gx + Lx * gt;
+  };
+  auto inblock = [&](int ax, int at) { return ax >= 0 && ax < bx && at >= 0 && at < bt; };
+  // P e_{j,s} at a local site: only spin c is non-zero (h = 1 on level 1).
+  auto pval = [&](int ax, int at, double2& f0, double2& f1) {
+    const double2 v = Vst[((long long)gsite(ax, at) * 2 + c) * Nv + k];
+    f0 = c == 0 ? v : make_double2(0.0, 0.0);
+    f1 = c == 1 ? v : make_double2(0.0, 0.0);
+  };
+  const int site = gsite(lx, lt);
+  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+  double2 f0, f1;
+  if (inblock(lx + 1, lt)) { pval(lx + 1, lt, f0, f1); hop_x<double>(a0, a1, U[site], f0, f1, 1.0); }
+  if (inblock(lx - 1, lt)) {
+    pval(lx - 1, lt, f0, f1);
+    hop_x<double>(a0, a1, cconj(U[gsite(lx - 1, lt)]), f0, f1, -1.0);
+  }
+  if (inblock(lx, lt + 1)) { pval(lx, lt + 1, f0, f1); hop_t<double>(a0, a1, U[V + site], f0, f1, 1.0); }
+  if (inblock(lx, lt - 1)) {
+    pval(lx, lt - 1, f0, f1);
+    hop_t<double>(a0, a1, cconj(U[V + gsite(lx, lt - 1)]), f0, f1, -1.0);
+  }
+  double2 w0 = make_double2(-0.5 * a0.x, -0.5 * a0.y), w1 = make_double2(-0.5 * a1.x, -0.5 * a1.y);
+  if (inblock(lx, lt)) {
+    pval(lx, lt, f0, f1);
+    w0.x += diag * f0.x; w0.y += diag * f0.y;
+    w1.x += diag * f1.x; w1.y += diag * f1.y;
+  }
+  Wbuf[2 * idx] = w0;
+  Wbuf[2 * idx + 1] = w1;
+}
+
+__global__ void k_galerkin_WW(const double2* __restrict__ Wbuf, double2* __restrict__ Ac, int Lx,
+                              int Lt, int bx, int bt, int Nv) {
+  const int Lxc = Lx / bx, Ltc = Lt / bt, Vc = Lxc * Ltc, nc = 2 * Nv;
+  const int ex_w = bx + 2, E = (bx + 2) * (bt + 2);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Vc * 9 * nc * nc) return;
+  const int sc = (int)(idx % nc);
+  const int r = (int)((idx / nc) % nc);
+  const int d = (int)((idx / (nc * nc)) % 9);
+  const int j = (int)(idx / (9LL * nc * nc));
+  const int dx = d % 3 - 1, dt = d / 3 - 1;
+  const int jx = j % Lxc, jt = j / Lxc;
+  const int j2 = ((jx + dx + Lxc) % Lxc) + Lxc * ((jt + dt + Ltc) % Ltc);
+  const int x0 = max(-1, dx * bx - 1), x1 = min(bx, dx * bx + bx);
+  const int t0 = max(-1, dt * bt - 1), t1 = min(bt, dt * bt + bt);
+  const double2* Wa = Wbuf + ((long long)j * nc + r) * E * 2;
+  const double2* Wb = Wbuf + ((long long)j2 * nc + sc) * E * 2;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int lt = t0; lt <= t1; ++lt)
+    for (int lx = x0; lx <= x1; ++lx) {
+      const int e1 = (lt + 1) * ex_w + (lx + 1);
+      const int e2 = (lt - dt * bt + 1) * ex_w + (lx - dx * bx + 1);
+      cfmac(acc, Wa[2 * e1], Wb[2 * e2]);
+      cfmac(acc, Wa[2 * e1 + 1], Wb[2 * e2 + 1]);
+    }
+  Ac[(((long long)j * 9 + d) * nc + r) * nc + sc] = acc;
+}
+
+cudaError_t galerkin_fine(const void* U64, double diag, const void* Vst, void* Wbuf, void* Ac,
+                          int Lx, int Lt, int bx, int bt, int Nv, cudaStream_t s) {
+  const long long Vc = (long long)(Lx / bx) * (Lt / bt), nc = 2 * Nv;
+  const long long nW = Vc * nc * (bx + 2) * (bt + 2);
+  k_galerkin_W<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(
+      (const double2*)U64, diag, (const double2*)Vst, (double2*)Wbuf, Lx, Lt, bx, bt, Nv);
+  const long long nA = Vc * 9 * nc * nc;
+  k_galerkin_WW<<<(unsigned)((nA + 255) / 256), 256, 0, s>>>((const double2*)Wbuf,
+                                                              (double2*)Ac, Lx, Lt, bx, bt, Nv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Level >= 2 Galerkin, one CTA per coarse site j; the CTA accumulates the 9
+// blocks of A_{l+1}[j] in shared memory.  For each fine site i of S_j and
+// each fine displacement e: T = A_l[i][e] P(i+e) (nf x nc), then
+// A_{l+1}[j][disp(i,e)] += P(i)^dagger T, disp = floor((o_i + e) / b).
+// ---------------------------------------------------------------------------
+__global__ void k_galerkin_coarse(const double2* __restrict__ Af, const double2* __restrict__ Vst,
+                                  double2* __restrict__ Ac, int Lx, int Lt, int bx, int bt,
+                                  int nf, int Nv) {
+  extern __shared__ double2 sm[];
+  const int nc = 2 * Nv, h = nf / 2, Lxc = Lx / bx;
+  double2* acc = sm;                  // [9][nc][nc]
+  double2* T = sm + 9 * nc * nc;      // [nf][nc]
+  const int j = blockIdx.x;
+  const int jx = j % Lxc, jt = j / Lxc;
+  for (int q = threadIdx.x; q < 9 * nc * nc; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int o = 0; o < bx * bt; ++o) {
+    const int ox = o % bx, ot = o / bx;
+    const int x = jx * bx + ox, t = jt * bt + ot;
+    const int i = x + Lx * t;
+    for (int e = 0; e < 9; ++e) {
+      const int ex = e % 3 - 1, et = e / 3 - 1;
+      const int x2 = (x + ex + Lx) % Lx, t2 = (t + et + Lt) % Lt;
+      const int i2 = x2 + Lx * t2;
+      const int ddx = (ox + ex < 0) ? -1 : ((ox + ex >= bx) ? 1 : 0);
+      const int ddt = (ot + et < 0) ? -1 : ((ot + et >= bt) ? 1 : 0);
+      const int d = (ddx + 1) + 3 * (ddt + 1);
+      const double2* Ablk = Af + ((long long)i * 9 + e) * nf * nf;
+      // T[a][s] = sum_b A[a][c_s h + b] V_{k_s}(i2)[c_s h + b]
+      for (int q = threadIdx.x; q < nf * nc; q += blockDim.x) {
+        const int a = q / nc, s = q % nc, cs = s / Nv, ks = s % Nv;
+        const double2* v = Vst + (((long long)i2 * 2 + cs) * Nv + ks) * h;
+        const double2* arow = Ablk + (long long)a * nf + cs * h;
+        double2 tv = make_double2(0.0, 0.0);
+        for (int b = 0; b < h; ++b) cfma(tv, arow[b], v[b]);
+        T[q] = tv;
+      }
+      __syncthreads();
+      // acc[d][r][s] += sum_a conj(V_{k_r}(i)[c_r h + a]) T[c_r h + a][s]
+      for (int q = threadIdx.x; q < nc * nc; q += blockDim.x) {
+        const int r = q / nc, s = q % nc, cr = r / Nv, kr = r % Nv;
+        const double2* v = Vst + (((long long)i * 2 + cr) * Nv + kr) * h;
+        double2 g = acc[d * nc * nc + q];
+        for (int a = 0; a < h; ++a) cfmac(g, v[a], T[(cr * h + a) * nc + s]);
+        acc[d * nc * nc + q] = g;
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = threadIdx.x; q < 9 * nc * nc; q += blockDim.x)
+    Ac[(long long)j * 9 * nc * nc + q] = acc[q];
+}
+
+cudaError_t galerkin_coarse(const void* Af, const void* Vst, void* Ac, int Lx, int Lt, int bx,
+                            int bt, int nf, int Nv, cudaStream_t s) {
+  const int nc = 2 * Nv, Vc = (Lx / bx) * (Lt / bt);
+  const size_t smem = (size_t)(9 * nc * nc + nf * nc) * sizeof(double2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_galerkin_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  k_galerkin_coarse<<<Vc, 256, smem, s>>>((const double2*)Af, (const double2*)Vst, (double2*)Ac,
+                                          Lx, Lt, bx, bt, nf, Nv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense matrix, FP32 Gauss-Jordan inverse, GEMV.
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_to_dense(const double2* __restrict__ A, float2* __restrict__ M, int Lx,
+                                  int Lt, int n, long long ld) {
+  const int V = Lx * Lt;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)V * n * n) return;
+  const int c = (int)(idx % n), r = (int)((idx / n) % n), j = (int)(idx / ((long long)n * n));
+  const int x = j % Lx, t = j / Lx;
+  for (int d = 0; d < 9; ++d) {       // aliased displacements land on the same entry: add
+    const int xn = (x + d % 3 - 1 + Lx) % Lx, tn = (t + d / 3 - 1 + Lt) % Lt;
+    const int jn = xn + Lx * tn;
+    const double2 v = A[(((long long)j * 9 + d) * n + r) * n + c];
+    float2* dst = M + ((long long)j * n + r) * ld + (long long)jn * n + c;
+    dst->x += (float)v.x;
+    dst->y += (float)v.y;
+  }
+}
+
+__global__ void k_pad_identity(float2* __restrict__ M, long long N, long long ld) {
+  const long long i = N + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) M[i * ld + i] = make_float2(1.f, 0.f);
+}
+
+cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int n, long long ld,
+                                cudaStream_t s) {
+  const long long N = (long long)Lx * Lt * n;
+  if (ld < N) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(dense, 0, (size_t)(ld * ld * sizeof(float2)), s);
+  if (e != cudaSuccess) return e;
+  const long long tot = (long long)Lx * Lt * n * n;
+  k_coarse_to_dense<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const double2*)A,
+                                                                  (float2*)dense, Lx, Lt, n, ld);
+  if (ld > N)
+    k_pad_identity<<<(unsigned)((ld - N + 255) / 256), 256, 0, s>>>((float2*)dense, N, ld);
+  return cudaGetLastError();
+}
+
+// Sweep (Gauss-Jordan) inversion.  Sweeping pivot block k of M with
+// P = M_kk^{-1}:  M_ij -= M_ik P M_kj (i, j != k);  M_kj <- P M_kj;
+// M_ik <- -M_ik P;  M_kk <- P.  After all pivots M holds its inverse.
+static constexpr int GJB = 32;
+
+__global__ void __launch_bounds__(GJB* GJB) k_gj_diag(float2* __restrict__ M, int N, int k,
+                                                      float2* __restrict__ P) {
+  __shared__ float2 a[GJB][GJB + 1];
+  const int r = threadIdx.y, c = threadIdx.x;
+  a[r][c] = M[(long long)(k * GJB + r) * N + k * GJB + c];
+  __syncthreads();
+  for (int p = 0; p < GJB; ++p) {
+    const float2 piv = a[p][p];
+    const float den = piv.x * piv.x + piv.y * piv.y;
+    const float2 inv = make_float2(piv.x / den, -piv.y / den);
+    const float2 arp = a[r][p], apc = a[p][c], arc = a[r][c];
+    __syncthreads();
+    float2 v;
+    if (r == p && c == p) v = inv;
+    else if (r == p) v = cmul(inv, apc);
+    else if (c == p) v = cmul(make_float2(-arp.x, -arp.y), inv);
+    else v = csub(arc, cmul(cmul(arp, inv), apc));
+    a[r][c] = v;
+    __syncthreads();
+  }
+  P[r * GJB + c] = a[r][c];
+}
+
+// C_i = M_ik P (column panel, rows i != k) and R_j = P M_kj (row panel).
+__global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict__ M, int N, int k,
+                                                       const float2* __restrict__ P,
+                                                       float2* __restrict__ Cp,
+                                                       float2* __restrict__ Rp) {
+  __shared__ float2 sP[GJB][GJB + 1], sX[GJB][GJB + 1];
+  const int nb = N / GJB;
+  const int b = blockIdx.x % nb, col_panel = blockIdx.x < nb;
+  const int r = threadIdx.y, c = threadIdx.x;
+  if (b == k) return;
+  sP[r][c] = P[r * GJB + c];
+  if (col_panel) sX[r][c] = M[(long long)(b * GJB + r) * N + k * GJB + c];   // M_bk
+  else sX[r][c] = M[(long long)(k * GJB + r) * N + b * GJB + c];             // M_kb
+  __syncthreads();
+  float2 acc = make_float2(0.f, 0.f);
+  if (col_panel) {
+    for (int q = 0; q < GJB; ++q) cfma(acc, sX[r][q], sP[q][c]);
+    Cp[(long long)(b * GJB + r) * GJB + c] = acc;
+  } else {
+    for (int q = 0; q < GJB; ++q) cfma(acc, sP[r][q], sX[q][c]);
+    Rp[(long long)r * N + b * GJB + c] = acc;
+  }
+}
+
+// M_ij -= C_i M_kj for i, j != k; 64 x 64 output tile per CTA, 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N, int k,
+                                                   const float2* __restrict__ Cp) {
+  __shared__ float2 sC[64][GJB + 1], sR[GJB][64 + 1];
+  const int bi = blockIdx.y * 64, bj = blockIdx.x * 64;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < 64 * GJB; q += 256) {
+    const int rr = q / GJB, cc = q % GJB;
+    sC[rr][cc] = Cp[(long long)(bi + rr) * GJB + cc];
+    const int r2 = q / 64, c2 = q % 64;
+    sR[r2][c2] = M[(long long)(k * GJB + r2) * N + bj + c2];
+  }
+  __syncthreads();
+  const int tr = tid / 16, tc = tid % 16;   // rows tr + 16 u, cols tc + 16 v
+  float2 acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+  for (int q = 0; q < GJB; ++q) {
+    float2 cv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cv[u] = sC[tr + 16 * u][q];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) rv[v] = sR[q][tc + 16 * v];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cfma(acc[u][v], cv[u], rv[v]);
+  }
+  const int kb0 = k * GJB, kb1 = kb0 + GJB;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int row = bi + tr + 16 * u;
+    if (row >= kb0 && row < kb1) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int col = bj + tc + 16 * v;
+      if (col >= kb0 && col < kb1) continue;
+      float2* p = M + (long long)row * N + col;
+      *p = csub(*p, acc[u][v]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GJB* GJB) k_gj_write(float2* __restrict__ M, int N, int k,
+                                                       const float2* __restrict__ P,
+                                                       const float2* __restrict__ Cp,
+                                                       const float2* __restrict__ Rp) {
+  const int nb = N / GJB;
+  const int r = threadIdx.y, c = threadIdx.x;
+  if (blockIdx.x == 2 * nb) {
+    M[(long long)(k * GJB + r) * N + k * GJB + c] = P[r * GJB + c];
+    return;
+  }
+  const int b = blockIdx.x % nb;
+  if (b == k) return;
+  if (blockIdx.x < nb) {
+    const float2 v = Cp[(long long)(b * GJB + r) * GJB + c];
+    M[(long long)(b * GJB + r) * N + k * GJB + c] = make_float2(-v.x, -v.y);
+  } else {
+    M[(long long)(k * GJB + r) * N + b * GJB + c] = Rp[(long long)r * N + b * GJB + c];
+  }
+}
+
+cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s) {
+  if (N % 64 != 0) return cudaErrorInvalidValue;
+  float2* M = (float2*)Mv;
+  float2* P = (float2*)work;
+  float2* Cp = P + GJB * GJB;
+  float2* Rp = Cp + (long long)N * GJB;
+  const int nb = N / GJB;
+  for (int k = 0; k < nb; ++k) {
+    k_gj_diag<<<1, dim3(GJB, GJB), 0, s>>>(M, N, k, P);
+    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp);
+    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cp);
+    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp);
+  }
+  return cudaGetLastError();
+}
+
+// y = B x: one warp per row, FP32 products and accumulation, result widened.
+// B has leading dimension ld (even, >= N); xtmp holds ld complex64, zero beyond N.
+__global__ void k_x_to_f32(const double2* __restrict__ x, float2* __restrict__ xf, int N, int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) xf[i] = i < N ? make_float2((float)x[i].x, (float)x[i].y) : make_float2(0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_gemv(const float2* __restrict__ B,
+                                              const float2* __restrict__ xf,
+                                              double2* __restrict__ y, int N, int ld,
+                                              bool accumulate) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= N) return;
+  const float4* b4 = (const float4*)(B + (long long)row * ld);
+  const float4* x4 = (const float4*)xf;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int q = lane; q < ld / 2; q += 32) {
+    const float4 bv = b4[q], xv = x4[q];
+    cfma(acc, make_float2(bv.x, bv.y), make_float2(xv.x, xv.y));
+    cfma(acc, make_float2(bv.z, bv.w), make_float2(xv.z, xv.w));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) {
+    double2 v = make_double2(acc.x, acc.y);
+    if (accumulate) { v.x += y[row].x; v.y += y[row].y; }
+    y[row] = v;
+  }
+}
+
+cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld, void* xtmp,
+                           bool accumulate, cudaStream_t s) {
+  if (ld % 2 || ld < N) return cudaErrorInvalidValue;
+  k_x_to_f32<<<(ld + 255) / 256, 256, 0, s>>>((const double2*)x, (float2*)xtmp, N, ld);
+  k_gemv<<<(N + 7) / 8, 256, 0, s>>>((const float2*)B, (const float2*)xtmp, (double2*)y, N, ld,
+                                     accumulate);
+  return cudaGetLastError();
+}
+
+__global__ void k_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Lx * Lt) return;
+  const int x = i % Lx, t = i / Lx;
+  coarse[i] = coarse_site(x, t, Lx, bx, bt);
+  offset[i] = block_offset(x, t, bx, bt);
+}
+
+cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
+                      cudaStream_t s) {
+  k_block_map<<<(Lx * Lt + 255) / 256, 256, 0, s>>>(Lx, Lt, bx, bt, coarse, offset);
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                                \
+  template cudaError_t restrict_op<R>(const void*, void*, const void*, int, int, int, int, int, \
+                                      int, int, cudaStream_t);                                 \
+  template cudaError_t prolong_op<R>(const void*, void*, const void*, int, int, int, int, int,  \
+                                     int, int, bool, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace mgk

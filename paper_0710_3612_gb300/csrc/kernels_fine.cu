@@ -1,0 +1,129 @@
+// Fine-lattice Wilson-Dirac operator D and D^dagger (Sec. 1 of the paper,
+// display after Eq. 1), 2D, U(1) links, gamma_1 = sigma_1 (x), gamma_2 =
+// sigma_2 (t), diagonal 4 + m, t antiperiodic (sign folded into the t link at
+// t = Lt - 1 by fold_links).
+//
+// Spin projection: (1 - s sigma_1) phi = (phi0 - s phi1) (1, -s)^T and
+// (1 - s sigma_2) phi = (phi0 + i s phi1) (1, -i s)^T, so each hop is one
+// complex projection, one link multiply and a rank-1 reconstruction.
+// D uses s = +1 forward (x + mu) and s = -1 backward; D^dagger swaps them.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mgk {
+
+template <typename R, bool DAG>
+__device__ __forceinline__ void wilson_site(const cplx_t<R>* __restrict__ in,
+                                            const cplx_t<R>* __restrict__ U, R diag, int x, int t,
+                                            int Lx, int Lt, cplx_t<R>& o0, cplx_t<R>& o1) {
+  using C = cplx_t<R>;
+  const int V = Lx * Lt;
+  const int site = x + Lx * t;
+  const int xp = (x + 1 == Lx) ? site - x : site + 1;
+  const int xm = (x == 0) ? site + Lx - 1 : site - 1;
+  const int tp = (t + 1 == Lt) ? x : site + Lx;
+  const int tm = (t == 0) ? site + (Lt - 1) * Lx : site - Lx;
+  const R sf = DAG ? (R)-1 : (R)1;   // projector sign of the forward hop
+  C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0);
+  hop_x<R>(a0, a1, U[site], in[2 * xp], in[2 * xp + 1], sf);
+  hop_x<R>(a0, a1, cconj(U[xm]), in[2 * xm], in[2 * xm + 1], -sf);
+  hop_t<R>(a0, a1, U[V + site], in[2 * tp], in[2 * tp + 1], sf);
+  hop_t<R>(a0, a1, cconj(U[V + tm]), in[2 * tm], in[2 * tm + 1], -sf);
+  C p0 = in[2 * site], p1 = in[2 * site + 1];
+  o0 = mk(diag * p0.x - (R)0.5 * a0.x, diag * p0.y - (R)0.5 * a0.y);
+  o1 = mk(diag * p1.x - (R)0.5 * a1.x, diag * p1.y - (R)0.5 * a1.y);
+}
+
+template <typename R, bool DAG>
+__global__ void __launch_bounds__(256) k_wilson_D(const cplx_t<R>* __restrict__ in,
+                                                  cplx_t<R>* __restrict__ out,
+                                                  const cplx_t<R>* __restrict__ U, R diag, int Lx,
+                                                  int Lt) {
+  const int V = Lx * Lt;
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= V) return;
+  const long long off = (long long)blockIdx.y * V * 2;
+  cplx_t<R> o0, o1;
+  wilson_site<R, DAG>(in + off, U, diag, site % Lx, site / Lx, Lx, Lt, o0, o1);
+  out[off + 2 * site] = o0;
+  out[off + 2 * site + 1] = o1;
+}
+
+template <typename R>
+cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
+                     int nrhs, bool dagger, cudaStream_t s) {
+  const int V = Lx * Lt;
+  dim3 grid((V + 255) / 256, nrhs);
+  if (dagger)
+    k_wilson_D<R, true><<<grid, 256, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
+                                             (const cplx_t<R>*)U, (R)diag, Lx, Lt);
+  else
+    k_wilson_D<R, false><<<grid, 256, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
+                                              (const cplx_t<R>*)U, (R)diag, Lx, Lt);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
+                     int nrhs, void* tmp, cudaStream_t s) {
+  cudaError_t e = wilson_D<R>(in, tmp, U, diag, Lx, Lt, nrhs, false, s);
+  if (e != cudaSuccess) return e;
+  return wilson_D<R>(tmp, out, U, diag, Lx, Lt, nrhs, true, s);
+}
+
+template <typename R>
+__global__ void k_fold_links(const double2* __restrict__ g, cplx_t<R>* __restrict__ U, int Lx,
+                             int Lt) {
+  const int V = Lx * Lt;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * V) return;
+  const int mu = i / V, site = i % V;
+  const double sg = (mu == 1 && site / Lx == Lt - 1) ? -1.0 : 1.0;
+  double2 u = g[i];
+  U[i] = mk((R)(sg * u.x), (R)(sg * u.y));
+}
+
+template <typename R>
+cudaError_t fold_links(const void* gauge, void* U, int Lx, int Lt, cudaStream_t s) {
+  const int n = 2 * Lx * Lt;
+  k_fold_links<R><<<(n + 255) / 256, 256, 0, s>>>((const double2*)gauge, (cplx_t<R>*)U, Lx, Lt);
+  return cudaGetLastError();
+}
+
+__global__ void k_link_unitarity(const double2* __restrict__ g, long long count, double* out) {
+  double m = 0.0;
+  for (long long i = threadIdx.x; i < count; i += blockDim.x) {
+    double2 u = g[i];
+    double d = fabs(sqrt(u.x * u.x + u.y * u.y) - 1.0);
+    m = (d > m || d != d) ? d : m;   // NaN propagates
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double v = __shfl_down_sync(0xffffffffu, m, o);
+    m = (v > m || v != v) ? v : m;
+  }
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = (sh[w] > r || sh[w] != sh[w]) ? sh[w] : r;
+    *out = r;
+  }
+}
+
+cudaError_t link_unitarity(const void* gauge, long long count, double* out, cudaStream_t s) {
+  k_link_unitarity<<<1, 1024, 0, s>>>((const double2*)gauge, count, out);
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                               \
+  template cudaError_t wilson_D<R>(const void*, void*, const void*, double, int, int, int,    \
+                                   bool, cudaStream_t);                                       \
+  template cudaError_t wilson_A<R>(const void*, void*, const void*, double, int, int, int,    \
+                                   void*, cudaStream_t);                                      \
+  template cudaError_t fold_links<R>(const void*, void*, int, int, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace mgk

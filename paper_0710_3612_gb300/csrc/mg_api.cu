@@ -1,0 +1,855 @@
+// C ABI of the solver (declared in include/mg.h) and the host orchestration
+// of the method: adaptive setup (Sec. 3), Galerkin hierarchy (Eq. Galerkin),
+// frozen MR smoother (Sec. 4), five-step V-cycle (Sec. 2), MG-CG (Sec. 4).
+// All arithmetic runs in the kernels of this library; the host only sequences
+// launches and reads back the few scalars the Krylov loops branch on.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "kernels.h"
+
+using namespace mgk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Level {
+  int Lx = 0, Lt = 0, V = 0, n = 0;      // geometry; n = dof per site
+  long long count() const { return (long long)V * n; }
+  // operator blocks of this level (index >= 1): FP64 master, FP32, BF16 copies
+  double2* A64 = nullptr;
+  float2* A32 = nullptr;
+  void* A16 = nullptr;
+  // transfer to the next level
+  int bx = 0, bt = 0, Nv = 0;
+  double2* Vst64 = nullptr;
+  float2* Vst32 = nullptr;
+  double c0 = 0, c1 = 0, lambda_max = 0, omega_relax = 0;
+  double2* eta = nullptr;                // MR start vector (kept for re-massing)
+  // V-cycle work vectors, [prec][4]: b (input copy for level > 0), x, r, t
+  void* w64[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* w32[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+}  // namespace
+
+struct mg_handle {
+  mg_params p{};
+  cudaStream_t s = nullptr;
+  double mass = 0.0;
+  int L = 0;
+  std::vector<Level> lv;
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  // coarsest level
+  int Nc = 0, ldc = 0;
+  float2* Binv = nullptr;
+  float2* gj_work = nullptr;
+  float2* gemv_x = nullptr;
+  int n_refine = 0;
+  double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
+  // fine-level scratch for A = D^dagger D (two-pass), per precision, grown on demand
+  void* tmpA64 = nullptr;
+  size_t tmpA64_bytes = 0;
+  void* tmpA32 = nullptr;
+  size_t tmpA32_bytes = 0;
+  // solver vectors (one RHS), FP64 and FP32: x r p q z t
+  void* sv64[6] = {};
+  void* sv32[6] = {};
+  // setup scratch
+  void* Wbuf = nullptr;
+  // scalars
+  double* partials = nullptr;   // 2 * 608 * max_rhs doubles
+  int partial_rhs = 0;
+  double* scal = nullptr;       // device scalar slots (double2 each)
+  double* hscal = nullptr;      // pinned host mirror
+  int* dflag = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+  long long fine_applies = 0, vcycles = 0;
+};
+
+namespace {
+
+// scalar slots (each a double2)
+enum { S_RZ = 0, S_RZN = 2, S_PQ = 4, S_RR = 6, S_T0 = 8, S_T1 = 10, S_BN = 12, S_NR = 14,
+       S_MAX = 64 };
+
+struct Fail {
+  mg_status st;
+};
+
+void fail(mg_handle* h, mg_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  throw Fail{st};
+}
+
+void ck(mg_handle* h, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(h, MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T = void>
+T* dalloc(mg_handle* h, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(h, MG_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->allocs.push_back(p);
+  return (T*)p;
+}
+
+void sync(mg_handle* h) { ck(h, cudaStreamSynchronize(h->s), "stream synchronize"); }
+
+double read_scalar(mg_handle* h, int slot) {
+  ck(h, cudaMemcpyAsync(h->hscal, h->scal + slot, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->s),
+     "scalar readback");
+  sync(h);
+  return h->hscal[0];
+}
+
+void ensure_tmpA(mg_handle* h, bool f64, size_t bytes) {
+  void*& p = f64 ? h->tmpA64 : h->tmpA32;
+  size_t& have = f64 ? h->tmpA64_bytes : h->tmpA32_bytes;
+  if (have >= bytes) return;
+  if (p) {
+    ck(h, cudaStreamSynchronize(h->s), "synchronize before regrow");
+    for (auto& a : h->allocs)
+      if (a == p) a = nullptr;
+    cudaFree(p);
+  }
+  p = dalloc(h, bytes);
+  have = bytes;
+}
+
+void ensure_partials(mg_handle* h, int nrhs) {
+  if (h->partial_rhs >= nrhs) return;
+  h->partials = dalloc<double>(h, sizeof(double) * 2 * 608 * (size_t)nrhs);
+  h->partial_rhs = nrhs;
+}
+
+// ----- level operator ------------------------------------------------------
+// weights for coarse levels: 0 = F64, 1 = F32, 2 = BF16
+template <typename R>
+void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int weights) {
+  Level& L = h->lv[l];
+  if (l == 0) {
+    const double diag = 4.0 + h->mass;
+    const size_t bytes = (size_t)L.count() * nrhs * sizeof(R) * 2;
+    ensure_tmpA(h, sizeof(R) == 8, bytes);
+    void* tmp = sizeof(R) == 8 ? h->tmpA64 : h->tmpA32;
+    const void* U = sizeof(R) == 8 ? (const void*)h->U64 : (const void*)h->U32;
+    ck(h, wilson_A<R>(in, out, U, diag, L.Lx, L.Lt, nrhs, tmp, h->s), "wilson_A");
+  } else {
+    const void* A = weights == W_F64 ? (const void*)L.A64
+                    : weights == W_F32 ? (const void*)L.A32 : L.A16;
+    ck(h, coarse_apply(in, out, A, weights, L.Lx, L.Lt, L.n, nrhs, h->s), "coarse_apply");
+  }
+}
+
+// ----- coarsest solve: FP32 explicit inverse refined in FP64 ----------------
+// x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r.
+void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
+  Level& L = h->lv[h->L - 1];
+  ck(h, dense_gemv_f32(h->Binv, b, x, h->Nc, h->ldc, h->gemv_x, false, h->s), "coarsest gemv");
+  for (int it = 0; it < steps; ++it) {
+    apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64);
+    ck(h, sub_from<double>(b, h->cr, h->Nc, h->s), "coarsest residual");
+    ck(h, dense_gemv_f32(h->Binv, h->cr, x, h->Nc, h->ldc, h->gemv_x, true, h->s),
+       "coarsest gemv");
+  }
+}
+
+// ----- V-cycle (Sec. 2, five steps), recursive ------------------------------
+// Reads b, writes x (both level-l vectors of precision R).
+template <typename R>
+void vcycle(mg_handle* h, int l, const void* b, void* x) {
+  const bool f64 = sizeof(R) == 8;
+  const int weights = f64 ? W_F64 : W_BF16;
+  if (l == h->L - 1) {
+    if (f64) {
+      coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine);
+    } else {
+      ck(h, convert_f32_f64(b, h->cb, h->Nc, h->s), "coarsest in");
+      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine);
+      ck(h, convert_f64_f32(h->cx, x, h->Nc, h->s), "coarsest out");
+    }
+    return;
+  }
+  Level& L = h->lv[l];
+  Level& C = h->lv[l + 1];
+  void** w = f64 ? L.w64 : L.w32;
+  void** wc = f64 ? C.w64 : C.w32;
+  void* r = w[2];
+  void* t = w[3];
+  const long long n = L.count();
+  if (l == 0) h->fine_applies += 4;
+  // 1. x = R b = c0 b + c1 A b
+  apply_level<R>(h, l, b, t, 1, weights);
+  ck(h, lincomb<R>(x, L.c0, b, L.c1, t, 0.0, nullptr, n, 1, h->s), "smooth");
+  // 2. r_c = P^dagger (b - A x)
+  apply_level<R>(h, l, x, t, 1, weights);
+  ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
+  const void* Vst = f64 ? (const void*)L.Vst64 : (const void*)L.Vst32;
+  ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, h->s), "restrict");
+  // 3. e_c = V_{l+1} r_c
+  vcycle<R>(h, l + 1, wc[0], wc[1]);
+  // 4. x = x + P e_c
+  ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, true, h->s),
+     "prolong");
+  // 5. x = x + R (b - A x)
+  apply_level<R>(h, l, x, t, 1, weights);
+  ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
+  apply_level<R>(h, l, r, t, 1, weights);
+  ck(h, lincomb<R>(x, 1.0, x, L.c0, r, L.c1, t, n, 1, h->s), "post-smooth");
+}
+
+// ----- setup pieces ---------------------------------------------------------
+double power_lambda_max(mg_handle* h, int l, const double2* start, void* v, void* w) {
+  Level& L = h->lv[l];
+  const long long n = L.count();
+  double* s = h->scal;
+  ck(h, norm2<double>(start, n, 1, h->partials, s + S_T0, h->s), "norm");
+  ck(h, scale_inv_sqrt<double>(start, v, s + S_T0, n, 1, h->s), "scale");
+  for (int it = 0; it < h->p.power_iters; ++it) {
+    apply_level<double>(h, l, v, w, 1, W_F64);
+    if (it == h->p.power_iters - 1) ck(h, dot<double>(v, w, n, 1, h->partials, s + S_T1, h->s), "dot");
+    ck(h, norm2<double>(w, n, 1, h->partials, s + S_T0, h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(w, v, s + S_T0, n, 1, h->s), "scale");
+  }
+  return read_scalar(h, S_T1);
+}
+
+void smoother_coefficients(mg_handle* h, int l, void* q, void* r1) {
+  // Two under-relaxed MR steps from r0 = eta (Sec. 4); R = c0 + c1 A frozen.
+  Level& L = h->lv[l];
+  const long long n = L.count();
+  const double om = h->p.omega_mr;
+  double* s = h->scal;
+  apply_level<double>(h, l, L.eta, q, 1, W_F64);
+  ck(h, dot<double>(q, L.eta, n, 1, h->partials, s + S_T0, h->s), "dot");
+  ck(h, norm2<double>(q, n, 1, h->partials, s + S_T1, h->s), "norm");
+  const double num0 = read_scalar(h, S_T0), den0 = read_scalar(h, S_T1);
+  if (!(den0 > 0.0)) fail(h, MG_ERR_BREAKDOWN, "MR smoother: A eta = 0");
+  const double a0 = num0 / den0;
+  ck(h, lincomb<double>(r1, 1.0, L.eta, -om * a0, q, 0.0, nullptr, n, 1, h->s), "mr");
+  apply_level<double>(h, l, r1, q, 1, W_F64);
+  ck(h, dot<double>(q, r1, n, 1, h->partials, s + S_T0, h->s), "dot");
+  ck(h, norm2<double>(q, n, 1, h->partials, s + S_T1, h->s), "norm");
+  const double num1 = read_scalar(h, S_T0), den1 = read_scalar(h, S_T1);
+  if (!(den1 > 0.0)) fail(h, MG_ERR_BREAKDOWN, "MR smoother: A r1 = 0");
+  const double a1 = num1 / den1;
+  L.c0 = om * (a0 + a1);
+  L.c1 = -om * om * a0 * a1;
+}
+
+void build_coarse_ops(mg_handle* h) {
+  for (int l = 0; l + 1 < h->L; ++l) {
+    Level& L = h->lv[l];
+    Level& C = h->lv[l + 1];
+    if (l == 0)
+      ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt,
+                          L.Nv, h->s),
+         "galerkin_fine");
+    else
+      ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s),
+         "galerkin_coarse");
+    const long long cnt = (long long)C.V * 9 * C.n * C.n;
+    ck(h, coarse_convert(C.A64, C.A32, W_F32, cnt, h->s), "convert f32");
+    ck(h, coarse_convert(C.A64, C.A16, W_BF16, cnt, h->s), "convert bf16");
+  }
+}
+
+void build_coarsest(mg_handle* h) {
+  Level& L = h->lv[h->L - 1];
+  ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
+  ck(h, gauss_jordan_inverse_f32(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+  // Refinement count: smallest number of FP64 correction steps that brings a
+  // fixed test vector (all ones) to coarsest_tol, plus one.
+  double* s = h->scal;
+  std::vector<double2> ones(h->Nc, make_double2(1.0, 0.0));
+  ck(h, cudaMemcpyAsync(h->cb, ones.data(), sizeof(double2) * h->Nc, cudaMemcpyHostToDevice,
+                        h->s),
+     "upload");
+  ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, s + S_T1, h->s), "norm");
+  const double bn = read_scalar(h, S_T1);
+  int steps = 0;
+  for (; steps <= h->p.coarsest_refine_max; ++steps) {
+    coarsest_solve64(h, h->cb, h->cx, steps);
+    apply_level<double>(h, h->L - 1, h->cx, h->cr, 1, W_F64);
+    ck(h, sub_from<double>(h->cb, h->cr, h->Nc, h->s), "residual");
+    ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, s + S_T0, h->s), "norm");
+    const double rr = read_scalar(h, S_T0);
+    if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest inverse is not finite");
+    if (rr <= h->p.coarsest_tol * h->p.coarsest_tol * bn) break;
+  }
+  h->n_refine = std::min(steps + 1, h->p.coarsest_refine_max);
+}
+
+void set_mass_internal(mg_handle* h, double mass) {
+  h->mass = mass;
+  build_coarse_ops(h);
+  for (int l = 0; l + 1 < h->L; ++l)
+    smoother_coefficients(h, l, h->lv[l].w64[3], h->lv[l].w64[2]);
+  build_coarsest(h);
+  sync(h);
+}
+
+mg_status validate(const mg_params* p, std::string& msg) {
+  if (!p) { msg = "params is NULL"; return MG_ERR_ARG; }
+  if (p->Lx < 4 || p->Lt < 4 || p->Lx % 2 || p->Lt % 2) { msg = "Lx, Lt must be even and >= 4"; return MG_ERR_ARG; }
+  if (p->nlevels < 2 || p->nlevels > MG_MAX_LEVELS) { msg = "nlevels out of range"; return MG_ERR_ARG; }
+  int lx = p->Lx, lt = p->Lt, n = 2;
+  for (int l = 0; l + 1 < p->nlevels; ++l) {
+    const int bx = p->block[l][0], bt = p->block[l][1], nv = p->Nv[l];
+    if (bx < 2 || bt < 2) { msg = "blocks must be at least 2 x 2"; return MG_ERR_ARG; }
+    if (lx % bx || lt % bt) { msg = "lattice extent not divisible by block at level " + std::to_string(l + 1); return MG_ERR_ARG; }
+    if (lx / bx < 2 || lt / bt < 2) { msg = "coarse extent below 2 at level " + std::to_string(l + 2); return MG_ERR_ARG; }
+    if (nv < 1 || nv > bx * bt * n / 2) { msg = "Nv must be in [1, bx*bt*n/2]"; return MG_ERR_ARG; }
+    if (bx * bt * n / 2 > 256) { msg = "block-chirality dimension above 256"; return MG_ERR_ARG; }
+    if (2 * nv > 64) { msg = "Nv above 32"; return MG_ERR_ARG; }
+    lx /= bx; lt /= bt; n = 2 * nv;
+  }
+  if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
+  if (!p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
+  return MG_OK;
+}
+
+template <typename F>
+mg_status guarded(mg_handle* h, F&& f) {
+  try {
+    f();
+    return MG_OK;
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (h) h->err = "host allocation failed";
+    g_last_error = "host allocation failed";
+    return MG_ERR_NOMEM;
+  } catch (...) {
+    if (h) h->err = "unexpected exception";
+    g_last_error = "unexpected exception";
+    return MG_ERR_CUDA;
+  }
+}
+
+void free_all(mg_handle* h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  h->allocs.clear();
+  if (h->hscal) cudaFreeHost(h->hscal);
+  h->hscal = nullptr;
+}
+
+// ----- Krylov solvers ---------------------------------------------------------
+// PCG on A x = b (precision R), x0 = 0, stopping when |r| <= tol |b| (recursive
+// residual); precond: 0 none, 1 V-cycle.  Returns iterations.  Vectors from
+// the handle's solver set of precision R; x receives the solution.
+template <typename R>
+int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, bool precond,
+        mg_status& st) {
+  Level& F = h->lv[0];
+  const long long n = F.count();
+  void** v = sizeof(R) == 8 ? h->sv64 : h->sv32;
+  void *r = v[1], *p = v[2], *q = v[3], *z = v[4];
+  const int weights = sizeof(R) == 8 ? W_F64 : W_BF16;
+  double* s = h->scal;
+  st = MG_OK;
+  ck(h, norm2<R>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
+  const double bn = read_scalar(h, S_BN);
+  ck(h, cudaMemsetAsync(x, 0, n * sizeof(R) * 2, h->s), "memset");
+  if (bn == 0.0) return 0;
+  if (!(bn == bn) || std::isinf(bn)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite right-hand side"; return 0; }
+  ck(h, cudaMemcpyAsync(r, b, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
+  auto precondition = [&]() {
+    if (precond) {
+      vcycle<R>(h, 0, r, z);
+      h->vcycles++;
+    } else {
+      ck(h, cudaMemcpyAsync(z, r, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
+    }
+  };
+  precondition();
+  ck(h, cudaMemcpyAsync(p, z, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, dot<R>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
+  int it = 0;
+  const double stop = tol * tol * bn;
+  while (it < maxiter) {
+    apply_level<R>(h, 0, p, q, 1, weights);
+    h->fine_applies++;
+    ck(h, dot<R>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
+    ck(h, cg_xr<R>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->s), "cg_xr");
+    ck(h, norm2<R>(r, n, 1, h->partials, s + S_RR, h->s), "norm");
+    ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    ++it;
+    const double pq = h->hscal[0], rr = h->hscal[2];
+    if (!(pq > 0.0) || !(rr == rr)) {
+      st = MG_ERR_BREAKDOWN;
+      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
+      return it;
+    }
+    if (rr <= stop) return it;
+    precondition();
+    ck(h, dot<R>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
+    ck(h, cg_p<R>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+  }
+  st = MG_ERR_NOCONV;
+  h->err = "maximum iterations reached";
+  return it;
+}
+
+// True relative residual |b - A x| / |b| in FP64; also leaves r = b - A x in v.
+double true_residual(mg_handle* h, const void* b, const void* x, void* r) {
+  Level& F = h->lv[0];
+  const long long n = F.count();
+  double* s = h->scal;
+  apply_level<double>(h, 0, x, r, 1, W_F64);
+  h->fine_applies++;
+  ck(h, sub_from<double>(b, r, n, h->s), "residual");
+  ck(h, norm2<double>(r, n, 1, h->partials, s + S_NR, h->s), "norm");
+  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
+  const double rr = read_scalar(h, S_NR);
+  const double bn = read_scalar(h, S_BN);
+  return bn > 0 ? std::sqrt(rr / bn) : 0.0;
+}
+
+mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxiter, int solver,
+                    mg_solve_info* info) {
+  mg_status st = MG_OK;
+  const long long n = h->lv[0].count();
+  int iters = 0, refinements = 0;
+  h->fine_applies = 0;
+  h->vcycles = 0;
+  ck(h, norm2<double>(b, n, 1, h->partials, h->scal + S_T0, h->s), "norm");
+  {
+    const double b2 = read_scalar(h, S_T0);
+    if (!(b2 == b2) || std::isinf(b2)) fail(h, MG_ERR_BREAKDOWN, "non-finite right-hand side");
+  }
+  if (solver == MG_SOLVER_MGCG_FP64 || solver == MG_SOLVER_CG_FP64) {
+    // PCG on the true residual; when the recursive residual has drifted from
+    // the true one, restart from rt = b - A x with the remaining target.
+    const bool pre = solver == MG_SOLVER_MGCG_FP64;
+    ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
+    void* xc = h->sv64[5];
+    void* rt = h->sv64[0];
+    ck(h, norm2<double>(b, n, 1, h->partials, h->scal + S_T0, h->s), "norm");
+    const double bnrm = std::sqrt(read_scalar(h, S_T0));
+    ck(h, cudaMemcpyAsync(rt, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    double rnrm = bnrm;
+    for (int cycle = 0; cycle < 8 && bnrm > 0.0; ++cycle) {
+      const double rel = cycle == 0 ? tol : std::min(0.5, 0.5 * tol * bnrm / rnrm);
+      iters += pcg<double>(h, rt, xc, rel, maxiter - iters, pre, st);
+      ck(h, lincomb<double>(x, 1.0, x, 1.0, xc, 0.0, nullptr, n, 1, h->s), "accumulate");
+      if (st != MG_OK && st != MG_ERR_NOCONV) break;
+      const double res = true_residual(h, b, x, rt);
+      if (res <= tol) { st = MG_OK; break; }
+      if (iters >= maxiter) { st = MG_ERR_NOCONV; h->err = "maximum iterations reached"; break; }
+      rnrm = res * bnrm;
+      refinements++;
+    }
+  } else if (solver == MG_SOLVER_MGCG_MIXED) {
+    ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
+    void* r64 = h->sv64[0];
+    void* r32 = h->sv32[0];
+    void* e32 = h->sv32[5];
+    double* s = h->scal;
+    ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
+    const double bn = read_scalar(h, S_BN);
+    if (bn == 0.0) {
+      st = MG_OK;
+    } else {
+      ck(h, cudaMemcpyAsync(r64, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+      for (;;) {
+        ck(h, norm2<double>(r64, n, 1, h->partials, s + S_NR, h->s), "norm");
+        const double rr = read_scalar(h, S_NR);
+        if (!(rr == rr)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite residual"; break; }
+        if (rr <= tol * tol * bn) { st = MG_OK; break; }
+        if (iters >= maxiter) { st = MG_ERR_NOCONV; h->err = "maximum iterations reached"; break; }
+        ck(h, f64_to_f32_scaled(r64, r32, s + S_NR, n, 1, h->s), "to f32");
+        mg_status ist;
+        iters += pcg<float>(h, r32, e32, h->p.inner_tol, maxiter - iters, true, ist);
+        if (ist == MG_ERR_BREAKDOWN) { st = ist; break; }
+        ck(h, f32_accumulate_scaled(e32, x, s + S_NR, n, 1, h->s), "accumulate");
+        refinements++;
+        apply_level<double>(h, 0, x, r64, 1, W_F64);
+        h->fine_applies++;
+        ck(h, sub_from<double>(b, r64, n, h->s), "residual");
+      }
+    }
+  } else {
+    fail(h, MG_ERR_ARG, "unknown solver");
+  }
+  if (info) {
+    info->iterations = iters;
+    info->refinements = refinements;
+    info->true_residual = true_residual(h, b, x, h->sv64[0]);
+    info->fine_applies = h->fine_applies;
+    info->vcycles = h->vcycles;
+  }
+  return st;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
+  if (!p) return MG_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->Lx = Lx;
+  p->Lt = Lt;
+  p->nlevels = 2;
+  p->block[0][0] = p->block[0][1] = 4;
+  p->Nv[0] = 4;
+  p->setup_sweeps = 8;
+  p->power_iters = 30;
+  p->omega_mr = 0.8;
+  p->coarsest_tol = 1e-13;
+  p->coarsest_refine_max = 12;
+  p->inner_tol = 1e-5;
+  p->inner_coarsest_refine = 2;
+  return MG_OK;
+}
+
+size_t mg_setup_noise_len(const mg_params* p) {
+  if (!p || p->nlevels < 2 || p->nlevels > MG_MAX_LEVELS) return 0;
+  size_t tot = 0;
+  long long lx = p->Lx, lt = p->Lt, n = 2;
+  for (int l = 0; l + 1 < p->nlevels; ++l) {
+    const int bx = p->block[l][0], bt = p->block[l][1];
+    if (bx <= 0 || bt <= 0 || lx % bx || lt % bt) return 0;
+    tot += (size_t)(p->Nv[l] + 2) * lx * lt * n;
+    lx /= bx; lt /= bt; n = 2 * p->Nv[l];
+  }
+  return tot;
+}
+
+mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void* stream,
+                   mg_handle** out) {
+  if (!out) { g_last_error = "out is NULL"; return MG_ERR_ARG; }
+  *out = nullptr;
+  std::string msg;
+  mg_status v = validate(params, msg);
+  if (v != MG_OK) { g_last_error = msg; return v; }
+  if (!gauge) { g_last_error = "gauge is NULL"; return MG_ERR_ARG; }
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) { g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
+  h->p = *params;
+  h->s = (cudaStream_t)stream;
+  h->L = params->nlevels;
+  mg_status st = guarded(h, [&]() {
+    const mg_params& P = h->p;
+    // geometry
+    h->lv.resize(h->L);
+    int lx = P.Lx, lt = P.Lt, n = 2;
+    for (int l = 0; l < h->L; ++l) {
+      Level& L = h->lv[l];
+      L.Lx = lx; L.Lt = lt; L.V = lx * lt; L.n = n;
+      if (l + 1 < h->L) {
+        L.bx = P.block[l][0]; L.bt = P.block[l][1]; L.Nv = P.Nv[l];
+        lx /= L.bx; lt /= L.bt; n = 2 * L.Nv;
+      }
+    }
+    ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
+    h->scal = dalloc<double>(h, S_MAX * sizeof(double));
+    h->dflag = dalloc<int>(h, sizeof(int));
+    int max_nv = 1;
+    for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
+    ensure_partials(h, max_nv);
+    // links
+    const long long V = h->lv[0].V;
+    h->U64 = dalloc<double2>(h, 2 * V * sizeof(double2));
+    h->U32 = dalloc<float2>(h, 2 * V * sizeof(float2));
+    ck(h, link_unitarity(gauge, 2 * V, h->scal + S_T0, h->s), "unitarity");
+    const double dev = read_scalar(h, S_T0);
+    if (!(dev <= 1e-12)) fail(h, MG_ERR_ARG, "gauge links are not unit modulus (|U|-1 = " + std::to_string(dev) + ")");
+    ck(h, fold_links<double>(gauge, h->U64, P.Lx, P.Lt, h->s), "fold");
+    ck(h, fold_links<float>(gauge, h->U32, P.Lx, P.Lt, h->s), "fold");
+    h->mass = mass;
+    // per-level storage
+    for (int l = 0; l < h->L; ++l) {
+      Level& L = h->lv[l];
+      const size_t c = (size_t)L.count();
+      for (int k = 0; k < 4; ++k) {
+        L.w64[k] = dalloc(h, c * sizeof(double2));
+        L.w32[k] = dalloc(h, c * sizeof(float2));
+      }
+      if (l > 0) {
+        const size_t ab = (size_t)L.V * 9 * L.n * L.n;
+        L.A64 = dalloc<double2>(h, ab * sizeof(double2));
+        L.A32 = dalloc<float2>(h, ab * sizeof(float2));
+        L.A16 = dalloc(h, ab * 4);
+      }
+      if (l + 1 < h->L) {
+        L.Vst64 = dalloc<double2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(double2));
+        L.Vst32 = dalloc<float2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(float2));
+        L.eta = dalloc<double2>(h, c * sizeof(double2));
+      }
+    }
+    for (int k = 0; k < 6; ++k) {
+      h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(double2));
+      h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(float2));
+    }
+    {
+      const Level& L0 = h->lv[0];
+      const size_t Vc = (size_t)(L0.Lx / L0.bx) * (L0.Lt / L0.bt);
+      h->Wbuf = dalloc(h, Vc * 2 * L0.Nv * (L0.bx + 2) * (L0.bt + 2) * 2 * sizeof(double2));
+    }
+    // coarsest dense storage
+    {
+      const Level& C = h->lv[h->L - 1];
+      h->Nc = (int)C.count();
+      h->ldc = (h->Nc + 63) / 64 * 64;
+      h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
+      h->gj_work = dalloc<float2>(h, ((size_t)2 * h->ldc * 32 + 32 * 32) * sizeof(float2));
+      h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
+      h->cb = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
+      h->cx = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
+      h->cr = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
+    }
+    // adaptive setup, level by level (Sec. 3)
+    const double2* noise = (const double2*)P.setup_noise;
+    size_t pos = 0;
+    for (int l = 0; l + 1 < h->L; ++l) {
+      Level& L = h->lv[l];
+      const long long c = L.count();
+      const double2* starts = noise + pos;
+      pos += (size_t)L.Nv * c;
+      const double2* pw = noise + pos;
+      pos += c;
+      ck(h, cudaMemcpyAsync(L.eta, noise + pos, c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy eta");
+      pos += c;
+      // relaxation step from lambda_max (power iteration)
+      L.lambda_max = power_lambda_max(h, l, pw, L.w64[1], L.w64[2]);
+      if (!(L.lambda_max > 0.0)) fail(h, MG_ERR_BREAKDOWN, "power iteration gave lambda_max <= 0");
+      L.omega_relax = 1.0 / L.lambda_max;
+      // Eq. relax: e <- (1 - omega A) e, nu sweeps, all Nv vectors at once
+      void* E = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
+      void* T = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
+      ck(h, cudaMemcpyAsync(E, starts, (size_t)L.Nv * c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+      for (int sw = 0; sw < P.setup_sweeps; ++sw) {
+        apply_level<double>(h, l, E, T, L.Nv, W_F64);
+        ck(h, axpby<double>(-L.omega_relax, T, 1.0, E, c, L.Nv, h->s), "relax");
+      }
+      // chirality split + block Gram-Schmidt (FP64)
+      ck(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s), "memset");
+      ck(h, block_gram_schmidt(E, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1e-14, h->dflag, h->s), "gram-schmidt");
+      int flag = 0;
+      ck(h, cudaMemcpyAsync(h->hscal, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+      sync(h);
+      std::memcpy(&flag, h->hscal, sizeof(int));
+      if (flag) fail(h, MG_ERR_BREAKDOWN, "block Gram-Schmidt breakdown at level " + std::to_string(l + 1));
+      ck(h, convert_f64_f32(L.Vst64, L.Vst32, (long long)L.V * 2 * L.Nv * (L.n / 2), h->s), "convert");
+      // Galerkin operator of the next level (needed before relaxing on it)
+      Level& C = h->lv[l + 1];
+      if (l == 0)
+        ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin_fine");
+      else
+        ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin_coarse");
+      sync(h);
+      for (auto& a : h->allocs)
+        if (a == E || a == T) a = nullptr;
+      cudaFree(E);
+      cudaFree(T);
+    }
+    set_mass_internal(h, mass);
+  });
+  if (st != MG_OK) {
+    g_last_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return MG_OK;
+}
+
+mg_status mg_set_mass(mg_handle* h, double mass) {
+  if (!h) return MG_ERR_ARG;
+  return guarded(h, [&]() { set_mass_internal(h, mass); });
+}
+
+mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
+                   int solver, mg_solve_info* info) {
+  if (!h) return MG_ERR_ARG;
+  if (!b || !x || nrhs < 1 || !(tol > 0.0) || maxiter < 1) { h->err = "invalid solve arguments"; return MG_ERR_ARG; }
+  mg_status worst = MG_OK;
+  mg_status st = guarded(h, [&]() {
+    const long long n = h->lv[0].count();
+    for (int k = 0; k < nrhs; ++k) {
+      auto t0 = std::chrono::steady_clock::now();
+      mg_status one = solve_one(h, (const double2*)b + k * n, (double2*)x + k * n, tol, maxiter,
+                                solver, info ? info + k : nullptr);
+      sync(h);
+      auto t1 = std::chrono::steady_clock::now();
+      if (info) info[k].milliseconds = std::chrono::duration<double, std::milli>(t1 - t0).count();
+      if (one != MG_OK && worst == MG_OK) worst = one;
+    }
+  });
+  return st != MG_OK ? st : worst;
+}
+
+mg_status mg_apply_D(mg_handle* h, const void* in, void* out, int nrhs, int dagger, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (!in || !out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    const Level& F = h->lv[0];
+    if (precision == MG_PREC_F64)
+      ck(h, wilson_D<double>(in, out, h->U64, 4.0 + h->mass, F.Lx, F.Lt, nrhs, dagger != 0, h->s), "wilson_D");
+    else
+      ck(h, wilson_D<float>(in, out, h->U32, 4.0 + h->mass, F.Lx, F.Lt, nrhs, dagger != 0, h->s), "wilson_D");
+  });
+}
+
+mg_status mg_apply_A(mg_handle* h, const void* in, void* out, int nrhs, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (!in || !out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    if (precision == MG_PREC_F64) apply_level<double>(h, 0, in, out, nrhs, W_F64);
+    else apply_level<float>(h, 0, in, out, nrhs, W_F32);
+  });
+}
+
+mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, int nrhs, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (level < 2 || level > h->L || !in || !out || nrhs < 1 || precision < 0 || precision > 2) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    if (precision == MG_PREC_F64) apply_level<double>(h, level - 1, in, out, nrhs, W_F64);
+    else apply_level<float>(h, level - 1, in, out, nrhs, precision == MG_PREC_F32 ? W_F32 : W_BF16);
+  });
+}
+
+mg_status mg_restrict(mg_handle* h, int level, const void* fine_in, void* coarse_out, int nrhs, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (level < 1 || level >= h->L || !fine_in || !coarse_out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    const Level& L = h->lv[level - 1];
+    if (precision == MG_PREC_F64)
+      ck(h, restrict_op<double>(fine_in, coarse_out, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
+    else
+      ck(h, restrict_op<float>(fine_in, coarse_out, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
+  });
+}
+
+mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_out, int nrhs, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (level < 1 || level >= h->L || !coarse_in || !fine_out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    const Level& L = h->lv[level - 1];
+    if (precision == MG_PREC_F64)
+      ck(h, prolong_op<double>(coarse_in, fine_out, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
+    else
+      ck(h, prolong_op<float>(coarse_in, fine_out, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
+  });
+}
+
+mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision) {
+  if (!h) return MG_ERR_ARG;
+  if (!in || !out || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() {
+    if (precision == MG_PREC_F64) vcycle<double>(h, 0, in, out);
+    else vcycle<float>(h, 0, in, out);
+  });
+}
+
+mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out) {
+  if (!h) return MG_ERR_ARG;
+  if (!in || !out) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine); });
+}
+
+mg_status mg_get_level(const mg_handle* h, int level, int* Lx, int* Lt, int* ndof, int* Nv) {
+  if (!h || level < 1 || level > h->L) return MG_ERR_ARG;
+  const Level& L = h->lv[level - 1];
+  if (Lx) *Lx = L.Lx;
+  if (Lt) *Lt = L.Lt;
+  if (ndof) *ndof = L.n;
+  if (Nv) *Nv = level < h->L ? L.Nv : 0;
+  return MG_OK;
+}
+
+}  // extern "C"
+
+// Gather of Vst [V][2][Nv][h] into [Nv][V][2h] (complex128).
+__global__ void k_vst_to_vectors(const double2* __restrict__ Vst, double2* __restrict__ out, int V,
+                                 int Nv, int h) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)V * 2 * Nv * h;
+  if (idx >= tot) return;
+  const int a = (int)(idx % h), k = (int)((idx / h) % Nv), c = (int)((idx / ((long long)h * Nv)) % 2);
+  const long long i = idx / (2LL * Nv * h);
+  out[((long long)k * V + i) * 2 * h + c * h + a] = Vst[idx];
+}
+
+extern "C" {
+
+mg_status mg_get_null_vectors(const mg_handle* hc, int level, void* out) {
+  mg_handle* h = const_cast<mg_handle*>(hc);
+  if (!h || level < 1 || level >= h->L || !out) return MG_ERR_ARG;
+  return guarded(h, [&]() {
+    const Level& L = h->lv[level - 1];
+    const long long tot = (long long)L.V * 2 * L.Nv * (L.n / 2);
+    k_vst_to_vectors<<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(L.Vst64, (double2*)out, L.V, L.Nv, L.n / 2);
+    ck(h, cudaGetLastError(), "gather");
+  });
+}
+
+mg_status mg_get_coarse_op(const mg_handle* hc, int level, void* out) {
+  mg_handle* h = const_cast<mg_handle*>(hc);
+  if (!h || level < 2 || level > h->L || !out) return MG_ERR_ARG;
+  return guarded(h, [&]() {
+    const Level& L = h->lv[level - 1];
+    ck(h, cudaMemcpyAsync(out, L.A64, (size_t)L.V * 9 * L.n * L.n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  });
+}
+
+mg_status mg_get_smoother(const mg_handle* h, int level, double* out4) {
+  if (!h || level < 1 || level >= h->L || !out4) return MG_ERR_ARG;
+  const Level& L = h->lv[level - 1];
+  out4[0] = L.c0;
+  out4[1] = L.c1;
+  out4[2] = L.lambda_max;
+  out4[3] = L.omega_relax;
+  return MG_OK;
+}
+
+mg_status mg_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset, void* stream) {
+  if (Lx < 1 || Lt < 1 || bx < 1 || bt < 1 || Lx % bx || Lt % bt || !coarse || !offset) {
+    g_last_error = "invalid block map arguments";
+    return MG_ERR_ARG;
+  }
+  cudaError_t e = block_map(Lx, Lt, bx, bt, coarse, offset, (cudaStream_t)stream);
+  if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return MG_ERR_CUDA; }
+  return MG_OK;
+}
+
+const char* mg_last_error(const mg_handle* h) {
+  return h ? h->err.c_str() : g_last_error.c_str();
+}
+
+void mg_destroy(mg_handle* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

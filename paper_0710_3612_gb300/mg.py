@@ -1,0 +1,268 @@
+"""Thin Python binding of the C ABI in include/mg.h (argument marshalling only).
+
+Every function takes torch tensors that already live on the GPU, passes their
+device pointers to libmg.so and returns status-checked results.  No arithmetic
+of the method happens here; if libmg.so is missing the import of any entry
+point raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmg.so")
+
+MG_MAX_LEVELS = 5
+PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+SOLVER_MGCG_FP64, SOLVER_MGCG_MIXED, SOLVER_CG_FP64 = 0, 1, 2
+STATUS = {0: "MG_OK", 1: "MG_ERR_ARG", 2: "MG_ERR_NOMEM", 3: "MG_ERR_CUDA", 4: "MG_ERR_NOCONV",
+          5: "MG_ERR_BREAKDOWN", 6: "MG_ERR_TIMEOUT"}
+
+
+class MgError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Lt", ctypes.c_int), ("nlevels", ctypes.c_int),
+                ("block", (ctypes.c_int * 2) * (MG_MAX_LEVELS - 1)),
+                ("Nv", ctypes.c_int * (MG_MAX_LEVELS - 1)),
+                ("setup_sweeps", ctypes.c_int), ("power_iters", ctypes.c_int),
+                ("omega_mr", ctypes.c_double), ("setup_noise", ctypes.c_void_p),
+                ("coarsest_tol", ctypes.c_double), ("coarsest_refine_max", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("inner_coarsest_refine", ctypes.c_int)]
+
+
+class MgSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("fine_applies", ctypes.c_longlong),
+                ("vcycles", ctypes.c_longlong), ("milliseconds", ctypes.c_double)]
+
+
+_lib = None
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "mg_params_default": (_i, [ctypes.POINTER(MgParams), _i, _i]),
+    "mg_setup_noise_len": (ctypes.c_size_t, [ctypes.POINTER(MgParams)]),
+    "mg_setup": (_i, [_vp, _d, ctypes.POINTER(MgParams), _vp, ctypes.POINTER(_vp)]),
+    "mg_set_mass": (_i, [_vp, _d]),
+    "mg_solve": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, ctypes.POINTER(MgSolveInfo)]),
+    "mg_apply_D": (_i, [_vp, _vp, _vp, _i, _i, _i]),
+    "mg_apply_A": (_i, [_vp, _vp, _vp, _i, _i]),
+    "mg_apply_coarse": (_i, [_vp, _i, _vp, _vp, _i, _i]),
+    "mg_restrict": (_i, [_vp, _i, _vp, _vp, _i, _i]),
+    "mg_prolong": (_i, [_vp, _i, _vp, _vp, _i, _i]),
+    "mg_vcycle": (_i, [_vp, _vp, _vp, _i]),
+    "mg_coarsest_solve": (_i, [_vp, _vp, _vp]),
+    "mg_get_level": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                          ctypes.POINTER(_i)]),
+    "mg_get_null_vectors": (_i, [_vp, _i, _vp]),
+    "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
+    "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
+    "mg_last_error": (ctypes.c_char_p, [_vp]),
+    "mg_destroy": (None, [_vp]),
+}
+
+
+def lib():
+    """Load libmg.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} missing "
+                               "(run `python __graft_entry__.py`)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().mg_last_error(handle)
+        raise MgError(status, msg.decode() if msg else "")
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(Lx, Lt, blocks, Nv, noise=None, **kw) -> MgParams:
+    p = MgParams()
+    _check(lib().mg_params_default(ctypes.byref(p), Lx, Lt))
+    p.nlevels = len(blocks) + 1
+    for l, ((bx, bt), nv) in enumerate(zip(blocks, Nv)):
+        p.block[l][0], p.block[l][1] = bx, bt
+        p.Nv[l] = nv
+    for k, v in kw.items():
+        setattr(p, k, v)
+    if noise is not None:
+        p.setup_noise = _ptr(noise).value
+    return p
+
+
+def mg_setup_noise_len(params: MgParams) -> int:
+    return int(lib().mg_setup_noise_len(ctypes.byref(params)))
+
+
+def mg_setup(gauge, mass, params: MgParams, stream=None):
+    import torch
+    h = ctypes.c_void_p()
+    _check(lib().mg_setup(_ptr(gauge, torch.complex128), float(mass), ctypes.byref(params),
+                          _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def mg_set_mass(h, mass):
+    _check(lib().mg_set_mass(h, float(mass)), h)
+
+
+def mg_solve(h, b, x, nrhs, tol, maxiter, solver):
+    import torch
+    infos = (MgSolveInfo * nrhs)()
+    st = lib().mg_solve(h, _ptr(b, torch.complex128), _ptr(x, torch.complex128), nrhs,
+                        float(tol), int(maxiter), int(solver), infos)
+    return st, list(infos)
+
+
+def _vec_dtype(precision):
+    import torch
+    return torch.complex128 if precision == PREC_F64 else torch.complex64
+
+
+def mg_apply_D(h, inp, out, nrhs, dagger, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_apply_D(h, _ptr(inp, dt), _ptr(out, dt), nrhs, int(dagger), precision), h)
+
+
+def mg_apply_A(h, inp, out, nrhs, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_apply_A(h, _ptr(inp, dt), _ptr(out, dt), nrhs, precision), h)
+
+
+def mg_apply_coarse(h, level, inp, out, nrhs, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_apply_coarse(h, level, _ptr(inp, dt), _ptr(out, dt), nrhs, precision), h)
+
+
+def mg_restrict(h, level, inp, out, nrhs, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_restrict(h, level, _ptr(inp, dt), _ptr(out, dt), nrhs, precision), h)
+
+
+def mg_prolong(h, level, inp, out, nrhs, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_prolong(h, level, _ptr(inp, dt), _ptr(out, dt), nrhs, precision), h)
+
+
+def mg_vcycle(h, inp, out, precision):
+    dt = _vec_dtype(precision)
+    _check(lib().mg_vcycle(h, _ptr(inp, dt), _ptr(out, dt), precision), h)
+
+
+def mg_coarsest_solve(h, inp, out):
+    import torch
+    _check(lib().mg_coarsest_solve(h, _ptr(inp, torch.complex128), _ptr(out, torch.complex128)), h)
+
+
+def mg_get_level(h, level):
+    a, b, c, d = _i(), _i(), _i(), _i()
+    _check(lib().mg_get_level(h, level, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                              ctypes.byref(d)), h)
+    return a.value, b.value, c.value, d.value
+
+
+def mg_get_null_vectors(h, level, out):
+    import torch
+    _check(lib().mg_get_null_vectors(h, level, _ptr(out, torch.complex128)), h)
+
+
+def mg_get_coarse_op(h, level, out):
+    import torch
+    _check(lib().mg_get_coarse_op(h, level, _ptr(out, torch.complex128)), h)
+
+
+def mg_get_smoother(h, level):
+    buf = (ctypes.c_double * 4)()
+    _check(lib().mg_get_smoother(h, level, buf), h)
+    return tuple(buf)
+
+
+def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
+    import torch
+    _check(lib().mg_block_map(Lx, Lt, bx, bt, _ptr(coarse, torch.int32), _ptr(offset, torch.int32),
+                              _stream_ptr(stream)))
+
+
+def mg_last_error(h=None) -> str:
+    msg = lib().mg_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def mg_destroy(h):
+    if h:
+        lib().mg_destroy(h)
+
+
+class Multigrid:
+    """Owns one mg_handle: setup at construction, solve/apply methods, destroy on close."""
+
+    def __init__(self, gauge, mass, blocks, Nv, noise, stream=None, **params):
+        _, Lt, Lx = gauge.shape
+        self.Lx, self.Lt = Lx, Lt
+        self.params = make_params(Lx, Lt, list(blocks), list(Nv), noise, **params)
+        self._noise = noise
+        self.h = mg_setup(gauge.contiguous(), mass, self.params, stream)
+
+    def set_mass(self, mass):
+        mg_set_mass(self.h, mass)
+
+    def level(self, level):
+        return mg_get_level(self.h, level)
+
+    def solve(self, b, tol=1e-10, maxiter=10000, solver=SOLVER_MGCG_MIXED, x=None):
+        import torch
+        nrhs = b.numel() // (self.Lx * self.Lt * 2)
+        if x is None:
+            x = torch.empty_like(b)
+        st, infos = mg_solve(self.h, b, x, nrhs, tol, maxiter, solver)
+        if st not in (0, 4):
+            _check(st, self.h)
+        return x, infos
+
+    def close(self):
+        if self.h:
+            mg_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

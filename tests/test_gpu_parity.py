@@ -1,0 +1,313 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against the
+CPU oracle on the same seeded inputs.
+
+Tolerances (per element): |gpu - oracle| <= tol * (|oracle| + M) where M is the
+sum of magnitudes of the terms that make up the element (computed by applying
+the absolute value of the operator to the absolute value of the input);
+tol = 1e-12 for FP64, 1e-6 for FP32, 8e-3 for BF16 coarse blocks (2^-8
+relative rounding of each block entry).  Integer maps are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov as okr
+from oracle import multigrid as omg
+from oracle import wilson as ow
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32, TOL16 = 1e-12, 1e-6, 8e-3
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0710_3612_gb300 import mg as m
+    return m
+
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def check(got, want, mag, tol, what=""):
+    err = np.abs(got - want)
+    bound = tol * (np.abs(want) + mag)
+    worst = np.max(err / np.maximum(bound, 1e-300))
+    assert worst <= 1.0, f"{what}: worst error / bound = {worst:.3g} (max err {err.max():.3e})"
+
+
+# ---------------------------------------------------------------------------
+# configurations: (Lx, Lt, beta, sweeps, seed, mass, blocks, Nv)
+# ---------------------------------------------------------------------------
+CASES = {
+    # two levels, coarse 6 x 4
+    "2lvl_24x16": (24, 16, 6.0, 40, 1, -0.7, [(4, 4)], [4]),
+    # three levels, coarse extents 6x6 -> 3x3 (odd coarse extent)
+    "3lvl_24x24": (24, 24, 6.0, 40, 2, -1.2, [(4, 4), (2, 2)], [3, 4]),
+    # three levels with a coarsest extent of 2 (+1 and -1 neighbours alias)
+    "3lvl_16x16_alias": (16, 16, 3.0, 30, 3, -0.4, [(4, 4), (2, 2)], [2, 3]),
+}
+
+
+class Case:
+    def __init__(self, mg, name):
+        Lx, Lt, beta, sweeps, seed, m, blocks, Nv = CASES[name]
+        self.Lx, self.Lt, self.m, self.blocks, self.Nv = Lx, Lt, m, blocks, Nv
+        self.U = W.links_from_angles(W.quenched_u1_angles(Lx, Lt, beta, sweeps, seed))
+        self.noise = W.setup_noise(Lx, Lt, blocks, Nv, seed + 100)
+        self.H = omg.setup(self.U, m, blocks, Nv, self.noise)
+        self.Ug, self.noise_g = dev(self.U), dev(self.noise)
+        self.solver = mg.Multigrid(self.Ug, m, blocks, Nv, self.noise_g)
+        self.h = self.solver.h
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, mg):
+    c = Case(mg, request.param)
+    yield c
+    c.solver.close()
+
+
+def abs_dirac(U, m):
+    return abs(ow.dirac_matrix(U, m))
+
+
+# ---------------------------------------------------------------------------
+def test_block_map_bit_exact(mg):
+    for Lx, Lt, bx, bt in [(16, 8, 4, 4), (12, 18, 2, 3), (128, 128, 4, 4), (6, 4, 2, 2)]:
+        c = torch.empty(Lx * Lt, dtype=torch.int32, device=DEV)
+        o = torch.empty(Lx * Lt, dtype=torch.int32, device=DEV)
+        mg.mg_block_map(Lx, Lt, bx, bt, c, o)
+        cw, ow_ = omg.block_map(Lx, Lt, bx, bt)
+        assert np.array_equal(host(c), cw) and np.array_equal(host(o), ow_)
+
+
+@pytest.mark.parametrize("dagger", [0, 1])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_D(case, mg, dagger, prec):
+    nrhs = 3
+    psi = W.gaussian_field((nrhs, case.Lt, case.Lx, 2), 5)
+    want = ow.apply_D(case.U, case.m, psi, dagger=bool(dagger))
+    Dabs = abs_dirac(case.U, case.m)
+    mag = (Dabs @ np.abs(psi).reshape(nrhs, -1).T).T.reshape(psi.shape)
+    if prec == "f64":
+        out = torch.empty_like(dev(psi))
+        mg.mg_apply_D(case.h, dev(psi), out, nrhs, dagger, mg.PREC_F64)
+        check(host(out), want, mag, TOL64, "D f64")
+    else:
+        inp = dev(psi.astype(np.complex64))
+        out = torch.empty_like(inp)
+        mg.mg_apply_D(case.h, inp, out, nrhs, dagger, mg.PREC_F32)
+        check(host(out), want, mag, TOL32, "D f32")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_A(case, mg, prec):
+    nrhs = 2
+    psi = W.gaussian_field((nrhs, case.Lt, case.Lx, 2), 6)
+    want = ow.apply_A(case.U, case.m, psi)
+    Dabs = abs_dirac(case.U, case.m)
+    mag = (Dabs.T @ (Dabs @ np.abs(psi).reshape(nrhs, -1).T)).T.reshape(psi.shape)
+    if prec == "f64":
+        out = torch.empty_like(dev(psi))
+        mg.mg_apply_A(case.h, dev(psi), out, nrhs, mg.PREC_F64)
+        check(host(out), want, mag, TOL64, "A f64")
+    else:
+        inp = dev(psi.astype(np.complex64))
+        out = torch.empty_like(inp)
+        mg.mg_apply_A(case.h, inp, out, nrhs, mg.PREC_F32)
+        check(host(out), want, mag, TOL32, "A f32")
+
+
+def test_null_vectors_and_smoother(case, mg):
+    H = case.H
+    for l in range(H.L - 1):
+        lv = H.levels[l]
+        Lx, Lt, n, Nv = mg.mg_get_level(case.h, l + 1)
+        assert (Lx, Lt, n, Nv) == (lv.Lx, lv.Lt, lv.n, lv.Nv)
+        out = torch.empty((Nv, Lt, Lx, n), dtype=torch.complex128, device=DEV)
+        mg.mg_get_null_vectors(case.h, l + 1, out)
+        got = host(out)
+        # unit-norm block vectors: entries O(1/sqrt(block dim)); relaxation and
+        # Gram-Schmidt amplify rounding mildly
+        check(got, lv.V, np.ones_like(np.abs(lv.V)), 1e-10, f"V level {l + 1}")
+        c0, c1, lam, om = mg.mg_get_smoother(case.h, l + 1)
+        assert c0 == pytest.approx(lv.c0, rel=1e-10) and c1 == pytest.approx(lv.c1, rel=1e-10)
+        assert om == pytest.approx(lv.omega_relax, rel=1e-11)
+
+
+def test_coarse_operators(case, mg):
+    H = case.H
+    for l in range(1, H.L):
+        op = H.levels[l].op
+        out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
+        mg.mg_get_coarse_op(case.h, l + 1, out)
+        got = host(out)
+        rowmax = np.max(np.abs(op.M), axis=(2, 4), keepdims=True)
+        check(got, op.M, rowmax, 1e-11, f"A_c level {l + 1}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_apply_coarse(case, mg, prec):
+    H = case.H
+    for l in range(1, H.L):
+        op = H.levels[l].op
+        nrhs = 2
+        v = W.gaussian_field((nrhs, op.Lt, op.Lx, op.n), 11 + l)
+        want = op.apply(v)
+        mag = omg.StencilOp(op.disp, np.abs(op.M)).apply(np.abs(v))
+        if prec == "f64":
+            out = torch.empty_like(dev(v))
+            mg.mg_apply_coarse(case.h, l + 1, dev(v), out, nrhs, mg.PREC_F64)
+            check(host(out), want, mag, 1e-11, "coarse f64")
+        else:
+            inp = dev(v.astype(np.complex64))
+            out = torch.empty_like(inp)
+            code = mg.PREC_F32 if prec == "f32" else mg.PREC_BF16
+            mg.mg_apply_coarse(case.h, l + 1, inp, out, nrhs, code)
+            check(host(out), want, mag, TOL32 if prec == "f32" else TOL16, f"coarse {prec}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_restrict_prolong(case, mg, prec):
+    H = case.H
+    tol = 1e-11 if prec == "f64" else TOL32
+    for l in range(H.L - 1):
+        lv = H.levels[l]
+        nrhs = 2
+        r = W.gaussian_field((nrhs, lv.Lt, lv.Lx, lv.n), 21 + l)
+        ec = W.gaussian_field((nrhs, lv.Lt // lv.bt, lv.Lx // lv.bx, 2 * lv.Nv), 31 + l)
+        Pabs = np.abs(omg.prolongator_matrix(lv.V))
+        want_c = omg.restrict(lv.V, lv.bx, lv.bt, r)
+        mag_c = np.stack([omg.restrict(np.abs(lv.V), lv.bx, lv.bt, np.abs(x)) for x in r])
+        want_f = omg.prolong(lv.V, lv.bx, lv.bt, ec)
+        mag_f = np.stack([omg.prolong(np.abs(lv.V), lv.bx, lv.bt, np.abs(x)) for x in ec])
+        del Pabs
+        dt = np.complex128 if prec == "f64" else np.complex64
+        code = mg.PREC_F64 if prec == "f64" else mg.PREC_F32
+        out_c = torch.empty(want_c.shape, dtype=torch.complex128 if prec == "f64" else torch.complex64, device=DEV)
+        mg.mg_restrict(case.h, l + 1, dev(r.astype(dt)), out_c, nrhs, code)
+        check(host(out_c), want_c, mag_c, tol, "restrict")
+        out_f = torch.empty(want_f.shape, dtype=out_c.dtype, device=DEV)
+        mg.mg_prolong(case.h, l + 1, dev(ec.astype(dt)), out_f, nrhs, code)
+        check(host(out_f), want_f, mag_f, tol, "prolong")
+
+
+def test_coarsest_solve(case, mg):
+    H = case.H
+    last = H.levels[-1]
+    b = W.gaussian_field((last.Lt, last.Lx, last.n), 41)
+    want = omg.coarsest_solve(H, b)
+    out = torch.empty_like(dev(b))
+    mg.mg_coarsest_solve(case.h, dev(b), out)
+    got = host(out)
+    assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+
+
+def test_vcycle_f64(case, mg):
+    r = W.gaussian_field((case.Lt, case.Lx, 2), 51)
+    want = omg.vcycle(case.H, r)
+    out = torch.empty_like(dev(r))
+    mg.mg_vcycle(case.h, dev(r), out, mg.PREC_F64)
+    got = host(out)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_vcycle_f32_is_close(case, mg):
+    """The FP32 V-cycle (BF16 coarse blocks) is a perturbed preconditioner: close
+    to the FP64 one at the BF16 level, and still Hermitian positive in effect."""
+    r = W.gaussian_field((case.Lt, case.Lx, 2), 52)
+    want = omg.vcycle(case.H, r)
+    inp = dev(r.astype(np.complex64))
+    out = torch.empty_like(inp)
+    mg.mg_vcycle(case.h, inp, out, mg.PREC_F32)
+    got = host(out)
+    assert np.linalg.norm(got - want) <= 5e-2 * np.linalg.norm(want)
+    assert np.vdot(r, got).real > 0
+
+
+@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "cg_fp64"])
+def test_solve_matches_oracle(case, mg, solver):
+    chi = W.gaussian_field((case.Lt, case.Lx, 2), 61)
+    b = ow.apply_D(case.U, case.m, chi, dagger=True)
+    tol = 1e-10
+    x_ora, it_ora, info_ora = okr.mgcg(case.H, b, 1e-12)
+    code = {"mgcg_fp64": mg.SOLVER_MGCG_FP64, "mixed": mg.SOLVER_MGCG_MIXED,
+            "cg_fp64": mg.SOLVER_CG_FP64}[solver]
+    x, infos = case.solver.solve(dev(b), tol=tol, maxiter=20000, solver=code)
+    got = host(x).reshape(b.shape)
+    A = case.H.levels[0].op
+    res = np.linalg.norm(b - A.apply(got)) / np.linalg.norm(b)
+    assert res <= tol and infos[0].true_residual <= tol
+    assert abs(infos[0].true_residual - res) <= 1e-3 * tol + 1e-15
+    # |x - x*| <= kappa * |r| / |b| * |x*|  (kappa from the oracle's dense operator)
+    lam = np.linalg.eigvalsh(A.dense()) if case.Lx * case.Lt <= 600 else None
+    kappa = lam[-1] / lam[0] if lam is not None else 1e6
+    assert np.linalg.norm(got - x_ora) <= (kappa * tol + 1e-10) * np.linalg.norm(x_ora)
+    if solver == "mgcg_fp64":
+        x10, it10, _ = okr.mgcg(case.H, b, tol)
+        assert abs(infos[0].iterations - it10) <= 1
+
+
+def test_zero_rhs_and_repeatability(case, mg):
+    b = torch.zeros((case.Lt, case.Lx, 2), dtype=torch.complex128, device=DEV)
+    x, infos = case.solver.solve(b, solver=mg.SOLVER_MGCG_FP64)
+    assert infos[0].iterations == 0 and not torch.any(x != 0)
+    chi = W.gaussian_field((case.Lt, case.Lx, 2), 71)
+    bb = dev(ow.apply_D(case.U, case.m, chi, dagger=True))
+    x1, _ = case.solver.solve(bb, solver=mg.SOLVER_MGCG_MIXED)
+    x1 = host(x1)
+    x2, _ = case.solver.solve(bb, solver=mg.SOLVER_MGCG_MIXED)
+    assert np.array_equal(x1, host(x2))     # fixed reduction order: identical bits
+
+
+def test_set_mass_rebuilds_galerkin(mg):
+    c = Case(mg, "2lvl_24x16")
+    try:
+        m2 = 0.3
+        omg.set_mass(c.H, m2)
+        c.solver.set_mass(m2)
+        op = c.H.levels[1].op
+        out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
+        mg.mg_get_coarse_op(c.h, 2, out)
+        rowmax = np.max(np.abs(op.M), axis=(2, 4), keepdims=True)
+        check(host(out), op.M, rowmax, 1e-11, "A_c after set_mass")
+        c0, c1, _, _ = mg.mg_get_smoother(c.h, 1)
+        assert c0 == pytest.approx(c.H.levels[0].c0, rel=1e-10)
+    finally:
+        c.solver.close()
+
+
+def test_argument_errors(mg):
+    U = W.links_from_angles(W.quenched_u1_angles(16, 16, 6.0, 5, 1))
+    noise = dev(W.setup_noise(16, 16, [(4, 4)], [4], 1))
+    with pytest.raises(mg.MgError) as e:           # 16 not divisible by 3
+        mg.Multigrid(dev(U), 0.1, [(3, 3)], [4], noise)
+    assert e.value.status == 1
+    with pytest.raises(mg.MgError) as e:           # Nv above block-chirality dimension
+        mg.Multigrid(dev(U), 0.1, [(2, 2)], [5], noise)
+    assert e.value.status == 1
+    bad = U.copy()
+    bad[0, 3, 4] *= 1.01
+    with pytest.raises(mg.MgError) as e:           # non-unit link
+        mg.Multigrid(dev(bad), 0.1, [(4, 4)], [4], noise)
+    assert e.value.status == 1
+    with mg.Multigrid(dev(U), 0.1, [(4, 4)], [4], noise) as s:
+        b = torch.full((16, 16, 2), float("nan"), dtype=torch.complex128, device=DEV)
+        with pytest.raises(mg.MgError) as e:
+            s.solve(b, solver=mg.SOLVER_MGCG_FP64)
+        assert e.value.status == 5
