@@ -1,0 +1,512 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive MG-CG solver on one GB300 (or N replicas).
+
+Workload (default "L128_b6_massweep"): 128 x 128 quenched U(1) lattice at
+beta = 6 (seeded Metropolis, 200 sweeps), three levels (4x4 then 2x2 blocks,
+Nv = 8 per chirality, 8 setup relaxation sweeps), one Gaussian source chi,
+b = D^dagger chi, tol 1e-10.  One step = the setup at the near-critical mass
+(lambda_min(A) < 1e-5) followed by the mass sweep {m_nc, -0.05, 0.0, 0.1},
+reusing the setup's vectors: for each mass, rebuild the Galerkin hierarchy
+and coarsest inverse (except for m_nc), form b = D^dagger chi, and solve to
+true FP64 relative residual 1e-10 -- 4 solves per step.
+
+Arms:
+  (default)          the CUDA library, mixed-precision MG-CG (value), plus the
+                     same step with plain FP64 MG-CG, an end-to-end leg with
+                     host buffers, roofline of the dominant kernel family and
+                     the CPU oracle timed on a bounded sample.
+  --impl reference   the CPU oracle on the same workload (bounded sample per
+                     step, scaled to whole solves with the oracle's own
+                     iteration counts).
+Multi-GPU: replicas only (each rank solves the same workload independently);
+value sums the solves of all ranks over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MG-CG solves/s & p50/p99 latency at rel.res 1e-10 vs plain FP64; stencil GB/s"
+UNIT = "solves/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured",
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+def workload_inputs(name):
+    wl = W.BENCH_WORKLOADS[name]
+    crit = json.load(open(os.path.join(ROOT, "workloads", "critical_masses.json")))[wl["critical_key"]]
+    theta = W.quenched_u1_angles(wl["Lx"], wl["Lt"], wl["beta"], wl["sweeps"], wl["seed"])
+    plaq = W.mean_plaquette(theta)
+    if abs(plaq - crit["plaquette"]) > 1e-12:
+        raise RuntimeError(f"regenerated gauge field differs from the stored one (plaquette {plaq})")
+    U = W.links_from_angles(theta)
+    noise = W.setup_noise(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], wl["noise_seed"])
+    chi = W.gaussian_field((wl["Lt"], wl["Lx"], 2), wl["chi_seed"])
+    masses = [crit["m_nc"]] + list(wl["heavy_masses"])
+    return wl, crit, U, noise, chi, masses
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_bench(args):
+    import torch
+    import torch.distributed as dist
+    from paper_0710_3612_gb300 import mg
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl, crit, U, noise, chi, masses = workload_inputs(args.workload)
+    mg.lib()
+    stream = torch.cuda.current_stream()
+    U_d = torch.from_numpy(U).to(dev)
+    noise_d = torch.from_numpy(noise).to(dev)
+    chi_d = torch.from_numpy(chi).to(dev)
+    b_d = torch.empty_like(chi_d)
+    x_d = torch.empty_like(chi_d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
+    tol = wl["tol"]
+    params = mg.make_params(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], noise_d,
+                            setup_sweeps=wl["setup_sweeps"])
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+
+    def step(solver, record=None, profile=False):
+        h = mg.mg_setup(U_d, masses[0], params, stream)
+        try:
+            if profile:
+                mg.mg_profile_enable(h, True)
+            for m in masses:
+                if m != masses[0]:
+                    mg.mg_set_mass(h, m)
+                mg.mg_apply_D(h, chi_d, b_d, 1, 1, mg.PREC_F64)
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                st, info = mg.mg_solve(h, b_d, x_d, 1, tol, 200000, solver)
+                e1.record(stream)
+                if st != 0 or not info[0].true_residual <= tol:
+                    raise RuntimeError(f"solve failed at m={m}: status {st}, "
+                                       f"residual {info[0].true_residual}: {mg.mg_last_error(h)}")
+                if record is not None:
+                    record.append((m, e0, e1, info[0]))
+            prof = None
+            if profile:
+                prof = {f: mg.mg_profile_read(h, f) for f in range(7)}
+            return prof
+        finally:
+            mg.mg_destroy(h)
+
+    def timed(solver, K, clocks=None):
+        recs, steps = [], []
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if clocks:
+            clocks.start()
+        launches0 = mg.mg_kernel_launches()
+        for _ in range(K):
+            flush.zero_()                      # L2 flush between timed steps
+            s0, s1 = ev(), ev()
+            s0.record(stream)
+            step(solver, recs)
+            s1.record(stream)
+            steps.append((s0, s1))
+        torch.cuda.synchronize()
+        launches = mg.mg_kernel_launches() - launches0
+        if world > 1:
+            dist.barrier()
+        ck = clocks.stop() if clocks else None
+        step_ms = [a.elapsed_time(b) for a, b in steps]
+        total = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        solve_ms = [a.elapsed_time(b) for _, a, b, _ in recs]
+        per_mass = {}
+        for (m, a, b, info), t in zip(recs, solve_ms):
+            d = per_mass.setdefault(repr(m), {"ms": [], "iterations": info.iterations,
+                                              "fine_applies": info.fine_applies,
+                                              "refinements": info.refinements,
+                                              "true_residual": info.true_residual})
+            d["ms"].append(t)
+        for d in per_mass.values():
+            d["median_ms"] = round(statistics.median(d.pop("ms")), 3)
+        return {"total_ms": total, "step_ms": step_ms, "solve_ms": solve_ms, "per_mass": per_mass,
+                "launches": launches, "clocks": ck}
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(mg.SOLVER_MGCG_MIXED)
+    clocks = Clocks(local) if rank == 0 else None
+    res = timed(mg.SOLVER_MGCG_MIXED, args.steps, clocks)
+    solves = len(masses) * args.steps * world
+    value = solves / (res["total_ms"] / 1000.0)
+
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT,
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": round(res["total_ms"] / args.steps, 3),
+                              "per_mass": res["per_mass"], "gpu_launches": int(res["launches"]),
+                              "note": "timed-only profiling run"}))
+        return
+    # plain FP64 MG-CG, same step
+    kp = max(1, min(args.steps, args.plain_steps))
+    step(mg.SOLVER_MGCG_FP64)
+    plain = timed(mg.SOLVER_MGCG_FP64, kp)
+    plain_value = len(masses) * kp * world / (plain["total_ms"] / 1000.0)
+
+    # roofline: one profiled step, dominant kernel family by device time
+    prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
+    roof = roofline(prof, wl, load_peaks())
+
+    # end-to-end through the public API with host buffers
+    e2e = e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, world)
+
+    if rank == 0:
+        sm = sorted(res["solve_ms"])
+        pct = lambda q: sm[min(len(sm) - 1, int(math.ceil(q * len(sm))) - 1)]   # noqa: E731
+        psm = sorted(plain["solve_ms"])
+        ppct = lambda q: psm[min(len(psm) - 1, int(math.ceil(q * len(psm))) - 1)]   # noqa: E731
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["total_ms"] / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16 (V-cycle) / f64 (outer, residual, coarsest)",
+            "data": "synthetic: seeded quenched U(1) Metropolis configuration, Gaussian source",
+            "config": {"workload": args.workload, "lattice": [wl["Lx"], wl["Lt"]], "beta": wl["beta"],
+                       "levels": len(wl["blocks"]) + 1, "blocks": wl["blocks"], "Nv": wl["Nv"],
+                       "masses": [round(m, 12) for m in masses], "m_crit": crit["m_crit"],
+                       "tol": wl["tol"], "rhs_per_solve": 1, "solves_per_step": len(masses),
+                       "step": "setup at m_nc + 4 x (re-Galerkin/coarsest inverse, b = D^dag chi, solve)",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "latency_ms": {"p50": round(pct(0.5), 3), "p99": round(pct(0.99), 3),
+                           "per_mass": res["per_mass"]},
+            "plain_fp64": {"value": round(plain_value, 3), "unit": UNIT, "steps": kp,
+                           "ms_per_step": round(plain["total_ms"] / kp, 3),
+                           "p50_ms": round(ppct(0.5), 3), "p99_ms": round(ppct(0.99), 3),
+                           "per_mass": plain["per_mass"]},
+            "mixed_vs_plain_fp64": round(value / plain_value, 3),
+            "roofline": roof,
+            "stencil": stencil_gbs(mg, torch, dev, stream),
+            "e2e": e2e,
+            "gpu_launches": int(res["launches"]),
+            "clocks": res["clocks"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+FAM_NAMES = ["fine_A_f32", "coarse_apply", "transfer", "coarsest_solve", "coarsest_inverse",
+             "galerkin", "fine_A_f64"]
+
+
+def roofline(prof, wl, peaks):
+    """Dominant family by device time in one profiled step; achieved = algorithmic
+    bytes (or flops) per call / average call duration."""
+    fam = max(prof, key=lambda f: prof[f][0])
+    ms, calls = prof[fam]
+    Lx, Lt = wl["Lx"], wl["Lt"]
+    V = Lx * Lt
+    Nv1, Nv2 = wl["Nv"]
+    V2 = V // 16
+    V3 = V2 // 4
+    n3 = 2 * Nv2
+    N3 = V3 * n3
+    ld = (N3 + 63) // 64 * 64
+    shares = {FAM_NAMES[f]: round(prof[f][0], 3) for f in prof}
+    per_call_s = ms / 1000.0 / max(calls, 1)
+    out = {"kernel": FAM_NAMES[fam], "calls": calls, "avg_us": round(per_call_s * 1e6, 3),
+           "family_ms_in_step": shares, "traffic": None}
+    if fam == 4:       # Gauss-Jordan inverse: 8 ld^3 real flops per inversion (FP32 SIMT)
+        flops = 8.0 * ld ** 3
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        out.update({"bound": "alu", "achieved": round(flops / per_call_s / 1e12, 3),
+                    "peak": round(peak, 1), "unit": "TFLOP/s",
+                    "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"})
+    else:
+        if fam == 0:
+            byts = 48.0 * V
+        elif fam == 6:
+            byts = 96.0 * V
+        elif fam == 1:      # mostly the BF16 V-cycle applies on level 2
+            byts = V2 * (9 * (2 * Nv1) ** 2 * 4 + 2 * 2 * Nv1 * 8)
+        elif fam == 2:
+            byts = V * (2 * 8 + 2 * Nv1 * 8) + V2 * 2 * Nv1 * 8
+        elif fam == 3:      # GEMV over the FP32 inverse dominates
+            byts = 8.0 * ld * ld * 3
+        else:
+            byts = 16.0 * V2 * 9 * (2 * Nv1) ** 2
+        out.update({"bound": "hbm", "achieved": round(byts / per_call_s / 1e9, 1),
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s"})
+    out["frac"] = round(out["achieved"] / out["peak"], 4)
+    out["peak_note"] = f"of {peaks['src']}"
+    return out
+
+
+def stencil_gbs(mg, torch, dev, stream):
+    """Fused A = D^dagger D (FP32) on a 4096 x 4096 lattice (above L2): algorithmic
+    48 B/site over CUDA-event time, median of 50 after 10 warm-ups."""
+    L = 4096
+    U = torch.polar(torch.ones(2, L, L, dtype=torch.float64, device=dev),
+                    torch.rand(2, L, L, dtype=torch.float64, device=dev) * 0.5).contiguous()
+    params = mg.make_params(L, L, [], [])          # nlevels = 1: fine operator only
+    h = mg.mg_setup(U, 0.1, params, stream)
+    try:
+        x = torch.randn(L * L * 2, dtype=torch.complex64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(10):
+            mg.mg_apply_A(h, x, y, 1, mg.PREC_F32)
+        ts = []
+        for _ in range(50):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mg.mg_apply_A(h, x, y, 1, mg.PREC_F32)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        med = statistics.median(a.elapsed_time(b) for a, b in ts)
+        gbs = 48.0 * L * L / (med / 1000.0) / 1e9
+        peaks = load_peaks()
+        return {"lattice": [L, L], "precision": "f32", "median_us": round(med * 1000, 2),
+                "gbs": round(gbs, 1), "frac_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                "bytes_per_site": 48}
+    finally:
+        mg.mg_destroy(h)
+
+
+def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, world):
+    """Same step through the public API with pinned host buffers copied in and
+    the solutions copied out inside the timed region."""
+    Uh = torch.from_numpy(U).pin_memory()
+    nh = torch.from_numpy(noise).pin_memory()
+    ch = torch.from_numpy(chi).pin_memory()
+    xh = torch.empty_like(ch).pin_memory()
+    K = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        Ud = Uh.to(dev, non_blocking=True)
+        nd = nh.to(dev, non_blocking=True)
+        cd = ch.to(dev, non_blocking=True)
+        with mg.Multigrid(Ud, masses[0], wl["blocks"], wl["Nv"], nd,
+                          setup_sweeps=wl["setup_sweeps"]) as s:
+            b = torch.empty_like(cd)
+            for m in masses:
+                if m != masses[0]:
+                    s.set_mass(m)
+                mg.mg_apply_D(s.h, cd, b, 1, 1, mg.PREC_F64)
+                x, info = s.solve(b, tol=wl["tol"], maxiter=200000, solver=mg.SOLVER_MGCG_MIXED)
+                xh.copy_(x, non_blocking=True)
+                torch.cuda.synchronize()
+                if not info[0].true_residual <= wl["tol"]:
+                    raise RuntimeError("e2e solve did not converge")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(len(masses) * K * world / dt, 3), "unit": UNIT, "steps": K,
+            "h2d_bytes_per_step": int(Uh.nbytes + nh.nbytes + ch.nbytes),
+            "d2h_bytes_per_step": int(len(masses) * xh.nbytes)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample, scaled to whole solves
+# ---------------------------------------------------------------------------
+def oracle_sample(name, nc_iters_sample):
+    """Runs in a subprocess with one BLAS thread: setup at m_nc, re-mass + solve at
+    the heaviest mass, and nc_iters_sample MG-CG iterations at m_nc.  Returns
+    per-phase seconds."""
+    from oracle import krylov, multigrid, wilson
+    wl, crit, U, noise, chi, masses = workload_inputs(name)
+    t0 = time.perf_counter()
+    H = multigrid.setup(U, masses[0], wl["blocks"], wl["Nv"], noise, sweeps=wl["setup_sweeps"])
+    t_setup = time.perf_counter() - t0
+    b = wilson.apply_D(U, masses[0], chi, dagger=True)
+    t0 = time.perf_counter()
+    krylov.mgcg(H, b, 1e-300, nc_iters_sample)
+    t_nc = (time.perf_counter() - t0) / nc_iters_sample
+    t0 = time.perf_counter()
+    multigrid.set_mass(H, masses[-1])
+    t_mass = time.perf_counter() - t0
+    b = wilson.apply_D(U, masses[-1], chi, dagger=True)
+    t0 = time.perf_counter()
+    _, it_heavy, _ = krylov.mgcg(H, b, wl["tol"], 20000)
+    t_heavy = time.perf_counter() - t0
+    return {"setup_s": t_setup, "nc_iter_s": t_nc, "set_mass_s": t_mass,
+            "heavy_solve_s": t_heavy, "heavy_iters": it_heavy}
+
+
+def scale_oracle(name, s):
+    """Seconds of one full 4-mass step from the sample, using the oracle's own
+    iteration counts (workloads/oracle_iterations.json)."""
+    its = json.load(open(os.path.join(ROOT, "workloads", "oracle_iterations.json")))[name]["masses"]
+    wl, crit, *_ = (W.BENCH_WORKLOADS[name], json.load(open(os.path.join(
+        ROOT, "workloads", "critical_masses.json")))[W.BENCH_WORKLOADS[name]["critical_key"]])
+    n_nc = its[repr(crit["m_nc"])]["iterations"]
+    heavy = [its[repr(m)]["iterations"] for m in wl["heavy_masses"]]
+    per_heavy_iter = s["heavy_solve_s"] / max(s["heavy_iters"], 1)
+    step_s = (s["setup_s"] + n_nc * s["nc_iter_s"] + 3 * s["set_mass_s"]
+              + sum(heavy) * per_heavy_iter)
+    return step_s, n_nc
+
+
+def run_oracle_subprocess(name, iters):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%r, %d)))" % (ROOT, name, iters))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       cwd=ROOT, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args):
+    t0 = time.perf_counter()
+    s = run_oracle_subprocess(args.workload, args.oracle_iters)
+    wall = time.perf_counter() - t0
+    step_s, n_nc = scale_oracle(args.workload, s)
+    return {"value": round(4.0 / step_s, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"numpy FP64 oracle, 1 thread: setup at m_nc, {args.oracle_iters} MG-CG "
+                       f"iterations at m_nc, re-mass + full solve at m=0.1; scaled to the 4-mass "
+                       f"step with the oracle's iteration counts (m_nc: {n_nc})"),
+            "sample_wall_s": round(wall, 1), "scaled_step_s": round(step_s, 2)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        run_oracle_subprocess(args.workload, 2)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s = run_oracle_subprocess(args.workload, args.oracle_iters)
+        walls.append(time.perf_counter() - t0)
+        step_s, n_nc = scale_oracle(args.workload, s)
+        vals.append(step_s)
+    value = 4.0 * len(vals) / sum(vals)
+    wl = W.BENCH_WORKLOADS[args.workload]
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", 1)), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1000 * sum(vals) / len(vals), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: seeded quenched U(1) Metropolis configuration, Gaussian source",
+            "config": {"workload": args.workload, "lattice": [wl["Lx"], wl["Lt"]],
+                       "levels": len(wl["blocks"]) + 1, "Nv": wl["Nv"], "solves_per_step": 4},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": (f"per step: setup at m_nc, {args.oracle_iters} MG-CG iterations "
+                                        f"at m_nc, re-mass + solve at m=0.1; scaled to the 4-mass "
+                                        f"step with the oracle's iteration counts (m_nc: {n_nc})"),
+                             "sample_wall_s_per_step": round(sum(walls) / len(walls), 1)},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="L128_b6_massweep", choices=list(W.BENCH_WORKLOADS))
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--oracle-iters", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_bench(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -75,7 +75,8 @@ typedef enum {
 
 typedef struct {
   int Lx, Lt;                           /* fine lattice                          */
-  int nlevels;                          /* 2 .. MG_MAX_LEVELS                    */
+  int nlevels;                          /* 1 .. MG_MAX_LEVELS; 1 = fine operator
+                                           only (apply calls and plain CG)       */
   int block[MG_MAX_LEVELS - 1][2];      /* (bx, bt) blocking level l -> l+1      */
   int Nv[MG_MAX_LEVELS - 1];            /* vectors per chirality, level l -> l+1 */
   int setup_sweeps;                     /* nu of Eq. relax (default 8)           */
@@ -110,7 +111,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt);
  * Eq. relax, then one start vector for the power iteration that sets the
  * relaxation step 1/lambda_max(A_l), then one start vector for the two MR
  * steps that fix the smoother (Sec. 4).  Each is a level-l vector.
- * Returns 0 for invalid parameters. */
+ * Returns 0 for invalid parameters and for nlevels = 1 (no noise needed). */
 size_t mg_setup_noise_len(const mg_params* p);
 
 /* Adaptive setup (Sec. 3, Eq. relax, Eq. P1, Eq. Galerkin; Sec. 4 smoother).
@@ -120,7 +121,9 @@ size_t mg_setup_noise_len(const mg_params* p);
  * stream: cudaStream_t to use (NULL: the legacy default stream).
  * Validation: Lx, Lt even; each extent divisible by its block; every coarse
  *   extent >= 2; blocks >= 2 x 2; 1 <= Nv_l <= (bx * bt * n_l / 2);
- *   2 <= nlevels <= MG_MAX_LEVELS.  MG_ERR_ARG otherwise.
+ *   1 <= nlevels <= MG_MAX_LEVELS; the coarsest level has at most 16384
+ *   unknowns (dense inverse).  MG_ERR_ARG otherwise.  With nlevels = 1 no
+ *   hierarchy is built and setup_noise may be NULL.
  * On success *out owns all device memory of the hierarchy. */
 mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void* stream,
                    mg_handle** out);
@@ -188,6 +191,27 @@ mg_status mg_get_smoother(const mg_handle* h, int level, double* out4);
  * for i = x + Lx t.  Device int32 arrays of Lx * Lt entries.  stream may be NULL. */
 mg_status mg_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
                        void* stream);
+
+/* Kernel launches made by this library in this process so far (all handles). */
+unsigned long long mg_kernel_launches(void);
+
+/* Per-family device timing for roofline reporting.  When enabled, every call
+ * of a family is bracketed by CUDA events on the handle's stream (adds a few
+ * microseconds per call); mg_profile_read synchronises and returns the summed
+ * device time and the number of calls since the last enable. */
+typedef enum {
+  MG_KF_FINE_A = 0,     /* fused A = D^dagger D on the fine lattice            */
+  MG_KF_COARSE = 1,     /* coarse stencil apply, any level and precision       */
+  MG_KF_TRANSFER = 2,   /* restriction and prolongation                        */
+  MG_KF_COARSEST = 3,   /* coarsest solve (GEMV + FP64 refinement)             */
+  MG_KF_INVERSE = 4,    /* coarsest dense inverse (Gauss-Jordan)               */
+  MG_KF_GALERKIN = 5,   /* Galerkin coarse-operator build                      */
+  MG_KF_FINE_A64 = 6,   /* A = D^dagger D on the fine lattice in FP64 (MG_KF_FINE_A
+                           counts the FP32 applications)                        */
+  MG_KF_COUNT = 7
+} mg_kernel_family;
+mg_status mg_profile_enable(mg_handle* h, int on);
+mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long* calls);
 
 /* Message of the last error on h (h == NULL: last mg_setup / mg_block_map
  * error of the calling thread). */

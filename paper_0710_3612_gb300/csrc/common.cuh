@@ -8,6 +8,10 @@
 
 namespace mgk {
 
+// Number of kernel launches made by this library (all threads), for reporting.
+void count_launch();
+unsigned long long launch_count();
+
 template <typename R> struct cplx_of;
 template <> struct cplx_of<double> { using type = double2; };
 template <> struct cplx_of<float> { using type = float2; };

@@ -9,6 +9,10 @@
 
 namespace mgk {
 
+// Kernel launches made by this library so far (counted at every launch site).
+unsigned long long launch_count();
+void count_launch();
+
 // ---- deterministic reductions -------------------------------------------
 // Number of partial sums a reduction over `count` complex entries produces.
 int reduce_blocks(long long count);

@@ -1,10 +1,16 @@
 // Vector kernels of the Krylov solvers: deterministic reductions (fixed block
 // count and fixed summation tree, so repeated solves give identical bits),
 // CG updates on per-RHS device scalars, precision conversions.
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace mgk {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static constexpr int RT = 256;   // threads per reduction block
 
@@ -82,8 +88,8 @@ cudaError_t dot(const void* a, const void* b, long long count, int nrhs, double*
                 double* out, cudaStream_t s) {
   int g = reduce_blocks(count);
   k_dot_partial<R, false><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, (const cplx_t<R>*)b,
-                                                       count, partials);
-  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out);
+                                                       count, partials); count_launch();
+  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -92,8 +98,8 @@ cudaError_t norm2(const void* a, long long count, int nrhs, double* partials, do
                   cudaStream_t s) {
   int g = reduce_blocks(count);
   k_dot_partial<R, true><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, nullptr, count,
-                                                      partials);
-  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out);
+                                                      partials); count_launch();
+  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out); count_launch();
   return cudaGetLastError();
 }
 
@@ -116,7 +122,7 @@ template <typename R>
 cudaError_t axpby(double a, const void* x, double b, void* y, long long count, int nrhs,
                   cudaStream_t s) {
   k_axpby<R><<<grid1(count, nrhs), RT, 0, s>>>((R)a, (const cplx_t<R>*)x, (R)b, (cplx_t<R>*)y,
-                                                count);
+                                                count); count_launch();
   return cudaGetLastError();
 }
 
@@ -136,7 +142,7 @@ template <typename R>
 cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long count, int nrhs,
                            cudaStream_t s) {
   k_scale_inv_sqrt<R><<<grid1(count, nrhs), RT, 0, s>>>((const cplx_t<R>*)x, (cplx_t<R>*)y, nrm,
-                                                         count);
+                                                         count); count_launch();
   return cudaGetLastError();
 }
 
@@ -159,7 +165,7 @@ template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
                   const double* pq, const int* frozen, long long count, int nrhs, cudaStream_t s) {
   k_cg_xr<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
-                                                (const cplx_t<R>*)q, rz, pq, frozen, count);
+                                                (const cplx_t<R>*)q, rz, pq, frozen, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -181,7 +187,7 @@ template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
                  const int* frozen, long long count, int nrhs, cudaStream_t s) {
   k_cg_p<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)p, (const cplx_t<R>*)z, rz_new, rz_old,
-                                               frozen, count);
+                                               frozen, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -199,7 +205,7 @@ __global__ void k_f64_to_f32_scaled(const double2* __restrict__ in, float2* __re
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s) {
   k_f64_to_f32_scaled<<<grid1(count, nrhs), RT, 0, s>>>((const double2*)in, (float2*)out, nrm,
-                                                         count);
+                                                         count); count_launch();
   return cudaGetLastError();
 }
 
@@ -216,7 +222,7 @@ __global__ void k_f32_acc_scaled(const float2* __restrict__ in, double2* __restr
 
 cudaError_t f32_accumulate_scaled(const void* in, void* x, const double* nrm, long long count,
                                   int nrhs, cudaStream_t s) {
-  k_f32_acc_scaled<<<grid1(count, nrhs), RT, 0, s>>>((const float2*)in, (double2*)x, nrm, count);
+  k_f32_acc_scaled<<<grid1(count, nrhs), RT, 0, s>>>((const float2*)in, (double2*)x, nrm, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -231,11 +237,11 @@ __global__ void k_cvt_32_64(const float2* __restrict__ in, double2* __restrict__
   if (i < count) out[i] = make_double2(in[i].x, in[i].y);
 }
 cudaError_t convert_f64_f32(const void* in, void* out, long long count, cudaStream_t s) {
-  k_cvt_64_32<<<grid1(count, 1), RT, 0, s>>>((const double2*)in, (float2*)out, count);
+  k_cvt_64_32<<<grid1(count, 1), RT, 0, s>>>((const double2*)in, (float2*)out, count); count_launch();
   return cudaGetLastError();
 }
 cudaError_t convert_f32_f64(const void* in, void* out, long long count, cudaStream_t s) {
-  k_cvt_32_64<<<grid1(count, 1), RT, 0, s>>>((const float2*)in, (double2*)out, count);
+  k_cvt_32_64<<<grid1(count, 1), RT, 0, s>>>((const float2*)in, (double2*)out, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -260,7 +266,7 @@ cudaError_t lincomb(void* out, double a, const void* u, double b, const void* v,
                     const void* w, long long count, int nrhs, cudaStream_t s) {
   k_lincomb<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)out, (R)a, (const cplx_t<R>*)u, (R)b,
                                                   (const cplx_t<R>*)v, (R)c,
-                                                  (const cplx_t<R>*)w, count);
+                                                  (const cplx_t<R>*)w, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -272,7 +278,7 @@ __global__ void k_sub_from(const cplx_t<R>* __restrict__ b, cplx_t<R>* __restric
 }
 template <typename R>
 cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s) {
-  k_sub_from<R><<<grid1(count, 1), RT, 0, s>>>((const cplx_t<R>*)b, (cplx_t<R>*)r, count);
+  k_sub_from<R><<<grid1(count, 1), RT, 0, s>>>((const cplx_t<R>*)b, (cplx_t<R>*)r, count); count_launch();
   return cudaGetLastError();
 }
 

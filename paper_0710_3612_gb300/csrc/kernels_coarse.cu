@@ -63,6 +63,7 @@ cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, 
   else
     k_coarse_apply<float, __nv_bfloat162><<<grid, 256, 0, s>>>(
         (const float2*)in, (float2*)out, (const __nv_bfloat162*)A, Lx, Lt, n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -80,7 +81,7 @@ __global__ void k_coarse_convert(const double2* __restrict__ a, void* out, int w
 cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
                            cudaStream_t s) {
   k_coarse_convert<<<(unsigned)((count + 255) / 256), 256, 0, s>>>((const double2*)A64, out,
-                                                                   weights, count);
+                                                                   weights, count); count_launch();
   return cudaGetLastError();
 }
 
@@ -117,7 +118,7 @@ cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx,
                         int bt, int h, int Nv, int nrhs, cudaStream_t s) {
   const int tot = (Lx / bx) * (Lt / bt) * 2 * Nv;
   k_restrict<R><<<dim3((tot + 127) / 128, nrhs), 128, 0, s>>>(
-      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
+      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv); count_launch();
   return cudaGetLastError();
 }
 
@@ -146,7 +147,7 @@ cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, 
   const int tot = Lx * Lt * 2 * h;
   k_prolong<R><<<dim3((tot + 255) / 256, nrhs), 256, 0, s>>>(
       (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-      accumulate);
+      accumulate); count_launch();
   return cudaGetLastError();
 }
 
@@ -242,7 +243,7 @@ cudaError_t block_gram_schmidt(const void* E, void* Vst, int Lx, int Lt, int bx,
   const int Vc = (Lx / bx) * (Lt / bt);
   const size_t smem = (size_t)Nv * m * sizeof(double2);
   k_block_gs<<<2 * Vc, 32, smem, s>>>((const double2*)E, (double2*)Vst, Lx, Lt, bx, bt, h, Nv,
-                                     breakdown_tol, flag);
+                                     breakdown_tol, flag); count_launch();
   return cudaGetLastError();
 }
 
@@ -336,10 +337,10 @@ cudaError_t galerkin_fine(const void* U64, double diag, const void* Vst, void* W
   const long long Vc = (long long)(Lx / bx) * (Lt / bt), nc = 2 * Nv;
   const long long nW = Vc * nc * (bx + 2) * (bt + 2);
   k_galerkin_W<<<(unsigned)((nW + 255) / 256), 256, 0, s>>>(
-      (const double2*)U64, diag, (const double2*)Vst, (double2*)Wbuf, Lx, Lt, bx, bt, Nv);
+      (const double2*)U64, diag, (const double2*)Vst, (double2*)Wbuf, Lx, Lt, bx, bt, Nv); count_launch();
   const long long nA = Vc * 9 * nc * nc;
   k_galerkin_WW<<<(unsigned)((nA + 255) / 256), 256, 0, s>>>((const double2*)Wbuf,
-                                                              (double2*)Ac, Lx, Lt, bx, bt, Nv);
+                                                              (double2*)Ac, Lx, Lt, bx, bt, Nv); count_launch();
   return cudaGetLastError();
 }
 
@@ -409,7 +410,7 @@ cudaError_t galerkin_coarse(const void* Af, const void* Vst, void* Ac, int Lx, i
   }
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   k_galerkin_coarse<<<Vc, 256, smem, s>>>((const double2*)Af, (const double2*)Vst, (double2*)Ac,
-                                          Lx, Lt, bx, bt, nf, Nv);
+                                          Lx, Lt, bx, bt, nf, Nv); count_launch();
   return cudaGetLastError();
 }
 
@@ -446,9 +447,11 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
   if (e != cudaSuccess) return e;
   const long long tot = (long long)Lx * Lt * n * n;
   k_coarse_to_dense<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const double2*)A,
-                                                                  (float2*)dense, Lx, Lt, n, ld);
-  if (ld > N)
+                                                                  (float2*)dense, Lx, Lt, n, ld); count_launch();
+  if (ld > N) {
     k_pad_identity<<<(unsigned)((ld - N + 255) / 256), 256, 0, s>>>((float2*)dense, N, ld);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -577,10 +580,10 @@ cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s
   float2* Rp = Cp + (long long)N * GJB;
   const int nb = N / GJB;
   for (int k = 0; k < nb; ++k) {
-    k_gj_diag<<<1, dim3(GJB, GJB), 0, s>>>(M, N, k, P);
-    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp);
-    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cp);
-    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp);
+    k_gj_diag<<<1, dim3(GJB, GJB), 0, s>>>(M, N, k, P); count_launch();
+    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp); count_launch();
+    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cp); count_launch();
+    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp); count_launch();
   }
   return cudaGetLastError();
 }
@@ -620,9 +623,9 @@ __global__ void __launch_bounds__(256) k_gemv(const float2* __restrict__ B,
 cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld, void* xtmp,
                            bool accumulate, cudaStream_t s) {
   if (ld % 2 || ld < N) return cudaErrorInvalidValue;
-  k_x_to_f32<<<(ld + 255) / 256, 256, 0, s>>>((const double2*)x, (float2*)xtmp, N, ld);
+  k_x_to_f32<<<(ld + 255) / 256, 256, 0, s>>>((const double2*)x, (float2*)xtmp, N, ld); count_launch();
   k_gemv<<<(N + 7) / 8, 256, 0, s>>>((const float2*)B, (const float2*)xtmp, (double2*)y, N, ld,
-                                     accumulate);
+                                     accumulate); count_launch();
   return cudaGetLastError();
 }
 
@@ -636,7 +639,7 @@ __global__ void k_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int
 
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
                       cudaStream_t s) {
-  k_block_map<<<(Lx * Lt + 255) / 256, 256, 0, s>>>(Lx, Lt, bx, bt, coarse, offset);
+  k_block_map<<<(Lx * Lt + 255) / 256, 256, 0, s>>>(Lx, Lt, bx, bt, coarse, offset); count_launch();
   return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
   else
     k_wilson_D<R, false><<<grid, 256, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
                                               (const cplx_t<R>*)U, (R)diag, Lx, Lt);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -86,7 +87,7 @@ __global__ void k_fold_links(const double2* __restrict__ g, cplx_t<R>* __restric
 template <typename R>
 cudaError_t fold_links(const void* gauge, void* U, int Lx, int Lt, cudaStream_t s) {
   const int n = 2 * Lx * Lt;
-  k_fold_links<R><<<(n + 255) / 256, 256, 0, s>>>((const double2*)gauge, (cplx_t<R>*)U, Lx, Lt);
+  k_fold_links<R><<<(n + 255) / 256, 256, 0, s>>>((const double2*)gauge, (cplx_t<R>*)U, Lx, Lt); count_launch();
   return cudaGetLastError();
 }
 
@@ -112,7 +113,7 @@ __global__ void k_link_unitarity(const double2* __restrict__ g, long long count,
 }
 
 cudaError_t link_unitarity(const void* gauge, long long count, double* out, cudaStream_t s) {
-  k_link_unitarity<<<1, 1024, 0, s>>>((const double2*)gauge, count, out);
+  k_link_unitarity<<<1, 1024, 0, s>>>((const double2*)gauge, count, out); count_launch();
   return cudaGetLastError();
 }
 

@@ -74,9 +74,16 @@ struct mg_handle {
   std::vector<void*> allocs;
   std::string err;
   long long fine_applies = 0, vcycles = 0;
+  // optional per-family event timing
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev[MG_KF_COUNT];
+  size_t prof_used[MG_KF_COUNT] = {};
 };
 
 namespace {
+
+// Largest coarsest level handled by the dense inverse (FP32 N x N: 2 GiB).
+constexpr long long MG_DENSE_MAX = 16384;
 
 // scalar slots (each a double2)
 enum { S_RZ = 0, S_RZN = 2, S_PQ = 4, S_RR = 6, S_T0 = 8, S_T1 = 10, S_BN = 12, S_NR = 14,
@@ -139,11 +146,35 @@ void ensure_partials(mg_handle* h, int nrhs) {
   h->partial_rhs = nrhs;
 }
 
+// Brackets one call of a kernel family with CUDA events when profiling is on.
+struct ProfScope {
+  mg_handle* h;
+  int fam;
+  cudaEvent_t end = nullptr;
+  ProfScope(mg_handle* h_, int fam_) : h(h_), fam(fam_) {
+    if (!h->prof_on) return;
+    auto& ev = h->prof_ev[fam];
+    size_t& u = h->prof_used[fam];
+    while (ev.size() < 2 * (u + 1)) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[2 * u], h->s);
+    end = ev[2 * u + 1];
+    ++u;
+  }
+  ~ProfScope() {
+    if (end) cudaEventRecord(end, h->s);
+  }
+};
+
 // ----- level operator ------------------------------------------------------
 // weights for coarse levels: 0 = F64, 1 = F32, 2 = BF16
 template <typename R>
 void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int weights) {
   Level& L = h->lv[l];
+  ProfScope prof(h, l == 0 ? (sizeof(R) == 8 ? MG_KF_FINE_A64 : MG_KF_FINE_A) : MG_KF_COARSE);
   if (l == 0) {
     const double diag = 4.0 + h->mass;
     const size_t bytes = (size_t)L.count() * nrhs * sizeof(R) * 2;
@@ -161,7 +192,7 @@ void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int w
 // ----- coarsest solve: FP32 explicit inverse refined in FP64 ----------------
 // x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r.
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
-  Level& L = h->lv[h->L - 1];
+  ProfScope prof(h, MG_KF_COARSEST);
   ck(h, dense_gemv_f32(h->Binv, b, x, h->Nc, h->ldc, h->gemv_x, false, h->s), "coarsest gemv");
   for (int it = 0; it < steps; ++it) {
     apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64);
@@ -202,12 +233,18 @@ void vcycle(mg_handle* h, int l, const void* b, void* x) {
   apply_level<R>(h, l, x, t, 1, weights);
   ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
   const void* Vst = f64 ? (const void*)L.Vst64 : (const void*)L.Vst32;
-  ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, h->s), "restrict");
+  {
+    ProfScope prof(h, MG_KF_TRANSFER);
+    ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, h->s), "restrict");
+  }
   // 3. e_c = V_{l+1} r_c
   vcycle<R>(h, l + 1, wc[0], wc[1]);
   // 4. x = x + P e_c
-  ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, true, h->s),
+  {
+    ProfScope prof(h, MG_KF_TRANSFER);
+    ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, true, h->s),
      "prolong");
+  }
   // 5. x = x + R (b - A x)
   apply_level<R>(h, l, x, t, 1, weights);
   ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
@@ -258,6 +295,7 @@ void build_coarse_ops(mg_handle* h) {
   for (int l = 0; l + 1 < h->L; ++l) {
     Level& L = h->lv[l];
     Level& C = h->lv[l + 1];
+    ProfScope prof(h, MG_KF_GALERKIN);
     if (l == 0)
       ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt,
                           L.Nv, h->s),
@@ -274,7 +312,10 @@ void build_coarse_ops(mg_handle* h) {
 void build_coarsest(mg_handle* h) {
   Level& L = h->lv[h->L - 1];
   ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
-  ck(h, gauss_jordan_inverse_f32(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+  {
+    ProfScope prof(h, MG_KF_INVERSE);
+    ck(h, gauss_jordan_inverse_f32(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+  }
   // Refinement count: smallest number of FP64 correction steps that brings a
   // fixed test vector (all ones) to coarsest_tol, plus one.
   double* s = h->scal;
@@ -302,14 +343,14 @@ void set_mass_internal(mg_handle* h, double mass) {
   build_coarse_ops(h);
   for (int l = 0; l + 1 < h->L; ++l)
     smoother_coefficients(h, l, h->lv[l].w64[3], h->lv[l].w64[2]);
-  build_coarsest(h);
+  if (h->L > 1) build_coarsest(h);
   sync(h);
 }
 
 mg_status validate(const mg_params* p, std::string& msg) {
   if (!p) { msg = "params is NULL"; return MG_ERR_ARG; }
   if (p->Lx < 4 || p->Lt < 4 || p->Lx % 2 || p->Lt % 2) { msg = "Lx, Lt must be even and >= 4"; return MG_ERR_ARG; }
-  if (p->nlevels < 2 || p->nlevels > MG_MAX_LEVELS) { msg = "nlevels out of range"; return MG_ERR_ARG; }
+  if (p->nlevels < 1 || p->nlevels > MG_MAX_LEVELS) { msg = "nlevels out of range"; return MG_ERR_ARG; }
   int lx = p->Lx, lt = p->Lt, n = 2;
   for (int l = 0; l + 1 < p->nlevels; ++l) {
     const int bx = p->block[l][0], bt = p->block[l][1], nv = p->Nv[l];
@@ -322,7 +363,11 @@ mg_status validate(const mg_params* p, std::string& msg) {
     lx /= bx; lt /= bt; n = 2 * nv;
   }
   if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
-  if (!p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
+  if (p->nlevels > 1 && !p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
+  if (p->nlevels > 1 && (long long)lx * lt * n > MG_DENSE_MAX) {
+    msg = "coarsest level has more than " + std::to_string(MG_DENSE_MAX) + " unknowns";
+    return MG_ERR_ARG;
+  }
   return MG_OK;
 }
 
@@ -347,6 +392,8 @@ mg_status guarded(mg_handle* h, F&& f) {
 void free_all(mg_handle* h) {
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
+  for (auto& v : h->prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   for (void* p : h->allocs)
     if (p) cudaFree(p);
   h->allocs.clear();
@@ -531,7 +578,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
 }
 
 size_t mg_setup_noise_len(const mg_params* p) {
-  if (!p || p->nlevels < 2 || p->nlevels > MG_MAX_LEVELS) return 0;
+  if (!p || p->nlevels < 1 || p->nlevels > MG_MAX_LEVELS) return 0;
   size_t tot = 0;
   long long lx = p->Lx, lt = p->Lt, n = 2;
   for (int l = 0; l + 1 < p->nlevels; ++l) {
@@ -609,13 +656,13 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(double2));
       h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(float2));
     }
-    {
+    if (h->L > 1) {
       const Level& L0 = h->lv[0];
       const size_t Vc = (size_t)(L0.Lx / L0.bx) * (L0.Lt / L0.bt);
       h->Wbuf = dalloc(h, Vc * 2 * L0.Nv * (L0.bx + 2) * (L0.bt + 2) * 2 * sizeof(double2));
     }
     // coarsest dense storage
-    {
+    if (h->L > 1) {
       const Level& C = h->lv[h->L - 1];
       h->Nc = (int)C.count();
       h->ldc = (h->Nc + 63) / 64 * 64;
@@ -692,6 +739,7 @@ mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, i
                    int solver, mg_solve_info* info) {
   if (!h) return MG_ERR_ARG;
   if (!b || !x || nrhs < 1 || !(tol > 0.0) || maxiter < 1) { h->err = "invalid solve arguments"; return MG_ERR_ARG; }
+  if (h->L < 2 && solver != MG_SOLVER_CG_FP64) { h->err = "multigrid solvers need nlevels >= 2"; return MG_ERR_ARG; }
   mg_status worst = MG_OK;
   mg_status st = guarded(h, [&]() {
     const long long n = h->lv[0].count();
@@ -764,7 +812,7 @@ mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_
 
 mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision) {
   if (!h) return MG_ERR_ARG;
-  if (!in || !out || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  if (!in || !out || h->L < 2 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
   return guarded(h, [&]() {
     if (precision == MG_PREC_F64) vcycle<double>(h, 0, in, out);
     else vcycle<float>(h, 0, in, out);
@@ -773,7 +821,7 @@ mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision) {
 
 mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out) {
   if (!h) return MG_ERR_ARG;
-  if (!in || !out) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  if (!in || !out || h->L < 2) { h->err = "invalid arguments"; return MG_ERR_ARG; }
   return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine); });
 }
 
@@ -808,7 +856,7 @@ mg_status mg_get_null_vectors(const mg_handle* hc, int level, void* out) {
   return guarded(h, [&]() {
     const Level& L = h->lv[level - 1];
     const long long tot = (long long)L.V * 2 * L.Nv * (L.n / 2);
-    k_vst_to_vectors<<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(L.Vst64, (double2*)out, L.V, L.Nv, L.n / 2);
+    k_vst_to_vectors<<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(L.Vst64, (double2*)out, L.V, L.Nv, L.n / 2); count_launch();
     ck(h, cudaGetLastError(), "gather");
   });
 }
@@ -840,6 +888,30 @@ mg_status mg_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t*
   cudaError_t e = block_map(Lx, Lt, bx, bt, coarse, offset, (cudaStream_t)stream);
   if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return MG_ERR_CUDA; }
   return MG_OK;
+}
+
+unsigned long long mg_kernel_launches(void) { return launch_count(); }
+
+mg_status mg_profile_enable(mg_handle* h, int on) {
+  if (!h) return MG_ERR_ARG;
+  h->prof_on = on != 0;
+  for (int f = 0; f < MG_KF_COUNT; ++f) h->prof_used[f] = 0;
+  return MG_OK;
+}
+
+mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long* calls) {
+  if (!h || family < 0 || family >= MG_KF_COUNT) return MG_ERR_ARG;
+  return guarded(h, [&]() {
+    sync(h);
+    double tot = 0.0;
+    for (size_t u = 0; u < h->prof_used[family]; ++u) {
+      float ms = 0.f;
+      ck(h, cudaEventElapsedTime(&ms, h->prof_ev[family][2 * u], h->prof_ev[family][2 * u + 1]), "event time");
+      tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (calls) *calls = (long long)h->prof_used[family];
+  });
 }
 
 const char* mg_last_error(const mg_handle* h) {

@@ -63,6 +63,9 @@ _SIGS = {
     "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
+    "mg_kernel_launches": (ctypes.c_ulonglong, []),
+    "mg_profile_enable": (_i, [_vp, _i]),
+    "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
     "mg_last_error": (ctypes.c_char_p, [_vp]),
     "mg_destroy": (None, [_vp]),
 }
@@ -212,6 +215,23 @@ def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
     import torch
     _check(lib().mg_block_map(Lx, Lt, bx, bt, _ptr(coarse, torch.int32), _ptr(offset, torch.int32),
                               _stream_ptr(stream)))
+
+
+KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64 = range(7)
+
+
+def mg_kernel_launches() -> int:
+    return int(lib().mg_kernel_launches())
+
+
+def mg_profile_enable(h, on=True):
+    _check(lib().mg_profile_enable(h, int(on)), h)
+
+
+def mg_profile_read(h, family):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().mg_profile_read(h, family, ctypes.byref(ms), ctypes.byref(n)), h)
+    return ms.value, n.value
 
 
 def mg_last_error(h=None) -> str:

@@ -164,3 +164,17 @@ def setup_noise(Lx: int, Lt: int, blocks, Nv, seed: int) -> np.ndarray:
     [t][x][dof] order.
     """
     return gaussian_field((setup_noise_len(Lx, Lt, blocks, Nv),), seed)
+
+
+# ---------------------------------------------------------------------------
+# Benchmark workload definitions (sizes and seeds only).
+# ---------------------------------------------------------------------------
+# 128 x 128, beta = 6 (200 sweeps from cold start), 3 levels (4x4 then 2x2
+# blocks), Nv = 8 per chirality, 8 setup sweeps; setup at the near-critical
+# mass, reused for the heavier masses of the sweep; one Gaussian source chi,
+# b = D^dagger chi, tol 1e-10.
+BENCH_WORKLOADS = {
+    "L128_b6_massweep": dict(Lx=128, Lt=128, beta=6.0, sweeps=200, seed=1, blocks=[(4, 4), (2, 2)],
+                             Nv=[8, 8], setup_sweeps=8, heavy_masses=[-0.05, 0.0, 0.1],
+                             critical_key="L128_b6_s1", noise_seed=7, chi_seed=101, tol=1e-10),
+}
