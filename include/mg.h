@@ -67,9 +67,12 @@ typedef enum { MG_PREC_F64 = 0, MG_PREC_F32 = 1, MG_PREC_BF16 = 2 } mg_precision
 
 typedef enum {
   MG_SOLVER_MGCG_FP64 = 0,  /* MG-CG, everything in FP64 (Sec. 4)                */
-  MG_SOLVER_MGCG_MIXED = 1, /* FP64 iterative refinement around an FP32 MG-CG
-                               whose coarse blocks are BF16 (FP32 accumulate);
-                               true residual, solution, coarsest solve in FP64 */
+  MG_SOLVER_MGCG_MIXED = 1, /* FP32 MG-CG with FP64 reliable updates: the true
+                               residual b - A x and the solution are kept in
+                               FP64 and replace the FP32 recursion whenever its
+                               residual drops by reliable_delta; V-cycle in
+                               FP32 (coarse blocks FP32 or BF16 with FP32
+                               accumulation), coarsest solve in FP64 */
   MG_SOLVER_CG_FP64 = 2     /* plain CG on A, FP64 (the paper's baseline)        */
 } mg_solver;
 
@@ -92,11 +95,15 @@ typedef struct {
   int inner_coarsest_refine;            /* mixed solver: FP64 refinement steps of
                                            the coarsest solve inside the FP32
                                            V-cycle (2)                           */
+  int vcycle_coarse_bf16;               /* mixed solver: 1 = coarse blocks of the
+                                           FP32 V-cycle in BF16, 0 = FP32 (0)    */
+  double reliable_delta;                /* mixed solver: FP64 residual replacement
+                                           when |r| drops by this factor (0.1)   */
 } mg_params;
 
 typedef struct {
   int iterations;             /* Krylov iterations (inner iterations summed)   */
-  int refinements;            /* mixed solver: outer FP64 corrections          */
+  int refinements;            /* FP64 residual replacements (reliable updates) */
   double true_residual;       /* |b - A x| / |b| recomputed in FP64            */
   long long fine_applies;     /* applications of the fine A = D^dagger D        */
   long long vcycles;          /* V-cycles applied                               */

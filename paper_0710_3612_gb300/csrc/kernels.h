@@ -16,8 +16,11 @@ void count_launch();
 // ---- deterministic reductions -------------------------------------------
 // Number of partial sums a reduction over `count` complex entries produces.
 int reduce_blocks(long long count);
+// Reductions take a workspace ws of (64 + 2 * 608 * nrhs) doubles whose first
+// 64 doubles (tickets) are zero before the first call (they are left zero);
+// nrhs <= 64.  One launch: the last block adds the partials in fixed order.
 
-// partial[rhs][blk] (2 doubles: re, im) of sum conj(a) b; then out[rhs] (double2).
+// out[rhs] (double2) = sum conj(a) b.
 template <typename R>
 cudaError_t dot(const void* a, const void* b, long long count, int nrhs, double* partials,
                 double* out, cudaStream_t s);
@@ -36,10 +39,12 @@ template <typename R>
 cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long count, int nrhs,
                            cudaStream_t s);
 // CG step on per-RHS device scalars (double2 arrays, real part used):
-//   alpha = rz / pq (0 when frozen[rhs]); x += alpha p; r -= alpha q.
+//   alpha = rz / pq (0 when frozen[rhs]); x += alpha p; r -= alpha q;
+//   rr[rhs] = |r|^2 (one launch, reduction workspace ws).
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
-                  const double* pq, const int* frozen, long long count, int nrhs, cudaStream_t s);
+                  const double* pq, const int* frozen, long long count, int nrhs, double* ws,
+                  double* rr, cudaStream_t s);
 //   beta = rz_new / rz_old; p = z + beta p; then rz_old <- rz_new is done by the caller.
 template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
@@ -47,7 +52,7 @@ cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_
 // out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s);
-// x(FP64) += in(FP32) * sqrt(nrm[rhs].x)
+// x(FP64) += in(FP32) * sqrt(nrm[rhs].x)   (scale 1 when nrm is null)
 cudaError_t f32_accumulate_scaled(const void* in, void* x, const double* nrm, long long count,
                                   int nrhs, cudaStream_t s);
 // out = in (precision convert, no scaling)

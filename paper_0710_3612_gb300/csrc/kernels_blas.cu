@@ -41,10 +41,44 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
   }
 }
 
+// Single-pass deterministic reduction.  Every block writes its partial sum;
+// the last block to finish (found with an atomic ticket) adds the partials in
+// a fixed order and resets the ticket.  ws = [64 tickets (as doubles)][partials].
+__device__ __forceinline__ void finish_reduction(double re, double im, double* ws, double* out,
+                                                 double* sh) {
+  unsigned* tickets = (unsigned*)ws;
+  double* partials = ws + 64;
+  const int rhs = blockIdx.y, G = gridDim.x;
+  __shared__ bool last;
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * ((long long)rhs * G + blockIdx.x)] = re;
+    partials[2 * ((long long)rhs * G + blockIdx.x) + 1] = im;
+    __threadfence();
+    last = atomicAdd(&tickets[rhs], 1u) == (unsigned)(G - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  re = 0.0;
+  im = 0.0;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    re += __ldcg(&partials[2 * ((long long)rhs * G + i)]);
+    im += __ldcg(&partials[2 * ((long long)rhs * G + i) + 1]);
+  }
+  __syncthreads();
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) {
+    out[2 * rhs] = re;
+    out[2 * rhs + 1] = im;
+    tickets[rhs] = 0u;
+  }
+}
+
 template <typename R, bool NORM>
-__global__ void __launch_bounds__(RT) k_dot_partial(const cplx_t<R>* __restrict__ a,
-                                                    const cplx_t<R>* __restrict__ b,
-                                                    long long count, double* partials) {
+__global__ void __launch_bounds__(RT) k_dot(const cplx_t<R>* __restrict__ a,
+                                            const cplx_t<R>* __restrict__ b, long long count,
+                                            double* ws, double* out) {
   __shared__ double sh[2 * RT / 32];
   const int rhs = blockIdx.y;
   const cplx_t<R>* pa = a + (long long)rhs * count;
@@ -64,42 +98,27 @@ __global__ void __launch_bounds__(RT) k_dot_partial(const cplx_t<R>* __restrict_
       im = fma(-(double)u.y, (double)v.x, im);
     }
   }
-  block_sum2(re, im, sh);
-  if (threadIdx.x == 0) {
-    partials[2 * ((long long)rhs * gridDim.x + blockIdx.x)] = re;
-    partials[2 * ((long long)rhs * gridDim.x + blockIdx.x) + 1] = im;
-  }
-}
-
-__global__ void __launch_bounds__(RT) k_finalize(const double* partials, int nblk, double* out) {
-  __shared__ double sh[2 * RT / 32];
-  const int rhs = blockIdx.x;
-  double re = 0.0, im = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += RT) {
-    re += partials[2 * (rhs * nblk + i)];
-    im += partials[2 * (rhs * nblk + i) + 1];
-  }
-  block_sum2(re, im, sh);
-  if (threadIdx.x == 0) { out[2 * rhs] = re; out[2 * rhs + 1] = im; }
+  finish_reduction(re, im, ws, out, sh);
 }
 
 template <typename R>
 cudaError_t dot(const void* a, const void* b, long long count, int nrhs, double* partials,
                 double* out, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
   int g = reduce_blocks(count);
-  k_dot_partial<R, false><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, (const cplx_t<R>*)b,
-                                                       count, partials); count_launch();
-  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out); count_launch();
+  k_dot<R, false><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, (const cplx_t<R>*)b, count,
+                                               partials, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t norm2(const void* a, long long count, int nrhs, double* partials, double* out,
                   cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
   int g = reduce_blocks(count);
-  k_dot_partial<R, true><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, nullptr, count,
-                                                      partials); count_launch();
-  k_finalize<<<nrhs, RT, 0, s>>>(partials, g, out); count_launch();
+  k_dot<R, true><<<dim3(g, nrhs), RT, 0, s>>>((const cplx_t<R>*)a, nullptr, count, partials, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -147,25 +166,43 @@ cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long 
 }
 
 template <typename R>
-__global__ void k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ r,
-                        const cplx_t<R>* __restrict__ p, const cplx_t<R>* __restrict__ q,
-                        const double* rz, const double* pq, const int* frozen, long long count) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ r,
+                                              const cplx_t<R>* __restrict__ p,
+                                              const cplx_t<R>* __restrict__ q, const double* rz,
+                                              const double* pq, const int* frozen,
+                                              long long count, double* ws, double* rr) {
+  __shared__ double sh[2 * RT / 32];
   const int rhs = blockIdx.y;
-  if (i >= count || (frozen && frozen[rhs])) return;
+  const bool skip = frozen && frozen[rhs];
   const double d = pq[2 * rhs];
-  const R alpha = d != 0.0 ? (R)(rz[2 * rhs] / d) : (R)0;
-  i += (long long)rhs * count;
-  cplx_t<R> xv = x[i], rv = r[i], pv = p[i], qv = q[i];
-  x[i] = mk(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
-  r[i] = mk(fma(-alpha, qv.x, rv.x), fma(-alpha, qv.y, rv.y));
+  const R alpha = (d != 0.0 && !skip) ? (R)(rz[2 * rhs] / d) : (R)0;
+  double acc = 0.0;
+  const long long base = (long long)rhs * count;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const long long k = base + i;
+    cplx_t<R> rv = r[k];
+    if (!skip) {
+      const cplx_t<R> xv = x[k], pv = p[k], qv = q[k];
+      x[k] = mk(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
+      rv = mk(fma(-alpha, qv.x, rv.x), fma(-alpha, qv.y, rv.y));
+      r[k] = rv;
+    }
+    acc = fma((double)rv.x, (double)rv.x, acc);
+    acc = fma((double)rv.y, (double)rv.y, acc);
+  }
+  finish_reduction(acc, 0.0, ws, rr, sh);
 }
 
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
-                  const double* pq, const int* frozen, long long count, int nrhs, cudaStream_t s) {
-  k_cg_xr<R><<<grid1(count, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
-                                                (const cplx_t<R>*)q, rz, pq, frozen, count); count_launch();
+                  const double* pq, const int* frozen, long long count, int nrhs, double* ws,
+                  double* rr, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  int g = reduce_blocks(count);
+  k_cg_xr<R><<<dim3(g, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
+                                          (const cplx_t<R>*)q, rz, pq, frozen, count, ws, rr);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -213,7 +250,7 @@ __global__ void k_f32_acc_scaled(const float2* __restrict__ in, double2* __restr
                                  const double* nrm, long long count) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const double sc = sqrt(nrm[2 * blockIdx.y]);
+  const double sc = nrm ? sqrt(nrm[2 * blockIdx.y]) : 1.0;
   i += (long long)blockIdx.y * count;
   float2 v = in[i];
   double2 xv = x[i];
@@ -291,7 +328,8 @@ cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s) {
   template cudaError_t scale_inv_sqrt<R>(const void*, void*, const double*, long long, int,  \
                                          cudaStream_t);                                      \
   template cudaError_t cg_xr<R>(void*, void*, const void*, const void*, const double*,       \
-                                const double*, const int*, long long, int, cudaStream_t);    \
+                                const double*, const int*, long long, int, double*, double*, \
+                                cudaStream_t);                                               \
   template cudaError_t cg_p<R>(void*, const void*, const double*, const double*, const int*, \
                                long long, int, cudaStream_t);                                \
   template cudaError_t sub_from<R>(const void*, void*, long long, cudaStream_t);             \

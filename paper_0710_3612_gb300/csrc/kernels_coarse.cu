@@ -25,43 +25,90 @@ template <> struct wload<__nv_bfloat162> {
   static __device__ __forceinline__ float2 get(const __nv_bfloat162* p) { return bf2_to_f2(*p); }
 };
 
+// One CTA per (coarse site, rhs), 9 n threads: thread (d, r) forms the partial
+// row product A[j][d][r][:] . x(j + d); the 9 partials of a row are summed in
+// a fixed order (deterministic).  The 9 neighbour vectors are staged in shared
+// memory; each thread streams one contiguous block row with vector loads.
+template <typename R> struct row_dot;
+template <> struct row_dot<double> {
+  template <typename WT>
+  static __device__ __forceinline__ double2 run(const WT* row, const double2* x, int n) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < n; ++c) cfma(acc, row[c], x[c]);
+    return acc;
+  }
+};
+template <> struct row_dot<float> {
+  static __device__ __forceinline__ float2 run(const float2* row, const float2* x, int n) {
+    float2 acc = make_float2(0.f, 0.f);
+    const float4* r4 = (const float4*)row;
+    for (int c = 0; c < n / 2; ++c) {
+      const float4 w = r4[c];
+      cfma(acc, make_float2(w.x, w.y), x[2 * c]);
+      cfma(acc, make_float2(w.z, w.w), x[2 * c + 1]);
+    }
+    return acc;
+  }
+  static __device__ __forceinline__ float2 run(const __nv_bfloat162* row, const float2* x, int n) {
+    float2 acc = make_float2(0.f, 0.f);
+    const uint2* r2 = (const uint2*)row;
+    for (int c = 0; c < n / 2; ++c) {
+      const uint2 w = r2[c];
+      cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.x), x[2 * c]);
+      cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.y), x[2 * c + 1]);
+    }
+    return acc;
+  }
+};
+
 template <typename R, typename WT>
-__global__ void __launch_bounds__(256) k_coarse_apply(const cplx_t<R>* __restrict__ in,
+__global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restrict__ in,
                                                       cplx_t<R>* __restrict__ out,
                                                       const WT* __restrict__ A, int Lx, int Lt,
                                                       int n) {
+  extern __shared__ unsigned char smraw[];
+  cplx_t<R>* xs = (cplx_t<R>*)smraw;            // [9][n] neighbour vectors
+  cplx_t<R>* part = xs + 9 * n;                 // [9][n] partial row products
   const int V = Lx * Lt;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)V * n) return;
-  const int j = (int)(idx / n), r = (int)(idx % n);
+  const int j = blockIdx.x;
   const int x = j % Lx, t = j / Lx;
   const cplx_t<R>* vin = in + (long long)blockIdx.y * V * n;
-  cplx_t<R> acc = mk((R)0, (R)0);
-#pragma unroll 1
-  for (int d = 0; d < 9; ++d) {
-    const int dx = d % 3 - 1, dt = d / 3 - 1;
-    int xn = x + dx, tn = t + dt;
+  for (int q = threadIdx.x; q < 9 * n; q += blockDim.x) {
+    const int d = q / n, c = q % n;
+    int xn = x + d % 3 - 1, tn = t + d / 3 - 1;
     xn = xn < 0 ? xn + Lx : (xn >= Lx ? xn - Lx : xn);
     tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
-    const cplx_t<R>* v = vin + (long long)(xn + Lx * tn) * n;
-    const WT* row = A + (((long long)j * 9 + d) * n + r) * n;
-    for (int c = 0; c < n; ++c) cfma(acc, wload<WT>::get(row + c), v[c]);
+    xs[q] = vin[(long long)(xn + Lx * tn) * n + c];
   }
-  out[(long long)blockIdx.y * V * n + idx] = acc;
+  __syncthreads();
+  const int q = threadIdx.x;
+  if (q < 9 * n) {
+    const int d = q / n, r = q % n;
+    const WT* row = A + (((long long)j * 9 + d) * n + r) * n;
+    part[q] = row_dot<R>::run(row, xs + d * n, n);
+  }
+  __syncthreads();
+  if (q < n) {
+    cplx_t<R> acc = part[q];
+#pragma unroll
+    for (int d = 1; d < 9; ++d) acc = cadd(acc, part[d * n + q]);
+    out[((long long)blockIdx.y * V + j) * n + q] = acc;
+  }
 }
 
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
                          int n, int nrhs, cudaStream_t s) {
-  const long long tot = (long long)Lx * Lt * n;
-  dim3 grid((unsigned)((tot + 255) / 256), nrhs);
+  if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
+  dim3 grid(Lx * Lt, nrhs);
+  const int threads = (9 * n + 31) / 32 * 32;
   if (weights == W_F64)
-    k_coarse_apply<double, double2><<<grid, 256, 0, s>>>((const double2*)in, (double2*)out,
-                                                         (const double2*)A, Lx, Lt, n);
+    k_coarse_apply<double, double2><<<grid, threads, 18 * n * sizeof(double2), s>>>(
+        (const double2*)in, (double2*)out, (const double2*)A, Lx, Lt, n);
   else if (weights == W_F32)
-    k_coarse_apply<float, float2><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out,
-                                                       (const float2*)A, Lx, Lt, n);
+    k_coarse_apply<float, float2><<<grid, threads, 18 * n * sizeof(float2), s>>>(
+        (const float2*)in, (float2*)out, (const float2*)A, Lx, Lt, n);
   else
-    k_coarse_apply<float, __nv_bfloat162><<<grid, 256, 0, s>>>(
+    k_coarse_apply<float, __nv_bfloat162><<<grid, threads, 18 * n * sizeof(float2), s>>>(
         (const float2*)in, (float2*)out, (const __nv_bfloat162*)A, Lx, Lt, n);
   count_launch();
   return cudaGetLastError();

@@ -142,7 +142,8 @@ void ensure_tmpA(mg_handle* h, bool f64, size_t bytes) {
 
 void ensure_partials(mg_handle* h, int nrhs) {
   if (h->partial_rhs >= nrhs) return;
-  h->partials = dalloc<double>(h, sizeof(double) * 2 * 608 * (size_t)nrhs);
+  h->partials = dalloc<double>(h, sizeof(double) * (64 + 2 * 608 * (size_t)nrhs));
+  ck(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 64, h->s), "memset tickets");
   h->partial_rhs = nrhs;
 }
 
@@ -207,7 +208,7 @@ void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
 template <typename R>
 void vcycle(mg_handle* h, int l, const void* b, void* x) {
   const bool f64 = sizeof(R) == 8;
-  const int weights = f64 ? W_F64 : W_BF16;
+  const int weights = f64 ? W_F64 : (h->p.vcycle_coarse_bf16 ? W_BF16 : W_F32);
   if (l == h->L - 1) {
     if (f64) {
       coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine);
@@ -438,8 +439,7 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, bool prec
     apply_level<R>(h, 0, p, q, 1, weights);
     h->fine_applies++;
     ck(h, dot<R>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
-    ck(h, cg_xr<R>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->s), "cg_xr");
-    ck(h, norm2<R>(r, n, 1, h->partials, s + S_RR, h->s), "norm");
+    ck(h, cg_xr<R>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
     ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
     ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
     sync(h);
@@ -474,6 +474,75 @@ double true_residual(mg_handle* h, const void* b, const void* x, void* r) {
   const double rr = read_scalar(h, S_NR);
   const double bn = read_scalar(h, S_BN);
   return bn > 0 ? std::sqrt(rr / bn) : 0.0;
+}
+
+// FP32 PCG with FP64 reliable updates (mixed solver).  The FP32 recursion
+// (x32, r32, p, z) runs on the FP32 V-cycle; whenever |r32| has dropped by
+// reliable_delta since the last replacement, or reaches the target, x64 += x32
+// and r32 is replaced by the true FP64 residual b - A x64 (the search
+// direction is kept).  Stops when the true residual reaches tol |b|.
+int pcg_reliable(mg_handle* h, const void* b, void* x64, double tol, int maxiter, mg_status& st,
+                 int& replacements) {
+  Level& F = h->lv[0];
+  const long long n = F.count();
+  void* r64 = h->sv64[0];
+  void *x32 = h->sv32[0], *r = h->sv32[1], *p = h->sv32[2], *q = h->sv32[3], *z = h->sv32[4];
+  double* s = h->scal;
+  st = MG_OK;
+  replacements = 0;
+  ck(h, cudaMemsetAsync(x64, 0, n * sizeof(double2), h->s), "memset");
+  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
+  const double bn = read_scalar(h, S_BN);
+  if (bn == 0.0) return 0;
+  const double target = tol * tol * bn;
+  const double delta2 = h->p.reliable_delta * h->p.reliable_delta;
+  ck(h, convert_f64_f32(b, r, n, h->s), "to f32");
+  ck(h, cudaMemsetAsync(x32, 0, n * sizeof(float2), h->s), "memset");
+  vcycle<float>(h, 0, r, z);
+  h->vcycles++;
+  ck(h, cudaMemcpyAsync(p, z, n * sizeof(float2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, dot<float>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
+  double rmax2 = bn;        // |r|^2 at the last replacement
+  int it = 0;
+  while (it < maxiter) {
+    apply_level<float>(h, 0, p, q, 1, W_F32);
+    h->fine_applies++;
+    ck(h, dot<float>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
+    ck(h, cg_xr<float>(x32, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
+    ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    ++it;
+    const double pq = h->hscal[0], rr = h->hscal[2];
+    if (!(pq > 0.0) || !(rr == rr)) {
+      st = MG_ERR_BREAKDOWN;
+      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
+      return it;
+    }
+    if (rr <= delta2 * rmax2 || rr <= target) {
+      // reliable update: x64 += x32; r = b - A x64 in FP64
+      ck(h, f32_accumulate_scaled(x32, x64, nullptr, n, 1, h->s), "accumulate");
+      ck(h, cudaMemsetAsync(x32, 0, n * sizeof(float2), h->s), "memset");
+      apply_level<double>(h, 0, x64, r64, 1, W_F64);
+      h->fine_applies++;
+      ck(h, sub_from<double>(b, r64, n, h->s), "residual");
+      ck(h, norm2<double>(r64, n, 1, h->partials, s + S_NR, h->s), "norm");
+      const double tr = read_scalar(h, S_NR);
+      replacements++;
+      if (!(tr == tr)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite residual"; return it; }
+      if (tr <= target) return it;
+      ck(h, convert_f64_f32(r64, r, n, h->s), "to f32");
+      rmax2 = tr;
+    }
+    vcycle<float>(h, 0, r, z);
+    h->vcycles++;
+    ck(h, dot<float>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
+    ck(h, cg_p<float>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+  }
+  st = MG_ERR_NOCONV;
+  h->err = "maximum iterations reached";
+  return it;
 }
 
 mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxiter, int solver,
@@ -511,34 +580,7 @@ mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxite
       refinements++;
     }
   } else if (solver == MG_SOLVER_MGCG_MIXED) {
-    ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
-    void* r64 = h->sv64[0];
-    void* r32 = h->sv32[0];
-    void* e32 = h->sv32[5];
-    double* s = h->scal;
-    ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
-    const double bn = read_scalar(h, S_BN);
-    if (bn == 0.0) {
-      st = MG_OK;
-    } else {
-      ck(h, cudaMemcpyAsync(r64, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-      for (;;) {
-        ck(h, norm2<double>(r64, n, 1, h->partials, s + S_NR, h->s), "norm");
-        const double rr = read_scalar(h, S_NR);
-        if (!(rr == rr)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite residual"; break; }
-        if (rr <= tol * tol * bn) { st = MG_OK; break; }
-        if (iters >= maxiter) { st = MG_ERR_NOCONV; h->err = "maximum iterations reached"; break; }
-        ck(h, f64_to_f32_scaled(r64, r32, s + S_NR, n, 1, h->s), "to f32");
-        mg_status ist;
-        iters += pcg<float>(h, r32, e32, h->p.inner_tol, maxiter - iters, true, ist);
-        if (ist == MG_ERR_BREAKDOWN) { st = ist; break; }
-        ck(h, f32_accumulate_scaled(e32, x, s + S_NR, n, 1, h->s), "accumulate");
-        refinements++;
-        apply_level<double>(h, 0, x, r64, 1, W_F64);
-        h->fine_applies++;
-        ck(h, sub_from<double>(b, r64, n, h->s), "residual");
-      }
-    }
+    iters = pcg_reliable(h, b, x, tol, maxiter, st, refinements);
   } else {
     fail(h, MG_ERR_ARG, "unknown solver");
   }
@@ -574,6 +616,8 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->coarsest_refine_max = 12;
   p->inner_tol = 1e-5;
   p->inner_coarsest_refine = 2;
+  p->vcycle_coarse_bf16 = 0;
+  p->reliable_delta = 0.1;
   return MG_OK;
 }
 
