@@ -67,12 +67,11 @@ typedef enum { MG_PREC_F64 = 0, MG_PREC_F32 = 1, MG_PREC_BF16 = 2 } mg_precision
 
 typedef enum {
   MG_SOLVER_MGCG_FP64 = 0,  /* MG-CG, everything in FP64 (Sec. 4)                */
-  MG_SOLVER_MGCG_MIXED = 1, /* FP32 MG-CG with FP64 reliable updates: the true
-                               residual b - A x and the solution are kept in
-                               FP64 and replace the FP32 recursion whenever its
-                               residual drops by reliable_delta; V-cycle in
-                               FP32 (coarse blocks FP32 or BF16 with FP32
-                               accumulation), coarsest solve in FP64 */
+  MG_SOLVER_MGCG_MIXED = 1, /* FP64 flexible CG (Krylov recursion, residual and
+                               solution in FP64) preconditioned by the FP32
+                               V-cycle: FP32 smoother, restriction, prolongation
+                               and coarse applies (coarse blocks FP32, or BF16
+                               with FP32 accumulation), coarsest solve in FP64 */
   MG_SOLVER_CG_FP64 = 2     /* plain CG on A, FP64 (the paper's baseline)        */
 } mg_solver;
 
@@ -90,20 +89,16 @@ typedef struct {
   double coarsest_tol;                  /* FP64 refinement target of the coarsest
                                            solve, relative (1e-13)               */
   int coarsest_refine_max;              /* cap on refinement steps (12)          */
-  double inner_tol;                     /* mixed solver: inner FP32 MG-CG
-                                           relative tolerance (1e-5)             */
   int inner_coarsest_refine;            /* mixed solver: FP64 refinement steps of
                                            the coarsest solve inside the FP32
                                            V-cycle (2)                           */
   int vcycle_coarse_bf16;               /* mixed solver: 1 = coarse blocks of the
                                            FP32 V-cycle in BF16, 0 = FP32 (0)    */
-  double reliable_delta;                /* mixed solver: FP64 residual replacement
-                                           when |r| drops by this factor (0.1)   */
 } mg_params;
 
 typedef struct {
   int iterations;             /* Krylov iterations (inner iterations summed)   */
-  int refinements;            /* FP64 residual replacements (reliable updates) */
+  int refinements;            /* restarts from the true FP64 residual          */
   double true_residual;       /* |b - A x| / |b| recomputed in FP64            */
   long long fine_applies;     /* applications of the fine A = D^dagger D        */
   long long vcycles;          /* V-cycles applied                               */

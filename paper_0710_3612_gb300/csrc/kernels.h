@@ -49,6 +49,14 @@ cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* 
 template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
                  const int* frozen, long long count, int nrhs, cudaStream_t s);
+// Graph-resident CG loop control: ctrl = {iterations, status, limit};
+// status 0 running, 1 converged (rr <= stop), 2 breakdown, 3 limit reached.
+cudaError_t cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
+                       cudaGraphConditionalHandle cond, cudaStream_t s);
+cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, cudaStream_t s);
+// Flexible CG (FP64, one RHS): beta = -Re(zq) / Re(pq); p = z + beta p.
+cudaError_t cg_p_pr(void* p, const void* z, const double* zq, const double* pq, long long count,
+                    cudaStream_t s);
 // out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s);

@@ -228,6 +228,62 @@ cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_
   return cudaGetLastError();
 }
 
+// Device-side loop control of the graph-resident CG: counts the iteration,
+// classifies it (0 running, 1 converged, 2 breakdown, 3 iteration limit) and
+// sets the WHILE condition of the enclosing graph node.
+__global__ void k_cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
+                             cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = ctrl[0] + 1;
+  ctrl[0] = it;
+  const double r = rr[0], d = pq[0];
+  int status = 0;
+  if (!(d > 0.0) || !(r == r)) status = 2;
+  else if (r <= stop[0]) status = 1;
+  else if (it >= ctrl[2]) status = 3;
+  ctrl[1] = status;
+  cudaGraphSetConditional(cond, status == 0 ? 1u : 0u);
+}
+
+cudaError_t cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
+                       cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_cg_control<<<1, 32, 0, s>>>(rr, pq, stop, ctrl, cond);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_set_control(int* ctrl, int maxiter, double* stop_slot, double stop) {
+  if (threadIdx.x != 0) return;
+  ctrl[0] = 0;
+  ctrl[1] = 0;
+  ctrl[2] = maxiter;
+  stop_slot[0] = stop;
+}
+
+cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, cudaStream_t s) {
+  k_set_control<<<1, 32, 0, s>>>(ctrl, maxiter, stop_slot, stop);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Flexible-CG direction update: beta = -Re(zq) / Re(pq); p = z + beta p.
+__global__ void k_cg_p_pr(double2* __restrict__ p, const double2* __restrict__ z, const double* zq,
+                          const double* pq, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double d = pq[0];
+  const double beta = d != 0.0 ? -zq[0] / d : 0.0;
+  const double2 pv = p[i], zv = z[i];
+  p[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+}
+
+cudaError_t cg_p_pr(void* p, const void* z, const double* zq, const double* pq, long long count,
+                    cudaStream_t s) {
+  k_cg_p_pr<<<grid1(count, 1), RT, 0, s>>>((double2*)p, (const double2*)z, zq, pq, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_f64_to_f32_scaled(const double2* __restrict__ in, float2* __restrict__ out,
                                     const double* nrm, long long count) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -55,11 +56,13 @@ struct mg_handle {
   float2* gemv_x = nullptr;
   int n_refine = 0;
   double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
-  // fine-level scratch for A = D^dagger D (two-pass), per precision, grown on demand
-  void* tmpA64 = nullptr;
-  size_t tmpA64_bytes = 0;
-  void* tmpA32 = nullptr;
-  size_t tmpA32_bytes = 0;
+  // CUDA graphs of the Krylov loop (one per preconditioner mode), launched on
+  // the internal stream gs and fenced to the user's stream with events
+  cudaStream_t gs = nullptr;
+  cudaEvent_t fence[2] = {nullptr, nullptr};
+  cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
+  int* dctrl = nullptr;         // [0] iterations, [1] status, [2] iteration limit
+  bool use_graphs = true;
   // solver vectors (one RHS), FP64 and FP32: x r p q z t
   void* sv64[6] = {};
   void* sv32[6] = {};
@@ -87,7 +90,7 @@ constexpr long long MG_DENSE_MAX = 16384;
 
 // scalar slots (each a double2)
 enum { S_RZ = 0, S_RZN = 2, S_PQ = 4, S_RR = 6, S_T0 = 8, S_T1 = 10, S_BN = 12, S_NR = 14,
-       S_MAX = 64 };
+       S_STOP = 16, S_MAX = 64 };
 
 struct Fail {
   mg_status st;
@@ -124,20 +127,6 @@ double read_scalar(mg_handle* h, int slot) {
      "scalar readback");
   sync(h);
   return h->hscal[0];
-}
-
-void ensure_tmpA(mg_handle* h, bool f64, size_t bytes) {
-  void*& p = f64 ? h->tmpA64 : h->tmpA32;
-  size_t& have = f64 ? h->tmpA64_bytes : h->tmpA32_bytes;
-  if (have >= bytes) return;
-  if (p) {
-    ck(h, cudaStreamSynchronize(h->s), "synchronize before regrow");
-    for (auto& a : h->allocs)
-      if (a == p) a = nullptr;
-    cudaFree(p);
-  }
-  p = dalloc(h, bytes);
-  have = bytes;
 }
 
 void ensure_partials(mg_handle* h, int nrhs) {
@@ -178,11 +167,8 @@ void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int w
   ProfScope prof(h, l == 0 ? (sizeof(R) == 8 ? MG_KF_FINE_A64 : MG_KF_FINE_A) : MG_KF_COARSE);
   if (l == 0) {
     const double diag = 4.0 + h->mass;
-    const size_t bytes = (size_t)L.count() * nrhs * sizeof(R) * 2;
-    ensure_tmpA(h, sizeof(R) == 8, bytes);
-    void* tmp = sizeof(R) == 8 ? h->tmpA64 : h->tmpA32;
     const void* U = sizeof(R) == 8 ? (const void*)h->U64 : (const void*)h->U32;
-    ck(h, wilson_A<R>(in, out, U, diag, L.Lx, L.Lt, nrhs, tmp, h->s), "wilson_A");
+    ck(h, wilson_A<R>(in, out, U, diag, L.Lx, L.Lt, nrhs, nullptr, h->s), "wilson_A");
   } else {
     const void* A = weights == W_F64 ? (const void*)L.A64
                     : weights == W_F32 ? (const void*)L.A32 : L.A16;
@@ -226,7 +212,6 @@ void vcycle(mg_handle* h, int l, const void* b, void* x) {
   void* r = w[2];
   void* t = w[3];
   const long long n = L.count();
-  if (l == 0) h->fine_applies += 4;
   // 1. x = R b = c0 b + c1 A b
   apply_level<R>(h, l, b, t, 1, weights);
   ck(h, lincomb<R>(x, L.c0, b, L.c1, t, 0.0, nullptr, n, 1, h->s), "smooth");
@@ -339,7 +324,16 @@ void build_coarsest(mg_handle* h) {
   h->n_refine = std::min(steps + 1, h->p.coarsest_refine_max);
 }
 
+void drop_graphs(mg_handle* h) {
+  for (auto& e : h->loop_exec)
+    if (e) {
+      cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
+}
+
 void set_mass_internal(mg_handle* h, double mass) {
+  drop_graphs(h);
   h->mass = mass;
   build_coarse_ops(h);
   for (int l = 0; l + 1 < h->L; ++l)
@@ -393,6 +387,12 @@ mg_status guarded(mg_handle* h, F&& f) {
 void free_all(mg_handle* h) {
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
+  if (h->gs) cudaStreamSynchronize(h->gs);
+  drop_graphs(h);
+  for (auto& e : h->fence)
+    if (e) cudaEventDestroy(e);
+  if (h->gs) cudaStreamDestroy(h->gs);
+  h->gs = nullptr;
   for (auto& v : h->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
   for (void* p : h->allocs)
@@ -403,43 +403,157 @@ void free_all(mg_handle* h) {
 }
 
 // ----- Krylov solvers ---------------------------------------------------------
-// PCG on A x = b (precision R), x0 = 0, stopping when |r| <= tol |b| (recursive
-// residual); precond: 0 none, 1 V-cycle.  Returns iterations.  Vectors from
-// the handle's solver set of precision R; x receives the solution.
-template <typename R>
-int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, bool precond,
+// PCG on A x = b in FP64, x0 = 0, stopping when the recursive residual
+// |r| <= tol |b|.  pmode 0: no preconditioner (plain CG); 1: FP64 V-cycle,
+// standard PCG (beta = <r+, z+>/<r, z>); 2: FP32 V-cycle (FP32 vectors, FP32
+// or BF16 coarse blocks, FP64 coarsest solve) on the FP64 residual, flexible
+// CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with r+ = r - alpha A p),
+// so that rounding in the low-precision preconditioner does not break the
+// recursion.  Returns iterations; x receives the solution.
+void precondition(mg_handle* h, int pmode) {
+  const long long n = h->lv[0].count();
+  void *r = h->sv64[1], *z = h->sv64[4];
+  if (pmode == 1) {
+    vcycle<double>(h, 0, r, z);
+  } else if (pmode == 2) {
+    ck(h, convert_f64_f32(r, h->sv32[1], n, h->s), "to f32");
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
+    ck(h, convert_f32_f64(h->sv32[4], z, n, h->s), "to f64");
+  } else {
+    ck(h, cudaMemcpyAsync(z, r, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  }
+}
+
+// One CG iteration after q = A p: update x, r; precondition; new direction.
+void pcg_update(mg_handle* h, void* x, int pmode) {
+  (void)pmode;
+  const long long n = h->lv[0].count();
+  void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3];
+  double* s = h->scal;
+  ck(h, dot<double>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
+  ck(h, cg_xr<double>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
+}
+
+void pcg_direction(mg_handle* h, int pmode) {
+  const long long n = h->lv[0].count();
+  void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
+  double* s = h->scal;
+  precondition(h, pmode);
+  if (pmode == 2) {
+    // beta = -Re<z+, q> / <p, q>;  rz = <r+, z+> for the next alpha
+    ck(h, dot<double>(z, q, n, 1, h->partials, s + S_T0, h->s), "dot");
+    ck(h, cg_p_pr(p, z, s + S_T0, s + S_PQ, n, h->s), "cg_p");
+    ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
+  } else {
+    ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
+    ck(h, cg_p<double>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+  }
+}
+
+// Captures the CG loop body into the body of a conditional WHILE node: the
+// control kernel at the end of each iteration decides on the device whether
+// to run another iteration, so the whole loop is one graph launch.
+cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
+  cudaGraph_t g = nullptr;
+  ck(h, cudaGraphCreate(&g, 0), "graph create");
+  cudaGraphConditionalHandle cond;
+  ck(h, cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  ck(h, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np), "conditional node");
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t saved = h->s;
+  const long long fa = h->fine_applies, vc = h->vcycles;
+  h->s = h->gs;
+  ck(h, cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    apply_level<double>(h, 0, h->sv64[2], h->sv64[3], 1, W_F64);
+    pcg_update(h, x, pmode);
+    pcg_direction(h, pmode);
+    ck(h, cg_control(h->scal + S_RR, h->scal + S_PQ, h->scal + S_STOP, h->dctrl, cond, h->s), "control");
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(h->gs, &dummy);
+    h->s = saved;
+    cudaGraphDestroy(g);
+    throw;
+  }
+  h->s = saved;
+  h->fine_applies = fa;
+  h->vcycles = vc;
+  ck(h, cudaStreamEndCapture(h->gs, &body), "end capture");
+  cudaGraphExec_t exec = nullptr;
+  ck(h, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
+  cudaGraphDestroy(g);
+  return exec;
+}
+
+
+// PCG on A x = b in FP64, x0 = 0, stopping when the recursive residual
+// |r| <= tol |b|.  pmode 0: no preconditioner (plain CG); 1: FP64 V-cycle,
+// standard PCG (beta = <r+, z+>/<r, z>); 2: FP32 V-cycle (FP32 vectors, FP32
+// or BF16 coarse blocks, FP64 coarsest solve) on the FP64 residual, flexible
+// CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with r+ = r - alpha A p),
+// so that rounding in the low-precision preconditioner does not break the
+// recursion.  The iteration loop runs as one CUDA graph with a device-side
+// WHILE condition (or eagerly, with a host check per iteration, while
+// per-kernel profiling is on).  Returns iterations; x receives the solution
+// and must be the handle's solver vector sv64[5].
+int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode,
         mg_status& st) {
   Level& F = h->lv[0];
   const long long n = F.count();
-  void** v = sizeof(R) == 8 ? h->sv64 : h->sv32;
-  void *r = v[1], *p = v[2], *q = v[3], *z = v[4];
-  const int weights = sizeof(R) == 8 ? W_F64 : W_BF16;
+  void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
   double* s = h->scal;
   st = MG_OK;
-  ck(h, norm2<R>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
+  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
   const double bn = read_scalar(h, S_BN);
-  ck(h, cudaMemsetAsync(x, 0, n * sizeof(R) * 2, h->s), "memset");
+  ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
   if (bn == 0.0) return 0;
   if (!(bn == bn) || std::isinf(bn)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite right-hand side"; return 0; }
-  ck(h, cudaMemcpyAsync(r, b, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
-  auto precondition = [&]() {
-    if (precond) {
-      vcycle<R>(h, 0, r, z);
-      h->vcycles++;
-    } else {
-      ck(h, cudaMemcpyAsync(z, r, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
-    }
-  };
-  precondition();
-  ck(h, cudaMemcpyAsync(p, z, n * sizeof(R) * 2, cudaMemcpyDeviceToDevice, h->s), "copy");
-  ck(h, dot<R>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
-  int it = 0;
+  ck(h, cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  precondition(h, pmode);
+  if (pmode) h->vcycles++;
+  ck(h, cudaMemcpyAsync(p, z, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
   const double stop = tol * tol * bn;
+  const int per_it_fine = 1 + (pmode ? 4 : 0);
+  if (h->use_graphs && !h->prof_on) {
+    if (!h->loop_exec[pmode]) h->loop_exec[pmode] = build_loop_graph(h, x, pmode);
+    ck(h, set_control(h->dctrl, maxiter, s + S_STOP, stop, h->s), "control init");
+    ck(h, cudaEventRecord(h->fence[0], h->s), "event");
+    ck(h, cudaStreamWaitEvent(h->gs, h->fence[0], 0), "wait");
+    ck(h, cudaGraphLaunch(h->loop_exec[pmode], h->gs), "graph launch");
+    ck(h, cudaEventRecord(h->fence[1], h->gs), "event");
+    ck(h, cudaStreamWaitEvent(h->s, h->fence[1], 0), "wait");
+    ck(h, cudaMemcpyAsync(h->hscal, h->dctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    int ctrl[2];
+    std::memcpy(ctrl, h->hscal, sizeof(ctrl));
+    const int it = ctrl[0];
+    h->fine_applies += (long long)it * per_it_fine;
+    if (pmode) h->vcycles += it;
+    if (ctrl[1] == 2) {
+      st = MG_ERR_BREAKDOWN;
+      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
+    } else if (ctrl[1] == 3) {
+      st = MG_ERR_NOCONV;
+      h->err = "maximum iterations reached";
+    }
+    return it;
+  }
+  int it = 0;
   while (it < maxiter) {
-    apply_level<R>(h, 0, p, q, 1, weights);
+    apply_level<double>(h, 0, p, q, 1, W_F64);
     h->fine_applies++;
-    ck(h, dot<R>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
-    ck(h, cg_xr<R>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
+    pcg_update(h, x, pmode);
     ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
     ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
     sync(h);
@@ -451,10 +565,11 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, bool prec
       return it;
     }
     if (rr <= stop) return it;
-    precondition();
-    ck(h, dot<R>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
-    ck(h, cg_p<R>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
-    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+    pcg_direction(h, pmode);
+    if (pmode) {
+      h->vcycles++;
+      h->fine_applies += 4;
+    }
   }
   st = MG_ERR_NOCONV;
   h->err = "maximum iterations reached";
@@ -476,75 +591,6 @@ double true_residual(mg_handle* h, const void* b, const void* x, void* r) {
   return bn > 0 ? std::sqrt(rr / bn) : 0.0;
 }
 
-// FP32 PCG with FP64 reliable updates (mixed solver).  The FP32 recursion
-// (x32, r32, p, z) runs on the FP32 V-cycle; whenever |r32| has dropped by
-// reliable_delta since the last replacement, or reaches the target, x64 += x32
-// and r32 is replaced by the true FP64 residual b - A x64 (the search
-// direction is kept).  Stops when the true residual reaches tol |b|.
-int pcg_reliable(mg_handle* h, const void* b, void* x64, double tol, int maxiter, mg_status& st,
-                 int& replacements) {
-  Level& F = h->lv[0];
-  const long long n = F.count();
-  void* r64 = h->sv64[0];
-  void *x32 = h->sv32[0], *r = h->sv32[1], *p = h->sv32[2], *q = h->sv32[3], *z = h->sv32[4];
-  double* s = h->scal;
-  st = MG_OK;
-  replacements = 0;
-  ck(h, cudaMemsetAsync(x64, 0, n * sizeof(double2), h->s), "memset");
-  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
-  const double bn = read_scalar(h, S_BN);
-  if (bn == 0.0) return 0;
-  const double target = tol * tol * bn;
-  const double delta2 = h->p.reliable_delta * h->p.reliable_delta;
-  ck(h, convert_f64_f32(b, r, n, h->s), "to f32");
-  ck(h, cudaMemsetAsync(x32, 0, n * sizeof(float2), h->s), "memset");
-  vcycle<float>(h, 0, r, z);
-  h->vcycles++;
-  ck(h, cudaMemcpyAsync(p, z, n * sizeof(float2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  ck(h, dot<float>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
-  double rmax2 = bn;        // |r|^2 at the last replacement
-  int it = 0;
-  while (it < maxiter) {
-    apply_level<float>(h, 0, p, q, 1, W_F32);
-    h->fine_applies++;
-    ck(h, dot<float>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
-    ck(h, cg_xr<float>(x32, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
-    ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
-    ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
-    sync(h);
-    ++it;
-    const double pq = h->hscal[0], rr = h->hscal[2];
-    if (!(pq > 0.0) || !(rr == rr)) {
-      st = MG_ERR_BREAKDOWN;
-      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
-      return it;
-    }
-    if (rr <= delta2 * rmax2 || rr <= target) {
-      // reliable update: x64 += x32; r = b - A x64 in FP64
-      ck(h, f32_accumulate_scaled(x32, x64, nullptr, n, 1, h->s), "accumulate");
-      ck(h, cudaMemsetAsync(x32, 0, n * sizeof(float2), h->s), "memset");
-      apply_level<double>(h, 0, x64, r64, 1, W_F64);
-      h->fine_applies++;
-      ck(h, sub_from<double>(b, r64, n, h->s), "residual");
-      ck(h, norm2<double>(r64, n, 1, h->partials, s + S_NR, h->s), "norm");
-      const double tr = read_scalar(h, S_NR);
-      replacements++;
-      if (!(tr == tr)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite residual"; return it; }
-      if (tr <= target) return it;
-      ck(h, convert_f64_f32(r64, r, n, h->s), "to f32");
-      rmax2 = tr;
-    }
-    vcycle<float>(h, 0, r, z);
-    h->vcycles++;
-    ck(h, dot<float>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
-    ck(h, cg_p<float>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
-    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
-  }
-  st = MG_ERR_NOCONV;
-  h->err = "maximum iterations reached";
-  return it;
-}
-
 mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxiter, int solver,
                     mg_solve_info* info) {
   mg_status st = MG_OK;
@@ -557,10 +603,11 @@ mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxite
     const double b2 = read_scalar(h, S_T0);
     if (!(b2 == b2) || std::isinf(b2)) fail(h, MG_ERR_BREAKDOWN, "non-finite right-hand side");
   }
-  if (solver == MG_SOLVER_MGCG_FP64 || solver == MG_SOLVER_CG_FP64) {
+  if (solver == MG_SOLVER_MGCG_FP64 || solver == MG_SOLVER_CG_FP64 ||
+      solver == MG_SOLVER_MGCG_MIXED) {
     // PCG on the true residual; when the recursive residual has drifted from
     // the true one, restart from rt = b - A x with the remaining target.
-    const bool pre = solver == MG_SOLVER_MGCG_FP64;
+    const int pre = solver == MG_SOLVER_MGCG_FP64 ? 1 : solver == MG_SOLVER_MGCG_MIXED ? 2 : 0;
     ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
     void* xc = h->sv64[5];
     void* rt = h->sv64[0];
@@ -570,7 +617,7 @@ mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxite
     double rnrm = bnrm;
     for (int cycle = 0; cycle < 8 && bnrm > 0.0; ++cycle) {
       const double rel = cycle == 0 ? tol : std::min(0.5, 0.5 * tol * bnrm / rnrm);
-      iters += pcg<double>(h, rt, xc, rel, maxiter - iters, pre, st);
+      iters += pcg(h, rt, xc, rel, maxiter - iters, pre, st);
       ck(h, lincomb<double>(x, 1.0, x, 1.0, xc, 0.0, nullptr, n, 1, h->s), "accumulate");
       if (st != MG_OK && st != MG_ERR_NOCONV) break;
       const double res = true_residual(h, b, x, rt);
@@ -579,8 +626,6 @@ mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxite
       rnrm = res * bnrm;
       refinements++;
     }
-  } else if (solver == MG_SOLVER_MGCG_MIXED) {
-    iters = pcg_reliable(h, b, x, tol, maxiter, st, refinements);
   } else {
     fail(h, MG_ERR_ARG, "unknown solver");
   }
@@ -614,10 +659,8 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->omega_mr = 0.8;
   p->coarsest_tol = 1e-13;
   p->coarsest_refine_max = 12;
-  p->inner_tol = 1e-5;
   p->inner_coarsest_refine = 2;
   p->vcycle_coarse_bf16 = 0;
-  p->reliable_delta = 0.1;
   return MG_OK;
 }
 
@@ -663,6 +706,11 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
     ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
     h->scal = dalloc<double>(h, S_MAX * sizeof(double));
     h->dflag = dalloc<int>(h, sizeof(int));
+    h->dctrl = dalloc<int>(h, 4 * sizeof(int));
+    ck(h, cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream create");
+    ck(h, cudaEventCreateWithFlags(&h->fence[0], cudaEventDisableTiming), "event create");
+    ck(h, cudaEventCreateWithFlags(&h->fence[1], cudaEventDisableTiming), "event create");
+    if (const char* e = std::getenv("MG_NO_GRAPHS")) h->use_graphs = e[0] == '0';
     int max_nv = 1;
     for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
     ensure_partials(h, max_nv);

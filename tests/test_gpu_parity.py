@@ -275,6 +275,34 @@ def test_zero_rhs_and_repeatability(case, mg):
     assert np.array_equal(x1, host(x2))     # fixed reduction order: identical bits
 
 
+@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "cg_fp64"])
+def test_graph_loop_matches_eager_loop(case, mg, solver):
+    """The Krylov loop runs as one CUDA graph with a device-side WHILE condition;
+    with per-kernel profiling on it runs eagerly.  Both give identical bits."""
+    code = {"mgcg_fp64": mg.SOLVER_MGCG_FP64, "mixed": mg.SOLVER_MGCG_MIXED,
+            "cg_fp64": mg.SOLVER_CG_FP64}[solver]
+    chi = W.gaussian_field((case.Lt, case.Lx, 2), 81)
+    b = dev(ow.apply_D(case.U, case.m, chi, dagger=True))
+    xg, ig = case.solver.solve(b, tol=1e-10, maxiter=20000, solver=code)
+    xg = host(xg)
+    mg.mg_profile_enable(case.h, True)
+    try:
+        xe, ie = case.solver.solve(b, tol=1e-10, maxiter=20000, solver=code)
+        xe = host(xe)
+    finally:
+        mg.mg_profile_enable(case.h, False)
+    assert ig[0].iterations == ie[0].iterations
+    assert np.array_equal(xg, xe)
+
+
+def test_iteration_limit_reports_noconv(case, mg):
+    chi = W.gaussian_field((case.Lt, case.Lx, 2), 91)
+    b = dev(ow.apply_D(case.U, case.m, chi, dagger=True))
+    x = torch.empty_like(b)
+    st, infos = mg.mg_solve(case.h, b, x, 1, 1e-14, 3, mg.SOLVER_MGCG_FP64)
+    assert st == 4 and infos[0].iterations == 3
+
+
 def test_set_mass_rebuilds_galerkin(mg):
     c = Case(mg, "2lvl_24x16")
     try:
