@@ -12,6 +12,8 @@ namespace mgk {
 // Kernel launches made by this library so far (counted at every launch site).
 unsigned long long launch_count();
 void count_launch();
+// Adjusts the count (kernels recorded into a graph run later, once per replay).
+void add_launches(long long n);
 
 // ---- deterministic reductions -------------------------------------------
 // Number of partial sums a reduction over `count` complex entries produces.

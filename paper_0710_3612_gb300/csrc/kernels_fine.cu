@@ -64,83 +64,132 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
   return cudaGetLastError();
 }
 
-// Fused A = D^dagger D.  A CTA owns a TX x TT tile of output sites; it stages
-// psi on the tile plus a 2-site halo and the links on the tile plus a 2-site
-// halo below / 1-site halo above in shared memory, forms D psi on the tile plus
-// a 1-site halo, and applies D^dagger to it -- one pass over psi and the links.
+// Fused A = D^dagger D.  A CTA of TX x TY threads owns a TX x (TY * RPT) tile
+// of output sites (each thread RPT sites of one column).  It stages psi on the
+// tile plus a 2-site halo and the links on the tile plus a 2-site halo below /
+// 1-site halo above in shared memory, forms D psi on the tile plus a 1-site
+// halo, and applies D^dagger to it -- one pass over psi and the links.
 // Coordinates wrap periodically (the antiperiodic sign sits in the links), so
 // lattices that are not multiples of the tile work unchanged.
-static constexpr int TX = 32, TT = 8;
-static constexpr int PW = TX + 4, PH = TT + 4;     // psi region [-2, TX+1] x [-2, TT+1]
-static constexpr int DW = TX + 2, DH = TT + 2;     // D psi region [-1, TX] x [-1, TT]
-static constexpr int UW = TX + 3, UH = TT + 3;     // link region [-2, TX] x [-2, TT]
+// Tile geometry per precision: FP32 32 x 16 (two rows per thread), FP64
+// 32 x 8 (shared memory stays below 48 KB).
+template <typename R> struct tile;
+template <> struct tile<float> { static constexpr int RPT = 2; };
+template <> struct tile<double> { static constexpr int RPT = 1; };
+static constexpr int TX = 32, TY = 8;
+
+template <typename R> struct spinor_t;              // both spin components of a site
+template <> struct spinor_t<float> { using type = float4; };
+template <> struct spinor_t<double> { using type = double4_32a; };
+
+__device__ __forceinline__ void split(const float4& v, float2& a, float2& b) {
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void split(const double4_32a& v, double2& a, double2& b) {
+  a = make_double2(v.x, v.y);
+  b = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ float4 join(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ double4_32a join(double2 a, double2 b) {
+  double4_32a r;
+  r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+  return r;
+}
+__device__ __forceinline__ float4 ld_spinor(const float2* p) { return *(const float4*)p; }
+__device__ __forceinline__ double4_32a ld_spinor(const double2* p) {
+  const double2 a = p[0], b = p[1];
+  return join(a, b);
+}
+__device__ __forceinline__ void st_spinor(float2* p, float4 v) { *(float4*)p = v; }
+__device__ __forceinline__ void st_spinor(double2* p, double4_32a v) {
+  p[0] = make_double2(v.x, v.y);
+  p[1] = make_double2(v.z, v.w);
+}
+
+__device__ __forceinline__ int wrap(int g, int L) { return g < 0 ? g + L : (g >= L ? g - L : g); }
 
 template <typename R>
-__global__ void __launch_bounds__(TX* TT) k_wilson_A(const cplx_t<R>* __restrict__ in,
+__global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict__ in,
                                                      cplx_t<R>* __restrict__ out,
                                                      const cplx_t<R>* __restrict__ U, R diag,
                                                      int Lx, int Lt) {
+  constexpr int RPT = tile<R>::RPT, TT = TY * RPT;
+  constexpr int PW = TX + 4, PH = TT + 4;     // psi region [-2, TX+1] x [-2, TT+1]
+  constexpr int DW = TX + 2, DH = TT + 2;     // D psi region [-1, TX] x [-1, TT]
+  constexpr int UW = TX + 3, UH = TT + 3;     // link region [-2, TX] x [-2, TT]
   using C = cplx_t<R>;
-  __shared__ C sp[PH * PW][2];
-  __shared__ C sd[DH * DW][2];
+  using S = typename spinor_t<R>::type;
+  __shared__ S sp[PH * PW];
+  __shared__ S sd[DH * DW];
   __shared__ C su[UH * UW][2];
   const int V = Lx * Lt;
   const int x0 = blockIdx.x * TX, t0 = blockIdx.y * TT;
   const long long off = (long long)blockIdx.z * V * 2;
   const int tid = threadIdx.x;
-  for (int q = tid; q < PH * PW; q += TX * TT) {
-    const int lx = q % PW - 2, lt = q / PW - 2;
-    const int gx = (x0 + lx + Lx) % Lx, gt = (t0 + lt + Lt) % Lt;
-    const long long g = off + 2LL * (gx + Lx * gt);
-    sp[q][0] = in[g];
-    sp[q][1] = in[g + 1];
+  for (int q = tid; q < PH * PW; q += TX * TY) {
+    const int gx = wrap(x0 + q % PW - 2, Lx), gt = wrap(t0 + q / PW - 2, Lt);
+    sp[q] = ld_spinor(in + off + 2LL * (gx + Lx * gt));
   }
-  for (int q = tid; q < UH * UW; q += TX * TT) {
-    const int lx = q % UW - 2, lt = q / UW - 2;
-    const int gx = (x0 + lx + Lx) % Lx, gt = (t0 + lt + Lt) % Lt;
+  for (int q = tid; q < UH * UW; q += TX * TY) {
+    const int gx = wrap(x0 + q % UW - 2, Lx), gt = wrap(t0 + q / UW - 2, Lt);
     const int g = gx + Lx * gt;
     su[q][0] = U[g];
     su[q][1] = U[V + g];
   }
   __syncthreads();
   // D psi on [-1, TX] x [-1, TT]
-  for (int q = tid; q < DH * DW; q += TX * TT) {
+  for (int q = tid; q < DH * DW; q += TX * TY) {
     const int lx = q % DW - 1, lt = q / DW - 1;
     const int pc = (lt + 2) * PW + (lx + 2);
     const int uc = (lt + 2) * UW + (lx + 2);
-    C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0);
-    hop_x<R>(a0, a1, su[uc][0], sp[pc + 1][0], sp[pc + 1][1], (R)1);
-    hop_x<R>(a0, a1, cconj(su[uc - 1][0]), sp[pc - 1][0], sp[pc - 1][1], (R)-1);
-    hop_t<R>(a0, a1, su[uc][1], sp[pc + PW][0], sp[pc + PW][1], (R)1);
-    hop_t<R>(a0, a1, cconj(su[uc - UW][1]), sp[pc - PW][0], sp[pc - PW][1], (R)-1);
-    const C p0 = sp[pc][0], p1 = sp[pc][1];
-    sd[q][0] = mk(diag * p0.x - (R)0.5 * a0.x, diag * p0.y - (R)0.5 * a0.y);
-    sd[q][1] = mk(diag * p1.x - (R)0.5 * a1.x, diag * p1.y - (R)0.5 * a1.y);
+    C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0), f0, f1;
+    split(sp[pc + 1], f0, f1);
+    hop_x<R>(a0, a1, su[uc][0], f0, f1, (R)1);
+    split(sp[pc - 1], f0, f1);
+    hop_x<R>(a0, a1, cconj(su[uc - 1][0]), f0, f1, (R)-1);
+    split(sp[pc + PW], f0, f1);
+    hop_t<R>(a0, a1, su[uc][1], f0, f1, (R)1);
+    split(sp[pc - PW], f0, f1);
+    hop_t<R>(a0, a1, cconj(su[uc - UW][1]), f0, f1, (R)-1);
+    split(sp[pc], f0, f1);
+    sd[q] = join(mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y),
+                 mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y));
   }
   __syncthreads();
   // D^dagger on the tile
-  const int lx = tid % TX, lt = tid / TX;
-  const int gx = x0 + lx, gt = t0 + lt;
-  if (gx >= Lx || gt >= Lt) return;
-  const int dc = (lt + 1) * DW + (lx + 1);
-  const int uc = (lt + 2) * UW + (lx + 2);
-  C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0);
-  hop_x<R>(a0, a1, su[uc][0], sd[dc + 1][0], sd[dc + 1][1], (R)-1);
-  hop_x<R>(a0, a1, cconj(su[uc - 1][0]), sd[dc - 1][0], sd[dc - 1][1], (R)1);
-  hop_t<R>(a0, a1, su[uc][1], sd[dc + DW][0], sd[dc + DW][1], (R)-1);
-  hop_t<R>(a0, a1, cconj(su[uc - UW][1]), sd[dc - DW][0], sd[dc - DW][1], (R)1);
-  const C p0 = sd[dc][0], p1 = sd[dc][1];
-  const long long g = off + 2LL * (gx + Lx * gt);
-  out[g] = mk(diag * p0.x - (R)0.5 * a0.x, diag * p0.y - (R)0.5 * a0.y);
-  out[g + 1] = mk(diag * p1.x - (R)0.5 * a1.x, diag * p1.y - (R)0.5 * a1.y);
+  const int lx = tid % TX;
+  const int gx = x0 + lx;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int lt = tid / TX + TY * k;
+    const int gt = t0 + lt;
+    if (gx >= Lx || gt >= Lt) continue;
+    const int dc = (lt + 1) * DW + (lx + 1);
+    const int uc = (lt + 2) * UW + (lx + 2);
+    C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0), f0, f1;
+    split(sd[dc + 1], f0, f1);
+    hop_x<R>(a0, a1, su[uc][0], f0, f1, (R)-1);
+    split(sd[dc - 1], f0, f1);
+    hop_x<R>(a0, a1, cconj(su[uc - 1][0]), f0, f1, (R)1);
+    split(sd[dc + DW], f0, f1);
+    hop_t<R>(a0, a1, su[uc][1], f0, f1, (R)-1);
+    split(sd[dc - DW], f0, f1);
+    hop_t<R>(a0, a1, cconj(su[uc - UW][1]), f0, f1, (R)1);
+    split(sd[dc], f0, f1);
+    st_spinor(out + off + 2LL * (gx + Lx * gt),
+              join(mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y),
+                   mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y)));
+  }
 }
 
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, void* tmp, cudaStream_t s) {
   (void)tmp;
+  constexpr int TT = TY * tile<R>::RPT;
   dim3 grid((Lx + TX - 1) / TX, (Lt + TT - 1) / TT, nrhs);
-  k_wilson_A<R><<<grid, TX * TT, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
+  k_wilson_A<R><<<grid, TX * TY, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
                                          (const cplx_t<R>*)U, (R)diag, Lx, Lt);
   count_launch();
   return cudaGetLastError();

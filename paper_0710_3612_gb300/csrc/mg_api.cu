@@ -61,6 +61,7 @@ struct mg_handle {
   cudaStream_t gs = nullptr;
   cudaEvent_t fence[2] = {nullptr, nullptr};
   cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
+  long long loop_kernels[3] = {0, 0, 0};   // kernels per loop-body iteration
   int* dctrl = nullptr;         // [0] iterations, [1] status, [2] iteration limit
   bool use_graphs = true;
   // solver vectors (one RHS), FP64 and FP32: x r p q z t
@@ -455,6 +456,7 @@ void pcg_direction(mg_handle* h, int pmode) {
 // control kernel at the end of each iteration decides on the device whether
 // to run another iteration, so the whole loop is one graph launch.
 cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
+  const unsigned long long launches0 = launch_count();
   cudaGraph_t g = nullptr;
   ck(h, cudaGraphCreate(&g, 0), "graph create");
   cudaGraphConditionalHandle cond;
@@ -488,6 +490,9 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
   h->s = saved;
   h->fine_applies = fa;
   h->vcycles = vc;
+  // captured kernels did not run; they are counted once per executed iteration
+  h->loop_kernels[pmode] = (long long)(launch_count() - launches0);
+  add_launches(-h->loop_kernels[pmode]);
   ck(h, cudaStreamEndCapture(h->gs, &body), "end capture");
   cudaGraphExec_t exec = nullptr;
   ck(h, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
@@ -538,6 +543,7 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode
     int ctrl[2];
     std::memcpy(ctrl, h->hscal, sizeof(ctrl));
     const int it = ctrl[0];
+    add_launches((long long)it * h->loop_kernels[pmode]);
     h->fine_applies += (long long)it * per_it_fine;
     if (pmode) h->vcycles += it;
     if (ctrl[1] == 2) {
