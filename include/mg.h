@@ -91,7 +91,7 @@ typedef struct {
   int coarsest_refine_max;              /* cap on refinement steps (12)          */
   int inner_coarsest_refine;            /* mixed solver: FP64 refinement steps of
                                            the coarsest solve inside the FP32
-                                           V-cycle (2)                           */
+                                           V-cycle (1)                           */
   int vcycle_coarse_bf16;               /* mixed solver: 1 = coarse blocks of the
                                            FP32 V-cycle in BF16, 0 = FP32 (0)    */
 } mg_params;

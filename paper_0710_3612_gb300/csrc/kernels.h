@@ -128,13 +128,24 @@ cudaError_t galerkin_coarse(const void* Af, const void* Vst, void* Ac, int Lx, i
 cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int n, long long ld,
                                 cudaStream_t s);
 // In-place blocked Gauss-Jordan inversion of a Hermitian positive definite
-// complex64 N x N matrix (N multiple of 64).  work: 2 * N * 32 + 32 * 32 complex64.
+// complex64 N x N matrix (N multiple of 64), lower triangle kept (the upper
+// halves of diagonal 64 x 64 tiles are rebuilt by pack_hermitian).
+// work: 3 * N * 32 + 32 * 32 complex64.
 cudaError_t gauss_jordan_inverse_f32(void* M, int N, void* work, cudaStream_t s);
 // y = B x, or y += B x when accumulate (complex64 B, leading dimension ld);
 // x complex128 (N) -> y complex128 (N); FP32 products and accumulation, result
 // widened to FP64.  xtmp: ld complex64.
 cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld, void* xtmp,
                            bool accumulate, cudaStream_t s);
+
+// Packed Hermitian matrix: the lower-triangular 64 x 64 tiles (I >= J, stored
+// at I (I + 1) / 2 + J) of a dense ld x ld complex64 matrix (ld multiple of
+// 64); diagonal tiles are made Hermitian from their lower halves.
+cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s);
+// y = B x (or y += B x) with B Hermitian in packed tiles; x, y complex128 (N);
+// part: 2 * 64 * ntiles complex64 scratch.  FP32 products and accumulation.
+cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, void* part,
+                               bool accumulate, cudaStream_t s);
 
 // index map for tests
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,

@@ -530,10 +530,19 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_diag(float2* __restrict__ M, in
   P[r * GJB + c] = a[r][c];
 }
 
-// C_i = M_ik P (column panel, rows i != k) and R_j = P M_kj (row panel).
+// The matrix is Hermitian and, after sweeping the blocks K = {0..k-1}, so is
+// its swept form up to sign: S_ij = S_ji^H when i, j are both swept or both
+// unswept, S_ij = -S_ji^H otherwise.  Only the lower triangle is kept
+// current: the panels of column k and row k are rebuilt from it and the
+// rank-32 update touches lower tiles only (half the flops).  Upper entries of
+// diagonal 64 x 64 tiles may go stale; the packing step rebuilds them from the
+// lower triangle.
+//
+// Panel kernel: Cold_i = M_ik (all i != k), Cn_i = M_ik P, R_j = P M_kj.
 __global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict__ M, int N, int k,
                                                        const float2* __restrict__ P,
-                                                       float2* __restrict__ Cp,
+                                                       float2* __restrict__ Cold,
+                                                       float2* __restrict__ Cn,
                                                        float2* __restrict__ Rp) {
   __shared__ float2 sP[GJB][GJB + 1], sX[GJB][GJB + 1];
   const int nb = N / GJB;
@@ -541,30 +550,49 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict_
   const int r = threadIdx.y, c = threadIdx.x;
   if (b == k) return;
   sP[r][c] = P[r * GJB + c];
-  if (col_panel) sX[r][c] = M[(long long)(b * GJB + r) * N + k * GJB + c];   // M_bk
-  else sX[r][c] = M[(long long)(k * GJB + r) * N + b * GJB + c];             // M_kb
+  if (col_panel) {
+    // M_bk: stored below the diagonal for b > k; for b < k it is -(M_kb)^H
+    if (b > k) {
+      sX[r][c] = M[(long long)(b * GJB + r) * N + k * GJB + c];
+    } else {
+      const float2 v = M[(long long)(k * GJB + c) * N + b * GJB + r];
+      sX[r][c] = make_float2(-v.x, v.y);
+    }
+  } else {
+    // M_kb: stored for b < k; for b > k it is (M_bk)^H (both unswept)
+    if (b < k) {
+      sX[r][c] = M[(long long)(k * GJB + r) * N + b * GJB + c];
+    } else {
+      const float2 v = M[(long long)(b * GJB + c) * N + k * GJB + r];
+      sX[r][c] = make_float2(v.x, -v.y);
+    }
+  }
   __syncthreads();
   float2 acc = make_float2(0.f, 0.f);
   if (col_panel) {
     for (int q = 0; q < GJB; ++q) cfma(acc, sX[r][q], sP[q][c]);
-    Cp[(long long)(b * GJB + r) * GJB + c] = acc;
+    Cold[(long long)(b * GJB + r) * GJB + c] = sX[r][c];
+    Cn[(long long)(b * GJB + r) * GJB + c] = acc;
   } else {
     for (int q = 0; q < GJB; ++q) cfma(acc, sP[r][q], sX[q][c]);
     Rp[(long long)r * N + b * GJB + c] = acc;
   }
 }
 
-// M_ij -= C_i M_kj for i, j != k; 64 x 64 output tile per CTA, 4 outputs per thread.
+// M_ij -= M_ik (P M_kj) = Cold_i R_j on lower 64 x 64 tiles (i, j != k);
+// 4 x 4 outputs per thread.
 __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N, int k,
-                                                   const float2* __restrict__ Cp) {
+                                                   const float2* __restrict__ Cold,
+                                                   const float2* __restrict__ Rp) {
+  if (blockIdx.x > blockIdx.y) return;          // upper tile: not kept
   __shared__ float2 sC[64][GJB + 1], sR[GJB][64 + 1];
   const int bi = blockIdx.y * 64, bj = blockIdx.x * 64;
   const int tid = threadIdx.x;
   for (int q = tid; q < 64 * GJB; q += 256) {
     const int rr = q / GJB, cc = q % GJB;
-    sC[rr][cc] = Cp[(long long)(bi + rr) * GJB + cc];
+    sC[rr][cc] = Cold[(long long)(bi + rr) * GJB + cc];
     const int r2 = q / 64, c2 = q % 64;
-    sR[r2][c2] = M[(long long)(k * GJB + r2) * N + bj + c2];
+    sR[r2][c2] = Rp[(long long)r2 * N + bj + c2];
   }
   __syncthreads();
   const int tr = tid / 16, tc = tid % 16;   // rows tr + 16 u, cols tc + 16 v
@@ -573,6 +601,7 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
+#pragma unroll 4
   for (int q = 0; q < GJB; ++q) {
     float2 cv[4], rv[4];
 #pragma unroll
@@ -599,9 +628,10 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
   }
 }
 
+// Lower-triangle write-back: M_bk = -Cn_b (b > k), M_kb = R_b (b < k), M_kk = P.
 __global__ void __launch_bounds__(GJB* GJB) k_gj_write(float2* __restrict__ M, int N, int k,
                                                        const float2* __restrict__ P,
-                                                       const float2* __restrict__ Cp,
+                                                       const float2* __restrict__ Cn,
                                                        const float2* __restrict__ Rp) {
   const int nb = N / GJB;
   const int r = threadIdx.y, c = threadIdx.x;
@@ -610,11 +640,12 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_write(float2* __restrict__ M, i
     return;
   }
   const int b = blockIdx.x % nb;
-  if (b == k) return;
   if (blockIdx.x < nb) {
-    const float2 v = Cp[(long long)(b * GJB + r) * GJB + c];
+    if (b <= k) return;
+    const float2 v = Cn[(long long)(b * GJB + r) * GJB + c];
     M[(long long)(b * GJB + r) * N + k * GJB + c] = make_float2(-v.x, -v.y);
   } else {
+    if (b >= k) return;
     M[(long long)(k * GJB + r) * N + b * GJB + c] = Rp[(long long)r * N + b * GJB + c];
   }
 }
@@ -623,14 +654,15 @@ cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s
   if (N % 64 != 0) return cudaErrorInvalidValue;
   float2* M = (float2*)Mv;
   float2* P = (float2*)work;
-  float2* Cp = P + GJB * GJB;
-  float2* Rp = Cp + (long long)N * GJB;
+  float2* Cold = P + GJB * GJB;
+  float2* Cn = Cold + (long long)N * GJB;
+  float2* Rp = Cn + (long long)N * GJB;
   const int nb = N / GJB;
   for (int k = 0; k < nb; ++k) {
     k_gj_diag<<<1, dim3(GJB, GJB), 0, s>>>(M, N, k, P); count_launch();
-    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp); count_launch();
-    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cp); count_launch();
-    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cp, Rp); count_launch();
+    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cold, Cn, Rp); count_launch();
+    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cold, Rp); count_launch();
+    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cn, Rp); count_launch();
   }
   return cudaGetLastError();
 }
@@ -673,6 +705,124 @@ cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld,
   k_x_to_f32<<<(ld + 255) / 256, 256, 0, s>>>((const double2*)x, (float2*)xtmp, N, ld); count_launch();
   k_gemv<<<(N + 7) / 8, 256, 0, s>>>((const float2*)B, (const float2*)xtmp, (double2*)y, N, ld,
                                      accumulate); count_launch();
+  return cudaGetLastError();
+}
+
+// Hermitian inverse in packed lower-triangular 64 x 64 tiles.  Tile (I, J),
+// I >= J, is stored at k = I (I + 1) / 2 + J, row-major.  y = B x reads every
+// stored tile once: tile (I, J) contributes B_IJ x_J to rows of block I and,
+// off the diagonal, B_IJ^H x_I to rows of block J; partial products go to a
+// buffer and a second kernel sums them per row in a fixed order.
+static constexpr int HT = 64;
+
+__global__ void k_pack_hermitian(const float2* __restrict__ M, float2* __restrict__ P, int ld) {
+  const int k = blockIdx.x;
+  int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= k) ++I;
+  while (I * (I + 1) / 2 > k) --I;
+  const int J = k - I * (I + 1) / 2;
+  for (int q = threadIdx.x; q < HT * HT; q += blockDim.x) {
+    const int r = q / HT, c = q % HT;
+    float2 v;
+    if (I != J || r >= c) {
+      v = M[(long long)(I * HT + r) * ld + J * HT + c];
+    } else {     // upper half of a diagonal tile: Hermitian image of the lower half
+      const float2 w = M[(long long)(J * HT + c) * ld + I * HT + r];
+      v = make_float2(w.x, -w.y);
+    }
+    P[(long long)k * HT * HT + q] = v;
+  }
+}
+
+cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s) {
+  if (ld % HT) return cudaErrorInvalidValue;
+  const int nt = ld / HT;
+  k_pack_hermitian<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)M, (float2*)P, ld);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ P,
+                                                     const double2* __restrict__ x, int N,
+                                                     float2* __restrict__ part) {
+  __shared__ float2 T[HT][HT + 1];
+  __shared__ float2 xi[HT], xj[HT];
+  __shared__ float2 red[4][HT];
+  const int k = blockIdx.x;
+  int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= k) ++I;
+  while (I * (I + 1) / 2 > k) --I;
+  const int J = k - I * (I + 1) / 2;
+  const float4* src = (const float4*)(P + (long long)k * HT * HT);
+  for (int q = threadIdx.x; q < HT * HT / 2; q += 256) {
+    const float4 v = src[q];
+    const int e = 2 * q, r = e / HT, c = e % HT;
+    T[r][c] = make_float2(v.x, v.y);
+    T[r][c + 1] = make_float2(v.z, v.w);
+  }
+  if (threadIdx.x < HT) {
+    const int gi = I * HT + threadIdx.x, gj = J * HT + threadIdx.x;
+    xi[threadIdx.x] = gi < N ? make_float2((float)x[gi].x, (float)x[gi].y) : make_float2(0.f, 0.f);
+    xj[threadIdx.x] = gj < N ? make_float2((float)x[gj].x, (float)x[gj].y) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // u = T x_J: row r = t % 64, quarter g = t / 64 of the columns
+  const int r = threadIdx.x % HT, g = threadIdx.x / HT;
+  float2 u = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int c = g * 16; c < g * 16 + 16; ++c) cfma(u, T[r][c], xj[c]);
+  red[g][r] = u;
+  __syncthreads();
+  if (threadIdx.x < HT) {
+    float2 a = red[0][threadIdx.x];
+    a = cadd(a, red[1][threadIdx.x]);
+    a = cadd(a, red[2][threadIdx.x]);
+    a = cadd(a, red[3][threadIdx.x]);
+    part[(2LL * k) * HT + threadIdx.x] = a;
+  }
+  if (I == J) return;
+  __syncthreads();
+  // v = T^H x_I: column c = t % 64, quarter g of the rows
+  const int c = threadIdx.x % HT;
+  float2 v = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int rr = g * 16; rr < g * 16 + 16; ++rr) cfmac(v, T[rr][c], xi[rr]);
+  red[g][c] = v;
+  __syncthreads();
+  if (threadIdx.x < HT) {
+    float2 a = red[0][threadIdx.x];
+    a = cadd(a, red[1][threadIdx.x]);
+    a = cadd(a, red[2][threadIdx.x]);
+    a = cadd(a, red[3][threadIdx.x]);
+    part[(2LL * k + 1) * HT + threadIdx.x] = a;
+  }
+}
+
+__global__ void k_hgemv_reduce(const float2* __restrict__ part, double2* __restrict__ y, int N,
+                               int nt, bool accumulate) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const int I = row / HT, rr = row % HT;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int J = 0; J < nt; ++J) {
+    if (J <= I) acc = cadd(acc, part[(2LL * (I * (I + 1) / 2 + J)) * HT + rr]);
+    else acc = cadd(acc, part[(2LL * (J * (J + 1) / 2 + I) + 1) * HT + rr]);
+  }
+  double2 v = make_double2(acc.x, acc.y);
+  if (accumulate) { v.x += y[row].x; v.y += y[row].y; }
+  y[row] = v;
+}
+
+cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, void* part,
+                               bool accumulate, cudaStream_t s) {
+  if (ld % HT || ld < N) return cudaErrorInvalidValue;
+  const int nt = ld / HT;
+  k_hgemv_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)P, (const double2*)x, N,
+                                                  (float2*)part);
+  count_launch();
+  k_hgemv_reduce<<<(N + 127) / 128, 128, 0, s>>>((const float2*)part, (double2*)y, N, nt,
+                                                  accumulate);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ struct mg_handle {
   float2* Binv = nullptr;
   float2* gj_work = nullptr;
   float2* gemv_x = nullptr;
+  float2* Bpk = nullptr;        // packed Hermitian tiles of the inverse
+  float2* gemv_part = nullptr;  // partial products of the packed GEMV
   int n_refine = 0;
   double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
   // CUDA graphs of the Krylov loop (one per preconditioner mode), launched on
@@ -181,11 +183,11 @@ void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int w
 // x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r.
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
   ProfScope prof(h, MG_KF_COARSEST);
-  ck(h, dense_gemv_f32(h->Binv, b, x, h->Nc, h->ldc, h->gemv_x, false, h->s), "coarsest gemv");
+  ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, h->gemv_part, false, h->s), "coarsest gemv");
   for (int it = 0; it < steps; ++it) {
     apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64);
     ck(h, sub_from<double>(b, h->cr, h->Nc, h->s), "coarsest residual");
-    ck(h, dense_gemv_f32(h->Binv, h->cr, x, h->Nc, h->ldc, h->gemv_x, true, h->s),
+    ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, h->gemv_part, true, h->s),
        "coarsest gemv");
   }
 }
@@ -302,6 +304,7 @@ void build_coarsest(mg_handle* h) {
   {
     ProfScope prof(h, MG_KF_INVERSE);
     ck(h, gauss_jordan_inverse_f32(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+    ck(h, pack_hermitian(h->Binv, h->Bpk, h->ldc, h->s), "pack");
   }
   // Refinement count: smallest number of FP64 correction steps that brings a
   // fixed test vector (all ones) to coarsest_tol, plus one.
@@ -665,7 +668,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->omega_mr = 0.8;
   p->coarsest_tol = 1e-13;
   p->coarsest_refine_max = 12;
-  p->inner_coarsest_refine = 2;
+  p->inner_coarsest_refine = 1;
   p->vcycle_coarse_bf16 = 0;
   return MG_OK;
 }
@@ -765,8 +768,11 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       h->Nc = (int)C.count();
       h->ldc = (h->Nc + 63) / 64 * 64;
       h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
-      h->gj_work = dalloc<float2>(h, ((size_t)2 * h->ldc * 32 + 32 * 32) * sizeof(float2));
+      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 32 + 32 * 32) * sizeof(float2));
       h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
+      const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
+      h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
+      h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * sizeof(float2));
       h->cb = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
       h->cx = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
       h->cr = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
