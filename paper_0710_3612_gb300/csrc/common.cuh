@@ -76,6 +76,65 @@ __device__ __forceinline__ void hop_t(cplx_t<R>& a0, cplx_t<R>& a1, cplx_t<R> u,
 
 __device__ __forceinline__ float2 bf2_to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
 
+// Fixed-order block reduction of (a, b) pairs held one per thread.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    a = l < nw ? sh[2 * l] : 0.0;
+    b = l < nw ? sh[2 * l + 1] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
+// Single-pass deterministic reduction.  Every block writes its partial sum;
+// the last block to finish (found with an atomic ticket) adds the partials in
+// a fixed order and resets the ticket.  ws = [64 tickets (as doubles)][partials].
+// rhs selects the output and ticket; blk in [0, G) is this block's slot.
+__device__ __forceinline__ void finish_reduction_g(double re, double im, double* ws, double* out,
+                                                   double* sh, int rhs, int blk, int G) {
+  unsigned* tickets = (unsigned*)ws;
+  double* partials = ws + 64;
+  __shared__ bool last;
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * ((long long)rhs * G + blk)] = re;
+    partials[2 * ((long long)rhs * G + blk) + 1] = im;
+    __threadfence();
+    last = atomicAdd(&tickets[rhs], 1u) == (unsigned)(G - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  re = 0.0;
+  im = 0.0;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    re += __ldcg(&partials[2 * ((long long)rhs * G + i)]);
+    im += __ldcg(&partials[2 * ((long long)rhs * G + i) + 1]);
+  }
+  __syncthreads();
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) {
+    out[2 * rhs] = re;
+    out[2 * rhs + 1] = im;
+    tickets[rhs] = 0u;
+  }
+}
+
+__device__ __forceinline__ void finish_reduction(double re, double im, double* ws, double* out,
+                                                 double* sh) {
+  finish_reduction_g(re, im, ws, out, sh, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
 // Block map of the geometric blocking S_j: coarse site and in-block offset.
 __host__ __device__ __forceinline__ int coarse_site(int x, int t, int Lx, int bx, int bt) {
   return (t / bt) * (Lx / bx) + x / bx;

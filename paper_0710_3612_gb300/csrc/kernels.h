@@ -46,7 +46,7 @@ cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long 
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
-                  double* rr, cudaStream_t s);
+                  double* rr, cudaStream_t s, void* r32 = nullptr);
 //   beta = rz_new / rz_old; p = z + beta p; then rz_old <- rz_new is done by the caller.
 template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
@@ -56,9 +56,13 @@ cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_
 cudaError_t cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
                        cudaGraphConditionalHandle cond, cudaStream_t s);
 cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, cudaStream_t s);
-// Flexible CG (FP64, one RHS): beta = -Re(zq) / Re(pq); p = z + beta p.
-cudaError_t cg_p_pr(void* p, const void* z, const double* zq, const double* pq, long long count,
-                    cudaStream_t s);
+// Flexible CG (FP64 vectors, FP32 preconditioned residual z32, one RHS):
+// zr = {Re<z32, q>, Re<r, z32>} (one launch), then beta = -zr[0] / Re(pq),
+// p = z32 + beta p, and rz <- zr[1] for the next step length.
+cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, double* ws,
+                       double* zr, cudaStream_t s);
+cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq, double* rz,
+                    long long count, cudaStream_t s);
 // out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s);
@@ -76,6 +80,19 @@ cudaError_t lincomb(void* out, double a, const void* u, double b, const void* v,
 template <typename R>
 cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s);
 
+// ---- fused epilogue of the operator kernels -------------------------------
+// out = ca * (Op x) + cu * U + cw * W (U, W optional, same precision and layout
+// as out; out may alias W).  When dot_out is set (fine A only, one RHS), the
+// kernel also forms <x, Op x> (double2, deterministic, workspace dot_ws as
+// for the reductions).
+struct Epilogue {
+  double ca = 1.0, cu = 0.0, cw = 0.0;
+  const void* U = nullptr;
+  const void* W = nullptr;
+  double* dot_ws = nullptr;
+  double* dot_out = nullptr;
+};
+
 // ---- fine Wilson operator ------------------------------------------------
 // U: [2][V] complex of precision R with the antiperiodic sign folded into the
 // t links at t = Lt - 1.  diag = 4 + m.
@@ -84,7 +101,7 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
                      int nrhs, bool dagger, cudaStream_t s);
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
-                     int nrhs, void* tmp, cudaStream_t s);
+                     int nrhs, const Epilogue& ep, cudaStream_t s);
 // links: gauge complex128 [2][V] -> folded links of precision R
 template <typename R>
 cudaError_t fold_links(const void* gauge, void* U, int Lx, int Lt, cudaStream_t s);
@@ -96,7 +113,7 @@ cudaError_t link_unitarity(const void* gauge, long long count, double* out, cuda
 // (R=float, W=float) or bf16x2 (R=float, W=bf16).
 enum CoarseWeights { W_F64 = 0, W_F32 = 1, W_BF16 = 2 };
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
-                         int n, int nrhs, cudaStream_t s);
+                         int n, int nrhs, const Epilogue& ep, cudaStream_t s);
 // A (complex128) -> float2 or bf16x2 copy
 cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
                            cudaStream_t s);

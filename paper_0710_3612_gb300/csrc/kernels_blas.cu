@@ -22,60 +22,6 @@ int reduce_blocks(long long count) {
   return (int)g;
 }
 
-// Fixed-order block reduction of (a, b) pairs held one per thread.
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    a = l < nw ? sh[2 * l] : 0.0;
-    b = l < nw ? sh[2 * l + 1] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-  }
-}
-
-// Single-pass deterministic reduction.  Every block writes its partial sum;
-// the last block to finish (found with an atomic ticket) adds the partials in
-// a fixed order and resets the ticket.  ws = [64 tickets (as doubles)][partials].
-__device__ __forceinline__ void finish_reduction(double re, double im, double* ws, double* out,
-                                                 double* sh) {
-  unsigned* tickets = (unsigned*)ws;
-  double* partials = ws + 64;
-  const int rhs = blockIdx.y, G = gridDim.x;
-  __shared__ bool last;
-  block_sum2(re, im, sh);
-  if (threadIdx.x == 0) {
-    partials[2 * ((long long)rhs * G + blockIdx.x)] = re;
-    partials[2 * ((long long)rhs * G + blockIdx.x) + 1] = im;
-    __threadfence();
-    last = atomicAdd(&tickets[rhs], 1u) == (unsigned)(G - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  re = 0.0;
-  im = 0.0;
-  for (int i = threadIdx.x; i < G; i += blockDim.x) {
-    re += __ldcg(&partials[2 * ((long long)rhs * G + i)]);
-    im += __ldcg(&partials[2 * ((long long)rhs * G + i) + 1]);
-  }
-  __syncthreads();
-  block_sum2(re, im, sh);
-  if (threadIdx.x == 0) {
-    out[2 * rhs] = re;
-    out[2 * rhs + 1] = im;
-    tickets[rhs] = 0u;
-  }
-}
-
 template <typename R, bool NORM>
 __global__ void __launch_bounds__(RT) k_dot(const cplx_t<R>* __restrict__ a,
                                             const cplx_t<R>* __restrict__ b, long long count,
@@ -171,7 +117,8 @@ __global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<
                                               const cplx_t<R>* __restrict__ p,
                                               const cplx_t<R>* __restrict__ q, const double* rz,
                                               const double* pq, const int* frozen,
-                                              long long count, double* ws, double* rr) {
+                                              long long count, double* ws, double* rr,
+                                              float2* __restrict__ r32) {
   __shared__ double sh[2 * RT / 32];
   const int rhs = blockIdx.y;
   const bool skip = frozen && frozen[rhs];
@@ -189,6 +136,7 @@ __global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<
       rv = mk(fma(-alpha, qv.x, rv.x), fma(-alpha, qv.y, rv.y));
       r[k] = rv;
     }
+    if (r32) r32[k] = make_float2((float)rv.x, (float)rv.y);
     acc = fma((double)rv.x, (double)rv.x, acc);
     acc = fma((double)rv.y, (double)rv.y, acc);
   }
@@ -198,11 +146,12 @@ __global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
-                  double* rr, cudaStream_t s) {
+                  double* rr, cudaStream_t s, void* r32) {
   if (nrhs > 64) return cudaErrorInvalidValue;
   int g = reduce_blocks(count);
   k_cg_xr<R><<<dim3(g, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
-                                          (const cplx_t<R>*)q, rz, pq, frozen, count, ws, rr);
+                                          (const cplx_t<R>*)q, rz, pq, frozen, count, ws, rr,
+                                          (float2*)r32);
   count_launch();
   return cudaGetLastError();
 }
@@ -267,20 +216,53 @@ cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, 
   return cudaGetLastError();
 }
 
-// Flexible-CG direction update: beta = -Re(zq) / Re(pq); p = z + beta p.
-__global__ void k_cg_p_pr(double2* __restrict__ p, const double2* __restrict__ z, const double* zq,
-                          const double* pq, long long count) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const double d = pq[0];
-  const double beta = d != 0.0 ? -zq[0] / d : 0.0;
-  const double2 pv = p[i], zv = z[i];
-  p[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
+// Flexible CG with the FP32 preconditioned residual z32:
+// zr = {Re<z32, q>, Re<r, z32>} in one deterministic pass.
+__global__ void __launch_bounds__(RT) k_dot2_zq_rz(const float2* __restrict__ z,
+                                                   const double2* __restrict__ q,
+                                                   const double2* __restrict__ r, long long count,
+                                                   double* ws, double* zr) {
+  __shared__ double sh[2 * RT / 32];
+  double a = 0.0, b = 0.0;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const float2 zv = z[i];
+    const double2 qv = q[i], rv = r[i];
+    a = fma((double)zv.x, qv.x, a);
+    a = fma((double)zv.y, qv.y, a);
+    b = fma(rv.x, (double)zv.x, b);
+    b = fma(rv.y, (double)zv.y, b);
+  }
+  finish_reduction(a, b, ws, zr, sh);
 }
 
-cudaError_t cg_p_pr(void* p, const void* z, const double* zq, const double* pq, long long count,
-                    cudaStream_t s) {
-  k_cg_p_pr<<<grid1(count, 1), RT, 0, s>>>((double2*)p, (const double2*)z, zq, pq, count);
+cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, double* ws,
+                       double* zr, cudaStream_t s) {
+  k_dot2_zq_rz<<<reduce_blocks(count), RT, 0, s>>>((const float2*)z32, (const double2*)q,
+                                                   (const double2*)r, count, ws, zr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// beta = -zr[0] / Re(pq); p = z32 + beta p; rz <- {zr[1], 0}.
+__global__ void k_cg_p_pr(double2* __restrict__ p, const float2* __restrict__ z, const double* zr,
+                          const double* pq, double* rz, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    rz[0] = zr[1];
+    rz[1] = 0.0;
+  }
+  if (i >= count) return;
+  const double d = pq[0];
+  const double beta = d != 0.0 ? -zr[0] / d : 0.0;
+  const double2 pv = p[i];
+  const float2 zv = z[i];
+  p[i] = make_double2(fma(beta, pv.x, (double)zv.x), fma(beta, pv.y, (double)zv.y));
+}
+
+cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq, double* rz,
+                    long long count, cudaStream_t s) {
+  k_cg_p_pr<<<grid1(count, 1), RT, 0, s>>>((double2*)p, (const float2*)z32, zr, pq, rz, count);
   count_launch();
   return cudaGetLastError();
 }
@@ -386,7 +368,7 @@ cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s) {
                                          cudaStream_t);                                      \
   template cudaError_t cg_xr<R>(void*, void*, const void*, const void*, const double*,       \
                                 const double*, const int*, long long, int, double*, double*, \
-                                cudaStream_t);                                               \
+                                cudaStream_t, void*);                                        \
   template cudaError_t cg_p<R>(void*, const void*, const double*, const double*, const int*, \
                                long long, int, cudaStream_t);                                \
   template cudaError_t sub_from<R>(const void*, void*, long long, cudaStream_t);             \

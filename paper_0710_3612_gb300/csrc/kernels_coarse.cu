@@ -63,9 +63,9 @@ template <> struct row_dot<float> {
 
 template <typename R, typename WT>
 __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restrict__ in,
-                                                      cplx_t<R>* __restrict__ out,
+                                                      cplx_t<R>* out,
                                                       const WT* __restrict__ A, int Lx, int Lt,
-                                                      int n) {
+                                                      int n, Epilogue ep) {
   extern __shared__ unsigned char smraw[];
   cplx_t<R>* xs = (cplx_t<R>*)smraw;            // [9][n] neighbour vectors
   cplx_t<R>* part = xs + 9 * n;                 // [9][n] partial row products
@@ -92,24 +92,34 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
     cplx_t<R> acc = part[q];
 #pragma unroll
     for (int d = 1; d < 9; ++d) acc = cadd(acc, part[d * n + q]);
-    out[((long long)blockIdx.y * V + j) * n + q] = acc;
+    const long long o = ((long long)blockIdx.y * V + j) * n + q;
+    acc = mk((R)ep.ca * acc.x, (R)ep.ca * acc.y);
+    if (ep.U) {
+      const cplx_t<R> u = ((const cplx_t<R>*)ep.U)[o];
+      acc = mk(acc.x + (R)ep.cu * u.x, acc.y + (R)ep.cu * u.y);
+    }
+    if (ep.W) {
+      const cplx_t<R> w = ((const cplx_t<R>*)ep.W)[o];
+      acc = mk(acc.x + (R)ep.cw * w.x, acc.y + (R)ep.cw * w.y);
+    }
+    out[o] = acc;
   }
 }
 
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
-                         int n, int nrhs, cudaStream_t s) {
+                         int n, int nrhs, const Epilogue& ep, cudaStream_t s) {
   if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
   dim3 grid(Lx * Lt, nrhs);
   const int threads = (9 * n + 31) / 32 * 32;
   if (weights == W_F64)
     k_coarse_apply<double, double2><<<grid, threads, 18 * n * sizeof(double2), s>>>(
-        (const double2*)in, (double2*)out, (const double2*)A, Lx, Lt, n);
+        (const double2*)in, (double2*)out, (const double2*)A, Lx, Lt, n, ep);
   else if (weights == W_F32)
     k_coarse_apply<float, float2><<<grid, threads, 18 * n * sizeof(float2), s>>>(
-        (const float2*)in, (float2*)out, (const float2*)A, Lx, Lt, n);
+        (const float2*)in, (float2*)out, (const float2*)A, Lx, Lt, n, ep);
   else
     k_coarse_apply<float, __nv_bfloat162><<<grid, threads, 18 * n * sizeof(float2), s>>>(
-        (const float2*)in, (float2*)out, (const __nv_bfloat162*)A, Lx, Lt, n);
+        (const float2*)in, (float2*)out, (const __nv_bfloat162*)A, Lx, Lt, n, ep);
   count_launch();
   return cudaGetLastError();
 }
@@ -141,31 +151,43 @@ __device__ __forceinline__ int block_site(int j, int o, int Lxc, int Lx, int bx,
   return (jx * bx + o % bx) + Lx * (jt * bt + o / bx);
 }
 
+// One warp per output (j, c, k): the lanes stride over the bx*bt*h entries of
+// the block-chirality vector, the warp sums the products in a fixed
+// butterfly order.
 template <typename R>
-__global__ void k_restrict(const cplx_t<R>* __restrict__ fine, cplx_t<R>* __restrict__ coarse,
-                           const cplx_t<R>* __restrict__ Vst, int Lx, int Lt, int bx, int bt,
-                           int h, int Nv) {
+__global__ void __launch_bounds__(256) k_restrict(const cplx_t<R>* __restrict__ fine,
+                                                  cplx_t<R>* __restrict__ coarse,
+                                                  const cplx_t<R>* __restrict__ Vst, int Lx,
+                                                  int Lt, int bx, int bt, int h, int Nv) {
   const int Lxc = Lx / bx, Vc = Lxc * (Lt / bt), nc = 2 * Nv, nf = 2 * h;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= Vc * nc) return;
-  const int j = idx / nc, s = idx % nc, c = s / Nv, k = s % Nv;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= Vc * nc) return;
+  const int j = w / nc, s = w % nc, c = s / Nv, k = s % Nv;
   const cplx_t<R>* f = fine + (long long)blockIdx.y * Lx * Lt * nf;
-  cplx_t<R> acc = mk((R)0, (R)0);
-  for (int o = 0; o < bx * bt; ++o) {
+  const int m = bx * bt * h;
+  double re = 0.0, im = 0.0;
+  for (int e = lane; e < m; e += 32) {
+    const int o = e / h, a = e % h;
     const int i = block_site(j, o, Lxc, Lx, bx, bt);
-    const cplx_t<R>* v = Vst + (((long long)i * 2 + c) * Nv + k) * h;
-    const cplx_t<R>* r = f + (long long)i * nf + c * h;
-    for (int a = 0; a < h; ++a) cfmac(acc, v[a], r[a]);
+    const cplx_t<R> v = Vst[(((long long)i * 2 + c) * Nv + k) * h + a];
+    const cplx_t<R> r = f[(long long)i * nf + c * h + a];
+    re += (double)v.x * r.x + (double)v.y * r.y;
+    im += (double)v.x * r.y - (double)v.y * r.x;
   }
-  coarse[(long long)blockIdx.y * Vc * nc + idx] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) coarse[(long long)blockIdx.y * Vc * nc + w] = mk((R)re, (R)im);
 }
 
 template <typename R>
 cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
                         int bt, int h, int Nv, int nrhs, cudaStream_t s) {
-  const int tot = (Lx / bx) * (Lt / bt) * 2 * Nv;
-  k_restrict<R><<<dim3((tot + 127) / 128, nrhs), 128, 0, s>>>(
-      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv); count_launch();
+  const int warps = (Lx / bx) * (Lt / bt) * 2 * Nv;
+  k_restrict<R><<<dim3((warps + 7) / 8, nrhs), 256, 0, s>>>(
+      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -798,19 +820,30 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
   }
 }
 
-__global__ void k_hgemv_reduce(const float2* __restrict__ part, double2* __restrict__ y, int N,
-                               int nt, bool accumulate) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= N) return;
-  const int I = row / HT, rr = row % HT;
+// One CTA per 64-row block: 4 groups of 64 threads each sum a quarter of the
+// 64-wide tile row in order; the quarters are added in a fixed order.
+__global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__ part,
+                                                      double2* __restrict__ y, int N, int nt,
+                                                      bool accumulate) {
+  __shared__ float2 red[4][HT];
+  const int I = blockIdx.x, rr = threadIdx.x % HT, g = threadIdx.x / HT;
   float2 acc = make_float2(0.f, 0.f);
-  for (int J = 0; J < nt; ++J) {
+  for (int J = g; J < nt; J += 4) {
     if (J <= I) acc = cadd(acc, part[(2LL * (I * (I + 1) / 2 + J)) * HT + rr]);
     else acc = cadd(acc, part[(2LL * (J * (J + 1) / 2 + I) + 1) * HT + rr]);
   }
-  double2 v = make_double2(acc.x, acc.y);
-  if (accumulate) { v.x += y[row].x; v.y += y[row].y; }
-  y[row] = v;
+  red[g][rr] = acc;
+  __syncthreads();
+  const int row = I * HT + threadIdx.x;
+  if (threadIdx.x < HT && row < N) {
+    float2 a = red[0][threadIdx.x];
+    a = cadd(a, red[1][threadIdx.x]);
+    a = cadd(a, red[2][threadIdx.x]);
+    a = cadd(a, red[3][threadIdx.x]);
+    double2 v = make_double2(a.x, a.y);
+    if (accumulate) { v.x += y[row].x; v.y += y[row].y; }
+    y[row] = v;
+  }
 }
 
 cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, void* part,
@@ -820,8 +853,7 @@ cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int
   k_hgemv_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)P, (const double2*)x, N,
                                                   (float2*)part);
   count_launch();
-  k_hgemv_reduce<<<(N + 127) / 128, 128, 0, s>>>((const float2*)part, (double2*)y, N, nt,
-                                                  accumulate);
+  k_hgemv_reduce<<<nt, 256, 0, s>>>((const float2*)part, (double2*)y, N, nt, accumulate);
   count_launch();
   return cudaGetLastError();
 }

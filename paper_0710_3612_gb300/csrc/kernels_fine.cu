@@ -111,9 +111,9 @@ __device__ __forceinline__ int wrap(int g, int L) { return g < 0 ? g + L : (g >=
 
 template <typename R>
 __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict__ in,
-                                                     cplx_t<R>* __restrict__ out,
+                                                     cplx_t<R>* out,
                                                      const cplx_t<R>* __restrict__ U, R diag,
-                                                     int Lx, int Lt) {
+                                                     int Lx, int Lt, Epilogue ep) {
   constexpr int RPT = tile<R>::RPT, TT = TY * RPT;
   constexpr int PW = TX + 4, PH = TT + 4;     // psi region [-2, TX+1] x [-2, TT+1]
   constexpr int DW = TX + 2, DH = TT + 2;     // D psi region [-1, TX] x [-1, TT]
@@ -157,9 +157,13 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
                  mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y));
   }
   __syncthreads();
-  // D^dagger on the tile
+  // D^dagger on the tile, then the epilogue
   const int lx = tid % TX;
   const int gx = x0 + lx;
+  const R ca = (R)ep.ca, cu = (R)ep.cu, cw = (R)ep.cw;
+  const C* EU = (const C*)ep.U;
+  const C* EW = (const C*)ep.W;
+  double dre = 0.0, dim = 0.0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int lt = tid / TX + TY * k;
@@ -177,20 +181,48 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
     split(sd[dc - DW], f0, f1);
     hop_t<R>(a0, a1, cconj(su[uc - UW][1]), f0, f1, (R)1);
     split(sd[dc], f0, f1);
-    st_spinor(out + off + 2LL * (gx + Lx * gt),
-              join(mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y),
-                   mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y)));
+    C y0 = mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y);
+    C y1 = mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y);
+    const long long g = off + 2LL * (gx + Lx * gt);
+    if (ep.dot_out) {
+      C p0, p1;
+      split(sp[(lt + 2) * PW + (lx + 2)], p0, p1);
+      dre += (double)p0.x * y0.x + (double)p0.y * y0.y + (double)p1.x * y1.x + (double)p1.y * y1.y;
+      dim += (double)p0.x * y0.y - (double)p0.y * y0.x + (double)p1.x * y1.y - (double)p1.y * y1.x;
+    }
+    y0 = mk(ca * y0.x, ca * y0.y);
+    y1 = mk(ca * y1.x, ca * y1.y);
+    if (EU) {
+      const S u = ld_spinor(EU + g);
+      C u0, u1;
+      split(u, u0, u1);
+      y0 = mk(y0.x + cu * u0.x, y0.y + cu * u0.y);
+      y1 = mk(y1.x + cu * u1.x, y1.y + cu * u1.y);
+    }
+    if (EW) {
+      const S w = ld_spinor(EW + g);
+      C w0, w1;
+      split(w, w0, w1);
+      y0 = mk(y0.x + cw * w0.x, y0.y + cw * w0.y);
+      y1 = mk(y1.x + cw * w1.x, y1.y + cw * w1.y);
+    }
+    st_spinor(out + g, join(y0, y1));
+  }
+  if (ep.dot_out) {
+    __shared__ double sh[64];
+    finish_reduction_g(dre, dim, ep.dot_ws, ep.dot_out, sh, 0, blockIdx.y * gridDim.x + blockIdx.x,
+                       gridDim.x * gridDim.y);
   }
 }
 
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
-                     int nrhs, void* tmp, cudaStream_t s) {
-  (void)tmp;
+                     int nrhs, const Epilogue& ep, cudaStream_t s) {
   constexpr int TT = TY * tile<R>::RPT;
   dim3 grid((Lx + TX - 1) / TX, (Lt + TT - 1) / TT, nrhs);
+  if (ep.dot_out && (nrhs != 1 || grid.x * grid.y > 608)) return cudaErrorInvalidValue;
   k_wilson_A<R><<<grid, TX * TY, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
-                                         (const cplx_t<R>*)U, (R)diag, Lx, Lt);
+                                         (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
   count_launch();
   return cudaGetLastError();
 }
@@ -244,7 +276,7 @@ cudaError_t link_unitarity(const void* gauge, long long count, double* out, cuda
   template cudaError_t wilson_D<R>(const void*, void*, const void*, double, int, int, int,    \
                                    bool, cudaStream_t);                                       \
   template cudaError_t wilson_A<R>(const void*, void*, const void*, double, int, int, int,    \
-                                   void*, cudaStream_t);                                      \
+                                   const Epilogue&, cudaStream_t);                            \
   template cudaError_t fold_links<R>(const void*, void*, int, int, cudaStream_t);
 INST(double)
 INST(float)

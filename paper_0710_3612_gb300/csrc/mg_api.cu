@@ -164,19 +164,31 @@ struct ProfScope {
 
 // ----- level operator ------------------------------------------------------
 // weights for coarse levels: 0 = F64, 1 = F32, 2 = BF16
+// out = ca (A_l in) + cu U + cw W per the epilogue (default: out = A_l in).
 template <typename R>
-void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int weights) {
+void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int weights,
+                 const Epilogue& ep = Epilogue()) {
   Level& L = h->lv[l];
   ProfScope prof(h, l == 0 ? (sizeof(R) == 8 ? MG_KF_FINE_A64 : MG_KF_FINE_A) : MG_KF_COARSE);
   if (l == 0) {
     const double diag = 4.0 + h->mass;
     const void* U = sizeof(R) == 8 ? (const void*)h->U64 : (const void*)h->U32;
-    ck(h, wilson_A<R>(in, out, U, diag, L.Lx, L.Lt, nrhs, nullptr, h->s), "wilson_A");
+    ck(h, wilson_A<R>(in, out, U, diag, L.Lx, L.Lt, nrhs, ep, h->s), "wilson_A");
   } else {
     const void* A = weights == W_F64 ? (const void*)L.A64
                     : weights == W_F32 ? (const void*)L.A32 : L.A16;
-    ck(h, coarse_apply(in, out, A, weights, L.Lx, L.Lt, L.n, nrhs, h->s), "coarse_apply");
+    ck(h, coarse_apply(in, out, A, weights, L.Lx, L.Lt, L.n, nrhs, ep, h->s), "coarse_apply");
   }
+}
+
+Epilogue ep_lincomb(double ca, const void* U, double cu, const void* W = nullptr, double cw = 0.0) {
+  Epilogue e;
+  e.ca = ca;
+  e.U = U;
+  e.cu = cu;
+  e.W = W;
+  e.cw = cw;
+  return e;
 }
 
 // ----- coarsest solve: FP32 explicit inverse refined in FP64 ----------------
@@ -185,8 +197,7 @@ void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
   ProfScope prof(h, MG_KF_COARSEST);
   ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, h->gemv_part, false, h->s), "coarsest gemv");
   for (int it = 0; it < steps; ++it) {
-    apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64);
-    ck(h, sub_from<double>(b, h->cr, h->Nc, h->s), "coarsest residual");
+    apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64, ep_lincomb(-1.0, b, 1.0));
     ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, h->gemv_part, true, h->s),
        "coarsest gemv");
   }
@@ -213,14 +224,10 @@ void vcycle(mg_handle* h, int l, const void* b, void* x) {
   void** w = f64 ? L.w64 : L.w32;
   void** wc = f64 ? C.w64 : C.w32;
   void* r = w[2];
-  void* t = w[3];
-  const long long n = L.count();
   // 1. x = R b = c0 b + c1 A b
-  apply_level<R>(h, l, b, t, 1, weights);
-  ck(h, lincomb<R>(x, L.c0, b, L.c1, t, 0.0, nullptr, n, 1, h->s), "smooth");
+  apply_level<R>(h, l, b, x, 1, weights, ep_lincomb(L.c1, b, L.c0));
   // 2. r_c = P^dagger (b - A x)
-  apply_level<R>(h, l, x, t, 1, weights);
-  ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
+  apply_level<R>(h, l, x, r, 1, weights, ep_lincomb(-1.0, b, 1.0));
   const void* Vst = f64 ? (const void*)L.Vst64 : (const void*)L.Vst32;
   {
     ProfScope prof(h, MG_KF_TRANSFER);
@@ -234,11 +241,9 @@ void vcycle(mg_handle* h, int l, const void* b, void* x) {
     ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, true, h->s),
      "prolong");
   }
-  // 5. x = x + R (b - A x)
-  apply_level<R>(h, l, x, t, 1, weights);
-  ck(h, lincomb<R>(r, 1.0, b, -1.0, t, 0.0, nullptr, n, 1, h->s), "residual");
-  apply_level<R>(h, l, r, t, 1, weights);
-  ck(h, lincomb<R>(x, 1.0, x, L.c0, r, L.c1, t, n, 1, h->s), "post-smooth");
+  // 5. x = x + R (b - A x):  r = b - A x, then x = x + c0 r + c1 A r
+  apply_level<R>(h, l, x, r, 1, weights, ep_lincomb(-1.0, b, 1.0));
+  apply_level<R>(h, l, r, x, 1, weights, ep_lincomb(L.c1, r, L.c0, x, 1.0));
 }
 
 // ----- setup pieces ---------------------------------------------------------
@@ -414,45 +419,69 @@ void free_all(mg_handle* h) {
 // CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with r+ = r - alpha A p),
 // so that rounding in the low-precision preconditioner does not break the
 // recursion.  Returns iterations; x receives the solution.
-void precondition(mg_handle* h, int pmode) {
+// q = A p and <p, q> (fused when the kernel's block count allows it).
+void apply_pq(mg_handle* h) {
   const long long n = h->lv[0].count();
-  void *r = h->sv64[1], *z = h->sv64[4];
-  if (pmode == 1) {
-    vcycle<double>(h, 0, r, z);
-  } else if (pmode == 2) {
-    ck(h, convert_f64_f32(r, h->sv32[1], n, h->s), "to f32");
-    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
-    ck(h, convert_f32_f64(h->sv32[4], z, n, h->s), "to f64");
-  } else {
-    ck(h, cudaMemcpyAsync(z, r, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  const Level& F = h->lv[0];
+  Epilogue ep;
+  const long long ctas = (long long)((F.Lx + 31) / 32) * ((F.Lt + 7) / 8);
+  if (ctas <= 608) {
+    ep.dot_ws = h->partials;
+    ep.dot_out = h->scal + S_PQ;
   }
+  apply_level<double>(h, 0, h->sv64[2], h->sv64[3], 1, W_F64, ep);
+  if (!ep.dot_out)
+    ck(h, dot<double>(h->sv64[2], h->sv64[3], n, 1, h->partials, h->scal + S_PQ, h->s), "dot");
 }
 
-// One CG iteration after q = A p: update x, r; precondition; new direction.
+// x += alpha p, r -= alpha q, |r|^2 (and the FP32 copy of r for pmode 2).
 void pcg_update(mg_handle* h, void* x, int pmode) {
-  (void)pmode;
   const long long n = h->lv[0].count();
-  void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3];
   double* s = h->scal;
-  ck(h, dot<double>(p, q, n, 1, h->partials, s + S_PQ, h->s), "dot");
-  ck(h, cg_xr<double>(x, r, p, q, s + S_RZ, s + S_PQ, nullptr, n, 1, h->partials, s + S_RR, h->s), "cg_xr");
+  ck(h, cg_xr<double>(x, h->sv64[1], h->sv64[2], h->sv64[3], s + S_RZ, s + S_PQ, nullptr, n, 1,
+                      h->partials, s + S_RR, h->s, pmode == 2 ? h->sv32[1] : nullptr),
+     "cg_xr");
 }
 
+// Preconditioned residual and new search direction.
+//   pmode 0: p = r + (|r+|^2/|r|^2) p
+//   pmode 1: z = V64 r, p = z + (<r+,z+>/<r,z>) p
+//   pmode 2: z32 = V32 r32, p = z32 - (Re<z32, q>/<p, q>) p  (flexible)
 void pcg_direction(mg_handle* h, int pmode) {
   const long long n = h->lv[0].count();
   void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
   double* s = h->scal;
-  precondition(h, pmode);
   if (pmode == 2) {
-    // beta = -Re<z+, q> / <p, q>;  rz = <r+, z+> for the next alpha
-    ck(h, dot<double>(z, q, n, 1, h->partials, s + S_T0, h->s), "dot");
-    ck(h, cg_p_pr(p, z, s + S_T0, s + S_PQ, n, h->s), "cg_p");
-    ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
-  } else {
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
+    ck(h, dot2_zq_rz(h->sv32[4], q, r, n, h->partials, s + S_T0, h->s), "dot2");
+    ck(h, cg_p_pr(p, h->sv32[4], s + S_T0, s + S_PQ, s + S_RZ, n, h->s), "cg_p");
+  } else if (pmode == 1) {
+    vcycle<double>(h, 0, r, z);
     ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
     ck(h, cg_p<double>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
     ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+  } else {
+    ck(h, cg_p<double>(p, r, s + S_RR, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
   }
+}
+
+// First direction: p = z0 = M r0, rz = <r0, z0>.
+void pcg_start(mg_handle* h, int pmode) {
+  const long long n = h->lv[0].count();
+  void *r = h->sv64[1], *p = h->sv64[2], *z = h->sv64[4];
+  double* s = h->scal;
+  if (pmode == 2) {
+    ck(h, convert_f64_f32(r, h->sv32[1], n, h->s), "to f32");
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
+    ck(h, convert_f32_f64(h->sv32[4], p, n, h->s), "to f64");
+  } else if (pmode == 1) {
+    vcycle<double>(h, 0, r, z);
+    ck(h, cudaMemcpyAsync(p, z, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  } else {
+    ck(h, cudaMemcpyAsync(p, r, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  }
+  ck(h, dot<double>(r, p, n, 1, h->partials, s + S_RZ, h->s), "dot");
 }
 
 // Captures the CG loop body into the body of a conditional WHILE node: the
@@ -479,7 +508,7 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
   ck(h, cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal), "begin capture");
   try {
-    apply_level<double>(h, 0, h->sv64[2], h->sv64[3], 1, W_F64);
+    apply_pq(h);
     pcg_update(h, x, pmode);
     pcg_direction(h, pmode);
     ck(h, cg_control(h->scal + S_RR, h->scal + S_PQ, h->scal + S_STOP, h->dctrl, cond, h->s), "control");
@@ -518,7 +547,7 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode
         mg_status& st) {
   Level& F = h->lv[0];
   const long long n = F.count();
-  void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
+  void* r = h->sv64[1];
   double* s = h->scal;
   st = MG_OK;
   ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
@@ -527,10 +556,11 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode
   if (bn == 0.0) return 0;
   if (!(bn == bn) || std::isinf(bn)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite right-hand side"; return 0; }
   ck(h, cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  precondition(h, pmode);
-  if (pmode) h->vcycles++;
-  ck(h, cudaMemcpyAsync(p, z, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZ, h->s), "dot");
+  pcg_start(h, pmode);
+  if (pmode) {
+    h->vcycles++;
+    h->fine_applies += 4;
+  }
   const double stop = tol * tol * bn;
   const int per_it_fine = 1 + (pmode ? 4 : 0);
   if (h->use_graphs && !h->prof_on) {
@@ -560,7 +590,7 @@ int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode
   }
   int it = 0;
   while (it < maxiter) {
-    apply_level<double>(h, 0, p, q, 1, W_F64);
+    apply_pq(h);
     h->fine_applies++;
     pcg_update(h, x, pmode);
     ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
