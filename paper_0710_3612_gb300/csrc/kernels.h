@@ -102,6 +102,9 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, const Epilogue& ep, cudaStream_t s);
+// Thread blocks wilson_A launches per right-hand side (the fused <x, A x>
+// needs at most 608).
+int wilson_A_ctas(int Lx, int Lt, bool f64);
 // links: gauge complex128 [2][V] -> folded links of precision R
 template <typename R>
 cudaError_t fold_links(const void* gauge, void* U, int Lx, int Lt, cudaStream_t s);

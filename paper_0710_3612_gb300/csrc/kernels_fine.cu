@@ -71,12 +71,10 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
 // halo, and applies D^dagger to it -- one pass over psi and the links.
 // Coordinates wrap periodically (the antiperiodic sign sits in the links), so
 // lattices that are not multiples of the tile work unchanged.
-// Tile geometry per precision: FP32 32 x 16 (two rows per thread), FP64
-// 32 x 8 (shared memory stays below 48 KB).
-template <typename R> struct tile;
-template <> struct tile<float> { static constexpr int RPT = 2; };
-template <> struct tile<double> { static constexpr int RPT = 1; };
-static constexpr int TX = 32, TY = 8;
+// Tile geometry: TX x (TY * RPT) sites per CTA of TX x TY threads.  Large
+// lattices use 32 x 16 (FP32, two rows per thread) or 32 x 8 (FP64, shared
+// memory below 48 KB); lattices with fewer than two tiles per SM use 16 x 8
+// tiles so that every SM gets work.
 
 template <typename R> struct spinor_t;              // both spin components of a site
 template <> struct spinor_t<float> { using type = float4; };
@@ -109,12 +107,12 @@ __device__ __forceinline__ void st_spinor(double2* p, double4_32a v) {
 
 __device__ __forceinline__ int wrap(int g, int L) { return g < 0 ? g + L : (g >= L ? g - L : g); }
 
-template <typename R>
+template <typename R, int TX, int TY, int RPT>
 __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict__ in,
                                                      cplx_t<R>* out,
                                                      const cplx_t<R>* __restrict__ U, R diag,
                                                      int Lx, int Lt, Epilogue ep) {
-  constexpr int RPT = tile<R>::RPT, TT = TY * RPT;
+  constexpr int TT = TY * RPT;
   constexpr int PW = TX + 4, PH = TT + 4;     // psi region [-2, TX+1] x [-2, TT+1]
   constexpr int DW = TX + 2, DH = TT + 2;     // D psi region [-1, TX] x [-1, TT]
   constexpr int UW = TX + 3, UH = TT + 3;     // link region [-2, TX] x [-2, TT]
@@ -215,14 +213,34 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   }
 }
 
+int wilson_A_ctas(int Lx, int Lt, bool f64) {
+  const int big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16));
+  if (big >= 2 * 152) return big;
+  return ((Lx + 15) / 16) * ((Lt + 7) / 8);
+}
+
+template <typename R, int TX, int TY, int RPT>
+static void launch_wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
+                            int nrhs, const Epilogue& ep, cudaStream_t s) {
+  dim3 grid((Lx + TX - 1) / TX, (Lt + TY * RPT - 1) / (TY * RPT), nrhs);
+  k_wilson_A<R, TX, TY, RPT><<<grid, TX * TY, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
+                                                      (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
+}
+
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, const Epilogue& ep, cudaStream_t s) {
-  constexpr int TT = TY * tile<R>::RPT;
-  dim3 grid((Lx + TX - 1) / TX, (Lt + TT - 1) / TT, nrhs);
-  if (ep.dot_out && (nrhs != 1 || grid.x * grid.y > 608)) return cudaErrorInvalidValue;
-  k_wilson_A<R><<<grid, TX * TY, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
-                                         (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
+  const bool f64 = sizeof(R) == 8;
+  const int ctas = wilson_A_ctas(Lx, Lt, f64);
+  if (ep.dot_out && (nrhs != 1 || ctas > 608)) return cudaErrorInvalidValue;
+  const bool big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16)) >= 2 * 152;
+  if (!big) {
+    launch_wilson_A<R, 16, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
+  } else if constexpr (sizeof(R) == 8) {
+    launch_wilson_A<R, 32, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
+  } else {
+    launch_wilson_A<R, 32, 8, 2>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
+  }
   count_launch();
   return cudaGetLastError();
 }

@@ -424,8 +424,7 @@ void apply_pq(mg_handle* h) {
   const long long n = h->lv[0].count();
   const Level& F = h->lv[0];
   Epilogue ep;
-  const long long ctas = (long long)((F.Lx + 31) / 32) * ((F.Lt + 7) / 8);
-  if (ctas <= 608) {
+  if (wilson_A_ctas(F.Lx, F.Lt, true) <= 608) {
     ep.dot_ws = h->partials;
     ep.dot_out = h->scal + S_PQ;
   }
