@@ -215,6 +215,22 @@ typedef enum {
 mg_status mg_profile_enable(mg_handle* h, int on);
 mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long* calls);
 
+/* Allocation-free variant of mg_apply_A (FP64, one right-hand side) that also
+ * returns <x, A x>.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code that records its work into a
+ * CUDA graph under stream capture, where allocation is not allowed, or code
+ * that runs under a fixed device-memory budget.  out = A in (complex128
+ * [Lt][Lx][2], device) and *xAx (device double[2]: real, imaginary part of
+ * <in, A in>, deterministic) are written with the same fused kernel as
+ * mg_apply_A; its reduction scratch lives in a 10 KB array inside the library
+ * (every GPU that loads the library keeps it until exit) instead of the
+ * handle's workspace.  Maximum size: lattices needing at most 608 thread
+ * blocks (Lx * Lt <= 155648 sites, e.g. 384 x 384); larger ones get
+ * MG_ERR_ARG.  The first call on a device looks up the array's device address
+ * (make that call before any stream capture).  Calls share the array: calls
+ * whose kernels overlap on the GPU race and must be ordered by the caller. */
+mg_status mg_apply_A_dot_noalloc(mg_handle* h, const void* in, void* out, double* xAx);
+
 /* Message of the last error on h (h == NULL: last mg_setup / mg_block_map
  * error of the calling thread). */
 const char* mg_last_error(const mg_handle* h);

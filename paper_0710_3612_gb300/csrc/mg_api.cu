@@ -970,6 +970,48 @@ mg_status mg_get_level(const mg_handle* h, int level, int* Lx, int* Lt, int* ndo
 
 }  // extern "C"
 
+// ----- allocation-free fused A with <x, A x> -----------------------------------
+// Reduction scratch for mg_apply_A_dot_noalloc: 64 tickets (as doubles) plus
+// 2 x 608 partial sums -- the layout of the handle's reduction workspace.
+namespace {
+constexpr int NOALLOC_BLOCKS = 608;
+constexpr int NOALLOC_DOUBLES = 64 + 2 * NOALLOC_BLOCKS;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};   // device address per device
+}  // namespace
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+extern "C" mg_status mg_apply_A_dot_noalloc(mg_handle* h, const void* in, void* out,
+                                            double* xAx) {
+  if (!h) return MG_ERR_ARG;
+  if (!in || !out || !xAx) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  const Level& F = h->lv[0];
+  if (wilson_A_ctas(F.Lx, F.Lt, true) > NOALLOC_BLOCKS) {
+    h->err = "mg_apply_A_dot_noalloc: lattice needs more than " +
+             std::to_string(NOALLOC_BLOCKS) + " thread blocks (limit 155648 sites)";
+    return MG_ERR_ARG;
+  }
+  return guarded(h, [&]() {
+    int dev = 0;
+    ck(h, cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(h, MG_ERR_ARG, "device ordinal out of range");
+    if (!g_noalloc_ptr[dev]) {
+      // once per device, with that device current: the device address of the array
+      void* p = nullptr;
+      ck(h, cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    double* ws = g_noalloc_ptr[dev];
+    // the tickets must start at zero (the last block of a reduction clears them,
+    // but a previous kernel may have been interrupted)
+    ck(h, cudaMemsetAsync(ws, 0, 64 * sizeof(double), h->s), "clear tickets");
+    Epilogue ep;
+    ep.dot_ws = ws;
+    ep.dot_out = xAx;
+    ck(h, wilson_A<double>(in, out, h->U64, 4.0 + h->mass, F.Lx, F.Lt, 1, ep, h->s), "wilson_A");
+  });
+}
+
 // Gather of Vst [V][2][Nv][h] into [Nv][V][2h] (complex128).
 __global__ void k_vst_to_vectors(const double2* __restrict__ Vst, double2* __restrict__ out, int V,
                                  int Nv, int h) {

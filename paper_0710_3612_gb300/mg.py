@@ -63,6 +63,7 @@ _SIGS = {
     "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
+    "mg_apply_A_dot_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -220,6 +221,12 @@ def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
 KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64 = range(7)
 
 
+def mg_apply_A_dot_noalloc(h, inp, out, xAx):
+    import torch
+    _check(lib().mg_apply_A_dot_noalloc(h, _ptr(inp, torch.complex128), _ptr(out, torch.complex128),
+                                        _ptr(xAx, torch.float64)), h)
+
+
 def mg_kernel_launches() -> int:
     return int(lib().mg_kernel_launches())
 
@@ -247,7 +254,7 @@ def mg_destroy(h):
 class Multigrid:
     """Owns one mg_handle: setup at construction, solve/apply methods, destroy on close."""
 
-    def __init__(self, gauge, mass, blocks, Nv, noise, stream=None, **params):
+    def __init__(self, gauge, mass, blocks, Nv, noise=None, stream=None, **params):
         _, Lt, Lx = gauge.shape
         self.Lx, self.Lt = Lx, Lt
         self.params = make_params(Lx, Lt, list(blocks), list(Nv), noise, **params)
