@@ -93,7 +93,8 @@ typedef struct {
                                            the coarsest solve inside the FP32
                                            V-cycle (1)                           */
   int vcycle_coarse_bf16;               /* mixed solver: 1 = coarse blocks of the
-                                           FP32 V-cycle in BF16, 0 = FP32 (0)    */
+                                           FP32 V-cycle in BF16 (FP32 accumulate),
+                                           0 = FP32 (1)                          */
 } mg_params;
 
 typedef struct {

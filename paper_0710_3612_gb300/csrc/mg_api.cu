@@ -698,7 +698,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->coarsest_tol = 1e-13;
   p->coarsest_refine_max = 12;
   p->inner_coarsest_refine = 1;
-  p->vcycle_coarse_bf16 = 0;
+  p->vcycle_coarse_bf16 = 1;
   return MG_OK;
 }
 
