@@ -168,7 +168,7 @@ def gpu_bench(args):
                     record.append((m, e0, e1, info[0]))
             prof = None
             if profile:
-                prof = {f: mg.mg_profile_read(h, f) for f in range(7)}
+                prof = {f: mg.mg_profile_read(h, f) for f in range(8)}
             return prof
         finally:
             mg.mg_destroy(h)
@@ -281,47 +281,55 @@ def gpu_bench(args):
 
 
 FAM_NAMES = ["fine_A_f32", "coarse_apply", "transfer", "coarsest_solve", "coarsest_inverse",
-             "galerkin", "fine_A_f64"]
+             "galerkin", "fine_A_f64", "coarsest_dense_gemv"]
 
 
 def roofline(prof, wl, peaks):
-    """Dominant family by device time in one profiled step; achieved = algorithmic
-    bytes (or flops) per call / average call duration."""
+    """Dominant kernel family by device time in one profiled (eager) step, the
+    coarsest-solve family split into its dense GEMV and the rest; achieved =
+    algorithmic bytes (or flops) per call / average call duration."""
+    prof = dict(prof)
+    # the coarsest-solve family contains the dense GEMV calls: count the rest only
+    prof[3] = (max(prof[3][0] - prof[7][0], 0.0), prof[3][1])
     fam = max(prof, key=lambda f: prof[f][0])
     ms, calls = prof[fam]
     Lx, Lt = wl["Lx"], wl["Lt"]
     V = Lx * Lt
     Nv1, Nv2 = wl["Nv"]
-    V2 = V // 16
-    V3 = V2 // 4
-    n3 = 2 * Nv2
-    N3 = V3 * n3
+    b1, b2 = wl["blocks"]
+    V2 = V // (b1[0] * b1[1])
+    V3 = V2 // (b2[0] * b2[1])
+    N3 = V3 * 2 * Nv2
     ld = (N3 + 63) // 64 * 64
+    ntiles = (ld // 64) * (ld // 64 + 1) // 2
     shares = {FAM_NAMES[f]: round(prof[f][0], 3) for f in prof}
     per_call_s = ms / 1000.0 / max(calls, 1)
     out = {"kernel": FAM_NAMES[fam], "calls": calls, "avg_us": round(per_call_s * 1e6, 3),
-           "family_ms_in_step": shares, "traffic": None}
-    if fam == 4:       # Gauss-Jordan inverse: 8 ld^3 real flops per inversion (FP32 SIMT)
-        flops = 8.0 * ld ** 3
+           "family_ms_in_step": shares, "traffic": None,
+           "timing": "CUDA events around each call in one eager (non-graph) step"}
+    if fam == 4:       # Hermitian Gauss-Jordan: 4 ld^3 real flops (lower triangle)
+        flops = 4.0 * ld ** 3
         peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         out.update({"bound": "alu", "achieved": round(flops / per_call_s / 1e12, 3),
                     "peak": round(peak, 1), "unit": "TFLOP/s",
                     "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"})
     else:
         if fam == 0:
-            byts = 48.0 * V
+            byts = 48.0 * V                              # psi in/out + links, FP32
         elif fam == 6:
             byts = 96.0 * V
-        elif fam == 1:      # mostly the BF16 V-cycle applies on level 2
+        elif fam == 1:      # BF16 V-cycle applies on level 2 dominate
             byts = V2 * (9 * (2 * Nv1) ** 2 * 4 + 2 * 2 * Nv1 * 8)
         elif fam == 2:
             byts = V * (2 * 8 + 2 * Nv1 * 8) + V2 * 2 * Nv1 * 8
-        elif fam == 3:      # GEMV over the FP32 inverse dominates
-            byts = 8.0 * ld * ld * 3
+        elif fam == 7:      # packed lower-triangular tiles of the FP32 inverse
+            byts = ntiles * 64 * 64 * 8.0 + ntiles * 2 * 64 * 8 * 2
+        elif fam == 3:
+            byts = V3 * 9 * (2 * Nv2) ** 2 * 16.0
         else:
             byts = 16.0 * V2 * 9 * (2 * Nv1) ** 2
         out.update({"bound": "hbm", "achieved": round(byts / per_call_s / 1e9, 1),
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s"})
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes_per_call": int(byts)})
     out["frac"] = round(out["achieved"] / out["peak"], 4)
     out["peak_note"] = f"of {peaks['src']}"
     return out
@@ -488,6 +496,54 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def ncu_case(args):
+    """Small cases for kernel-level ncu captures (a few launches of one kernel):
+    stencil -- fused FP32 A on a 2048 x 2048 lattice (about 200 MB per launch,
+               above L2); coarse -- BF16 coarse apply on level 2 of the
+               benchmark workload; coarsest -- the coarsest solve (packed FP32
+               GEMV + FP64 refinement) of the benchmark workload; vcycle -- one
+               FP32 V-cycle."""
+    import torch
+    from paper_0710_3612_gb300 import mg
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if args.ncu_case == "stencil":
+        L = 2048
+        U = torch.polar(torch.ones(2, L, L, dtype=torch.float64, device=dev),
+                        torch.rand(2, L, L, dtype=torch.float64, device=dev)).contiguous()
+        h = mg.mg_setup(U, 0.1, mg.make_params(L, L, [], []), stream)
+        x = torch.randn(L * L * 2, dtype=torch.complex64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(4):
+            mg.mg_apply_A(h, x, y, 1, mg.PREC_F32)
+    else:
+        wl, crit, U, noise, chi, masses = workload_inputs(args.workload)
+        nd = torch.from_numpy(noise).to(dev)
+        h = mg.mg_setup(torch.from_numpy(U).to(dev), masses[0],
+                        mg.make_params(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], nd,
+                                       setup_sweeps=wl["setup_sweeps"]), stream)
+        if args.ncu_case == "coarse":
+            Lx, Lt, n, _ = mg.mg_get_level(h, 2)
+            x = torch.randn(Lx * Lt * n, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(4):
+                mg.mg_apply_coarse(h, 2, x, y, 1, mg.PREC_BF16)
+        elif args.ncu_case == "coarsest":
+            Lx, Lt, n, _ = mg.mg_get_level(h, len(wl["blocks"]) + 1)
+            x = torch.randn(Lx * Lt * n, dtype=torch.complex128, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(4):
+                mg.mg_coarsest_solve(h, x, y)
+        else:
+            x = torch.randn(wl["Lx"] * wl["Lt"] * 2, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(4):
+                mg.mg_vcycle(h, x, y, mg.PREC_F32)
+    torch.cuda.synchronize()
+    mg.mg_destroy(h)
+    print(json.dumps({"ncu_case": args.ncu_case, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,8 +557,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
+    ap.add_argument("--ncu-case", choices=["stencil", "coarse", "coarsest", "vcycle"],
+                    help="run a small kernel case for an ncu capture and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_case:
+        ncu_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_bench(args)

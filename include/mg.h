@@ -211,7 +211,9 @@ typedef enum {
   MG_KF_GALERKIN = 5,   /* Galerkin coarse-operator build                      */
   MG_KF_FINE_A64 = 6,   /* A = D^dagger D on the fine lattice in FP64 (MG_KF_FINE_A
                            counts the FP32 applications)                        */
-  MG_KF_COUNT = 7
+  MG_KF_DENSE = 7,      /* coarsest-level packed Hermitian GEMV (part of
+                           MG_KF_COARSEST)                                      */
+  MG_KF_COUNT = 8
 } mg_kernel_family;
 mg_status mg_profile_enable(mg_handle* h, int on);
 mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long* calls);

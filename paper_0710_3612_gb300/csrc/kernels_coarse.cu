@@ -527,14 +527,19 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 // Sweep (Gauss-Jordan) inversion.  Sweeping pivot block k of M with
 // P = M_kk^{-1}:  M_ij -= M_ik P M_kj (i, j != k);  M_kj <- P M_kj;
 // M_ik <- -M_ik P;  M_kk <- P.  After all pivots M holds its inverse.
+//
+// The matrix is Hermitian and, after sweeping the blocks K = {0..k-1}, so is
+// its swept form up to sign: S_ij = S_ji^H when i, j are both swept or both
+// unswept, S_ij = -S_ji^H otherwise.  Only the lower triangle is kept
+// current: the panels of column k and row k are rebuilt from it and the
+// rank-32 update touches lower tiles only (half the flops).  Upper entries of
+// diagonal 64 x 64 tiles may go stale; the packing step rebuilds them from the
+// lower triangle.  Two kernels per pivot block.
 static constexpr int GJB = 32;
 
-__global__ void __launch_bounds__(GJB* GJB) k_gj_diag(float2* __restrict__ M, int N, int k,
-                                                      float2* __restrict__ P) {
-  __shared__ float2 a[GJB][GJB + 1];
-  const int r = threadIdx.y, c = threadIdx.x;
-  a[r][c] = M[(long long)(k * GJB + r) * N + k * GJB + c];
-  __syncthreads();
+// In-place sweep of the 32 x 32 pivot block held in shared memory (one entry
+// per thread of a 32 x 32 block).
+__device__ __forceinline__ void sweep_diag(float2 (*a)[GJB + 1], int r, int c) {
   for (int p = 0; p < GJB; ++p) {
     const float2 piv = a[p][p];
     const float den = piv.x * piv.x + piv.y * piv.y;
@@ -549,20 +554,13 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_diag(float2* __restrict__ M, in
     a[r][c] = v;
     __syncthreads();
   }
-  P[r * GJB + c] = a[r][c];
 }
 
-// The matrix is Hermitian and, after sweeping the blocks K = {0..k-1}, so is
-// its swept form up to sign: S_ij = S_ji^H when i, j are both swept or both
-// unswept, S_ij = -S_ji^H otherwise.  Only the lower triangle is kept
-// current: the panels of column k and row k are rebuilt from it and the
-// rank-32 update touches lower tiles only (half the flops).  Upper entries of
-// diagonal 64 x 64 tiles may go stale; the packing step rebuilds them from the
-// lower triangle.
-//
-// Panel kernel: Cold_i = M_ik (all i != k), Cn_i = M_ik P, R_j = P M_kj.
+// Every CTA inverts the pivot block (P), then forms one panel block:
+// Cold_b = M_bk, Cn_b = M_bk P (column panel), R_b = P M_kb (row panel); the
+// column-panel CTA of the pivot itself stores P.
 __global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict__ M, int N, int k,
-                                                       const float2* __restrict__ P,
+                                                       float2* __restrict__ Pout,
                                                        float2* __restrict__ Cold,
                                                        float2* __restrict__ Cn,
                                                        float2* __restrict__ Rp) {
@@ -570,8 +568,14 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict_
   const int nb = N / GJB;
   const int b = blockIdx.x % nb, col_panel = blockIdx.x < nb;
   const int r = threadIdx.y, c = threadIdx.x;
-  if (b == k) return;
-  sP[r][c] = P[r * GJB + c];
+  if (b == k && !col_panel) return;
+  sP[r][c] = M[(long long)(k * GJB + r) * N + k * GJB + c];
+  __syncthreads();
+  sweep_diag(sP, r, c);
+  if (b == k) {
+    Pout[r * GJB + c] = sP[r][c];
+    return;
+  }
   if (col_panel) {
     // M_bk: stored below the diagonal for b > k; for b < k it is -(M_kb)^H
     if (b > k) {
@@ -601,10 +605,13 @@ __global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict_
   }
 }
 
-// M_ij -= M_ik (P M_kj) = Cold_i R_j on lower 64 x 64 tiles (i, j != k);
-// 4 x 4 outputs per thread.
+// Lower 64 x 64 tiles: M_ij -= M_ik (P M_kj) = Cold_i R_j for i, j != k, and
+// the sweep's write-back in the pivot row and column: M_kj = R_j (j < k),
+// M_ik = -Cn_i (i > k), M_kk = P.  4 x 4 outputs per thread.
 __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N, int k,
+                                                   const float2* __restrict__ P,
                                                    const float2* __restrict__ Cold,
+                                                   const float2* __restrict__ Cn,
                                                    const float2* __restrict__ Rp) {
   if (blockIdx.x > blockIdx.y) return;          // upper tile: not kept
   __shared__ float2 sC[64][GJB + 1], sR[GJB][64 + 1];
@@ -639,36 +646,25 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int row = bi + tr + 16 * u;
-    if (row >= kb0 && row < kb1) continue;
+    const bool prow = row >= kb0 && row < kb1;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int col = bj + tc + 16 * v;
-      if (col >= kb0 && col < kb1) continue;
+      const bool pcol = col >= kb0 && col < kb1;
       float2* p = M + (long long)row * N + col;
-      *p = csub(*p, acc[u][v]);
+      if (prow && pcol) {
+        *p = P[(row - kb0) * GJB + (col - kb0)];
+      } else if (prow) {
+        if (col < kb0) *p = Rp[(long long)(row - kb0) * N + col];
+      } else if (pcol) {
+        if (row >= kb1) {
+          const float2 w = Cn[(long long)row * GJB + (col - kb0)];
+          *p = make_float2(-w.x, -w.y);
+        }
+      } else {
+        *p = csub(*p, acc[u][v]);
+      }
     }
-  }
-}
-
-// Lower-triangle write-back: M_bk = -Cn_b (b > k), M_kb = R_b (b < k), M_kk = P.
-__global__ void __launch_bounds__(GJB* GJB) k_gj_write(float2* __restrict__ M, int N, int k,
-                                                       const float2* __restrict__ P,
-                                                       const float2* __restrict__ Cn,
-                                                       const float2* __restrict__ Rp) {
-  const int nb = N / GJB;
-  const int r = threadIdx.y, c = threadIdx.x;
-  if (blockIdx.x == 2 * nb) {
-    M[(long long)(k * GJB + r) * N + k * GJB + c] = P[r * GJB + c];
-    return;
-  }
-  const int b = blockIdx.x % nb;
-  if (blockIdx.x < nb) {
-    if (b <= k) return;
-    const float2 v = Cn[(long long)(b * GJB + r) * GJB + c];
-    M[(long long)(b * GJB + r) * N + k * GJB + c] = make_float2(-v.x, -v.y);
-  } else {
-    if (b >= k) return;
-    M[(long long)(k * GJB + r) * N + b * GJB + c] = Rp[(long long)r * N + b * GJB + c];
   }
 }
 
@@ -681,10 +677,8 @@ cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s
   float2* Rp = Cn + (long long)N * GJB;
   const int nb = N / GJB;
   for (int k = 0; k < nb; ++k) {
-    k_gj_diag<<<1, dim3(GJB, GJB), 0, s>>>(M, N, k, P); count_launch();
     k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cold, Cn, Rp); count_launch();
-    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, Cold, Rp); count_launch();
-    k_gj_write<<<2 * nb + 1, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cn, Rp); count_launch();
+    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, P, Cold, Cn, Rp); count_launch();
   }
   return cudaGetLastError();
 }

@@ -195,9 +195,13 @@ Epilogue ep_lincomb(double ca, const void* U, double cu, const void* W = nullptr
 // x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r.
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
   ProfScope prof(h, MG_KF_COARSEST);
-  ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, h->gemv_part, false, h->s), "coarsest gemv");
+  {
+    ProfScope pd(h, MG_KF_DENSE);
+    ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, h->gemv_part, false, h->s), "coarsest gemv");
+  }
   for (int it = 0; it < steps; ++it) {
     apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64, ep_lincomb(-1.0, b, 1.0));
+    ProfScope pd(h, MG_KF_DENSE);
     ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, h->gemv_part, true, h->s),
        "coarsest gemv");
   }

@@ -218,7 +218,7 @@ def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
                               _stream_ptr(stream)))
 
 
-KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64 = range(7)
+KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64, KF_DENSE = range(8)
 
 
 def mg_apply_A_dot_noalloc(h, inp, out, xAx):
