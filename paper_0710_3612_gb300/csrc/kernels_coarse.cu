@@ -770,11 +770,14 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
   while (I * (I + 1) / 2 > k) --I;
   const int J = k - I * (I + 1) / 2;
   const float4* src = (const float4*)(P + (long long)k * HT * HT);
-  for (int q = threadIdx.x; q < HT * HT / 2; q += 256) {
-    const float4 v = src[q];
-    const int e = 2 * q, r = e / HT, c = e % HT;
-    T[r][c] = make_float2(v.x, v.y);
-    T[r][c + 1] = make_float2(v.z, v.w);
+  float4 buf[HT * HT / 2 / 256];                 // all 8 loads in flight before the stores
+#pragma unroll
+  for (int u = 0; u < HT * HT / 2 / 256; ++u) buf[u] = __ldcs(src + threadIdx.x + 256 * u);
+#pragma unroll
+  for (int u = 0; u < HT * HT / 2 / 256; ++u) {
+    const int e = 2 * (threadIdx.x + 256 * u), r = e / HT, c = e % HT;
+    T[r][c] = make_float2(buf[u].x, buf[u].y);
+    T[r][c + 1] = make_float2(buf[u].z, buf[u].w);
   }
   if (threadIdx.x < HT) {
     const int gi = I * HT + threadIdx.x, gj = J * HT + threadIdx.x;

@@ -213,6 +213,137 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   }
 }
 
+// Register-streaming A = D^dagger D for large lattices.  A warp owns a strip
+// of 32 consecutive x sites (lanes 2..29 produce output, lanes 0, 1, 30, 31
+// are halo) and marches along t over SROWS output rows, keeping three rows of
+// psi, two rows of D psi and the needed link rows in registers; x neighbours
+// come from warp shuffles, t neighbours from the row window.  No shared
+// memory and no block barriers: every loaded byte is used from registers.
+// Row r + 2 of psi and the links of row r + 1 are prefetched one step ahead.
+static constexpr int SROWS = 32;
+static constexpr int SOUT = 28;            // output lanes per warp
+
+template <typename C>
+__device__ __forceinline__ C shfl_c(C v, int delta, bool up) {
+  C r;
+  if (up) {
+    r.x = __shfl_up_sync(0xffffffffu, v.x, delta);
+    r.y = __shfl_up_sync(0xffffffffu, v.y, delta);
+  } else {
+    r.x = __shfl_down_sync(0xffffffffu, v.x, delta);
+    r.y = __shfl_down_sync(0xffffffffu, v.y, delta);
+  }
+  return r;
+}
+
+// D (sf = +1) or D^dagger (sf = -1) at this lane's site for one row: (f0, f1)
+// the row's spinor, fu / fd the rows t+1 / t-1 at this x, ux and ut the links
+// here, utm the t link one row below; the x neighbours and U_x(x-1) come from
+// the adjacent lanes.
+template <typename R>
+__device__ __forceinline__ void dslash_row(cplx_t<R> f0, cplx_t<R> f1, cplx_t<R> fu0,
+                                           cplx_t<R> fu1, cplx_t<R> fd0, cplx_t<R> fd1,
+                                           cplx_t<R> ux, cplx_t<R> ut, cplx_t<R> utm, R diag,
+                                           R sf, cplx_t<R>& o0, cplx_t<R>& o1) {
+  using C = cplx_t<R>;
+  const C xp0 = shfl_c(f0, 1, false), xp1 = shfl_c(f1, 1, false);   // psi(x + 1)
+  const C xm0 = shfl_c(f0, 1, true), xm1 = shfl_c(f1, 1, true);     // psi(x - 1)
+  const C uxm = shfl_c(ux, 1, true);                                // U_x(x - 1)
+  C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0);
+  hop_x<R>(a0, a1, ux, xp0, xp1, sf);
+  hop_x<R>(a0, a1, cconj(uxm), xm0, xm1, -sf);
+  hop_t<R>(a0, a1, ut, fu0, fu1, sf);
+  hop_t<R>(a0, a1, cconj(utm), fd0, fd1, -sf);
+  o0 = mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y);
+  o1 = mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_wilson_A_stream(const cplx_t<R>* __restrict__ in,
+                                                         cplx_t<R>* out,
+                                                         const cplx_t<R>* __restrict__ U, R diag,
+                                                         int Lx, int Lt, Epilogue ep) {
+  using C = cplx_t<R>;
+  const int V = Lx * Lt;
+  const int lane = threadIdx.x & 31;
+  const int strips = (Lx + SOUT - 1) / SOUT;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int row_blocks = (Lt + SROWS - 1) / SROWS;
+  if (w >= strips * row_blocks) return;                  // whole warp
+  const int strip = w % strips, t0 = (w / strips) * SROWS;
+  const int xu = strip * SOUT - 2 + lane;                // unwrapped x
+  const int x = wrap(xu, Lx);
+  const bool writer = lane >= 2 && lane < 30 && xu < Lx;
+  const long long off = (long long)blockIdx.y * V * 2;
+  const int t1 = min(t0 + SROWS, Lt);                    // output rows [t0, t1)
+  auto ld_psi = [&](int t, C& a, C& b) {
+    split(ld_spinor(in + off + 2LL * (x + Lx * wrap(t, Lt))), a, b);
+  };
+  auto ld_u = [&](int t, C& ux, C& ut) {
+    const int g = x + Lx * wrap(t, Lt);
+    ux = U[g];
+    ut = U[V + g];
+  };
+  C pm0, pm1, pc0, pc1, pp0, pp1;          // psi rows r-1, r, r+1
+  C dm0, dm1, dc0, dc1;                    // D psi rows r-2, r-1
+  C uxc, utc, utm;                         // U_x(r), U_t(r), U_t(r-1)
+  C uxo, uto, utmo;                        // the same one row earlier (for D^dagger)
+  C nx0, nx1, nux, nut;                    // prefetched psi row r+2, links row r+1
+  C dummy;
+  ld_psi(t0 - 2, pm0, pm1);
+  ld_psi(t0 - 1, pc0, pc1);
+  ld_psi(t0, pp0, pp1);
+  ld_u(t0 - 2, dummy, utm);
+  ld_u(t0 - 1, uxc, utc);
+  ld_psi(t0 + 1, nx0, nx1);
+  ld_u(t0, nux, nut);
+  dm0 = dm1 = dc0 = dc1 = mk((R)0, (R)0);
+  uxo = uto = utmo = mk((R)0, (R)0);
+  const R ca = (R)ep.ca, cu = (R)ep.cu, cw = (R)ep.cw;
+  const C* EU = (const C*)ep.U;
+  const C* EW = (const C*)ep.W;
+  for (int r = t0 - 1; r <= t1; ++r) {
+    C e0, e1;                                            // D psi at row r
+    dslash_row<R>(pc0, pc1, pp0, pp1, pm0, pm1, uxc, utc, utm, diag, (R)1, e0, e1);
+    if (r >= t0 + 1) {                                   // output row r - 1
+      C o0, o1;
+      dslash_row<R>(dc0, dc1, e0, e1, dm0, dm1, uxo, uto, utmo, diag, (R)-1, o0, o1);
+      if (writer) {
+        const long long g = off + 2LL * (x + Lx * (r - 1));
+        o0 = mk(ca * o0.x, ca * o0.y);
+        o1 = mk(ca * o1.x, ca * o1.y);
+        if (EU) {
+          C u0, u1;
+          split(ld_spinor(EU + g), u0, u1);
+          o0 = mk(o0.x + cu * u0.x, o0.y + cu * u0.y);
+          o1 = mk(o1.x + cu * u1.x, o1.y + cu * u1.y);
+        }
+        if (EW) {
+          C w0, w1;
+          split(ld_spinor(EW + g), w0, w1);
+          o0 = mk(o0.x + cw * w0.x, o0.y + cw * w0.y);
+          o1 = mk(o1.x + cw * w1.x, o1.y + cw * w1.y);
+        }
+        st_spinor(out + g, join(o0, o1));
+      }
+    }
+    dm0 = dc0; dm1 = dc1; dc0 = e0; dc1 = e1;            // shift: row r becomes r - 1
+    uxo = uxc; uto = utc; utmo = utm;
+    pm0 = pc0; pm1 = pc1; pc0 = pp0; pc1 = pp1; pp0 = nx0; pp1 = nx1;
+    utm = utc; uxc = nux; utc = nut;
+    if (r + 1 <= t1) {
+      ld_psi(r + 3, nx0, nx1);
+      ld_u(r + 2, nux, nut);
+    }
+  }
+}
+
+// The streaming kernel serves lattices with enough strips to fill the GPU.
+bool wilson_A_streamed(int Lx, int Lt) {
+  const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);
+  return Lx >= 64 && Lt >= 2 * SROWS && warps >= 8LL * 152;
+}
+
 int wilson_A_ctas(int Lx, int Lt, bool f64) {
   const int big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16));
   if (big >= 2 * 152) return big;
@@ -234,7 +365,11 @@ cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int 
   const int ctas = wilson_A_ctas(Lx, Lt, f64);
   if (ep.dot_out && (nrhs != 1 || ctas > 608)) return cudaErrorInvalidValue;
   const bool big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16)) >= 2 * 152;
-  if (!big) {
+  if (!ep.dot_out && wilson_A_streamed(Lx, Lt)) {
+    const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);
+    k_wilson_A_stream<R><<<dim3((unsigned)((warps + 3) / 4), nrhs), 128, 0, s>>>(
+        (const cplx_t<R>*)in, (cplx_t<R>*)out, (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
+  } else if (!big) {
     launch_wilson_A<R, 16, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
   } else if constexpr (sizeof(R) == 8) {
     launch_wilson_A<R, 32, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
