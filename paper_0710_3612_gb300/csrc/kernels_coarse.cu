@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
   const float4* src = (const float4*)(P + (long long)k * HT * HT);
   float4 buf[HT * HT / 2 / 256];                 // all 8 loads in flight before the stores
 #pragma unroll
-  for (int u = 0; u < HT * HT / 2 / 256; ++u) buf[u] = __ldcs(src + threadIdx.x + 256 * u);
+  for (int u = 0; u < HT * HT / 2 / 256; ++u) buf[u] = src[threadIdx.x + 256 * u];
 #pragma unroll
   for (int u = 0; u < HT * HT / 2 / 256; ++u) {
     const int e = 2 * (threadIdx.x + 256 * u), r = e / HT, c = e % HT;

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(128) k_wilson_A_stream(const cplx_t<R>* __rest
 // The streaming kernel serves lattices with enough strips to fill the GPU.
 bool wilson_A_streamed(int Lx, int Lt) {
   const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);
-  return Lx >= 64 && Lt >= 2 * SROWS && warps >= 8LL * 152;
+  return Lx >= 64 && Lt >= 2 * SROWS && warps >= 4LL * 152;
 }
 
 int wilson_A_ctas(int Lx, int Lt, bool f64) {

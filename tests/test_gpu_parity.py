@@ -303,6 +303,45 @@ def test_iteration_limit_reports_noconv(case, mg):
     assert st == 4 and infos[0].iterations == 3
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_A_streamed_large_ragged(mg, prec):
+    """1000 x 998 lattice: the register-streaming stencil (not a multiple of its
+    28-site strips or 32-row blocks)."""
+    Lx, Lt, m = 1000, 998, -0.9
+    U = W.links_from_angles(W.quenched_u1_angles(Lx, Lt, 3.0, 2, 5))
+    psi = W.gaussian_field((Lt, Lx, 2), 7)
+    want = ow.apply_A(U, m, psi)
+    # uniform bound of the term magnitudes: |A_ij| summed over a row <= (4+|m|+2)^2
+    mag = np.full(psi.shape, (4 + abs(m) + 2) ** 2 * np.max(np.abs(psi)))
+    with mg.Multigrid(dev(U), m, [], []) as s:
+        if prec == "f64":
+            out = torch.empty_like(dev(psi))
+            mg.mg_apply_A(s.h, dev(psi), out, 1, mg.PREC_F64)
+            check(host(out), want, mag, TOL64, "A f64 streamed")
+        else:
+            inp = dev(psi.astype(np.complex64))
+            out = torch.empty_like(inp)
+            mg.mg_apply_A(s.h, inp, out, 1, mg.PREC_F32)
+            check(host(out), want, mag, TOL32, "A f32 streamed")
+
+
+def test_vcycle_streamed_stencil_768(mg):
+    """A V-cycle whose fine level uses the streaming stencil with the fused
+    smoother / residual epilogues (768 x 768, 4 levels)."""
+    Lx = Lt = 768
+    blocks, Nv, m = [(4, 4), (4, 4), (2, 2)], [4, 4, 4], -0.8
+    U = W.links_from_angles(W.quenched_u1_angles(Lx, Lt, 6.0, 4, 9))
+    noise = W.setup_noise(Lx, Lt, blocks, Nv, 10)
+    H = omg.setup(U, m, blocks, Nv, noise, sweeps=2, power_iters=5)
+    r = W.gaussian_field((Lt, Lx, 2), 11)
+    want = omg.vcycle(H, r)
+    with mg.Multigrid(dev(U), m, blocks, Nv, dev(noise), setup_sweeps=2, power_iters=5) as s:
+        out = torch.empty_like(dev(r))
+        mg.mg_vcycle(s.h, dev(r), out, mg.PREC_F64)
+        got = host(out)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
+
+
 def test_set_mass_rebuilds_galerkin(mg):
     c = Case(mg, "2lvl_24x16")
     try:
