@@ -238,20 +238,23 @@ __device__ __forceinline__ C shfl_c(C v, int delta, bool up) {
 
 // D (sf = +1) or D^dagger (sf = -1) at this lane's site for one row: (f0, f1)
 // the row's spinor, fu / fd the rows t+1 / t-1 at this x, ux and ut the links
-// here, utm the t link one row below; the x neighbours and U_x(x-1) come from
-// the adjacent lanes.
+// here, utm the t link one row below; the x-hop terms come from the adjacent
+// lanes.
 template <typename R>
 __device__ __forceinline__ void dslash_row(cplx_t<R> f0, cplx_t<R> f1, cplx_t<R> fu0,
                                            cplx_t<R> fu1, cplx_t<R> fd0, cplx_t<R> fd1,
                                            cplx_t<R> ux, cplx_t<R> ut, cplx_t<R> utm, R diag,
                                            R sf, cplx_t<R>& o0, cplx_t<R>& o1) {
   using C = cplx_t<R>;
-  const C xp0 = shfl_c(f0, 1, false), xp1 = shfl_c(f1, 1, false);   // psi(x + 1)
-  const C xm0 = shfl_c(f0, 1, true), xm1 = shfl_c(f1, 1, true);     // psi(x - 1)
-  const C uxm = shfl_c(ux, 1, true);                                // U_x(x - 1)
-  C a0 = mk((R)0, (R)0), a1 = mk((R)0, (R)0);
-  hop_x<R>(a0, a1, ux, xp0, xp1, sf);
-  hop_x<R>(a0, a1, cconj(uxm), xm0, xm1, -sf);
+  // x hops: each lane forms the projections of its own site and the lane
+  // x - 1 also applies its link, so only one complex per direction moves.
+  const C q = mk(f0.x - sf * f1.x, f0.y - sf * f1.y);               // (1 - sf s1) projection
+  const C g = cmul(cconj(ux), mk(f0.x + sf * f1.x, f0.y + sf * f1.y));
+  const C qn = shfl_c(q, 1, false);                                 // from x + 1
+  const C gp = shfl_c(g, 1, true);                                  // U_x(x-1)^* (...)(x - 1)
+  const C hf = cmul(ux, qn);
+  C a0 = cadd(hf, gp);
+  C a1 = mk(-sf * hf.x + sf * gp.x, -sf * hf.y + sf * gp.y);
   hop_t<R>(a0, a1, ut, fu0, fu1, sf);
   hop_t<R>(a0, a1, cconj(utm), fd0, fd1, -sf);
   o0 = mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y);
@@ -259,7 +262,7 @@ __device__ __forceinline__ void dslash_row(cplx_t<R> f0, cplx_t<R> f1, cplx_t<R>
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_wilson_A_stream(const cplx_t<R>* __restrict__ in,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 3) k_wilson_A_stream(const cplx_t<R>* __restrict__ in,
                                                          cplx_t<R>* out,
                                                          const cplx_t<R>* __restrict__ U, R diag,
                                                          int Lx, int Lt, Epilogue ep) {
