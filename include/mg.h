@@ -95,6 +95,9 @@ typedef struct {
   int vcycle_coarse_bf16;               /* mixed solver: 1 = coarse blocks of the
                                            FP32 V-cycle in BF16 (FP32 accumulate),
                                            0 = FP32 (1)                          */
+  int max_rhs;                          /* right-hand sides solved together by
+                                           mg_solve, 1..64 (1); work memory
+                                           scales with it                        */
 } mg_params;
 
 typedef struct {
@@ -136,10 +139,13 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
 mg_status mg_set_mass(mg_handle* h, double mass);
 
 /* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
- * b, x: device complex128 [nrhs][Lt][Lx][2].  Stops each RHS when the true
- * FP64 |b - A x| / |b| <= tol.  b = 0 gives x = 0.  info (host, may be NULL)
- * receives nrhs records.  Synchronises the stream.  MG_ERR_NOCONV when maxiter
- * Krylov iterations (outer + inner) are exhausted. */
+ * b, x: device complex128 [nrhs][Lt][Lx][2].  Right-hand sides are solved in
+ * batches of params->max_rhs that share one Krylov loop (one operator and
+ * V-cycle launch per iteration for the whole batch, per-RHS scalars; a
+ * converged RHS is frozen).  Stops each RHS when the true FP64
+ * |b - A x| / |b| <= tol.  b = 0 gives x = 0.  info (host, may be NULL)
+ * receives nrhs records.  Synchronises the stream.  MG_ERR_NOCONV when
+ * maxiter iterations are exhausted. */
 mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
                    int solver, mg_solve_info* info);
 

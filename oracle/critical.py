@@ -58,13 +58,60 @@ def lambda_min_A(U: np.ndarray, m: float) -> float:
     return float(np.min(np.abs(ev)) ** 2)
 
 
+def _min_abs_eig_H(U: np.ndarray, m: float, D0=None) -> float:
+    """min |eig(sigma_3 D(m))| by shift-invert Lanczos at 0."""
+    D = wilson.dirac_matrix(U, 0.0) if D0 is None else D0
+    n = D.shape[0]
+    H = (_sigma3(n // 2) @ (D + m * sp.identity(n, dtype=np.complex128, format="csr"))).tocsc()
+    ev = spla.eigsh(H, k=1, sigma=0.0, which="LM", return_eigenvectors=False, tol=1e-12)
+    return float(np.min(np.abs(ev)))
+
+
+def critical_mass_by_flow(U: np.ndarray, m_lo: float = -2.4, m_hi: float = -1.9, step: float = 0.01,
+                          zero: float = 1e-7):
+    """m_crit for large lattices: D(m) is singular where an eigenvalue of the
+    Hermitian sigma_3 D(m) crosses zero, i.e. where mu(m) = min |eig(sigma_3 D(m))|
+    vanishes.  Scan mu on a grid from heavy to light mass, refine each local
+    minimum by golden-section search, and return the heaviest mass where the
+    minimum is below `zero` (None if there is none)."""
+    D0 = wilson.dirac_matrix(U, 0.0)
+    ms = np.arange(m_hi, m_lo - 1e-12, -step)
+    mu = [_min_abs_eig_H(U, m, D0) for m in ms]
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    for i in range(1, len(ms) - 1):
+        if mu[i] <= mu[i - 1] and mu[i] <= mu[i + 1]:
+            a, b = ms[i + 1], ms[i - 1]
+            c, d = b - g * (b - a), a + g * (b - a)
+            fc, fd = _min_abs_eig_H(U, c, D0), _min_abs_eig_H(U, d, D0)
+            for _ in range(60):
+                if fc < fd:
+                    b, d, fd = d, c, fc
+                    c = b - g * (b - a)
+                    fc = _min_abs_eig_H(U, c, D0)
+                else:
+                    a, c, fc = c, d, fd
+                    d = a + g * (b - a)
+                    fd = _min_abs_eig_H(U, d, D0)
+                if b - a < 1e-13:
+                    break
+            m_star = 0.5 * (a + b)
+            if _min_abs_eig_H(U, m_star, D0) < zero:
+                return float(m_star)
+    return None
+
+
 def near_critical_mass(U: np.ndarray, threshold: float = 1e-5):
     """Returns dict(m_crit, m_nc, delta, lambda_min) or None when D_0 has no real
     eigenvalue near the physical branch (then the caller advances the seed)."""
-    real, _ = real_eigenvalues_D0(U)
-    if real.size == 0:
-        return None
-    m_crit = -float(real[0])
+    if U.shape[1] * U.shape[2] <= 64 * 64:
+        real, _ = real_eigenvalues_D0(U)
+        if real.size == 0:
+            return None
+        m_crit = -float(real[0])
+    else:
+        m_crit = critical_mass_by_flow(U)
+        if m_crit is None:
+            return None
     for delta in NEAR_CRITICAL_DELTAS:
         lam = lambda_min_A(U, m_crit + delta)
         if lam < threshold:

@@ -51,18 +51,21 @@ cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* 
 template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
                  const int* frozen, long long count, int nrhs, cudaStream_t s);
-// Graph-resident CG loop control: ctrl = {iterations, status, limit};
-// status 0 running, 1 converged (rr <= stop), 2 breakdown, 3 limit reached.
+// Graph-resident CG loop control for nrhs right-hand sides (nrhs <= 64):
+// ctrl = {iterations, status, limit, nrhs, frozen[nrhs], it_done[nrhs]};
+// status 0 running, 1 all converged, 2 breakdown, 3 limit reached.
 cudaError_t cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
                        cudaGraphConditionalHandle cond, cudaStream_t s);
-cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, cudaStream_t s);
-// Flexible CG (FP64 vectors, FP32 preconditioned residual z32, one RHS):
+// ctrl init and stop[rhs] = tol2 * bn[rhs] (double2 slots); b = 0 starts frozen.
+cudaError_t set_control(int* ctrl, int maxiter, int nrhs, const double* bn, double tol2,
+                        double* stop, cudaStream_t s);
+// Flexible CG (FP64 vectors, FP32 preconditioned residual z32) per rhs:
 // zr = {Re<z32, q>, Re<r, z32>} (one launch), then beta = -zr[0] / Re(pq),
 // p = z32 + beta p, and rz <- zr[1] for the next step length.
-cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, double* ws,
-                       double* zr, cudaStream_t s);
+cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, int nrhs,
+                       double* ws, double* zr, cudaStream_t s);
 cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq, double* rz,
-                    long long count, cudaStream_t s);
+                    const int* frozen, long long count, int nrhs, cudaStream_t s);
 // out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s);
@@ -162,10 +165,11 @@ cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld,
 // at I (I + 1) / 2 + J) of a dense ld x ld complex64 matrix (ld multiple of
 // 64); diagonal tiles are made Hermitian from their lower halves.
 cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s);
-// y = B x (or y += B x) with B Hermitian in packed tiles; x, y complex128 (N);
-// part: 2 * 64 * ntiles complex64 scratch.  FP32 products and accumulation.
-cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, void* part,
-                               bool accumulate, cudaStream_t s);
+// y = B x (or y += B x) with B Hermitian in packed tiles, for nrhs vectors;
+// x, y complex128 [nrhs][N]; part: nrhs * 2 * 64 * ntiles complex64 scratch.
+// FP32 products and accumulation; each tile is read once for all vectors.
+cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
+                               void* part, bool accumulate, cudaStream_t s);
 
 // index map for tests
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,

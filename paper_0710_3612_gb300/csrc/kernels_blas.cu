@@ -178,19 +178,41 @@ cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_
   return cudaGetLastError();
 }
 
-// Device-side loop control of the graph-resident CG: counts the iteration,
-// classifies it (0 running, 1 converged, 2 breakdown, 3 iteration limit) and
-// sets the WHILE condition of the enclosing graph node.
+// Device-side loop control of the graph-resident CG for nrhs right-hand
+// sides.  ctrl = {iterations, status, limit, nrhs}; frozen[rhs] (ctrl + 4) is
+// set when a right-hand side converges (rr <= stop) or breaks down, and
+// it_done[rhs] (ctrl + 4 + nrhs) records its iteration count.  status: 0
+// running, 1 all converged, 2 a breakdown, 3 limit reached.  Sets the WHILE
+// condition of the enclosing graph node.
 __global__ void k_cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
                              cudaGraphConditionalHandle cond) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int it = ctrl[0] + 1;
+  const int nrhs = ctrl[3];
+  int* frozen = ctrl + 4;
+  int* it_done = ctrl + 4 + nrhs;
   ctrl[0] = it;
-  const double r = rr[0], d = pq[0];
-  int status = 0;
-  if (!(d > 0.0) || !(r == r)) status = 2;
-  else if (r <= stop[0]) status = 1;
-  else if (it >= ctrl[2]) status = 3;
+  int running = 0, broken = 0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (frozen[k]) continue;
+    const double r = rr[2 * k], d = pq[2 * k];
+    if (!(d > 0.0) || !(r == r)) {
+      frozen[k] = 2;
+      it_done[k] = it;
+      broken = 1;
+    } else if (r <= stop[2 * k]) {
+      frozen[k] = 1;
+      it_done[k] = it;
+    } else {
+      ++running;
+    }
+  }
+  int status = running ? 0 : 1;
+  if (broken) status = 2;
+  else if (running && it >= ctrl[2]) status = 3;
+  if (status == 3)
+    for (int k = 0; k < nrhs; ++k)
+      if (!frozen[k]) it_done[k] = it;
   ctrl[1] = status;
   cudaGraphSetConditional(cond, status == 0 ? 1u : 0u);
 }
@@ -202,32 +224,43 @@ cudaError_t cg_control(const double* rr, const double* pq, const double* stop, i
   return cudaGetLastError();
 }
 
-__global__ void k_set_control(int* ctrl, int maxiter, double* stop_slot, double stop) {
+// Initialises ctrl and stop[rhs] = tol2 * bn[rhs]; right-hand sides with
+// b = 0 start frozen (x = 0 is exact).
+__global__ void k_set_control(int* ctrl, int maxiter, int nrhs, const double* bn, double tol2,
+                              double* stop) {
   if (threadIdx.x != 0) return;
   ctrl[0] = 0;
   ctrl[1] = 0;
   ctrl[2] = maxiter;
-  stop_slot[0] = stop;
+  ctrl[3] = nrhs;
+  for (int k = 0; k < nrhs; ++k) {
+    stop[2 * k] = tol2 * bn[2 * k];
+    stop[2 * k + 1] = 0.0;
+    ctrl[4 + k] = bn[2 * k] == 0.0 ? 1 : 0;
+    ctrl[4 + nrhs + k] = 0;
+  }
 }
 
-cudaError_t set_control(int* ctrl, int maxiter, double* stop_slot, double stop, cudaStream_t s) {
-  k_set_control<<<1, 32, 0, s>>>(ctrl, maxiter, stop_slot, stop);
+cudaError_t set_control(int* ctrl, int maxiter, int nrhs, const double* bn, double tol2,
+                        double* stop, cudaStream_t s) {
+  k_set_control<<<1, 32, 0, s>>>(ctrl, maxiter, nrhs, bn, tol2, stop);
   count_launch();
   return cudaGetLastError();
 }
 
-// Flexible CG with the FP32 preconditioned residual z32:
-// zr = {Re<z32, q>, Re<r, z32>} in one deterministic pass.
+// Flexible CG with the FP32 preconditioned residual z32, per right-hand side:
+// zr[rhs] = {Re<z32, q>, Re<r, z32>} in one deterministic pass.
 __global__ void __launch_bounds__(RT) k_dot2_zq_rz(const float2* __restrict__ z,
                                                    const double2* __restrict__ q,
                                                    const double2* __restrict__ r, long long count,
                                                    double* ws, double* zr) {
   __shared__ double sh[2 * RT / 32];
+  const long long base = (long long)blockIdx.y * count;
   double a = 0.0, b = 0.0;
   for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
        i += (long long)gridDim.x * RT) {
-    const float2 zv = z[i];
-    const double2 qv = q[i], rv = r[i];
+    const float2 zv = z[base + i];
+    const double2 qv = q[base + i], rv = r[base + i];
     a = fma((double)zv.x, qv.x, a);
     a = fma((double)zv.y, qv.y, a);
     b = fma(rv.x, (double)zv.x, b);
@@ -236,33 +269,39 @@ __global__ void __launch_bounds__(RT) k_dot2_zq_rz(const float2* __restrict__ z,
   finish_reduction(a, b, ws, zr, sh);
 }
 
-cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, double* ws,
-                       double* zr, cudaStream_t s) {
-  k_dot2_zq_rz<<<reduce_blocks(count), RT, 0, s>>>((const float2*)z32, (const double2*)q,
-                                                   (const double2*)r, count, ws, zr);
+cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long count, int nrhs,
+                       double* ws, double* zr, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  k_dot2_zq_rz<<<dim3(reduce_blocks(count), nrhs), RT, 0, s>>>(
+      (const float2*)z32, (const double2*)q, (const double2*)r, count, ws, zr);
   count_launch();
   return cudaGetLastError();
 }
 
-// beta = -zr[0] / Re(pq); p = z32 + beta p; rz <- {zr[1], 0}.
+// beta = -zr[0] / Re(pq); p = z32 + beta p; rz <- {zr[1], 0}; per rhs, frozen
+// right-hand sides untouched.
 __global__ void k_cg_p_pr(double2* __restrict__ p, const float2* __restrict__ z, const double* zr,
-                          const double* pq, double* rz, long long count) {
+                          const double* pq, double* rz, const int* frozen, long long count) {
+  const int rhs = blockIdx.y;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (frozen && frozen[rhs]) return;
   if (i == 0) {
-    rz[0] = zr[1];
-    rz[1] = 0.0;
+    rz[2 * rhs] = zr[2 * rhs + 1];
+    rz[2 * rhs + 1] = 0.0;
   }
   if (i >= count) return;
-  const double d = pq[0];
-  const double beta = d != 0.0 ? -zr[0] / d : 0.0;
-  const double2 pv = p[i];
-  const float2 zv = z[i];
-  p[i] = make_double2(fma(beta, pv.x, (double)zv.x), fma(beta, pv.y, (double)zv.y));
+  const double d = pq[2 * rhs];
+  const double beta = d != 0.0 ? -zr[2 * rhs] / d : 0.0;
+  const long long k = (long long)rhs * count + i;
+  const double2 pv = p[k];
+  const float2 zv = z[k];
+  p[k] = make_double2(fma(beta, pv.x, (double)zv.x), fma(beta, pv.y, (double)zv.y));
 }
 
 cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq, double* rz,
-                    long long count, cudaStream_t s) {
-  k_cg_p_pr<<<grid1(count, 1), RT, 0, s>>>((double2*)p, (const float2*)z32, zr, pq, rz, count);
+                    const int* frozen, long long count, int nrhs, cudaStream_t s) {
+  k_cg_p_pr<<<grid1(count, nrhs), RT, 0, s>>>((double2*)p, (const float2*)z32, zr, pq, rz, frozen,
+                                               count);
   count_launch();
   return cudaGetLastError();
 }

@@ -760,11 +760,12 @@ cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s) {
 
 __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ P,
                                                      const double2* __restrict__ x, int N,
-                                                     float2* __restrict__ part) {
+                                                     int nrhs, float2* __restrict__ part) {
   __shared__ float2 T[HT][HT + 1];
   __shared__ float2 xi[HT], xj[HT];
   __shared__ float2 red[4][HT];
   const int k = blockIdx.x;
+  const long long ntiles = gridDim.x;
   int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
   while ((I + 1) * (I + 2) / 2 <= k) ++I;
   while (I * (I + 1) / 2 > k) --I;
@@ -779,41 +780,45 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
     T[r][c] = make_float2(buf[u].x, buf[u].y);
     T[r][c + 1] = make_float2(buf[u].z, buf[u].w);
   }
-  if (threadIdx.x < HT) {
-    const int gi = I * HT + threadIdx.x, gj = J * HT + threadIdx.x;
-    xi[threadIdx.x] = gi < N ? make_float2((float)x[gi].x, (float)x[gi].y) : make_float2(0.f, 0.f);
-    xj[threadIdx.x] = gj < N ? make_float2((float)x[gj].x, (float)x[gj].y) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  // u = T x_J: row r = t % 64, quarter g = t / 64 of the columns
   const int r = threadIdx.x % HT, g = threadIdx.x / HT;
-  float2 u = make_float2(0.f, 0.f);
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+    const double2* xr = x + (long long)rhs * N;
+    float2* pr = part + (long long)rhs * ntiles * 2 * HT;
+    __syncthreads();                             // T loaded / previous rhs done with xi, xj, red
+    if (threadIdx.x < HT) {
+      const int gi = I * HT + threadIdx.x, gj = J * HT + threadIdx.x;
+      xi[threadIdx.x] = gi < N ? make_float2((float)xr[gi].x, (float)xr[gi].y) : make_float2(0.f, 0.f);
+      xj[threadIdx.x] = gj < N ? make_float2((float)xr[gj].x, (float)xr[gj].y) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // u = T x_J: row r = t % 64, quarter g = t / 64 of the columns
+    float2 u = make_float2(0.f, 0.f);
 #pragma unroll 4
-  for (int c = g * 16; c < g * 16 + 16; ++c) cfma(u, T[r][c], xj[c]);
-  red[g][r] = u;
-  __syncthreads();
-  if (threadIdx.x < HT) {
-    float2 a = red[0][threadIdx.x];
-    a = cadd(a, red[1][threadIdx.x]);
-    a = cadd(a, red[2][threadIdx.x]);
-    a = cadd(a, red[3][threadIdx.x]);
-    part[(2LL * k) * HT + threadIdx.x] = a;
-  }
-  if (I == J) return;
-  __syncthreads();
-  // v = T^H x_I: column c = t % 64, quarter g of the rows
-  const int c = threadIdx.x % HT;
-  float2 v = make_float2(0.f, 0.f);
+    for (int c = g * 16; c < g * 16 + 16; ++c) cfma(u, T[r][c], xj[c]);
+    red[g][r] = u;
+    __syncthreads();
+    if (threadIdx.x < HT) {
+      float2 a = red[0][threadIdx.x];
+      a = cadd(a, red[1][threadIdx.x]);
+      a = cadd(a, red[2][threadIdx.x]);
+      a = cadd(a, red[3][threadIdx.x]);
+      pr[(2LL * k) * HT + threadIdx.x] = a;
+    }
+    if (I == J) continue;
+    __syncthreads();
+    // v = T^H x_I: column c = t % 64, quarter g of the rows
+    float2 v = make_float2(0.f, 0.f);
 #pragma unroll 4
-  for (int rr = g * 16; rr < g * 16 + 16; ++rr) cfmac(v, T[rr][c], xi[rr]);
-  red[g][c] = v;
-  __syncthreads();
-  if (threadIdx.x < HT) {
-    float2 a = red[0][threadIdx.x];
-    a = cadd(a, red[1][threadIdx.x]);
-    a = cadd(a, red[2][threadIdx.x]);
-    a = cadd(a, red[3][threadIdx.x]);
-    part[(2LL * k + 1) * HT + threadIdx.x] = a;
+    for (int rr = g * 16; rr < g * 16 + 16; ++rr) cfmac(v, T[rr][r], xi[rr]);
+    red[g][r] = v;
+    __syncthreads();
+    if (threadIdx.x < HT) {
+      float2 a = red[0][threadIdx.x];
+      a = cadd(a, red[1][threadIdx.x]);
+      a = cadd(a, red[2][threadIdx.x]);
+      a = cadd(a, red[3][threadIdx.x]);
+      pr[(2LL * k + 1) * HT + threadIdx.x] = a;
+    }
   }
 }
 
@@ -824,6 +829,8 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
                                                       bool accumulate) {
   __shared__ float2 red[4][HT];
   const int I = blockIdx.x, rr = threadIdx.x % HT, g = threadIdx.x / HT;
+  part += (long long)blockIdx.y * (nt * (nt + 1) / 2) * 2 * HT;
+  y += (long long)blockIdx.y * N;
   float2 acc = make_float2(0.f, 0.f);
   for (int J = g; J < nt; J += 4) {
     if (J <= I) acc = cadd(acc, part[(2LL * (I * (I + 1) / 2 + J)) * HT + rr]);
@@ -843,14 +850,15 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
   }
 }
 
-cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, void* part,
-                               bool accumulate, cudaStream_t s) {
+cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
+                               void* part, bool accumulate, cudaStream_t s) {
   if (ld % HT || ld < N) return cudaErrorInvalidValue;
   const int nt = ld / HT;
-  k_hgemv_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)P, (const double2*)x, N,
+  k_hgemv_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)P, (const double2*)x, N, nrhs,
                                                   (float2*)part);
   count_launch();
-  k_hgemv_reduce<<<nt, 256, 0, s>>>((const float2*)part, (double2*)y, N, nt, accumulate);
+  k_hgemv_reduce<<<dim3(nt, nrhs), 256, 0, s>>>((const float2*)part, (double2*)y, N, nt,
+                                                accumulate);
   count_launch();
   return cudaGetLastError();
 }

@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   }
   if (ep.dot_out) {
     __shared__ double sh[64];
-    finish_reduction_g(dre, dim, ep.dot_ws, ep.dot_out, sh, 0, blockIdx.y * gridDim.x + blockIdx.x,
-                       gridDim.x * gridDim.y);
+    finish_reduction_g(dre, dim, ep.dot_ws, ep.dot_out, sh, blockIdx.z,
+                       blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
   }
 }
 
@@ -366,7 +366,7 @@ cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int 
                      int nrhs, const Epilogue& ep, cudaStream_t s) {
   const bool f64 = sizeof(R) == 8;
   const int ctas = wilson_A_ctas(Lx, Lt, f64);
-  if (ep.dot_out && (nrhs != 1 || ctas > 608)) return cudaErrorInvalidValue;
+  if (ep.dot_out && (nrhs > 64 || ctas > 608)) return cudaErrorInvalidValue;
   const bool big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16)) >= 2 * 152;
   if (!ep.dot_out && wilson_A_streamed(Lx, Lt)) {
     const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);

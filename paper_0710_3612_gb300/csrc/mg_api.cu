@@ -62,9 +62,12 @@ struct mg_handle {
   // the internal stream gs and fenced to the user's stream with events
   cudaStream_t gs = nullptr;
   cudaEvent_t fence[2] = {nullptr, nullptr};
-  cudaGraphExec_t loop_exec[3] = {nullptr, nullptr, nullptr};
-  long long loop_kernels[3] = {0, 0, 0};   // kernels per loop-body iteration
-  int* dctrl = nullptr;         // [0] iterations, [1] status, [2] iteration limit
+  static constexpr int MAXR = 64;
+  cudaGraphExec_t loop_exec[3 * MAXR] = {};     // per (preconditioner mode, nrhs)
+  long long loop_kernels[3] = {0, 0, 0};      // kernels per loop-body iteration
+  int* dctrl = nullptr;         // loop control (see k_cg_control)
+  int* hctrl = nullptr;         // pinned host mirror of dctrl
+  int R = 1;                    // right-hand sides per batch (max_rhs)
   bool use_graphs = true;
   // solver vectors (one RHS), FP64 and FP32: x r p q z t
   void* sv64[6] = {};
@@ -92,8 +95,8 @@ namespace {
 constexpr long long MG_DENSE_MAX = 16384;
 
 // scalar slots (each a double2)
-enum { S_RZ = 0, S_RZN = 2, S_PQ = 4, S_RR = 6, S_T0 = 8, S_T1 = 10, S_BN = 12, S_NR = 14,
-       S_STOP = 16, S_MAX = 64 };
+// scalar slots: slot k holds one double2 per right-hand side
+enum { S_RZ = 0, S_RZN, S_PQ, S_RR, S_T0, S_T1, S_BN, S_NR, S_STOP, S_COUNT };
 
 struct Fail {
   mg_status st;
@@ -124,8 +127,11 @@ T* dalloc(mg_handle* h, size_t bytes) {
 
 void sync(mg_handle* h) { ck(h, cudaStreamSynchronize(h->s), "stream synchronize"); }
 
-double read_scalar(mg_handle* h, int slot) {
-  ck(h, cudaMemcpyAsync(h->hscal, h->scal + slot, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+double* slot(mg_handle* h, int k) { return h->scal + (size_t)k * 2 * h->R; }
+
+// First double of a slot (right-hand side 0), read synchronously.
+double read_scalar(mg_handle* h, int k) {
+  ck(h, cudaMemcpyAsync(h->hscal, slot(h, k), 2 * sizeof(double), cudaMemcpyDeviceToHost,
                         h->s),
      "scalar readback");
   sync(h);
@@ -192,34 +198,37 @@ Epilogue ep_lincomb(double ca, const void* U, double cu, const void* W = nullptr
 }
 
 // ----- coarsest solve: FP32 explicit inverse refined in FP64 ----------------
-// x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r.
-void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps) {
+// x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r; for
+// nrhs vectors [nrhs][N].
+void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs) {
   ProfScope prof(h, MG_KF_COARSEST);
   {
     ProfScope pd(h, MG_KF_DENSE);
-    ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, h->gemv_part, false, h->s), "coarsest gemv");
+    ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, nrhs, h->gemv_part, false, h->s),
+       "coarsest gemv");
   }
   for (int it = 0; it < steps; ++it) {
-    apply_level<double>(h, h->L - 1, x, h->cr, 1, W_F64, ep_lincomb(-1.0, b, 1.0));
+    apply_level<double>(h, h->L - 1, x, h->cr, nrhs, W_F64, ep_lincomb(-1.0, b, 1.0));
     ProfScope pd(h, MG_KF_DENSE);
-    ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, h->gemv_part, true, h->s),
+    ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, nrhs, h->gemv_part, true, h->s),
        "coarsest gemv");
   }
 }
 
 // ----- V-cycle (Sec. 2, five steps), recursive ------------------------------
-// Reads b, writes x (both level-l vectors of precision R).
+// Reads b, writes x (both level-l vectors of precision R, nrhs of them).
 template <typename R>
-void vcycle(mg_handle* h, int l, const void* b, void* x) {
+void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
   const bool f64 = sizeof(R) == 8;
   const int weights = f64 ? W_F64 : (h->p.vcycle_coarse_bf16 ? W_BF16 : W_F32);
   if (l == h->L - 1) {
     if (f64) {
-      coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine);
+      coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine, nrhs);
     } else {
-      ck(h, convert_f32_f64(b, h->cb, h->Nc, h->s), "coarsest in");
-      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine);
-      ck(h, convert_f64_f32(h->cx, x, h->Nc, h->s), "coarsest out");
+      const long long c = (long long)h->Nc * nrhs;
+      ck(h, convert_f32_f64(b, h->cb, c, h->s), "coarsest in");
+      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs);
+      ck(h, convert_f64_f32(h->cx, x, c, h->s), "coarsest out");
     }
     return;
   }
@@ -229,39 +238,39 @@ void vcycle(mg_handle* h, int l, const void* b, void* x) {
   void** wc = f64 ? C.w64 : C.w32;
   void* r = w[2];
   // 1. x = R b = c0 b + c1 A b
-  apply_level<R>(h, l, b, x, 1, weights, ep_lincomb(L.c1, b, L.c0));
+  apply_level<R>(h, l, b, x, nrhs, weights, ep_lincomb(L.c1, b, L.c0));
   // 2. r_c = P^dagger (b - A x)
-  apply_level<R>(h, l, x, r, 1, weights, ep_lincomb(-1.0, b, 1.0));
+  apply_level<R>(h, l, x, r, nrhs, weights, ep_lincomb(-1.0, b, 1.0));
   const void* Vst = f64 ? (const void*)L.Vst64 : (const void*)L.Vst32;
   {
     ProfScope prof(h, MG_KF_TRANSFER);
-    ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, h->s), "restrict");
+    ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s),
+       "restrict");
   }
   // 3. e_c = V_{l+1} r_c
-  vcycle<R>(h, l + 1, wc[0], wc[1]);
+  vcycle<R>(h, l + 1, wc[0], wc[1], nrhs);
   // 4. x = x + P e_c
   {
     ProfScope prof(h, MG_KF_TRANSFER);
-    ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1, true, h->s),
-     "prolong");
+    ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, true, h->s),
+       "prolong");
   }
   // 5. x = x + R (b - A x):  r = b - A x, then x = x + c0 r + c1 A r
-  apply_level<R>(h, l, x, r, 1, weights, ep_lincomb(-1.0, b, 1.0));
-  apply_level<R>(h, l, r, x, 1, weights, ep_lincomb(L.c1, r, L.c0, x, 1.0));
+  apply_level<R>(h, l, x, r, nrhs, weights, ep_lincomb(-1.0, b, 1.0));
+  apply_level<R>(h, l, r, x, nrhs, weights, ep_lincomb(L.c1, r, L.c0, x, 1.0));
 }
 
 // ----- setup pieces ---------------------------------------------------------
 double power_lambda_max(mg_handle* h, int l, const double2* start, void* v, void* w) {
   Level& L = h->lv[l];
   const long long n = L.count();
-  double* s = h->scal;
-  ck(h, norm2<double>(start, n, 1, h->partials, s + S_T0, h->s), "norm");
-  ck(h, scale_inv_sqrt<double>(start, v, s + S_T0, n, 1, h->s), "scale");
+  ck(h, norm2<double>(start, n, 1, h->partials, slot(h, S_T0), h->s), "norm");
+  ck(h, scale_inv_sqrt<double>(start, v, slot(h, S_T0), n, 1, h->s), "scale");
   for (int it = 0; it < h->p.power_iters; ++it) {
     apply_level<double>(h, l, v, w, 1, W_F64);
-    if (it == h->p.power_iters - 1) ck(h, dot<double>(v, w, n, 1, h->partials, s + S_T1, h->s), "dot");
-    ck(h, norm2<double>(w, n, 1, h->partials, s + S_T0, h->s), "norm");
-    ck(h, scale_inv_sqrt<double>(w, v, s + S_T0, n, 1, h->s), "scale");
+    if (it == h->p.power_iters - 1) ck(h, dot<double>(v, w, n, 1, h->partials, slot(h, S_T1), h->s), "dot");
+    ck(h, norm2<double>(w, n, 1, h->partials, slot(h, S_T0), h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(w, v, slot(h, S_T0), n, 1, h->s), "scale");
   }
   return read_scalar(h, S_T1);
 }
@@ -271,17 +280,16 @@ void smoother_coefficients(mg_handle* h, int l, void* q, void* r1) {
   Level& L = h->lv[l];
   const long long n = L.count();
   const double om = h->p.omega_mr;
-  double* s = h->scal;
   apply_level<double>(h, l, L.eta, q, 1, W_F64);
-  ck(h, dot<double>(q, L.eta, n, 1, h->partials, s + S_T0, h->s), "dot");
-  ck(h, norm2<double>(q, n, 1, h->partials, s + S_T1, h->s), "norm");
+  ck(h, dot<double>(q, L.eta, n, 1, h->partials, slot(h, S_T0), h->s), "dot");
+  ck(h, norm2<double>(q, n, 1, h->partials, slot(h, S_T1), h->s), "norm");
   const double num0 = read_scalar(h, S_T0), den0 = read_scalar(h, S_T1);
   if (!(den0 > 0.0)) fail(h, MG_ERR_BREAKDOWN, "MR smoother: A eta = 0");
   const double a0 = num0 / den0;
   ck(h, lincomb<double>(r1, 1.0, L.eta, -om * a0, q, 0.0, nullptr, n, 1, h->s), "mr");
   apply_level<double>(h, l, r1, q, 1, W_F64);
-  ck(h, dot<double>(q, r1, n, 1, h->partials, s + S_T0, h->s), "dot");
-  ck(h, norm2<double>(q, n, 1, h->partials, s + S_T1, h->s), "norm");
+  ck(h, dot<double>(q, r1, n, 1, h->partials, slot(h, S_T0), h->s), "dot");
+  ck(h, norm2<double>(q, n, 1, h->partials, slot(h, S_T1), h->s), "norm");
   const double num1 = read_scalar(h, S_T0), den1 = read_scalar(h, S_T1);
   if (!(den1 > 0.0)) fail(h, MG_ERR_BREAKDOWN, "MR smoother: A r1 = 0");
   const double a1 = num1 / den1;
@@ -317,19 +325,18 @@ void build_coarsest(mg_handle* h) {
   }
   // Refinement count: smallest number of FP64 correction steps that brings a
   // fixed test vector (all ones) to coarsest_tol, plus one.
-  double* s = h->scal;
   std::vector<double2> ones(h->Nc, make_double2(1.0, 0.0));
   ck(h, cudaMemcpyAsync(h->cb, ones.data(), sizeof(double2) * h->Nc, cudaMemcpyHostToDevice,
                         h->s),
      "upload");
-  ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, s + S_T1, h->s), "norm");
+  ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, slot(h, S_T1), h->s), "norm");
   const double bn = read_scalar(h, S_T1);
   int steps = 0;
   for (; steps <= h->p.coarsest_refine_max; ++steps) {
-    coarsest_solve64(h, h->cb, h->cx, steps);
+    coarsest_solve64(h, h->cb, h->cx, steps, 1);
     apply_level<double>(h, h->L - 1, h->cx, h->cr, 1, W_F64);
     ck(h, sub_from<double>(h->cb, h->cr, h->Nc, h->s), "residual");
-    ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, s + S_T0, h->s), "norm");
+    ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, slot(h, S_T0), h->s), "norm");
     const double rr = read_scalar(h, S_T0);
     if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest inverse is not finite");
     if (rr <= h->p.coarsest_tol * h->p.coarsest_tol * bn) break;
@@ -371,6 +378,7 @@ mg_status validate(const mg_params* p, std::string& msg) {
     lx /= bx; lt /= bt; n = 2 * nv;
   }
   if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
+  if (p->max_rhs < 1 || p->max_rhs > 64) { msg = "max_rhs must be in [1, 64]"; return MG_ERR_ARG; }
   if (p->nlevels > 1 && !p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
   if (p->nlevels > 1 && (long long)lx * lt * n > MG_DENSE_MAX) {
     msg = "coarsest level has more than " + std::to_string(MG_DENSE_MAX) + " unknowns";
@@ -413,36 +421,37 @@ void free_all(mg_handle* h) {
   h->allocs.clear();
   if (h->hscal) cudaFreeHost(h->hscal);
   h->hscal = nullptr;
+  if (h->hctrl) cudaFreeHost(h->hctrl);
+  h->hctrl = nullptr;
 }
 
 // ----- Krylov solvers ---------------------------------------------------------
-// PCG on A x = b in FP64, x0 = 0, stopping when the recursive residual
-// |r| <= tol |b|.  pmode 0: no preconditioner (plain CG); 1: FP64 V-cycle,
-// standard PCG (beta = <r+, z+>/<r, z>); 2: FP32 V-cycle (FP32 vectors, FP32
-// or BF16 coarse blocks, FP64 coarsest solve) on the FP64 residual, flexible
-// CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with r+ = r - alpha A p),
-// so that rounding in the low-precision preconditioner does not break the
-// recursion.  Returns iterations; x receives the solution.
-// q = A p and <p, q> (fused when the kernel's block count allows it).
-void apply_pq(mg_handle* h) {
+// All loops below run nrhs right-hand sides in lockstep (nrhs <= max_rhs):
+// vectors are [nrhs][count], every scalar slot holds one double2 per rhs, and
+// a right-hand side whose residual has reached its target is frozen (the CG
+// updates skip it; the V-cycle still processes it, harmlessly).
+int* frozen_of(mg_handle* h) { return h->dctrl + 4; }
+
+// q = A p and <p, q> per rhs (fused when the kernel's block count allows it).
+void apply_pq(mg_handle* h, int nrhs) {
   const long long n = h->lv[0].count();
   const Level& F = h->lv[0];
   Epilogue ep;
   if (wilson_A_ctas(F.Lx, F.Lt, true) <= 608) {
     ep.dot_ws = h->partials;
-    ep.dot_out = h->scal + S_PQ;
+    ep.dot_out = slot(h, S_PQ);
   }
-  apply_level<double>(h, 0, h->sv64[2], h->sv64[3], 1, W_F64, ep);
+  apply_level<double>(h, 0, h->sv64[2], h->sv64[3], nrhs, W_F64, ep);
   if (!ep.dot_out)
-    ck(h, dot<double>(h->sv64[2], h->sv64[3], n, 1, h->partials, h->scal + S_PQ, h->s), "dot");
+    ck(h, dot<double>(h->sv64[2], h->sv64[3], n, nrhs, h->partials, slot(h, S_PQ), h->s), "dot");
 }
 
 // x += alpha p, r -= alpha q, |r|^2 (and the FP32 copy of r for pmode 2).
-void pcg_update(mg_handle* h, void* x, int pmode) {
+void pcg_update(mg_handle* h, void* x, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
-  double* s = h->scal;
-  ck(h, cg_xr<double>(x, h->sv64[1], h->sv64[2], h->sv64[3], s + S_RZ, s + S_PQ, nullptr, n, 1,
-                      h->partials, s + S_RR, h->s, pmode == 2 ? h->sv32[1] : nullptr),
+  ck(h, cg_xr<double>(x, h->sv64[1], h->sv64[2], h->sv64[3], slot(h, S_RZ), slot(h, S_PQ),
+                      frozen_of(h), n, nrhs, h->partials, slot(h, S_RR), h->s,
+                      pmode == 2 ? h->sv32[1] : nullptr),
      "cg_xr");
 }
 
@@ -450,47 +459,47 @@ void pcg_update(mg_handle* h, void* x, int pmode) {
 //   pmode 0: p = r + (|r+|^2/|r|^2) p
 //   pmode 1: z = V64 r, p = z + (<r+,z+>/<r,z>) p
 //   pmode 2: z32 = V32 r32, p = z32 - (Re<z32, q>/<p, q>) p  (flexible)
-void pcg_direction(mg_handle* h, int pmode) {
+void pcg_direction(mg_handle* h, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
   void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
-  double* s = h->scal;
+  const size_t sb = 2 * sizeof(double) * nrhs;
   if (pmode == 2) {
-    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
-    ck(h, dot2_zq_rz(h->sv32[4], q, r, n, h->partials, s + S_T0, h->s), "dot2");
-    ck(h, cg_p_pr(p, h->sv32[4], s + S_T0, s + S_PQ, s + S_RZ, n, h->s), "cg_p");
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
+    ck(h, dot2_zq_rz(h->sv32[4], q, r, n, nrhs, h->partials, slot(h, S_T0), h->s), "dot2");
+    ck(h, cg_p_pr(p, h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h), n,
+                  nrhs, h->s), "cg_p");
   } else if (pmode == 1) {
-    vcycle<double>(h, 0, r, z);
-    ck(h, dot<double>(r, z, n, 1, h->partials, s + S_RZN, h->s), "dot");
-    ck(h, cg_p<double>(p, z, s + S_RZN, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
-    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RZN, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+    vcycle<double>(h, 0, r, z, nrhs);
+    ck(h, dot<double>(r, z, n, nrhs, h->partials, slot(h, S_RZN), h->s), "dot");
+    ck(h, cg_p<double>(p, z, slot(h, S_RZN), slot(h, S_RZ), frozen_of(h), n, nrhs, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(slot(h, S_RZ), slot(h, S_RZN), sb, cudaMemcpyDeviceToDevice, h->s), "copy");
   } else {
-    ck(h, cg_p<double>(p, r, s + S_RR, s + S_RZ, nullptr, n, 1, h->s), "cg_p");
-    ck(h, cudaMemcpyAsync(s + S_RZ, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy");
+    ck(h, cg_p<double>(p, r, slot(h, S_RR), slot(h, S_RZ), frozen_of(h), n, nrhs, h->s), "cg_p");
+    ck(h, cudaMemcpyAsync(slot(h, S_RZ), slot(h, S_RR), sb, cudaMemcpyDeviceToDevice, h->s), "copy");
   }
 }
 
 // First direction: p = z0 = M r0, rz = <r0, z0>.
-void pcg_start(mg_handle* h, int pmode) {
+void pcg_start(mg_handle* h, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
   void *r = h->sv64[1], *p = h->sv64[2], *z = h->sv64[4];
-  double* s = h->scal;
   if (pmode == 2) {
-    ck(h, convert_f64_f32(r, h->sv32[1], n, h->s), "to f32");
-    vcycle<float>(h, 0, h->sv32[1], h->sv32[4]);
-    ck(h, convert_f32_f64(h->sv32[4], p, n, h->s), "to f64");
+    ck(h, convert_f64_f32(r, h->sv32[1], n * nrhs, h->s), "to f32");
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
+    ck(h, convert_f32_f64(h->sv32[4], p, n * nrhs, h->s), "to f64");
   } else if (pmode == 1) {
-    vcycle<double>(h, 0, r, z);
-    ck(h, cudaMemcpyAsync(p, z, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    vcycle<double>(h, 0, r, z, nrhs);
+    ck(h, cudaMemcpyAsync(p, z, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
   } else {
-    ck(h, cudaMemcpyAsync(p, r, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    ck(h, cudaMemcpyAsync(p, r, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
   }
-  ck(h, dot<double>(r, p, n, 1, h->partials, s + S_RZ, h->s), "dot");
+  ck(h, dot<double>(r, p, n, nrhs, h->partials, slot(h, S_RZ), h->s), "dot");
 }
 
 // Captures the CG loop body into the body of a conditional WHILE node: the
 // control kernel at the end of each iteration decides on the device whether
 // to run another iteration, so the whole loop is one graph launch.
-cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
+cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode, int nrhs) {
   const unsigned long long launches0 = launch_count();
   cudaGraph_t g = nullptr;
   ck(h, cudaGraphCreate(&g, 0), "graph create");
@@ -506,15 +515,14 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
   ck(h, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np), "conditional node");
   cudaGraph_t body = np.conditional.phGraph_out[0];
   cudaStream_t saved = h->s;
-  const long long fa = h->fine_applies, vc = h->vcycles;
   h->s = h->gs;
   ck(h, cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal), "begin capture");
   try {
-    apply_pq(h);
-    pcg_update(h, x, pmode);
-    pcg_direction(h, pmode);
-    ck(h, cg_control(h->scal + S_RR, h->scal + S_PQ, h->scal + S_STOP, h->dctrl, cond, h->s), "control");
+    apply_pq(h, nrhs);
+    pcg_update(h, x, pmode, nrhs);
+    pcg_direction(h, pmode, nrhs);
+    ck(h, cg_control(slot(h, S_RR), slot(h, S_PQ), slot(h, S_STOP), h->dctrl, cond, h->s), "control");
   } catch (...) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(h->gs, &dummy);
@@ -523,160 +531,173 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode) {
     throw;
   }
   h->s = saved;
-  h->fine_applies = fa;
-  h->vcycles = vc;
   // captured kernels did not run; they are counted once per executed iteration
-  h->loop_kernels[pmode] = (long long)(launch_count() - launches0);
-  add_launches(-h->loop_kernels[pmode]);
+  const long long kern = (long long)(launch_count() - launches0);
+  add_launches(-kern);
   ck(h, cudaStreamEndCapture(h->gs, &body), "end capture");
   cudaGraphExec_t exec = nullptr;
   ck(h, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
   cudaGraphDestroy(g);
+  h->loop_kernels[pmode] = kern;
   return exec;
 }
 
-
-// PCG on A x = b in FP64, x0 = 0, stopping when the recursive residual
-// |r| <= tol |b|.  pmode 0: no preconditioner (plain CG); 1: FP64 V-cycle,
-// standard PCG (beta = <r+, z+>/<r, z>); 2: FP32 V-cycle (FP32 vectors, FP32
-// or BF16 coarse blocks, FP64 coarsest solve) on the FP64 residual, flexible
-// CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with r+ = r - alpha A p),
-// so that rounding in the low-precision preconditioner does not break the
-// recursion.  The iteration loop runs as one CUDA graph with a device-side
-// WHILE condition (or eagerly, with a host check per iteration, while
-// per-kernel profiling is on).  Returns iterations; x receives the solution
-// and must be the handle's solver vector sv64[5].
-int pcg(mg_handle* h, const void* b, void* x, double tol, int maxiter, int pmode,
-        mg_status& st) {
+// PCG on A x = b in FP64 for nrhs right-hand sides, x0 = 0.  Right-hand side
+// k stops when |r_k|^2 <= tol2 * ref[k] (recursive residual; ref is the slot
+// S_BN, |b_original|^2).  pmode 0: no preconditioner (plain CG); 1: FP64
+// V-cycle, standard PCG (beta = <r+, z+>/<r, z>); 2: FP32 V-cycle (FP32
+// vectors, FP32 or BF16 coarse blocks, FP64 coarsest solve) on the FP64
+// residual, flexible CG: beta = -Re<z+, A p>/<p, A p> (Polak-Ribiere with
+// r+ = r - alpha A p), so that rounding in the low-precision preconditioner
+// does not break the recursion.  The iteration loop runs as one CUDA graph
+// with a device-side WHILE condition (or eagerly, with the same control
+// evaluated on the host, while per-kernel profiling is on).  iters[k]
+// receives the iterations of right-hand side k; returns the loop length.  x
+// must be the handle's solver vector sv64[5]; b is read only here.
+int pcg(mg_handle* h, const void* b, void* x, double tol2, int maxiter, int pmode, int nrhs,
+        std::vector<int>& iters, mg_status& st) {
   Level& F = h->lv[0];
   const long long n = F.count();
   void* r = h->sv64[1];
-  double* s = h->scal;
   st = MG_OK;
-  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
-  const double bn = read_scalar(h, S_BN);
-  ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
-  if (bn == 0.0) return 0;
-  if (!(bn == bn) || std::isinf(bn)) { st = MG_ERR_BREAKDOWN; h->err = "non-finite right-hand side"; return 0; }
-  ck(h, cudaMemcpyAsync(r, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  pcg_start(h, pmode);
+  ck(h, cudaMemsetAsync(x, 0, n * nrhs * sizeof(double2), h->s), "memset");
+  ck(h, cudaMemcpyAsync(r, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, set_control(h->dctrl, maxiter, nrhs, slot(h, S_BN), tol2, slot(h, S_STOP), h->s), "control init");
+  pcg_start(h, pmode, nrhs);
   if (pmode) {
     h->vcycles++;
     h->fine_applies += 4;
   }
-  const double stop = tol * tol * bn;
   const int per_it_fine = 1 + (pmode ? 4 : 0);
+  int it = 0, status = 0;
   if (h->use_graphs && !h->prof_on) {
-    if (!h->loop_exec[pmode]) h->loop_exec[pmode] = build_loop_graph(h, x, pmode);
-    ck(h, set_control(h->dctrl, maxiter, s + S_STOP, stop, h->s), "control init");
+    const int key = pmode + 3 * (nrhs - 1);
+    auto& exec = h->loop_exec[key];
+    if (!exec) exec = build_loop_graph(h, x, pmode, nrhs);
     ck(h, cudaEventRecord(h->fence[0], h->s), "event");
     ck(h, cudaStreamWaitEvent(h->gs, h->fence[0], 0), "wait");
-    ck(h, cudaGraphLaunch(h->loop_exec[pmode], h->gs), "graph launch");
+    ck(h, cudaGraphLaunch(exec, h->gs), "graph launch");
     ck(h, cudaEventRecord(h->fence[1], h->gs), "event");
     ck(h, cudaStreamWaitEvent(h->s, h->fence[1], 0), "wait");
-    ck(h, cudaMemcpyAsync(h->hscal, h->dctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+    ck(h, cudaMemcpyAsync(h->hctrl, h->dctrl, (4 + 2 * nrhs) * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
     sync(h);
-    int ctrl[2];
-    std::memcpy(ctrl, h->hscal, sizeof(ctrl));
-    const int it = ctrl[0];
+    it = h->hctrl[0];
+    status = h->hctrl[1];
     add_launches((long long)it * h->loop_kernels[pmode]);
     h->fine_applies += (long long)it * per_it_fine;
     if (pmode) h->vcycles += it;
-    if (ctrl[1] == 2) {
-      st = MG_ERR_BREAKDOWN;
-      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
-    } else if (ctrl[1] == 3) {
-      st = MG_ERR_NOCONV;
-      h->err = "maximum iterations reached";
-    }
-    return it;
-  }
-  int it = 0;
-  while (it < maxiter) {
-    apply_pq(h);
-    h->fine_applies++;
-    pcg_update(h, x, pmode);
-    ck(h, cudaMemcpyAsync(h->hscal, s + S_PQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
-    ck(h, cudaMemcpyAsync(h->hscal + 2, s + S_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+  } else {
+    // eager loop: the control decisions of k_cg_control, taken on the host
+    std::vector<int> ctrl(4 + 2 * nrhs);
+    ck(h, cudaMemcpyAsync(ctrl.data(), h->dctrl, ctrl.size() * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
     sync(h);
-    ++it;
-    const double pq = h->hscal[0], rr = h->hscal[2];
-    if (!(pq > 0.0) || !(rr == rr)) {
-      st = MG_ERR_BREAKDOWN;
-      h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
-      return it;
+    std::vector<double> pq(2 * nrhs), rr(2 * nrhs), stop(2 * nrhs);
+    ck(h, cudaMemcpyAsync(stop.data(), slot(h, S_STOP), stop.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    status = 0;
+    while (status == 0) {
+      apply_pq(h, nrhs);
+      h->fine_applies++;
+      pcg_update(h, x, pmode, nrhs);
+      ck(h, cudaMemcpyAsync(pq.data(), slot(h, S_PQ), pq.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+      ck(h, cudaMemcpyAsync(rr.data(), slot(h, S_RR), rr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+      sync(h);
+      ++it;
+      int running = 0, broken = 0;
+      for (int k = 0; k < nrhs; ++k) {
+        int& fr = ctrl[4 + k];
+        if (fr) continue;
+        if (!(pq[2 * k] > 0.0) || !(rr[2 * k] == rr[2 * k])) { fr = 2; ctrl[4 + nrhs + k] = it; broken = 1; }
+        else if (rr[2 * k] <= stop[2 * k]) { fr = 1; ctrl[4 + nrhs + k] = it; }
+        else ++running;
+      }
+      status = running ? 0 : 1;
+      if (broken) status = 2;
+      else if (running && it >= maxiter) status = 3;
+      if (status == 3)
+        for (int k = 0; k < nrhs; ++k)
+          if (!ctrl[4 + k]) ctrl[4 + nrhs + k] = it;
+      ck(h, cudaMemcpyAsync(h->dctrl + 4, ctrl.data() + 4, nrhs * sizeof(int), cudaMemcpyHostToDevice, h->s), "frozen");
+      sync(h);
+      if (status != 0) break;
+      pcg_direction(h, pmode, nrhs);
+      if (pmode) {
+        h->vcycles++;
+        h->fine_applies += 4;
+      }
     }
-    if (rr <= stop) return it;
-    pcg_direction(h, pmode);
-    if (pmode) {
-      h->vcycles++;
-      h->fine_applies += 4;
-    }
+    std::memcpy(h->hctrl, ctrl.data(), ctrl.size() * sizeof(int));
   }
-  st = MG_ERR_NOCONV;
-  h->err = "maximum iterations reached";
+  for (int k = 0; k < nrhs; ++k) iters[k] += h->hctrl[4 + nrhs + k];
+  if (status == 2) {
+    st = MG_ERR_BREAKDOWN;
+    h->err = "CG breakdown: <p, A p> <= 0 or non-finite residual";
+  } else if (status == 3) {
+    st = MG_ERR_NOCONV;
+    h->err = "maximum iterations reached";
+  }
   return it;
 }
 
-// True relative residual |b - A x| / |b| in FP64; also leaves r = b - A x in v.
-double true_residual(mg_handle* h, const void* b, const void* x, void* r) {
-  Level& F = h->lv[0];
-  const long long n = F.count();
-  double* s = h->scal;
-  apply_level<double>(h, 0, x, r, 1, W_F64);
+// True residuals |b - A x|^2 of nrhs vectors into slot S_NR (r receives b - A x).
+void true_residuals(mg_handle* h, const void* b, const void* x, void* r, int nrhs) {
+  const long long n = h->lv[0].count();
+  apply_level<double>(h, 0, x, r, nrhs, W_F64, ep_lincomb(-1.0, b, 1.0));
   h->fine_applies++;
-  ck(h, sub_from<double>(b, r, n, h->s), "residual");
-  ck(h, norm2<double>(r, n, 1, h->partials, s + S_NR, h->s), "norm");
-  ck(h, norm2<double>(b, n, 1, h->partials, s + S_BN, h->s), "norm");
-  const double rr = read_scalar(h, S_NR);
-  const double bn = read_scalar(h, S_BN);
-  return bn > 0 ? std::sqrt(rr / bn) : 0.0;
+  ck(h, norm2<double>(r, n, nrhs, h->partials, slot(h, S_NR), h->s), "norm");
 }
 
-mg_status solve_one(mg_handle* h, const void* b, void* x, double tol, int maxiter, int solver,
-                    mg_solve_info* info) {
-  mg_status st = MG_OK;
+// Solves nrhs <= max_rhs right-hand sides together; restarts from the true
+// residual when the recursive one has drifted from it.
+mg_status solve_batch(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
+                      int solver, mg_solve_info* info) {
   const long long n = h->lv[0].count();
-  int iters = 0, refinements = 0;
+  const int pmode = solver == MG_SOLVER_MGCG_FP64 ? 1 : solver == MG_SOLVER_MGCG_MIXED ? 2 : 0;
+  if (solver != MG_SOLVER_MGCG_FP64 && solver != MG_SOLVER_CG_FP64 && solver != MG_SOLVER_MGCG_MIXED)
+    fail(h, MG_ERR_ARG, "unknown solver");
   h->fine_applies = 0;
   h->vcycles = 0;
-  ck(h, norm2<double>(b, n, 1, h->partials, h->scal + S_T0, h->s), "norm");
-  {
-    const double b2 = read_scalar(h, S_T0);
-    if (!(b2 == b2) || std::isinf(b2)) fail(h, MG_ERR_BREAKDOWN, "non-finite right-hand side");
-  }
-  if (solver == MG_SOLVER_MGCG_FP64 || solver == MG_SOLVER_CG_FP64 ||
-      solver == MG_SOLVER_MGCG_MIXED) {
-    // PCG on the true residual; when the recursive residual has drifted from
-    // the true one, restart from rt = b - A x with the remaining target.
-    const int pre = solver == MG_SOLVER_MGCG_FP64 ? 1 : solver == MG_SOLVER_MGCG_MIXED ? 2 : 0;
-    ck(h, cudaMemsetAsync(x, 0, n * sizeof(double2), h->s), "memset");
-    void* xc = h->sv64[5];
-    void* rt = h->sv64[0];
-    ck(h, norm2<double>(b, n, 1, h->partials, h->scal + S_T0, h->s), "norm");
-    const double bnrm = std::sqrt(read_scalar(h, S_T0));
-    ck(h, cudaMemcpyAsync(rt, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-    double rnrm = bnrm;
-    for (int cycle = 0; cycle < 8 && bnrm > 0.0; ++cycle) {
-      const double rel = cycle == 0 ? tol : std::min(0.5, 0.5 * tol * bnrm / rnrm);
-      iters += pcg(h, rt, xc, rel, maxiter - iters, pre, st);
-      ck(h, lincomb<double>(x, 1.0, x, 1.0, xc, 0.0, nullptr, n, 1, h->s), "accumulate");
-      if (st != MG_OK && st != MG_ERR_NOCONV) break;
-      const double res = true_residual(h, b, x, rt);
-      if (res <= tol) { st = MG_OK; break; }
-      if (iters >= maxiter) { st = MG_ERR_NOCONV; h->err = "maximum iterations reached"; break; }
-      rnrm = res * bnrm;
-      refinements++;
-    }
-  } else {
-    fail(h, MG_ERR_ARG, "unknown solver");
+  std::vector<double> hb(2 * nrhs), hr(2 * nrhs);
+  ck(h, norm2<double>(b, n, nrhs, h->partials, slot(h, S_BN), h->s), "norm");
+  ck(h, cudaMemcpyAsync(hb.data(), slot(h, S_BN), hb.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+  sync(h);
+  for (int k = 0; k < nrhs; ++k)
+    if (!(hb[2 * k] == hb[2 * k]) || std::isinf(hb[2 * k]))
+      fail(h, MG_ERR_BREAKDOWN, "non-finite right-hand side");
+  ck(h, cudaMemsetAsync(x, 0, n * nrhs * sizeof(double2), h->s), "memset");
+  void* xc = h->sv64[5];
+  void* rt = h->sv64[0];
+  ck(h, cudaMemcpyAsync(rt, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  std::vector<int> iters(nrhs, 0);
+  mg_status st = MG_OK;
+  int total = 0, restarts = 0;
+  for (int cycle = 0; cycle < 8; ++cycle) {
+    // target |r|^2 <= tol2 |b|^2: tol^2 first, then half of it on restarts
+    const double tol2 = cycle == 0 ? tol * tol : 0.25 * tol * tol;
+    total += pcg(h, rt, xc, tol2, maxiter - total, pmode, nrhs, iters, st);
+    ck(h, lincomb<double>(x, 1.0, x, 1.0, xc, 0.0, nullptr, n * nrhs, 1, h->s), "accumulate");
+    if (st != MG_OK && st != MG_ERR_NOCONV) break;
+    true_residuals(h, b, x, rt, nrhs);
+    ck(h, cudaMemcpyAsync(hr.data(), slot(h, S_NR), hr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    bool done = true;
+    for (int k = 0; k < nrhs; ++k)
+      if (hr[2 * k] > tol * tol * hb[2 * k]) done = false;
+    if (done) { st = MG_OK; break; }
+    if (total >= maxiter) { st = MG_ERR_NOCONV; h->err = "maximum iterations reached"; break; }
+    restarts++;
   }
   if (info) {
-    info->iterations = iters;
-    info->refinements = refinements;
-    info->true_residual = true_residual(h, b, x, h->sv64[0]);
-    info->fine_applies = h->fine_applies;
-    info->vcycles = h->vcycles;
+    true_residuals(h, b, x, h->sv64[0], nrhs);
+    ck(h, cudaMemcpyAsync(hr.data(), slot(h, S_NR), hr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
+    sync(h);
+    for (int k = 0; k < nrhs; ++k) {
+      info[k].iterations = iters[k];
+      info[k].refinements = restarts;
+      info[k].true_residual = hb[2 * k] > 0 ? std::sqrt(hr[2 * k] / hb[2 * k]) : 0.0;
+      info[k].fine_applies = h->fine_applies;
+      info[k].vcycles = h->vcycles;
+    }
   }
   return st;
 }
@@ -703,6 +724,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->coarsest_refine_max = 12;
   p->inner_coarsest_refine = 1;
   p->vcycle_coarse_bf16 = 1;
+  p->max_rhs = 1;
   return MG_OK;
 }
 
@@ -732,6 +754,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
   h->p = *params;
   h->s = (cudaStream_t)stream;
   h->L = params->nlevels;
+  h->R = params->max_rhs;
   mg_status st = guarded(h, [&]() {
     const mg_params& P = h->p;
     // geometry
@@ -746,21 +769,22 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       }
     }
     ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
-    h->scal = dalloc<double>(h, S_MAX * sizeof(double));
+    h->scal = dalloc<double>(h, (size_t)S_COUNT * 2 * h->R * sizeof(double));
     h->dflag = dalloc<int>(h, sizeof(int));
-    h->dctrl = dalloc<int>(h, 4 * sizeof(int));
+    h->dctrl = dalloc<int>(h, (4 + 2 * h->R) * sizeof(int));
+    ck(h, cudaMallocHost((void**)&h->hctrl, (4 + 2 * h->R) * sizeof(int)), "pinned alloc");
     ck(h, cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream create");
     ck(h, cudaEventCreateWithFlags(&h->fence[0], cudaEventDisableTiming), "event create");
     ck(h, cudaEventCreateWithFlags(&h->fence[1], cudaEventDisableTiming), "event create");
     if (const char* e = std::getenv("MG_NO_GRAPHS")) h->use_graphs = e[0] == '0';
-    int max_nv = 1;
+    int max_nv = h->R;
     for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
     ensure_partials(h, max_nv);
     // links
     const long long V = h->lv[0].V;
     h->U64 = dalloc<double2>(h, 2 * V * sizeof(double2));
     h->U32 = dalloc<float2>(h, 2 * V * sizeof(float2));
-    ck(h, link_unitarity(gauge, 2 * V, h->scal + S_T0, h->s), "unitarity");
+    ck(h, link_unitarity(gauge, 2 * V, slot(h, S_T0), h->s), "unitarity");
     const double dev = read_scalar(h, S_T0);
     if (!(dev <= 1e-12)) fail(h, MG_ERR_ARG, "gauge links are not unit modulus (|U|-1 = " + std::to_string(dev) + ")");
     ck(h, fold_links<double>(gauge, h->U64, P.Lx, P.Lt, h->s), "fold");
@@ -771,8 +795,8 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       Level& L = h->lv[l];
       const size_t c = (size_t)L.count();
       for (int k = 0; k < 4; ++k) {
-        L.w64[k] = dalloc(h, c * sizeof(double2));
-        L.w32[k] = dalloc(h, c * sizeof(float2));
+        L.w64[k] = dalloc(h, c * h->R * sizeof(double2));
+        L.w32[k] = dalloc(h, c * h->R * sizeof(float2));
       }
       if (l > 0) {
         const size_t ab = (size_t)L.V * 9 * L.n * L.n;
@@ -787,8 +811,8 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       }
     }
     for (int k = 0; k < 6; ++k) {
-      h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(double2));
-      h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * sizeof(float2));
+      h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(double2));
+      h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(float2));
     }
     if (h->L > 1) {
       const Level& L0 = h->lv[0];
@@ -805,10 +829,10 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
       const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
       h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
-      h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * sizeof(float2));
-      h->cb = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
-      h->cx = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
-      h->cr = dalloc<double2>(h, (size_t)h->Nc * sizeof(double2));
+      h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
+      h->cb = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+      h->cx = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+      h->cr = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
     }
     // adaptive setup, level by level (Sec. 3)
     const double2* noise = (const double2*)P.setup_noise;
@@ -880,13 +904,16 @@ mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, i
   mg_status worst = MG_OK;
   mg_status st = guarded(h, [&]() {
     const long long n = h->lv[0].count();
-    for (int k = 0; k < nrhs; ++k) {
+    for (int k0 = 0; k0 < nrhs; k0 += h->R) {
+      const int nb = std::min(h->R, nrhs - k0);
       auto t0 = std::chrono::steady_clock::now();
-      mg_status one = solve_one(h, (const double2*)b + k * n, (double2*)x + k * n, tol, maxiter,
-                                solver, info ? info + k : nullptr);
+      mg_status one = solve_batch(h, (const double2*)b + k0 * n, (double2*)x + k0 * n, nb, tol,
+                                  maxiter, solver, info ? info + k0 : nullptr);
       sync(h);
       auto t1 = std::chrono::steady_clock::now();
-      if (info) info[k].milliseconds = std::chrono::duration<double, std::milli>(t1 - t0).count();
+      if (info)
+        for (int k = 0; k < nb; ++k)
+          info[k0 + k].milliseconds = std::chrono::duration<double, std::milli>(t1 - t0).count();
       if (one != MG_OK && worst == MG_OK) worst = one;
     }
   });
@@ -959,7 +986,7 @@ mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision) {
 mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out) {
   if (!h) return MG_ERR_ARG;
   if (!in || !out || h->L < 2) { h->err = "invalid arguments"; return MG_ERR_ARG; }
-  return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine); });
+  return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine, 1); });
 }
 
 mg_status mg_get_level(const mg_handle* h, int level, int* Lx, int* Lt, int* ndof, int* Nv) {

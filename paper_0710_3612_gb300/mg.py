@@ -33,7 +33,8 @@ class MgParams(ctypes.Structure):
                 ("setup_sweeps", ctypes.c_int), ("power_iters", ctypes.c_int),
                 ("omega_mr", ctypes.c_double), ("setup_noise", ctypes.c_void_p),
                 ("coarsest_tol", ctypes.c_double), ("coarsest_refine_max", ctypes.c_int),
-                ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int)]
+                ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int),
+                ("max_rhs", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):

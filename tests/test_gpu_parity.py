@@ -295,6 +295,49 @@ def test_graph_loop_matches_eager_loop(case, mg, solver):
     assert np.array_equal(xg, xe)
 
 
+@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed"])
+def test_batched_solve_matches_single(mg, solver):
+    """Five right-hand sides with max_rhs = 4 (one batch of 4, one of 1): every
+    solution meets the true-residual target and agrees with the one-at-a-time
+    solve within kappa * tol; iteration counts within one of each other."""
+    c = Case(mg, "3lvl_24x24")
+    code = mg.SOLVER_MGCG_FP64 if solver == "mgcg_fp64" else mg.SOLVER_MGCG_MIXED
+    try:
+        chis = W.gaussian_field((5, c.Lt, c.Lx, 2), 123)
+        b = np.stack([ow.apply_D(c.U, c.m, x, dagger=True) for x in chis])
+        A = c.H.levels[0].op
+        with mg.Multigrid(c.Ug, c.m, c.blocks, c.Nv, c.noise_g, max_rhs=4) as sb:
+            xb, ib = sb.solve(dev(b), tol=1e-10, maxiter=20000, solver=code)
+            xb = host(xb)
+        lam = np.linalg.eigvalsh(A.dense())
+        for k in range(5):
+            xs, i1 = c.solver.solve(dev(b[k]), tol=1e-10, maxiter=20000, solver=code)
+            xs = host(xs).reshape(b[k].shape)
+            res = np.linalg.norm(b[k] - A.apply(xb[k])) / np.linalg.norm(b[k])
+            assert res <= 1e-10 and ib[k].true_residual <= 1e-10
+            assert np.linalg.norm(xb[k] - xs) <= 2 * lam[-1] / lam[0] * 1e-10 * np.linalg.norm(xs)
+            assert abs(ib[k].iterations - i1[0].iterations) <= 1
+    finally:
+        c.solver.close()
+
+
+def test_batched_graph_matches_eager(mg):
+    c = Case(mg, "2lvl_24x16")
+    try:
+        chis = W.gaussian_field((3, c.Lt, c.Lx, 2), 7)
+        b = dev(np.stack([ow.apply_D(c.U, c.m, x, dagger=True) for x in chis]))
+        with mg.Multigrid(c.Ug, c.m, c.blocks, c.Nv, c.noise_g, max_rhs=3) as sb:
+            xg, ig = sb.solve(b, tol=1e-10, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+            xg = host(xg)
+            mg.mg_profile_enable(sb.h, True)
+            xe, ie = sb.solve(b, tol=1e-10, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+            xe = host(xe)
+        assert [i.iterations for i in ig] == [i.iterations for i in ie]
+        assert np.array_equal(xg, xe)
+    finally:
+        c.solver.close()
+
+
 def test_iteration_limit_reports_noconv(case, mg):
     chi = W.gaussian_field((case.Lt, case.Lx, 2), 91)
     b = dev(ow.apply_D(case.U, case.m, chi, dagger=True))
