@@ -106,9 +106,115 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
   }
 }
 
+// Multi-RHS coarse apply on tensor cores (BF16 operands, FP32 accumulation).
+// One CTA per coarse site j.  The complex contraction Y = sum_d A_j,d X_{j+d}
+// (n x 9n times 9n x nrhs) is realified with K ordered as (re, im) pairs, so
+// that one 32-bit register of an A fragment is one complex block entry --
+// (re, -im) for the rows of Re Y and (im, re) for the rows of Im Y -- and one
+// register of a B fragment is one complex entry of X.  mma.sync m16n8k16:
+// M = 16 complex rows (Re and Im tiles), N = 8 right-hand sides, K = 8
+// complex columns per step.  X is staged in shared memory as bf16 pairs,
+// [9n][nrhs8 + 8] (padding keeps the fragment loads conflict-free).
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *(uint32_t*)&v; }
+
+__global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restrict__ in, float2* out,
+                                                          const __nv_bfloat162* __restrict__ A,
+                                                          int Lx, int Lt, int n, int nrhs,
+                                                          Epilogue ep) {
+  extern __shared__ __nv_bfloat162 Xs[];
+  const int V = Lx * Lt;
+  const int j = blockIdx.x;
+  const int x = j % Lx, t = j / Lx;
+  const int R8 = (nrhs + 7) / 8 * 8, RS = R8 + 8;
+  const int tid = threadIdx.x;
+  // stage X(j + d) for the 9 displacements, all right-hand sides
+  for (int q = tid; q < 9 * n * R8; q += blockDim.x) {
+    const int rhs = q % R8, c = q / R8, d = c / n, sdof = c % n;
+    int xn = x + d % 3 - 1, tn = t + d / 3 - 1;
+    xn = xn < 0 ? xn + Lx : (xn >= Lx ? xn - Lx : xn);
+    tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
+    float2 v = make_float2(0.f, 0.f);
+    if (rhs < nrhs) v = in[((long long)rhs * V + xn + Lx * tn) * n + sdof];
+    Xs[c * RS + rhs] = __floats2bfloat162_rn(v.x, v.y);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tg = lane & 3;
+  const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
+  for (int nt = warp; nt < R8 / 8; nt += 4) {
+    for (int r0 = 0; r0 < n; r0 += 16) {
+      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int c0 = 0; c0 < 9 * n; c0 += 8) {
+        const int d = c0 / n, s0 = c0 % n;
+        const __nv_bfloat162* Ab = A + (((long long)j * 9 + d) * n) * n;
+        __nv_bfloat162 e[4];
+        const int ra = r0 + g, rb = r0 + g + 8;
+        e[0] = ra < n ? Ab[ra * n + s0 + tg] : zero;
+        e[1] = rb < n ? Ab[rb * n + s0 + tg] : zero;
+        e[2] = ra < n ? Ab[ra * n + s0 + tg + 4] : zero;
+        e[3] = rb < n ? Ab[rb * n + s0 + tg + 4] : zero;
+        uint32_t aRe[4], aIm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          aRe[u] = bf2_bits(__halves2bfloat162(e[u].x, __hneg(e[u].y)));   // (re, -im)
+          aIm[u] = bf2_bits(__halves2bfloat162(e[u].y, e[u].x));           // (im, re)
+        }
+        const uint32_t b0 = bf2_bits(Xs[(c0 + tg) * RS + nt * 8 + g]);
+        const uint32_t b1 = bf2_bits(Xs[(c0 + tg + 4) * RS + nt * 8 + g]);
+        mma_bf16_16816(re, aRe, b0, b1);
+        mma_bf16_16816(im, aIm, b0, b1);
+      }
+      // c[0], c[1]: row g, rhs 2tg, 2tg+1; c[2], c[3]: row g + 8
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + g + (u >= 2 ? 8 : 0);
+        const int rhs = nt * 8 + 2 * tg + (u & 1);
+        if (r >= n || rhs >= nrhs) continue;
+        const long long o = ((long long)rhs * V + j) * n + r;
+        float2 y = make_float2((float)ep.ca * re[u], (float)ep.ca * im[u]);
+        if (ep.U) {
+          const float2 w = ((const float2*)ep.U)[o];
+          y = make_float2(y.x + (float)ep.cu * w.x, y.y + (float)ep.cu * w.y);
+        }
+        if (ep.W) {
+          const float2 w = ((const float2*)ep.W)[o];
+          y = make_float2(y.x + (float)ep.cw * w.x, y.y + (float)ep.cw * w.y);
+        }
+        out[o] = y;
+      }
+    }
+  }
+}
+
+bool coarse_apply_tensor(int weights, int n, int nrhs) {
+  return weights == W_BF16 && nrhs >= 8 && n % 8 == 0 && n <= 32 && nrhs <= 64;
+}
+
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
                          int n, int nrhs, const Epilogue& ep, cudaStream_t s) {
   if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
+  if (coarse_apply_tensor(weights, n, nrhs)) {
+    const int R8 = (nrhs + 7) / 8 * 8;
+    const size_t smem = (size_t)9 * n * (R8 + 8) * sizeof(__nv_bfloat162);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_coarse_apply_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           100 * 1024);
+      attr = true;
+    }
+    k_coarse_apply_mma<<<Lx * Lt, 128, smem, s>>>((const float2*)in, (float2*)out,
+                                                  (const __nv_bfloat162*)A, Lx, Lt, n, nrhs, ep);
+    count_launch();
+    return cudaGetLastError();
+  }
   dim3 grid(Lx * Lt, nrhs);
   const int threads = (9 * n + 31) / 32 * 32;
   if (weights == W_F64)

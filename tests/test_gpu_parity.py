@@ -161,12 +161,14 @@ def test_coarse_operators(case, mg):
         check(got, op.M, rowmax, 1e-11, f"A_c level {l + 1}")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
-def test_apply_coarse(case, mg, prec):
+@pytest.mark.parametrize("prec,nrhs", [("f64", 2), ("f32", 2), ("bf16", 2), ("bf16", 16),
+                                       ("bf16", 13)])
+def test_apply_coarse(case, mg, prec, nrhs):
+    """nrhs >= 8 with BF16 blocks runs on the tensor cores (BF16 operands,
+    FP32 accumulation); 13 checks the right-hand-side padding."""
     H = case.H
     for l in range(1, H.L):
         op = H.levels[l].op
-        nrhs = 2
         v = W.gaussian_field((nrhs, op.Lt, op.Lx, op.n), 11 + l)
         want = op.apply(v)
         mag = omg.StencilOp(op.disp, np.abs(op.M)).apply(np.abs(v))
@@ -317,6 +319,28 @@ def test_batched_solve_matches_single(mg, solver):
             assert res <= 1e-10 and ib[k].true_residual <= 1e-10
             assert np.linalg.norm(xb[k] - xs) <= 2 * lam[-1] / lam[0] * 1e-10 * np.linalg.norm(xs)
             assert abs(ib[k].iterations - i1[0].iterations) <= 1
+    finally:
+        c.solver.close()
+
+
+def test_batched_tensor_core_vcycle_solve(mg):
+    """Eight right-hand sides together: the coarse applies of the FP32 V-cycle
+    run on the tensor cores; every solve meets the true-residual target and
+    matches the oracle's solution within kappa * tol."""
+    c = Case(mg, "3lvl_24x24")
+    try:
+        chis = W.gaussian_field((8, c.Lt, c.Lx, 2), 321)
+        b = np.stack([ow.apply_D(c.U, c.m, x, dagger=True) for x in chis])
+        A = c.H.levels[0].op
+        lam = np.linalg.eigvalsh(A.dense())
+        with mg.Multigrid(c.Ug, c.m, c.blocks, c.Nv, c.noise_g, max_rhs=8) as sb:
+            xb, ib = sb.solve(dev(b), tol=1e-10, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+            xb = host(xb)
+        for k in range(8):
+            xo, _, _ = okr.mgcg(c.H, b[k], 1e-12)
+            res = np.linalg.norm(b[k] - A.apply(xb[k])) / np.linalg.norm(b[k])
+            assert res <= 1e-10 and ib[k].true_residual <= 1e-10
+            assert np.linalg.norm(xb[k] - xo) <= 2 * lam[-1] / lam[0] * 1e-10 * np.linalg.norm(xo)
     finally:
         c.solver.close()
 
