@@ -234,6 +234,10 @@ def gpu_bench(args):
     plain = timed(mg.SOLVER_MGCG_FP64, kp)
     plain_value = len(masses) * kp * world / (plain["total_ms"] / 1000.0)
 
+    # batched mixed-precision MG-CG: many right-hand sides of the same
+    # configuration at the near-critical mass in one Krylov loop
+    batched = batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world)
+
     # roofline: one profiled step, dominant kernel family by device time
     prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
     roof = roofline(prof, wl, load_peaks())
@@ -268,6 +272,7 @@ def gpu_bench(args):
                            "p50_ms": round(ppct(0.5), 3), "p99_ms": round(ppct(0.99), 3),
                            "per_mass": plain["per_mass"]},
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
+            "batched": batched,
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
             "e2e": e2e,
@@ -364,6 +369,58 @@ def stencil_gbs(mg, torch, dev, stream):
                 "bytes_per_site": 48}
     finally:
         mg.mg_destroy(h)
+
+
+def batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
+    """nrhs Gaussian sources chi_k (seeds chi_seed + 1000 + k), b_k = D^dagger chi_k,
+    solved together at the near-critical mass with the mixed solver (BF16 coarse
+    blocks on the tensor cores); solves/s against plain FP64 single-RHS MG-CG on
+    the same right-hand sides (first two of them)."""
+    nrhs = args.batch_rhs
+    if nrhs < 1:
+        return None
+    chis = np.stack([W.gaussian_field((wl["Lt"], wl["Lx"], 2), wl["chi_seed"] + 1000 + k)
+                     for k in range(nrhs)])
+    chi_d = torch.from_numpy(chis).to(dev)
+    b_d = torch.empty_like(chi_d)
+    x_d = torch.empty_like(chi_d)
+    tol = wl["tol"]
+    out = {"nrhs": nrhs, "mass": masses[0]}
+    with mg.Multigrid(U_d, masses[0], wl["blocks"], wl["Nv"], noise_d,
+                      setup_sweeps=wl["setup_sweeps"], max_rhs=nrhs) as s:
+        mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, mg.SOLVER_MGCG_MIXED)     # warm-up
+        reps = []
+        for _ in range(max(1, args.batch_reps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, mg.SOLVER_MGCG_MIXED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != 0 or max(i.true_residual for i in info) > tol:
+                raise RuntimeError("batched solve did not converge")
+            reps.append(e0.elapsed_time(e1))
+        ms = statistics.median(reps)
+        out.update({"value": round(world * nrhs / (ms / 1000.0), 3), "unit": UNIT,
+                    "ms_per_batch": round(ms, 3),
+                    "iterations_max": max(i.iterations for i in info),
+                    "max_true_residual": max(i.true_residual for i in info)})
+    with mg.Multigrid(U_d, masses[0], wl["blocks"], wl["Nv"], noise_d,
+                      setup_sweeps=wl["setup_sweeps"]) as s:
+        ts = []
+        for k in range(2):
+            bk = b_d[k].contiguous()
+            xk = torch.empty_like(bk)
+            mg.mg_solve(s.h, bk, xk, 1, tol, 200000, mg.SOLVER_MGCG_FP64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mg.mg_solve(s.h, bk, xk, 1, tol, 200000, mg.SOLVER_MGCG_FP64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out["plain_fp64_single_rhs"] = round(1000.0 / statistics.median(ts), 3)
+        out["vs_plain_fp64_single_rhs"] = round(out["value"] / world / out["plain_fp64_single_rhs"], 2)
+    return out
 
 
 def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, world):
@@ -554,6 +611,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--oracle-iters", type=int, default=20)
+    ap.add_argument("--batch-rhs", type=int, default=64,
+                    help="right-hand sides of the batched leg (0 skips it)")
+    ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
