@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
 // (re, -im) for the rows of Re Y and (im, re) for the rows of Im Y -- and one
 // register of a B fragment is one complex entry of X.  mma.sync m16n8k16:
 // M = 16 complex rows (Re and Im tiles), N = 8 right-hand sides, K = 8
-// complex columns per step.  X is staged in shared memory as bf16 pairs,
-// [9n][nrhs8 + 8] (padding keeps the fragment loads conflict-free).
+// complex columns per step.  X is staged in shared memory as a pair of bf16
+// splits, X = Xhi + Xlo (Xlo = bf16(X - Xhi)), each [9n][nrhs8 + 8] (padding
+// keeps the fragment loads conflict-free); two MMAs per product carry X to
+// about 16 significant bits, so only the stored BF16 blocks round.
 __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
                                                uint32_t b1) {
   asm volatile(
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restri
   const int j = blockIdx.x;
   const int x = j % Lx, t = j / Lx;
   const int R8 = (nrhs + 7) / 8 * 8, RS = R8 + 8;
+  __nv_bfloat162* Xl = Xs + 9 * n * RS;
   const int tid = threadIdx.x;
   // stage X(j + d) for the 9 displacements, all right-hand sides
   for (int q = tid; q < 9 * n * R8; q += blockDim.x) {
@@ -144,7 +147,10 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restri
     tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
     float2 v = make_float2(0.f, 0.f);
     if (rhs < nrhs) v = in[((long long)rhs * V + xn + Lx * tn) * n + sdof];
-    Xs[c * RS + rhs] = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+    const float2 hf = __bfloat1622float2(hi);
+    Xs[c * RS + rhs] = hi;
+    Xl[c * RS + rhs] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tg = lane & 3;
@@ -167,10 +173,13 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restri
           aRe[u] = bf2_bits(__halves2bfloat162(e[u].x, __hneg(e[u].y)));   // (re, -im)
           aIm[u] = bf2_bits(__halves2bfloat162(e[u].y, e[u].x));           // (im, re)
         }
-        const uint32_t b0 = bf2_bits(Xs[(c0 + tg) * RS + nt * 8 + g]);
-        const uint32_t b1 = bf2_bits(Xs[(c0 + tg + 4) * RS + nt * 8 + g]);
+        const int i0 = (c0 + tg) * RS + nt * 8 + g, i1 = (c0 + tg + 4) * RS + nt * 8 + g;
+        const uint32_t b0 = bf2_bits(Xs[i0]), b1 = bf2_bits(Xs[i1]);
+        const uint32_t l0 = bf2_bits(Xl[i0]), l1 = bf2_bits(Xl[i1]);
         mma_bf16_16816(re, aRe, b0, b1);
         mma_bf16_16816(im, aIm, b0, b1);
+        mma_bf16_16816(re, aRe, l0, l1);
+        mma_bf16_16816(im, aIm, l0, l1);
       }
       // c[0], c[1]: row g, rhs 2tg, 2tg+1; c[2], c[3]: row g + 8
 #pragma unroll
@@ -203,11 +212,11 @@ cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, 
   if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
   if (coarse_apply_tensor(weights, n, nrhs)) {
     const int R8 = (nrhs + 7) / 8 * 8;
-    const size_t smem = (size_t)9 * n * (R8 + 8) * sizeof(__nv_bfloat162);
+    const size_t smem = (size_t)2 * 9 * n * (R8 + 8) * sizeof(__nv_bfloat162);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_coarse_apply_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           100 * 1024);
+                           200 * 1024);
       attr = true;
     }
     k_coarse_apply_mma<<<Lx * Lt, 128, smem, s>>>((const float2*)in, (float2*)out,
