@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restri
   __nv_bfloat162* Xl = Xs + 9 * n * RS;
   const int tid = threadIdx.x;
   // stage X(j + d) for the 9 displacements, all right-hand sides
-  for (int q = tid; q < 9 * n * R8; q += blockDim.x) {
-    const int rhs = q % R8, c = q / R8, d = c / n, sdof = c % n;
+  for (int q = tid; q < 9 * n * R8; q += blockDim.x) {        // dof fastest: coalesced reads
+    const int sdof = q % n, rhs = (q / n) % R8, d = q / (n * R8), c = d * n + sdof;
     int xn = x + d % 3 - 1, tn = t + d / 3 - 1;
     xn = xn < 0 ? xn + Lx : (xn >= Lx ? xn - Lx : xn);
     tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
@@ -296,9 +296,29 @@ __global__ void __launch_bounds__(256) k_restrict(const cplx_t<R>* __restrict__ 
   if (lane == 0) coarse[(long long)blockIdx.y * Vc * nc + w] = mk((R)re, (R)im);
 }
 
+template <typename R> __global__ void k_restrict_multi(const cplx_t<R>*, cplx_t<R>*,
+                                                       const cplx_t<R>*, int, int, int, int, int,
+                                                       int, int);
+template <typename R> __global__ void k_prolong_multi(const cplx_t<R>*, cplx_t<R>*, const cplx_t<R>*,
+                                                      int, int, int, int, int, int, int, bool);
+static size_t transfer_multi_smem(int, int, int, int, int, size_t, bool);
+
 template <typename R>
 cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
                         int bt, int h, int Nv, int nrhs, cudaStream_t s) {
+  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), true);
+  if (nrhs >= 8 && sm <= 96 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_restrict_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr = true;
+    }
+    k_restrict_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
+        (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+        nrhs);
+    count_launch();
+    return cudaGetLastError();
+  }
   const int warps = (Lx / bx) * (Lt / bt) * 2 * Nv;
   k_restrict<R><<<dim3((warps + 7) / 8, nrhs), 256, 0, s>>>(
       (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
@@ -328,11 +348,96 @@ __global__ void k_prolong(const cplx_t<R>* __restrict__ coarse, cplx_t<R>* __res
 template <typename R>
 cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
                        int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s) {
+  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), false);
+  if (nrhs >= 8 && sm <= 96 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_prolong_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr = true;
+    }
+    k_prolong_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
+        (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+        nrhs, accumulate);
+    count_launch();
+    return cudaGetLastError();
+  }
   const int tot = Lx * Lt * 2 * h;
   k_prolong<R><<<dim3((tot + 255) / 256, nrhs), 256, 0, s>>>(
       (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
       accumulate); count_launch();
   return cudaGetLastError();
+}
+
+// Many right-hand sides: one CTA per coarse site j stages the block's vectors
+// and the block's slice of every right-hand side in shared memory, so the
+// vectors are read once per site instead of once per right-hand side.
+template <typename R>
+__global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restrict__ fine,
+                                                        cplx_t<R>* __restrict__ coarse,
+                                                        const cplx_t<R>* __restrict__ Vst, int Lx,
+                                                        int Lt, int bx, int bt, int h, int Nv,
+                                                        int nrhs) {
+  using C = cplx_t<R>;
+  extern __shared__ unsigned char smraw[];
+  const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
+  C* sv = (C*)smraw;                                 // [b2][2][Nv][h]
+  C* sr = sv + b2 * 2 * Nv * h;                      // [nrhs][b2][nf]
+  const int j = blockIdx.x, V = Lx * Lt;
+  for (int q = threadIdx.x; q < b2 * 2 * Nv * h; q += blockDim.x) {
+    const int o = q / (2 * Nv * h), rest = q % (2 * Nv * h);
+    sv[q] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
+  }
+  for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
+    const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
+    sr[q] = fine[((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nrhs * nc; q += blockDim.x) {
+    const int s = q % nc, rhs = q / nc, c = s / Nv, k = s % Nv;
+    double re = 0.0, im = 0.0;
+    for (int o = 0; o < b2; ++o)
+      for (int a = 0; a < h; ++a) {
+        const C v = sv[((o * 2 + c) * Nv + k) * h + a];
+        const C r = sr[(rhs * b2 + o) * nf + c * h + a];
+        re += (double)v.x * r.x + (double)v.y * r.y;
+        im += (double)v.x * r.y - (double)v.y * r.x;
+      }
+    coarse[((long long)rhs * Vc + j) * nc + s] = mk((R)re, (R)im);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restrict__ coarse,
+                                                       cplx_t<R>* __restrict__ fine,
+                                                       const cplx_t<R>* __restrict__ Vst, int Lx,
+                                                       int Lt, int bx, int bt, int h, int Nv,
+                                                       int nrhs, bool accumulate) {
+  using C = cplx_t<R>;
+  extern __shared__ unsigned char smraw[];
+  const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
+  C* sv = (C*)smraw;                                 // [b2][2][Nv][h]
+  C* se = sv + b2 * 2 * Nv * h;                      // [nrhs][nc]
+  const int j = blockIdx.x, V = Lx * Lt;
+  for (int q = threadIdx.x; q < b2 * 2 * Nv * h; q += blockDim.x) {
+    const int o = q / (2 * Nv * h), rest = q % (2 * Nv * h);
+    sv[q] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
+  }
+  for (int q = threadIdx.x; q < nrhs * nc; q += blockDim.x)
+    se[q] = coarse[((long long)(q / nc) * Vc + j) * nc + q % nc];
+  __syncthreads();
+  for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
+    const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
+    const int c = comp / h, a = comp % h;
+    C acc = mk((R)0, (R)0);
+    for (int k = 0; k < Nv; ++k) cfma(acc, sv[((o * 2 + c) * Nv + k) * h + a], se[rhs * nc + c * Nv + k]);
+    const long long g = ((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp;
+    fine[g] = accumulate ? cadd(fine[g], acc) : acc;
+  }
+}
+
+static size_t transfer_multi_smem(int bx, int bt, int h, int Nv, int nrhs, size_t csz, bool restr) {
+  const size_t b2 = (size_t)bx * bt;
+  return csz * (b2 * 2 * Nv * h + (restr ? (size_t)nrhs * b2 * 2 * h : (size_t)nrhs * 2 * Nv));
 }
 
 // ---------------------------------------------------------------------------

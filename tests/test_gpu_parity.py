@@ -184,13 +184,13 @@ def test_apply_coarse(case, mg, prec, nrhs):
             check(host(out), want, mag, TOL32 if prec == "f32" else TOL16, f"coarse {prec}")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_restrict_prolong(case, mg, prec):
+@pytest.mark.parametrize("prec,nrhs", [("f64", 2), ("f32", 2), ("f64", 9), ("f32", 9)])
+def test_restrict_prolong(case, mg, prec, nrhs):
+    """nrhs >= 8 uses the one-CTA-per-coarse-site kernels."""
     H = case.H
     tol = 1e-11 if prec == "f64" else TOL32
     for l in range(H.L - 1):
         lv = H.levels[l]
-        nrhs = 2
         r = W.gaussian_field((nrhs, lv.Lt, lv.Lx, lv.n), 21 + l)
         ec = W.gaussian_field((nrhs, lv.Lt // lv.bt, lv.Lx // lv.bx, 2 * lv.Nv), 31 + l)
         Pabs = np.abs(omg.prolongator_matrix(lv.V))
