@@ -296,78 +296,6 @@ __global__ void __launch_bounds__(256) k_restrict(const cplx_t<R>* __restrict__ 
   if (lane == 0) coarse[(long long)blockIdx.y * Vc * nc + w] = mk((R)re, (R)im);
 }
 
-template <typename R> __global__ void k_restrict_multi(const cplx_t<R>*, cplx_t<R>*,
-                                                       const cplx_t<R>*, int, int, int, int, int,
-                                                       int, int);
-template <typename R> __global__ void k_prolong_multi(const cplx_t<R>*, cplx_t<R>*, const cplx_t<R>*,
-                                                      int, int, int, int, int, int, int, bool);
-static size_t transfer_multi_smem(int, int, int, int, int, size_t, bool);
-
-template <typename R>
-cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
-                        int bt, int h, int Nv, int nrhs, cudaStream_t s) {
-  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), true);
-  if (nrhs >= 8 && sm <= 96 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_restrict_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr = true;
-    }
-    k_restrict_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
-        (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-        nrhs);
-    count_launch();
-    return cudaGetLastError();
-  }
-  const int warps = (Lx / bx) * (Lt / bt) * 2 * Nv;
-  k_restrict<R><<<dim3((warps + 7) / 8, nrhs), 256, 0, s>>>(
-      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
-  count_launch();
-  return cudaGetLastError();
-}
-
-template <typename R>
-__global__ void k_prolong(const cplx_t<R>* __restrict__ coarse, cplx_t<R>* __restrict__ fine,
-                          const cplx_t<R>* __restrict__ Vst, int Lx, int Lt, int bx, int bt, int h,
-                          int Nv, bool accumulate) {
-  const int V = Lx * Lt, nf = 2 * h, nc = 2 * Nv;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= V * nf) return;
-  const int i = idx / nf, comp = idx % nf, c = comp / h, a = comp % h;
-  const int x = i % Lx, t = i / Lx;
-  const int j = coarse_site(x, t, Lx, bx, bt);
-  const cplx_t<R>* e = coarse + (long long)blockIdx.y * (V / (bx * bt)) * nc + (long long)j * nc +
-                       c * Nv;
-  const cplx_t<R>* v = Vst + ((long long)i * 2 + c) * Nv * h + a;
-  cplx_t<R> acc = mk((R)0, (R)0);
-  for (int k = 0; k < Nv; ++k) cfma(acc, v[(long long)k * h], e[k]);
-  const long long o = (long long)blockIdx.y * V * nf + idx;
-  fine[o] = accumulate ? cadd(fine[o], acc) : acc;
-}
-
-template <typename R>
-cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
-                       int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s) {
-  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), false);
-  if (nrhs >= 8 && sm <= 96 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_prolong_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr = true;
-    }
-    k_prolong_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
-        (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-        nrhs, accumulate);
-    count_launch();
-    return cudaGetLastError();
-  }
-  const int tot = Lx * Lt * 2 * h;
-  k_prolong<R><<<dim3((tot + 255) / 256, nrhs), 256, 0, s>>>(
-      (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-      accumulate); count_launch();
-  return cudaGetLastError();
-}
-
 // Many right-hand sides: one CTA per coarse site j stages the block's vectors
 // and the block's slice of every right-hand side in shared memory, so the
 // vectors are read once per site instead of once per right-hand side.
@@ -438,6 +366,71 @@ __global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restri
 static size_t transfer_multi_smem(int bx, int bt, int h, int Nv, int nrhs, size_t csz, bool restr) {
   const size_t b2 = (size_t)bx * bt;
   return csz * (b2 * 2 * Nv * h + (restr ? (size_t)nrhs * b2 * 2 * h : (size_t)nrhs * 2 * Nv));
+}
+
+template <typename R>
+cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
+                        int bt, int h, int Nv, int nrhs, cudaStream_t s) {
+  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), true);
+  if (nrhs >= 8 && sm <= 96 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_restrict_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr = true;
+    }
+    k_restrict_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
+        (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+        nrhs);
+    count_launch();
+    return cudaGetLastError();
+  }
+  const int warps = (Lx / bx) * (Lt / bt) * 2 * Nv;
+  k_restrict<R><<<dim3((warps + 7) / 8, nrhs), 256, 0, s>>>(
+      (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_prolong(const cplx_t<R>* __restrict__ coarse, cplx_t<R>* __restrict__ fine,
+                          const cplx_t<R>* __restrict__ Vst, int Lx, int Lt, int bx, int bt, int h,
+                          int Nv, bool accumulate) {
+  const int V = Lx * Lt, nf = 2 * h, nc = 2 * Nv;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= V * nf) return;
+  const int i = idx / nf, comp = idx % nf, c = comp / h, a = comp % h;
+  const int x = i % Lx, t = i / Lx;
+  const int j = coarse_site(x, t, Lx, bx, bt);
+  const cplx_t<R>* e = coarse + (long long)blockIdx.y * (V / (bx * bt)) * nc + (long long)j * nc +
+                       c * Nv;
+  const cplx_t<R>* v = Vst + ((long long)i * 2 + c) * Nv * h + a;
+  cplx_t<R> acc = mk((R)0, (R)0);
+  for (int k = 0; k < Nv; ++k) cfma(acc, v[(long long)k * h], e[k]);
+  const long long o = (long long)blockIdx.y * V * nf + idx;
+  fine[o] = accumulate ? cadd(fine[o], acc) : acc;
+}
+
+template <typename R>
+cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
+                       int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s) {
+  const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), false);
+  if (nrhs >= 8 && sm <= 96 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_prolong_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr = true;
+    }
+    k_prolong_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
+        (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+        nrhs, accumulate);
+    count_launch();
+    return cudaGetLastError();
+  }
+  const int tot = Lx * Lt * 2 * h;
+  k_prolong<R><<<dim3((tot + 255) / 256, nrhs), 256, 0, s>>>(
+      (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
+      accumulate); count_launch();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
