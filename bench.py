@@ -557,9 +557,10 @@ def ncu_case(args):
     """Small cases for kernel-level ncu captures (a few launches of one kernel):
     stencil -- fused FP32 A on a 2048 x 2048 lattice (about 200 MB per launch,
                above L2); coarse -- BF16 coarse apply on level 2 of the
-               benchmark workload; coarsest -- the coarsest solve (packed FP32
-               GEMV + FP64 refinement) of the benchmark workload; vcycle -- one
-               FP32 V-cycle."""
+               benchmark workload, one right-hand side; coarse_mma -- the same
+               with 64 right-hand sides (tensor cores); coarsest -- the
+               coarsest solve (packed FP32 GEMV + FP64 refinement) of the
+               benchmark workload; vcycle -- one FP32 V-cycle."""
     import torch
     from paper_0710_3612_gb300 import mg
     dev = torch.device("cuda", 0)
@@ -579,12 +580,13 @@ def ncu_case(args):
         h = mg.mg_setup(torch.from_numpy(U).to(dev), masses[0],
                         mg.make_params(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], nd,
                                        setup_sweeps=wl["setup_sweeps"]), stream)
-        if args.ncu_case == "coarse":
+        if args.ncu_case in ("coarse", "coarse_mma"):
+            nrhs = 64 if args.ncu_case == "coarse_mma" else 1
             Lx, Lt, n, _ = mg.mg_get_level(h, 2)
-            x = torch.randn(Lx * Lt * n, dtype=torch.complex64, device=dev)
+            x = torch.randn(nrhs * Lx * Lt * n, dtype=torch.complex64, device=dev)
             y = torch.empty_like(x)
             for _ in range(4):
-                mg.mg_apply_coarse(h, 2, x, y, 1, mg.PREC_BF16)
+                mg.mg_apply_coarse(h, 2, x, y, nrhs, mg.PREC_BF16)
         elif args.ncu_case == "coarsest":
             Lx, Lt, n, _ = mg.mg_get_level(h, len(wl["blocks"]) + 1)
             x = torch.randn(Lx * Lt * n, dtype=torch.complex128, device=dev)
@@ -617,7 +619,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
-    ap.add_argument("--ncu-case", choices=["stencil", "coarse", "coarsest", "vcycle"],
+    ap.add_argument("--ncu-case", choices=["stencil", "coarse", "coarse_mma", "coarsest", "vcycle"],
                     help="run a small kernel case for an ncu capture and exit")
     args = ap.parse_args()
     if args.ncu_case:

@@ -296,9 +296,10 @@ __global__ void __launch_bounds__(256) k_restrict(const cplx_t<R>* __restrict__ 
   if (lane == 0) coarse[(long long)blockIdx.y * Vc * nc + w] = mk((R)re, (R)im);
 }
 
-// Many right-hand sides: one CTA per coarse site j stages the block's vectors
-// and the block's slice of every right-hand side in shared memory, so the
-// vectors are read once per site instead of once per right-hand side.
+// One CTA per coarse site j stages the block's vectors and the block's slice
+// of every right-hand side in shared memory, so the vectors are read once per
+// site for all right-hand sides and every output is a short in-CTA sum.
+// (The warp-per-output kernels serve blocks too large for shared memory.)
 template <typename R>
 __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restrict__ fine,
                                                         cplx_t<R>* __restrict__ coarse,
@@ -372,7 +373,7 @@ template <typename R>
 cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx, int Lt, int bx,
                         int bt, int h, int Nv, int nrhs, cudaStream_t s) {
   const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), true);
-  if (nrhs >= 8 && sm <= 96 * 1024) {
+  if (sm <= 96 * 1024) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_restrict_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -414,7 +415,7 @@ template <typename R>
 cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, int Lt, int bx,
                        int bt, int h, int Nv, int nrhs, bool accumulate, cudaStream_t s) {
   const size_t sm = transfer_multi_smem(bx, bt, h, Nv, nrhs, sizeof(cplx_t<R>), false);
-  if (nrhs >= 8 && sm <= 96 * 1024) {
+  if (sm <= 96 * 1024) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_prolong_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);

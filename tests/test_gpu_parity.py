@@ -186,7 +186,7 @@ def test_apply_coarse(case, mg, prec, nrhs):
 
 @pytest.mark.parametrize("prec,nrhs", [("f64", 2), ("f32", 2), ("f64", 9), ("f32", 9)])
 def test_restrict_prolong(case, mg, prec, nrhs):
-    """nrhs >= 8 uses the one-CTA-per-coarse-site kernels."""
+    """Several right-hand sides per call (one CTA per coarse site)."""
     H = case.H
     tol = 1e-11 if prec == "f64" else TOL32
     for l in range(H.L - 1):
