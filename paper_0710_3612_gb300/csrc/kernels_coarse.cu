@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
 // register of a B fragment is one complex entry of X.  mma.sync m16n8k16:
 // M = 16 complex rows (Re and Im tiles), N = 8 right-hand sides, K = 8
 // complex columns per step.  X is staged in shared memory as a pair of bf16
-// splits, X = Xhi + Xlo (Xlo = bf16(X - Xhi)), each [9n][nrhs8 + 8] (padding
-// keeps the fragment loads conflict-free); two MMAs per product carry X to
-// about 16 significant bits, so only the stored BF16 blocks round.
+// splits, X = Xhi + Xlo (Xlo = bf16(X - Xhi)), each [9n][16 + 8] per chunk of
+// 16 right-hand sides (padding keeps the fragment loads conflict-free); two
+// MMAs per product carry X to about 16 significant bits, so only the stored
+// BF16 blocks round.
 __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
                                                uint32_t b1) {
   asm volatile(
@@ -128,77 +129,82 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a
 
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *(uint32_t*)&v; }
 
-__global__ void __launch_bounds__(128) k_coarse_apply_mma(const float2* __restrict__ in, float2* out,
-                                                          const __nv_bfloat162* __restrict__ A,
-                                                          int Lx, int Lt, int n, int nrhs,
-                                                          Epilogue ep) {
+// CTA = (coarse site j, chunk of 16 right-hand sides), two warps, one 8-wide
+// n-tile each; the A fragments of a K step are loaded once per warp.
+static constexpr int MMA_RC = 16;            // right-hand sides per CTA
+
+__global__ void __launch_bounds__(64) k_coarse_apply_mma(const float2* __restrict__ in, float2* out,
+                                                         const __nv_bfloat162* __restrict__ A,
+                                                         int Lx, int Lt, int n, int nrhs,
+                                                         Epilogue ep) {
   extern __shared__ __nv_bfloat162 Xs[];
+  constexpr int RS = MMA_RC + 8;             // padded row: conflict-free fragment loads
   const int V = Lx * Lt;
-  const int j = blockIdx.x;
+  const int j = blockIdx.x, rhs0 = blockIdx.y * MMA_RC;
   const int x = j % Lx, t = j / Lx;
-  const int R8 = (nrhs + 7) / 8 * 8, RS = R8 + 8;
-  __nv_bfloat162* Xl = Xs + 9 * n * RS;
   const int tid = threadIdx.x;
-  // stage X(j + d) for the 9 displacements, all right-hand sides
-  for (int q = tid; q < 9 * n * R8; q += blockDim.x) {        // dof fastest: coalesced reads
-    const int sdof = q % n, rhs = (q / n) % R8, d = q / (n * R8), c = d * n + sdof;
+  __nv_bfloat162* Xl = Xs + 9 * n * RS;
+  // stage X(j + d) for the 9 displacements, this chunk of right-hand sides
+  // (dof fastest: one 8 n-byte segment per (d, rhs)), as hi + lo bf16 parts
+  for (int q = tid; q < 9 * n * MMA_RC; q += blockDim.x) {
+    const int sdof = q % n, rr = (q / n) % MMA_RC, d = q / (n * MMA_RC), c = d * n + sdof;
     int xn = x + d % 3 - 1, tn = t + d / 3 - 1;
     xn = xn < 0 ? xn + Lx : (xn >= Lx ? xn - Lx : xn);
     tn = tn < 0 ? tn + Lt : (tn >= Lt ? tn - Lt : tn);
     float2 v = make_float2(0.f, 0.f);
-    if (rhs < nrhs) v = in[((long long)rhs * V + xn + Lx * tn) * n + sdof];
+    if (rhs0 + rr < nrhs) v = in[((long long)(rhs0 + rr) * V + xn + Lx * tn) * n + sdof];
     const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
     const float2 hf = __bfloat1622float2(hi);
-    Xs[c * RS + rhs] = hi;
-    Xl[c * RS + rhs] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    Xs[c * RS + rr] = hi;
+    Xl[c * RS + rr] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tg = lane & 3;
+  const int nt = warp;                        // 8 right-hand sides per warp
   const __nv_bfloat162 zero = __floats2bfloat162_rn(0.f, 0.f);
-  for (int nt = warp; nt < R8 / 8; nt += 4) {
-    for (int r0 = 0; r0 < n; r0 += 16) {
-      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int c0 = 0; c0 < 9 * n; c0 += 8) {
-        const int d = c0 / n, s0 = c0 % n;
-        const __nv_bfloat162* Ab = A + (((long long)j * 9 + d) * n) * n;
-        __nv_bfloat162 e[4];
-        const int ra = r0 + g, rb = r0 + g + 8;
-        e[0] = ra < n ? Ab[ra * n + s0 + tg] : zero;
-        e[1] = rb < n ? Ab[rb * n + s0 + tg] : zero;
-        e[2] = ra < n ? Ab[ra * n + s0 + tg + 4] : zero;
-        e[3] = rb < n ? Ab[rb * n + s0 + tg + 4] : zero;
-        uint32_t aRe[4], aIm[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          aRe[u] = bf2_bits(__halves2bfloat162(e[u].x, __hneg(e[u].y)));   // (re, -im)
-          aIm[u] = bf2_bits(__halves2bfloat162(e[u].y, e[u].x));           // (im, re)
-        }
-        const int i0 = (c0 + tg) * RS + nt * 8 + g, i1 = (c0 + tg + 4) * RS + nt * 8 + g;
-        const uint32_t b0 = bf2_bits(Xs[i0]), b1 = bf2_bits(Xs[i1]);
-        const uint32_t l0 = bf2_bits(Xl[i0]), l1 = bf2_bits(Xl[i1]);
-        mma_bf16_16816(re, aRe, b0, b1);
-        mma_bf16_16816(im, aIm, b0, b1);
-        mma_bf16_16816(re, aRe, l0, l1);
-        mma_bf16_16816(im, aIm, l0, l1);
-      }
-      // c[0], c[1]: row g, rhs 2tg, 2tg+1; c[2], c[3]: row g + 8
+  for (int r0 = 0; r0 < n; r0 += 16) {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    const int ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll 2
+    for (int c0 = 0; c0 < 9 * n; c0 += 8) {
+      const int d = c0 / n, s0 = c0 % n;
+      const __nv_bfloat162* Ab = A + (((long long)j * 9 + d) * n) * n;
+      __nv_bfloat162 e[4];
+      e[0] = ra < n ? Ab[ra * n + s0 + tg] : zero;
+      e[1] = rb < n ? Ab[rb * n + s0 + tg] : zero;
+      e[2] = ra < n ? Ab[ra * n + s0 + tg + 4] : zero;
+      e[3] = rb < n ? Ab[rb * n + s0 + tg + 4] : zero;
+      uint32_t aRe[4], aIm[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int r = r0 + g + (u >= 2 ? 8 : 0);
-        const int rhs = nt * 8 + 2 * tg + (u & 1);
-        if (r >= n || rhs >= nrhs) continue;
-        const long long o = ((long long)rhs * V + j) * n + r;
-        float2 y = make_float2((float)ep.ca * re[u], (float)ep.ca * im[u]);
-        if (ep.U) {
-          const float2 w = ((const float2*)ep.U)[o];
-          y = make_float2(y.x + (float)ep.cu * w.x, y.y + (float)ep.cu * w.y);
-        }
-        if (ep.W) {
-          const float2 w = ((const float2*)ep.W)[o];
-          y = make_float2(y.x + (float)ep.cw * w.x, y.y + (float)ep.cw * w.y);
-        }
-        out[o] = y;
+        aRe[u] = bf2_bits(__halves2bfloat162(e[u].x, __hneg(e[u].y)));   // (re, -im)
+        aIm[u] = bf2_bits(__halves2bfloat162(e[u].y, e[u].x));           // (im, re)
       }
+      const int i0 = (c0 + tg) * RS + nt * 8 + g, i1 = (c0 + tg + 4) * RS + nt * 8 + g;
+      const uint32_t b0 = bf2_bits(Xs[i0]), b1 = bf2_bits(Xs[i1]);
+      const uint32_t l0 = bf2_bits(Xl[i0]), l1 = bf2_bits(Xl[i1]);
+      mma_bf16_16816(re, aRe, b0, b1);
+      mma_bf16_16816(im, aIm, b0, b1);
+      mma_bf16_16816(re, aRe, l0, l1);
+      mma_bf16_16816(im, aIm, l0, l1);
+    }
+    // c[0], c[1]: row g, rhs 2tg, 2tg+1; c[2], c[3]: row g + 8
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + g + (u >= 2 ? 8 : 0);
+      const int rhs = rhs0 + nt * 8 + 2 * tg + (u & 1);
+      if (r >= n || rhs >= nrhs) continue;
+      const long long o = ((long long)rhs * V + j) * n + r;
+      float2 y = make_float2((float)ep.ca * re[u], (float)ep.ca * im[u]);
+      if (ep.U) {
+        const float2 w = ((const float2*)ep.U)[o];
+        y = make_float2(y.x + (float)ep.cu * w.x, y.y + (float)ep.cu * w.y);
+      }
+      if (ep.W) {
+        const float2 w = ((const float2*)ep.W)[o];
+        y = make_float2(y.x + (float)ep.cw * w.x, y.y + (float)ep.cw * w.y);
+      }
+      out[o] = y;
     }
   }
 }
@@ -211,16 +217,16 @@ cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, 
                          int n, int nrhs, const Epilogue& ep, cudaStream_t s) {
   if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
   if (coarse_apply_tensor(weights, n, nrhs)) {
-    const int R8 = (nrhs + 7) / 8 * 8;
-    const size_t smem = (size_t)2 * 9 * n * (R8 + 8) * sizeof(__nv_bfloat162);
+    const size_t smem = (size_t)2 * 9 * n * (MMA_RC + 8) * sizeof(__nv_bfloat162);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_coarse_apply_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
+                           64 * 1024);
       attr = true;
     }
-    k_coarse_apply_mma<<<Lx * Lt, 128, smem, s>>>((const float2*)in, (float2*)out,
-                                                  (const __nv_bfloat162*)A, Lx, Lt, n, nrhs, ep);
+    dim3 grid(Lx * Lt, (nrhs + MMA_RC - 1) / MMA_RC);
+    k_coarse_apply_mma<<<grid, 64, smem, s>>>((const float2*)in, (float2*)out,
+                                              (const __nv_bfloat162*)A, Lx, Lt, n, nrhs, ep);
     count_launch();
     return cudaGetLastError();
   }

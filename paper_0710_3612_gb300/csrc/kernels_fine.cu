@@ -261,16 +261,34 @@ __device__ __forceinline__ void dslash_row(cplx_t<R> f0, cplx_t<R> f1, cplx_t<R>
   o1 = mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y);
 }
 
+// Asynchronous row prefetch for the streaming stencil: each lane copies its
+// own spinor and links of a future row into a per-warp ring of SNB slots in
+// shared memory (cp.async), SNB - 1 iterations ahead of use.
+static constexpr int SNB = 4;
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 3) k_wilson_A_stream(const cplx_t<R>* __restrict__ in,
-                                                         cplx_t<R>* out,
-                                                         const cplx_t<R>* __restrict__ U, R diag,
-                                                         int Lx, int Lt, Epilogue ep) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 3) k_wilson_A_stream(
+    const cplx_t<R>* __restrict__ in, cplx_t<R>* out, const cplx_t<R>* __restrict__ U, R diag,
+    int Lx, int Lt, Epilogue ep) {
   using C = cplx_t<R>;
+  using S = typename spinor_t<R>::type;
+  __shared__ S ring_psi[4][SNB][32];           // [warp][slot][lane]
+  __shared__ C ring_u[4][SNB][32][2];
   const int V = Lx * Lt;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int strips = (Lx + SOUT - 1) / SOUT;
-  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int w = blockIdx.x * (blockDim.x >> 5) + wl;
   const int row_blocks = (Lt + SROWS - 1) / SROWS;
   if (w >= strips * row_blocks) return;                  // whole warp
   const int strip = w % strips, t0 = (w / strips) * SROWS;
@@ -287,19 +305,36 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 3) k_wilson_A_stream
     ux = U[g];
     ut = U[V + g];
   };
+  // group for loop step r: psi(r + 2) and links(r + 1), into slot
+  // (r - t0 + 1) mod SNB; empty past the last step that reads one
+  auto issue = [&](int r) {
+    if (r < t1) {
+      const int slot = (r - t0 + 1 + SNB) % SNB;
+      const C* ps = in + off + 2LL * (x + Lx * wrap(r + 2, Lt));
+      char* dst = (char*)&ring_psi[wl][slot][lane];
+      if (sizeof(S) == 16) {
+        cp_async(dst, ps, 16);
+      } else {
+        cp_async(dst, ps, 16);
+        cp_async(dst + 16, ps + 1, 16);
+      }
+      const int g = x + Lx * wrap(r + 1, Lt);
+      cp_async(&ring_u[wl][slot][lane][0], U + g, (int)sizeof(C));
+      cp_async(&ring_u[wl][slot][lane][1], U + V + g, (int)sizeof(C));
+    }
+    cp_commit();
+  };
   C pm0, pm1, pc0, pc1, pp0, pp1;          // psi rows r-1, r, r+1
   C dm0, dm1, dc0, dc1;                    // D psi rows r-2, r-1
   C uxc, utc, utm;                         // U_x(r), U_t(r), U_t(r-1)
   C uxo, uto, utmo;                        // the same one row earlier (for D^dagger)
-  C nx0, nx1, nux, nut;                    // prefetched psi row r+2, links row r+1
   C dummy;
   ld_psi(t0 - 2, pm0, pm1);
   ld_psi(t0 - 1, pc0, pc1);
   ld_psi(t0, pp0, pp1);
   ld_u(t0 - 2, dummy, utm);
   ld_u(t0 - 1, uxc, utc);
-  ld_psi(t0 + 1, nx0, nx1);
-  ld_u(t0, nux, nut);
+  for (int k = 0; k < SNB - 1; ++k) issue(t0 - 1 + k);
   dm0 = dm1 = dc0 = dc1 = mk((R)0, (R)0);
   uxo = uto = utmo = mk((R)0, (R)0);
   const R ca = (R)ep.ca, cu = (R)ep.cu, cw = (R)ep.cw;
@@ -332,13 +367,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 7 : 3) k_wilson_A_stream
     }
     dm0 = dc0; dm1 = dc1; dc0 = e0; dc1 = e1;            // shift: row r becomes r - 1
     uxo = uxc; uto = utc; utmo = utm;
-    pm0 = pc0; pm1 = pc1; pc0 = pp0; pc1 = pp1; pp0 = nx0; pp1 = nx1;
-    utm = utc; uxc = nux; utc = nut;
-    if (r + 1 <= t1) {
-      ld_psi(r + 3, nx0, nx1);
-      ld_u(r + 2, nux, nut);
+    pm0 = pc0; pm1 = pc1; pc0 = pp0; pc1 = pp1;
+    utm = utc;
+    if (r + 1 <= t1) {                                   // psi(r + 2), links(r + 1)
+      cp_wait<SNB - 2>();
+      const int slot = (r - t0 + 1 + SNB) % SNB;
+      split(ring_psi[wl][slot][lane], pp0, pp1);
+      uxc = ring_u[wl][slot][lane][0];
+      utc = ring_u[wl][slot][lane][1];
     }
+    issue(r + SNB - 1);
   }
+  cp_wait<0>();
 }
 
 // The streaming kernel serves lattices with enough strips to fill the GPU.
