@@ -11,8 +11,9 @@ lambda_min(A(m)) = sigma_min(D(m))^2 = min |eig(sigma_3 D(m))|^2 (sigma_3 D is
 Hermitian by gamma_5-hermiticity).
 
 Library primitives: scipy's ARPACK shift-invert eigensolvers on the explicit
-sparse matrix of D (``wilson.dirac_matrix``).  Parity unpinned beyond the
-small-lattice check against a dense eigendecomposition in the tests.
+sparse matrix of D (``wilson.dirac_matrix``).  Pinned on small lattices: the
+spectral-flow finder used for large lattices against the real eigenvalues of
+a dense D_0, and the singularity of D(m_crit) by a dense SVD.
 """
 from __future__ import annotations
 
@@ -58,45 +59,59 @@ def lambda_min_A(U: np.ndarray, m: float) -> float:
     return float(np.min(np.abs(ev)) ** 2)
 
 
-def _min_abs_eig_H(U: np.ndarray, m: float, D0=None) -> float:
-    """min |eig(sigma_3 D(m))| by shift-invert Lanczos at 0."""
+def nearest_eig_H(U: np.ndarray, m: float, D0=None):
+    """(lambda, dlambda/dm): the eigenvalue of the Hermitian H(m) = sigma_3 D(m)
+    nearest zero, by shift-invert Lanczos at 0, and its derivative in m.  Since
+    dH/dm = sigma_3, the derivative is <v, sigma_3 v> for the unit eigenvector v
+    (first-order perturbation theory, Hellmann-Feynman)."""
     D = wilson.dirac_matrix(U, 0.0) if D0 is None else D0
     n = D.shape[0]
-    H = (_sigma3(n // 2) @ (D + m * sp.identity(n, dtype=np.complex128, format="csr"))).tocsc()
-    ev = spla.eigsh(H, k=1, sigma=0.0, which="LM", return_eigenvectors=False, tol=1e-12)
-    return float(np.min(np.abs(ev)))
+    s3 = _sigma3(n // 2)
+    H = (s3 @ (D + m * sp.identity(n, dtype=np.complex128, format="csr"))).tocsc()
+    ev, vec = spla.eigsh(H, k=1, sigma=0.0, which="LM", tol=1e-13)
+    v = vec[:, 0] / np.linalg.norm(vec[:, 0])
+    return float(ev[0]), float(np.real(np.vdot(v, s3 @ v)))
 
 
-def critical_mass_by_flow(U: np.ndarray, m_lo: float = -2.4, m_hi: float = -1.9, step: float = 0.01,
-                          zero: float = 1e-7):
-    """m_crit for large lattices: D(m) is singular where an eigenvalue of the
-    Hermitian sigma_3 D(m) crosses zero, i.e. where mu(m) = min |eig(sigma_3 D(m))|
-    vanishes.  Scan mu on a grid from heavy to light mass, refine each local
-    minimum by golden-section search, and return the heaviest mass where the
-    minimum is below `zero` (None if there is none)."""
+def critical_mass_by_flow(U: np.ndarray, m_lo: float = -2.4, m_hi: float = -1.9,
+                          zero: float = 1e-11, newton_below: float = 1e-3, safety: float = 0.9,
+                          max_evals: int = 2000):
+    """m_crit for large lattices: the heaviest mass at which an eigenvalue of
+    the Hermitian H(m) = sigma_3 D(m) crosses zero (D(m) is singular exactly
+    there).  Changing m by dm moves every eigenvalue of H by at most |dm|
+    (dH/dm = sigma_3 has norm 1), so mu(m) = min |eig H(m)| is 1-Lipschitz and
+    no crossing lies within mu(m) of m.  Coming down from m_hi in steps of
+    safety * mu(m) therefore cannot pass over a crossing.  Once mu < newton_below
+    the crossing ahead is located by Newton's method on the nearest eigenvalue
+    (derivative from nearest_eig_H); a Newton run that leaves the interval
+    (m - 2 mu / |slope| ... m], or stops contracting, is discarded and the
+    scan goes on.  Returns None if no crossing lies above m_lo."""
     D0 = wilson.dirac_matrix(U, 0.0)
-    ms = np.arange(m_hi, m_lo - 1e-12, -step)
-    mu = [_min_abs_eig_H(U, m, D0) for m in ms]
-    g = (np.sqrt(5.0) - 1.0) / 2.0
-    for i in range(1, len(ms) - 1):
-        if mu[i] <= mu[i - 1] and mu[i] <= mu[i + 1]:
-            a, b = ms[i + 1], ms[i - 1]
-            c, d = b - g * (b - a), a + g * (b - a)
-            fc, fd = _min_abs_eig_H(U, c, D0), _min_abs_eig_H(U, d, D0)
-            for _ in range(60):
-                if fc < fd:
-                    b, d, fd = d, c, fc
-                    c = b - g * (b - a)
-                    fc = _min_abs_eig_H(U, c, D0)
-                else:
-                    a, c, fc = c, d, fd
-                    d = a + g * (b - a)
-                    fd = _min_abs_eig_H(U, d, D0)
-                if b - a < 1e-13:
+    m, evals = m_hi, 0
+    while m > m_lo and evals < max_evals:
+        lam, slope = nearest_eig_H(U, m, D0)
+        evals += 1
+        mu = abs(lam)
+        if mu < zero:
+            return float(m)
+        if mu < newton_below and abs(slope) > 1e-3:
+            mn, ln, ok = m, lam, False
+            for _ in range(40):
+                step = -ln / slope
+                mn_new = mn + step
+                if not (m - 4.0 * mu / abs(slope) <= mn_new <= m + 1e-15):
                     break
-            m_star = 0.5 * (a + b)
-            if _min_abs_eig_H(U, m_star, D0) < zero:
-                return float(m_star)
+                ln_new, slope_new = nearest_eig_H(U, mn_new, D0)
+                evals += 1
+                if abs(ln_new) > 0.5 * abs(ln) and abs(ln_new) > zero:
+                    break
+                mn, ln, slope = mn_new, ln_new, slope_new
+                if abs(ln) < zero:
+                    ok = True
+                    break
+            if ok:
+                return float(mn)
+        m -= safety * mu
     return None
 
 

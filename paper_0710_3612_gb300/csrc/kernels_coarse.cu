@@ -1042,6 +1042,95 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
   }
 }
 
+// Warp-per-tile variant for up to four right-hand sides: each warp streams
+// one stored tile straight from global memory in four chunks of 16 rows, lane
+// l holding columns 2l and 2l + 1 of every row (one 16-byte load per row).
+// The row products B_IJ x_J are summed across the warp by a transposing
+// butterfly (after it, lanes 2r and 2r + 1 hold row r of the chunk); the column
+// products B_IJ^H x_I stay in registers for the whole tile.  The partial sums
+// use the buffer layout of k_hgemv_tiles.
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+template <int NR>
+__global__ void __launch_bounds__(128) k_hgemv_warp(const float2* __restrict__ P,
+                                                    const double2* __restrict__ x, int N,
+                                                    int ntiles, int nrhs,
+                                                    float2* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (k >= ntiles) return;                               // whole warp
+  int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= k) ++I;
+  while (I * (I + 1) / 2 > k) --I;
+  const int J = k - I * (I + 1) / 2;
+  const float4* src = (const float4*)(P + (long long)k * HT * HT) + lane;
+  for (int q0 = 0; q0 < nrhs; q0 += NR) {
+    float2 xj0[NR], xj1[NR], xi0[NR], xi1[NR], ac0[NR], ac1[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      xj0[q] = xj1[q] = xi0[q] = xi1[q] = ac0[q] = ac1[q] = make_float2(0.f, 0.f);
+      if (q0 + q < nrhs) {
+        const double2* xr = x + (long long)(q0 + q) * N;
+        const int cj = J * HT + 2 * lane, ri = I * HT + lane;
+        if (cj < N) xj0[q] = make_float2((float)xr[cj].x, (float)xr[cj].y);
+        if (cj + 1 < N) xj1[q] = make_float2((float)xr[cj + 1].x, (float)xr[cj + 1].y);
+        if (ri < N) xi0[q] = make_float2((float)xr[ri].x, (float)xr[ri].y);
+        if (ri + 32 < N) xi1[q] = make_float2((float)xr[ri + 32].x, (float)xr[ri + 32].y);
+      }
+    }
+#pragma unroll 1
+    for (int ch = 0; ch < 4; ++ch) {
+      float4 t[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) t[i] = __ldg(src + (ch * 16 + i) * (HT / 2));
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        float2 p[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float2 a = make_float2(t[i].x, t[i].y), b = make_float2(t[i].z, t[i].w);
+          p[i] = make_float2(0.f, 0.f);
+          cfma(p[i], a, xj0[q]);
+          cfma(p[i], b, xj1[q]);
+          const float2 xr = shfl2(ch < 2 ? xi0[q] : xi1[q], (ch * 16 + i) & 31);
+          cfmac(ac0[q], a, xr);
+          cfmac(ac1[q], b, xr);
+        }
+        float2 v8[8], v4[4], v2[2];
+        bool hi = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          v8[i] = cadd(hi ? p[i + 8] : p[i], shfl_xor2(hi ? p[i] : p[i + 8], 16));
+        hi = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          v4[i] = cadd(hi ? v8[i + 4] : v8[i], shfl_xor2(hi ? v8[i] : v8[i + 4], 8));
+        hi = lane & 4;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+          v2[i] = cadd(hi ? v4[i + 2] : v4[i], shfl_xor2(hi ? v4[i] : v4[i + 2], 4));
+        hi = lane & 2;
+        float2 v = cadd(hi ? v2[1] : v2[0], shfl_xor2(hi ? v2[0] : v2[1], 2));
+        v = cadd(v, shfl_xor2(v, 1));
+        if (!(lane & 1) && q0 + q < nrhs)
+          part[(long long)(q0 + q) * ntiles * 2 * HT + 2LL * k * HT + ch * 16 + (lane >> 1)] = v;
+      }
+    }
+    if (I != J) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q0 + q < nrhs)
+          *(float4*)(part + (long long)(q0 + q) * ntiles * 2 * HT + (2LL * k + 1) * HT + 2 * lane) =
+              make_float4(ac0[q].x, ac0[q].y, ac1[q].x, ac1[q].y);
+    }
+  }
+}
+
 // One CTA per 64-row block: 4 groups of 64 threads each sum a quarter of the
 // 64-wide tile row in order; the quarters are added in a fixed order.
 __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__ part,
@@ -1073,9 +1162,22 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
 cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
                                void* part, bool accumulate, cudaStream_t s) {
   if (ld % HT || ld < N) return cudaErrorInvalidValue;
-  const int nt = ld / HT;
-  k_hgemv_tiles<<<nt * (nt + 1) / 2, 256, 0, s>>>((const float2*)P, (const double2*)x, N, nrhs,
-                                                  (float2*)part);
+  const int nt = ld / HT, ntiles = nt * (nt + 1) / 2;
+  if (nrhs <= 4) {                               // streamed from global, one warp per tile
+    const dim3 grid((ntiles + 3) / 4);
+    if (nrhs == 1)
+      k_hgemv_warp<1><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+                                           (float2*)part);
+    else if (nrhs == 2)
+      k_hgemv_warp<2><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+                                           (float2*)part);
+    else
+      k_hgemv_warp<4><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+                                           (float2*)part);
+  } else {
+    k_hgemv_tiles<<<ntiles, 256, 0, s>>>((const float2*)P, (const double2*)x, N, nrhs,
+                                         (float2*)part);
+  }
   count_launch();
   k_hgemv_reduce<<<dim3(nt, nrhs), 256, 0, s>>>((const float2*)part, (double2*)y, N, nt,
                                                 accumulate);

@@ -72,3 +72,16 @@ def test_critical_mass_small_lattice():
     ev = np.linalg.eigvals(w.dirac_matrix(U, 0.0).toarray())
     real = ev[np.abs(ev.imag) < 1e-7 * np.abs(ev)].real
     assert real.min() == pytest.approx(-res["m_crit"], abs=1e-10)
+
+
+@pytest.mark.parametrize("L,beta,sweeps,seed", [(16, 3.0, 100, 2), (32, 6.0, 200, 1), (32, 3.0, 100, 3)])
+def test_flow_finder_matches_dense_real_eigenvalue(L, beta, sweeps, seed):
+    """The spectral-flow finder used on large lattices returns the heaviest
+    singular mass, -(smallest real eigenvalue of D_0), found here by a dense
+    eigendecomposition; these configurations have two or more real modes."""
+    U = W.links_from_angles(W.quenched_u1_angles(L, L, beta, sweeps, seed))
+    ev = np.linalg.eigvals(w.dirac_matrix(U, 0.0).toarray())
+    real = np.sort(ev[np.abs(ev.imag) < 1e-7 * np.abs(ev)].real)
+    assert real.size >= 2
+    m = critical.critical_mass_by_flow(U)
+    assert m == pytest.approx(-real[0], abs=1e-9)
