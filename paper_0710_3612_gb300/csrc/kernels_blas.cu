@@ -16,7 +16,8 @@ void add_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std
 static constexpr int RT = 256;   // threads per reduction block
 
 int reduce_blocks(long long count) {
-  long long g = (count + 4 * RT - 1) / (4 * RT);
+  long long g = (count + RT - 1) / RT;           // one entry per thread until 608 blocks
+
   if (g < 1) g = 1;
   if (g > 608) g = 608;           // 4 x 152 SMs
   return (int)g;

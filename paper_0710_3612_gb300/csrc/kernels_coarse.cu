@@ -306,47 +306,70 @@ __global__ void __launch_bounds__(256) k_restrict(const cplx_t<R>* __restrict__ 
 // of every right-hand side in shared memory, so the vectors are read once per
 // site for all right-hand sides and every output is a short in-CTA sum.
 // (The warp-per-output kernels serve blocks too large for shared memory.)
+// Transfer kernels with one CTA per coarse site j.  The block's null-vector
+// rows and the inputs of all right-hand sides are staged in shared memory;
+// each output is then summed by a group of G consecutive lanes (G a power of
+// two, chosen so that the outputs x G fill the CTA), which split the terms and
+// combine them with a fixed shuffle tree.
+template <typename C>
+__device__ __forceinline__ C group_sum(C v, int G) {
+  for (int off = G >> 1; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// Restriction: coarse(j, c Nv + k) = sum over the T = b2 h entries t = (o, a)
+// of chirality c in block j of conj(v_k(t)) r(t).  Shared layouts keep t
+// fastest: sv[(c Nv + k) T + t], sr[(rhs 2 + c) T + t].
 template <typename R>
 __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restrict__ fine,
                                                         cplx_t<R>* __restrict__ coarse,
                                                         const cplx_t<R>* __restrict__ Vst, int Lx,
                                                         int Lt, int bx, int bt, int h, int Nv,
-                                                        int nrhs) {
+                                                        int nrhs, int G) {
   using C = cplx_t<R>;
   extern __shared__ unsigned char smraw[];
-  const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
-  C* sv = (C*)smraw;                                 // [b2][2][Nv][h]
-  C* sr = sv + b2 * 2 * Nv * h;                      // [nrhs][b2][nf]
+  const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, T = b2 * h, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
+  C* sv = (C*)smraw;
+  C* sr = sv + 2 * Nv * T;
   const int j = blockIdx.x, V = Lx * Lt;
   for (int q = threadIdx.x; q < b2 * 2 * Nv * h; q += blockDim.x) {
     const int o = q / (2 * Nv * h), rest = q % (2 * Nv * h);
-    sv[q] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
+    const int ck = rest / h, a = rest % h;                // ck = c Nv + k
+    sv[ck * T + o * h + a] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
   }
   for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
     const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
-    sr[q] = fine[((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp];
+    const int c = comp / h, a = comp % h;
+    sr[(rhs * 2 + c) * T + o * h + a] =
+        fine[((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < nrhs * nc; q += blockDim.x) {
-    const int s = q % nc, rhs = q / nc, c = s / Nv, k = s % Nv;
-    double re = 0.0, im = 0.0;
-    for (int o = 0; o < b2; ++o)
-      for (int a = 0; a < h; ++a) {
-        const C v = sv[((o * 2 + c) * Nv + k) * h + a];
-        const C r = sr[(rhs * b2 + o) * nf + c * h + a];
-        re += (double)v.x * r.x + (double)v.y * r.y;
-        im += (double)v.x * r.y - (double)v.y * r.x;
-      }
-    coarse[((long long)rhs * Vc + j) * nc + s] = mk((R)re, (R)im);
+  const int g = threadIdx.x % G, per = blockDim.x / G, nout = nrhs * nc;
+  for (int q0 = 0; q0 < nout; q0 += per) {
+    const int q = q0 + threadIdx.x / G;
+    C acc = mk((R)0, (R)0);
+    if (q < nout) {
+      const int sidx = q % nc, rhs = q / nc, c = sidx / Nv;
+      const C* v = sv + sidx * T;
+      const C* r = sr + (rhs * 2 + c) * T;
+      for (int t = g; t < T; t += G) cfmac(acc, v[t], r[t]);
+    }
+    acc = group_sum(acc, G);
+    if (q < nout && g == 0) coarse[((long long)(q / nc) * Vc + j) * nc + q % nc] = acc;
   }
 }
 
+// Prolongation: fine(i, c, a) (+)= sum over k of v_k(i, c, a) e(j, c Nv + k);
+// G lanes split the Nv terms of one output.
 template <typename R>
 __global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restrict__ coarse,
                                                        cplx_t<R>* __restrict__ fine,
                                                        const cplx_t<R>* __restrict__ Vst, int Lx,
                                                        int Lt, int bx, int bt, int h, int Nv,
-                                                       int nrhs, bool accumulate) {
+                                                       int nrhs, bool accumulate, int G) {
   using C = cplx_t<R>;
   extern __shared__ unsigned char smraw[];
   const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
@@ -360,14 +383,33 @@ __global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restri
   for (int q = threadIdx.x; q < nrhs * nc; q += blockDim.x)
     se[q] = coarse[((long long)(q / nc) * Vc + j) * nc + q % nc];
   __syncthreads();
-  for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
-    const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
-    const int c = comp / h, a = comp % h;
+  const int g = threadIdx.x % G, per = blockDim.x / G, nout = nrhs * b2 * nf;
+  for (int q0 = 0; q0 < nout; q0 += per) {
+    const int q = q0 + threadIdx.x / G;
     C acc = mk((R)0, (R)0);
-    for (int k = 0; k < Nv; ++k) cfma(acc, sv[((o * 2 + c) * Nv + k) * h + a], se[rhs * nc + c * Nv + k]);
-    const long long g = ((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp;
-    fine[g] = accumulate ? cadd(fine[g], acc) : acc;
+    int o = 0, comp = 0, rhs = 0;
+    if (q < nout) {
+      comp = q % nf;
+      o = (q / nf) % b2;
+      rhs = q / (nf * b2);
+      const int c = comp / h, a = comp % h;
+      for (int k = g; k < Nv; k += G)
+        cfma(acc, sv[((o * 2 + c) * Nv + k) * h + a], se[rhs * nc + c * Nv + k]);
+    }
+    acc = group_sum(acc, G);
+    if (q < nout && g == 0) {
+      const long long gi = ((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp;
+      fine[gi] = accumulate ? cadd(fine[gi], acc) : acc;
+    }
   }
+}
+
+// Lanes per output: the largest power of two <= min(terms, 16) whose product
+// with the output count still fits in one 256-thread CTA (at least 1).
+static int transfer_group(int outputs, int terms) {
+  int G = 16;
+  while (G > 1 && (G > terms || (long long)outputs * G > 256)) G >>= 1;
+  return G;
 }
 
 static size_t transfer_multi_smem(int bx, int bt, int h, int Nv, int nrhs, size_t csz, bool restr) {
@@ -387,7 +429,7 @@ cudaError_t restrict_op(const void* fine, void* coarse, const void* Vst, int Lx,
     }
     k_restrict_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
         (const cplx_t<R>*)fine, (cplx_t<R>*)coarse, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-        nrhs);
+        nrhs, transfer_group(nrhs * 2 * Nv, bx * bt * h));
     count_launch();
     return cudaGetLastError();
   }
@@ -429,7 +471,7 @@ cudaError_t prolong_op(const void* coarse, void* fine, const void* Vst, int Lx, 
     }
     k_prolong_multi<R><<<(Lx / bx) * (Lt / bt), 256, sm, s>>>(
         (const cplx_t<R>*)coarse, (cplx_t<R>*)fine, (const cplx_t<R>*)Vst, Lx, Lt, bx, bt, h, Nv,
-        nrhs, accumulate);
+        nrhs, accumulate, transfer_group(nrhs * bx * bt * 2 * h, Nv));
     count_launch();
     return cudaGetLastError();
   }
