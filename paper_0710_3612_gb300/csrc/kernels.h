@@ -153,7 +153,7 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 // In-place blocked Gauss-Jordan inversion of a Hermitian positive definite
 // complex64 N x N matrix (N multiple of 64), lower triangle kept (the upper
 // halves of diagonal 64 x 64 tiles are rebuilt by pack_hermitian).
-// work: 3 * N * 32 + 32 * 32 complex64.
+// work: 3 * N * 64 + 2 * 64 * 64 complex64.
 cudaError_t gauss_jordan_inverse_f32(void* M, int N, void* work, cudaStream_t s);
 // y = B x, or y += B x when accumulate (complex64 B, leading dimension ld);
 // x complex128 (N) -> y complex128 (N); FP32 products and accumulation, result

@@ -792,101 +792,167 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 //
 // The matrix is Hermitian and, after sweeping the blocks K = {0..k-1}, so is
 // its swept form up to sign: S_ij = S_ji^H when i, j are both swept or both
-// unswept, S_ij = -S_ji^H otherwise.  Only the lower triangle is kept
-// current: the panels of column k and row k are rebuilt from it and the
-// rank-32 update touches lower tiles only (half the flops).  Upper entries of
-// diagonal 64 x 64 tiles may go stale; the packing step rebuilds them from the
-// lower triangle.  Two kernels per pivot block.
-static constexpr int GJB = 32;
+// unswept, S_ij = -S_ji^H otherwise.  Only the lower 64 x 64 tiles are kept
+// current (diagonal tiles in full): the panels of column k and row k are
+// rebuilt from them and the rank-64 update touches lower tiles only (half
+// the flops).  Pivot blocks are the 64 x 64 diagonal tiles; every pivot block
+// is Hermitian positive definite (a Schur complement of a positive definite
+// matrix), so the sweep needs no pivoting.  Per pivot block two kernels: the
+// panels, then the update, whose first CTA also inverts the next pivot block.
+static constexpr int GJB = 64;
+static constexpr int GJS = GJB + 1;              // shared row stride (float2)
 
-// In-place sweep of the 32 x 32 pivot block held in shared memory (one entry
-// per thread of a 32 x 32 block).
-__device__ __forceinline__ void sweep_diag(float2 (*a)[GJB + 1], int r, int c) {
+// In-place sweep of the 64 x 64 block a[][GJS] in shared memory by 256
+// threads (16 entries each: row tid / 4, columns tid % 4 + 4 v).
+__device__ void sweep_block64(float2* a) {
+  const int r = threadIdx.x >> 2, c0 = threadIdx.x & 3;
   for (int p = 0; p < GJB; ++p) {
-    const float2 piv = a[p][p];
+    const float2 piv = a[p * GJS + p];
     const float den = piv.x * piv.x + piv.y * piv.y;
     const float2 inv = make_float2(piv.x / den, -piv.y / den);
-    const float2 arp = a[r][p], apc = a[p][c], arc = a[r][c];
+    const float2 arp = a[r * GJS + p];
+    const float2 f = cmul(arp, inv);                     // M_rp / M_pp
+    float2 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int c = c0 + 4 * u;
+      const float2 apc = a[p * GJS + c], arc = a[r * GJS + c];
+      if (r == p && c == p) v[u] = inv;
+      else if (r == p) v[u] = cmul(inv, apc);
+      else if (c == p) v[u] = make_float2(-f.x, -f.y);
+      else v[u] = csub(arc, cmul(f, apc));
+    }
     __syncthreads();
-    float2 v;
-    if (r == p && c == p) v = inv;
-    else if (r == p) v = cmul(inv, apc);
-    else if (c == p) v = cmul(make_float2(-arp.x, -arp.y), inv);
-    else v = csub(arc, cmul(cmul(arp, inv), apc));
-    a[r][c] = v;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) a[r * GJS + c0 + 4 * u] = v[u];
     __syncthreads();
   }
 }
 
-// Every CTA inverts the pivot block (P), then forms one panel block:
-// Cold_b = M_bk, Cn_b = M_bk P (column panel), R_b = P M_kb (row panel); the
-// column-panel CTA of the pivot itself stores P.
-__global__ void __launch_bounds__(GJB* GJB) k_gj_panel(const float2* __restrict__ M, int N, int k,
-                                                       float2* __restrict__ Pout,
-                                                       float2* __restrict__ Cold,
-                                                       float2* __restrict__ Cn,
-                                                       float2* __restrict__ Rp) {
-  __shared__ float2 sP[GJB][GJB + 1], sX[GJB][GJB + 1];
+// Inverts the first pivot block: P = M_00^{-1}.
+__global__ void __launch_bounds__(256) k_gj_pivot0(const float2* __restrict__ M, int N,
+                                                   float2* __restrict__ P) {
+  extern __shared__ float2 gsm[];
+  for (int q = threadIdx.x; q < GJB * GJB; q += 256)
+    gsm[(q / GJB) * GJS + q % GJB] = M[(long long)(q / GJB) * N + q % GJB];
+  __syncthreads();
+  sweep_block64(gsm);
+  for (int q = threadIdx.x; q < GJB * GJB; q += 256) P[q] = gsm[(q / GJB) * GJS + q % GJB];
+}
+
+// Panels of pivot block k, one CTA per block b != k: Cold_b = M_bk and
+// Cn_b = M_bk P (column panel, CTAs 0..nb-1), R_b = P M_kb (row panel, CTAs
+// nb..2nb-1).  M_bk and M_kb come from the stored lower tiles by the sign rule.
+__global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, int N, int k,
+                                                  const float2* __restrict__ P,
+                                                  float2* __restrict__ Cold,
+                                                  float2* __restrict__ Cn,
+                                                  float2* __restrict__ Rp) {
+  extern __shared__ float2 gsm[];
+  float2* sP = gsm;
+  float2* sX = gsm + GJB * GJS;
   const int nb = N / GJB;
   const int b = blockIdx.x % nb, col_panel = blockIdx.x < nb;
-  const int r = threadIdx.y, c = threadIdx.x;
-  if (b == k && !col_panel) return;
-  sP[r][c] = M[(long long)(k * GJB + r) * N + k * GJB + c];
-  __syncthreads();
-  sweep_diag(sP, r, c);
-  if (b == k) {
-    Pout[r * GJB + c] = sP[r][c];
-    return;
-  }
-  if (col_panel) {
-    // M_bk: stored below the diagonal for b > k; for b < k it is -(M_kb)^H
-    if (b > k) {
-      sX[r][c] = M[(long long)(b * GJB + r) * N + k * GJB + c];
+  if (b == k) return;
+  for (int q = threadIdx.x; q < GJB * GJB; q += 256) {
+    const int r = q / GJB, c = q % GJB;
+    sP[r * GJS + c] = P[q];
+    float2 x;
+    if (col_panel) {
+      // M_bk: stored for b > k; for b < k it is -(M_kb)^H (swept row, unswept column)
+      if (b > k) {
+        x = M[(long long)(b * GJB + r) * N + k * GJB + c];
+      } else {
+        const float2 v = M[(long long)(k * GJB + c) * N + b * GJB + r];
+        x = make_float2(-v.x, v.y);
+      }
     } else {
-      const float2 v = M[(long long)(k * GJB + c) * N + b * GJB + r];
-      sX[r][c] = make_float2(-v.x, v.y);
+      // M_kb: stored for b < k; for b > k it is (M_bk)^H (both unswept)
+      if (b < k) {
+        x = M[(long long)(k * GJB + r) * N + b * GJB + c];
+      } else {
+        const float2 v = M[(long long)(b * GJB + c) * N + k * GJB + r];
+        x = make_float2(v.x, -v.y);
+      }
     }
-  } else {
-    // M_kb: stored for b < k; for b > k it is (M_bk)^H (both unswept)
-    if (b < k) {
-      sX[r][c] = M[(long long)(k * GJB + r) * N + b * GJB + c];
-    } else {
-      const float2 v = M[(long long)(b * GJB + c) * N + k * GJB + r];
-      sX[r][c] = make_float2(v.x, -v.y);
-    }
+    sX[r * GJS + c] = x;
   }
   __syncthreads();
-  float2 acc = make_float2(0.f, 0.f);
+  const int r = threadIdx.x >> 2, c0 = threadIdx.x & 3;
+  float2 acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
   if (col_panel) {
-    for (int q = 0; q < GJB; ++q) cfma(acc, sX[r][q], sP[q][c]);
-    Cold[(long long)(b * GJB + r) * GJB + c] = sX[r][c];
-    Cn[(long long)(b * GJB + r) * GJB + c] = acc;
+    for (int q = 0; q < GJB; ++q) {
+      const float2 xv = sX[r * GJS + q];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) cfma(acc[u], xv, sP[q * GJS + c0 + 4 * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int c = c0 + 4 * u;
+      Cold[(long long)(b * GJB + r) * GJB + c] = sX[r * GJS + c];
+      Cn[(long long)(b * GJB + r) * GJB + c] = acc[u];
+    }
   } else {
-    for (int q = 0; q < GJB; ++q) cfma(acc, sP[r][q], sX[q][c]);
-    Rp[(long long)r * N + b * GJB + c] = acc;
+    for (int q = 0; q < GJB; ++q) {
+      const float2 pv = sP[r * GJS + q];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) cfma(acc[u], pv, sX[q * GJS + c0 + 4 * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) Rp[(long long)r * N + b * GJB + c0 + 4 * u] = acc[u];
   }
 }
 
-// Lower 64 x 64 tiles: M_ij -= M_ik (P M_kj) = Cold_i R_j for i, j != k, and
-// the sweep's write-back in the pivot row and column: M_kj = R_j (j < k),
-// M_ik = -Cn_i (i > k), M_kk = P.  4 x 4 outputs per thread.
+// Lower tiles (I, J) for pivot block k: M_IJ -= Cold_I R_J for I, J != k, and
+// the sweep's write-back: M_kJ = R_J (J < k), M_Ik = -Cn_I (I > k), M_kk = P.
+// 4 x 4 complex outputs per thread.  CTA 0 takes tile (k+1, k+1) and, after
+// updating it, inverts it into Pnext (the next pivot block), overlapping that
+// sweep with the other tiles.
 __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N, int k,
                                                    const float2* __restrict__ P,
+                                                   float2* __restrict__ Pnext,
                                                    const float2* __restrict__ Cold,
                                                    const float2* __restrict__ Cn,
                                                    const float2* __restrict__ Rp) {
-  if (blockIdx.x > blockIdx.y) return;          // upper tile: not kept
-  __shared__ float2 sC[64][GJB + 1], sR[GJB][64 + 1];
-  const int bi = blockIdx.y * 64, bj = blockIdx.x * 64;
+  extern __shared__ float2 gsm[];
+  const int nt = N / GJB;
+  // tile index: CTA 0 -> (k+1, k+1) if it exists; the rest in order, skipping it
+  const long long kp = (k + 1 < nt) ? (long long)(k + 1) * (k + 2) / 2 + (k + 1) : -1;
+  long long t = blockIdx.x;
+  if (kp >= 0) t = (t == 0) ? kp : (t <= kp ? t - 1 : t);
+  int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
+  while ((long long)I * (I + 1) / 2 > t) --I;
+  const int J = (int)(t - (long long)I * (I + 1) / 2);
   const int tid = threadIdx.x;
-  for (int q = tid; q < 64 * GJB; q += 256) {
-    const int rr = q / GJB, cc = q % GJB;
-    sC[rr][cc] = Cold[(long long)(bi + rr) * GJB + cc];
-    const int r2 = q / 64, c2 = q % 64;
-    sR[r2][c2] = Rp[(long long)r2 * N + bj + c2];
+  float2* tile = M + (long long)I * GJB * N + J * GJB;
+  if (I == k || J == k) {                              // pivot row / column / block
+    for (int q = tid; q < GJB * GJB; q += 256) {
+      const int r = q / GJB, c = q % GJB;
+      float2 v;
+      if (I == k && J == k) {
+        v = P[q];
+      } else if (I == k) {
+        v = Rp[(long long)r * N + J * GJB + c];
+      } else {
+        const float2 w = Cn[(long long)(I * GJB + r) * GJB + c];
+        v = make_float2(-w.x, -w.y);
+      }
+      tile[(long long)r * N + c] = v;
+    }
+    return;
+  }
+  float2* sC = gsm;                                    // Cold_I [64][GJS]
+  float2* sR = gsm + GJB * GJS;                        // R_J    [64][GJS]
+  for (int q = tid; q < GJB * GJB; q += 256) {
+    const int r = q / GJB, c = q % GJB;
+    sC[r * GJS + c] = Cold[(long long)(I * GJB + r) * GJB + c];
+    sR[r * GJS + c] = Rp[(long long)r * N + J * GJB + c];
   }
   __syncthreads();
-  const int tr = tid / 16, tc = tid % 16;   // rows tr + 16 u, cols tc + 16 v
+  const int tr = tid >> 4, tc = tid & 15;              // rows tr + 16 u, cols tc + 16 v
   float2 acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -896,51 +962,54 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
   for (int q = 0; q < GJB; ++q) {
     float2 cv[4], rv[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) cv[u] = sC[tr + 16 * u][q];
+    for (int u = 0; u < 4; ++u) cv[u] = sC[(tr + 16 * u) * GJS + q];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) rv[v] = sR[q][tc + 16 * v];
+    for (int v = 0; v < 4; ++v) rv[v] = sR[q * GJS + tc + 16 * v];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 4; ++v) cfma(acc[u][v], cv[u], rv[v]);
   }
-  const int kb0 = k * GJB, kb1 = kb0 + GJB;
+  const bool next_pivot = (long long)t == kp;
+  if (next_pivot) __syncthreads();                     // sC is reused for the new tile
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int row = bi + tr + 16 * u;
-    const bool prow = row >= kb0 && row < kb1;
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int col = bj + tc + 16 * v;
-      const bool pcol = col >= kb0 && col < kb1;
-      float2* p = M + (long long)row * N + col;
-      if (prow && pcol) {
-        *p = P[(row - kb0) * GJB + (col - kb0)];
-      } else if (prow) {
-        if (col < kb0) *p = Rp[(long long)(row - kb0) * N + col];
-      } else if (pcol) {
-        if (row >= kb1) {
-          const float2 w = Cn[(long long)row * GJB + (col - kb0)];
-          *p = make_float2(-w.x, -w.y);
-        }
-      } else {
-        *p = csub(*p, acc[u][v]);
-      }
+      const int r = tr + 16 * u, c = tc + 16 * v;
+      float2* p = tile + (long long)r * N + c;
+      const float2 nv = csub(*p, acc[u][v]);
+      *p = nv;
+      if (next_pivot) sC[r * GJS + c] = nv;
     }
+  if (next_pivot) {
+    __syncthreads();
+    sweep_block64(sC);
+    for (int q = tid; q < GJB * GJB; q += 256) Pnext[q] = sC[(q / GJB) * GJS + q % GJB];
   }
 }
 
 cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s) {
-  if (N % 64 != 0) return cudaErrorInvalidValue;
+  if (N % GJB != 0) return cudaErrorInvalidValue;
   float2* M = (float2*)Mv;
-  float2* P = (float2*)work;
-  float2* Cold = P + GJB * GJB;
+  float2* Pb[2] = {(float2*)work, (float2*)work + GJB * GJB};
+  float2* Cold = Pb[1] + GJB * GJB;
   float2* Cn = Cold + (long long)N * GJB;
   float2* Rp = Cn + (long long)N * GJB;
   const int nb = N / GJB;
+  const size_t sm = 2 * GJB * GJS * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_gj_pivot0<<<1, 256, GJB * GJS * sizeof(float2), s>>>(M, N, Pb[0]); count_launch();
+  const int ntiles = nb * (nb + 1) / 2;
   for (int k = 0; k < nb; ++k) {
-    k_gj_panel<<<2 * nb, dim3(GJB, GJB), 0, s>>>(M, N, k, P, Cold, Cn, Rp); count_launch();
-    k_gj_update<<<dim3(N / 64, N / 64), 256, 0, s>>>(M, N, k, P, Cold, Cn, Rp); count_launch();
+    k_gj_panel<<<2 * nb, 256, sm, s>>>(M, N, k, Pb[k & 1], Cold, Cn, Rp); count_launch();
+    k_gj_update<<<ntiles, 256, sm, s>>>(M, N, k, Pb[k & 1], Pb[(k + 1) & 1], Cold, Cn, Rp);
+    count_launch();
   }
   return cudaGetLastError();
 }

@@ -825,7 +825,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       h->Nc = (int)C.count();
       h->ldc = (h->Nc + 63) / 64 * 64;
       h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
-      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 32 + 32 * 32) * sizeof(float2));
+      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
       h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
       const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
       h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
