@@ -802,29 +802,81 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 static constexpr int GJB = 64;
 static constexpr int GJS = GJB + 1;              // shared row stride (float2)
 
-// In-place sweep of the 64 x 64 block a[][GJS] in shared memory by 256
-// threads (16 entries each: row tid / 4, columns tid % 4 + 4 v).
-__device__ void sweep_block64(float2* a) {
-  const int r = threadIdx.x >> 2, c0 = threadIdx.x & 3;
-  for (int p = 0; p < GJB; ++p) {
-    const float2 piv = a[p * GJS + p];
-    const float den = piv.x * piv.x + piv.y * piv.y;
-    const float2 inv = make_float2(piv.x / den, -piv.y / den);
-    const float2 arp = a[r * GJS + p];
-    const float2 f = cmul(arp, inv);                     // M_rp / M_pp
-    float2 v[16];
+// In-place inversion of the Hermitian positive definite 64 x 64 block
+// a[][GJS] in shared memory by 256 threads: the same sweep, blocked in four
+// 16 x 16 sub-pivots K.  Each sub-pivot is swept element by element (one
+// entry per thread, 16 steps), then the rest of the block is updated with
+// rank-16 products: a_ij -= a_iK P a_Kj, a_Kj <- P a_Kj, a_iK <- -a_iK P for
+// i, j outside K.  tmp holds 2 x 16 x 48 complex (the row and column panels).
+__device__ void sweep_block64(float2* a, float2* tmp) {
+  const int tid = threadIdx.x;
+  float2* TR = tmp;                                    // [16][48]  P a_Kj
+  float2* TC = tmp + 16 * 48;                          // [48][16]  a_iK P
+  for (int K = 0; K < 4; ++K) {
+    const int k0 = 16 * K;
+    {                                                  // sweep the 16 x 16 sub-pivot
+      const int r = k0 + (tid >> 4), c = k0 + (tid & 15);
+      for (int p = k0; p < k0 + 16; ++p) {
+        const float2 piv = a[p * GJS + p];
+        const float den = piv.x * piv.x + piv.y * piv.y;
+        const float2 inv = make_float2(piv.x / den, -piv.y / den);
+        const float2 arp = a[r * GJS + p], apc = a[p * GJS + c], arc = a[r * GJS + c];
+        float2 v;
+        if (r == p && c == p) v = inv;
+        else if (r == p) v = cmul(inv, apc);
+        else if (c == p) v = make_float2(-(arp.x * inv.x - arp.y * inv.y),
+                                         -(arp.x * inv.y + arp.y * inv.x));
+        else v = csub(arc, cmul(cmul(arp, inv), apc));
+        __syncthreads();
+        a[r * GJS + c] = v;
+        __syncthreads();
+      }
+    }
+    // panels: TR[q][x] = sum_s P[q][s] a[k0+s][col(x)], TC[x][q] = sum_s a[row(x)][k0+s] P[s][q]
+    for (int o = tid; o < 2 * 16 * 48; o += 256) {
+      const int e = o % (16 * 48);
+      float2 acc = make_float2(0.f, 0.f);
+      if (o < 16 * 48) {
+        const int q = e / 48, x = e % 48, col = x < k0 ? x : x + 16;
+        for (int s2 = 0; s2 < 16; ++s2)
+          cfma(acc, a[(k0 + q) * GJS + k0 + s2], a[(k0 + s2) * GJS + col]);
+        TR[e] = acc;
+      } else {
+        const int x = e / 16, q = e % 16, row = x < k0 ? x : x + 16;
+        for (int s2 = 0; s2 < 16; ++s2)
+          cfma(acc, a[row * GJS + k0 + s2], a[(k0 + s2) * GJS + k0 + q]);
+        TC[e] = acc;
+      }
+    }
+    __syncthreads();
+    // rank-16 update of the 48 x 48 entries outside row and column block K
+    float2 nv[9];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int c = c0 + 4 * u;
-      const float2 apc = a[p * GJS + c], arc = a[r * GJS + c];
-      if (r == p && c == p) v[u] = inv;
-      else if (r == p) v[u] = cmul(inv, apc);
-      else if (c == p) v[u] = make_float2(-f.x, -f.y);
-      else v[u] = csub(arc, cmul(f, apc));
+    for (int u = 0; u < 9; ++u) {
+      const int e = tid + 256 * u, xi = e / 48, xj = e % 48;
+      const int row = xi < k0 ? xi : xi + 16, col = xj < k0 ? xj : xj + 16;
+      float2 acc = a[row * GJS + col];
+      for (int s2 = 0; s2 < 16; ++s2) {
+        const float2 c = a[row * GJS + k0 + s2], rv = TR[s2 * 48 + xj];
+        acc.x -= c.x * rv.x - c.y * rv.y;
+        acc.y -= c.x * rv.y + c.y * rv.x;
+      }
+      nv[u] = acc;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 16; ++u) a[r * GJS + c0 + 4 * u] = v[u];
+    for (int u = 0; u < 9; ++u) {
+      const int e = tid + 256 * u, xi = e / 48, xj = e % 48;
+      const int row = xi < k0 ? xi : xi + 16, col = xj < k0 ? xj : xj + 16;
+      a[row * GJS + col] = nv[u];
+    }
+    for (int o = tid; o < 16 * 48; o += 256) {         // panel write-back
+      const int q = o / 48, x = o % 48, col = x < k0 ? x : x + 16;
+      a[(k0 + q) * GJS + col] = TR[o];
+      const int x2 = o / 16, q2 = o % 16, row = x2 < k0 ? x2 : x2 + 16;
+      const float2 w = TC[o];
+      a[row * GJS + k0 + q2] = make_float2(-w.x, -w.y);
+    }
     __syncthreads();
   }
 }
@@ -836,13 +888,14 @@ __global__ void __launch_bounds__(256) k_gj_pivot0(const float2* __restrict__ M,
   for (int q = threadIdx.x; q < GJB * GJB; q += 256)
     gsm[(q / GJB) * GJS + q % GJB] = M[(long long)(q / GJB) * N + q % GJB];
   __syncthreads();
-  sweep_block64(gsm);
+  sweep_block64(gsm, gsm + GJB * GJS);
   for (int q = threadIdx.x; q < GJB * GJB; q += 256) P[q] = gsm[(q / GJB) * GJS + q % GJB];
 }
 
-// Panels of pivot block k, one CTA per block b != k: Cold_b = M_bk and
-// Cn_b = M_bk P (column panel, CTAs 0..nb-1), R_b = P M_kb (row panel, CTAs
-// nb..2nb-1).  M_bk and M_kb come from the stored lower tiles by the sign rule.
+// Panels of pivot block k for blocks b != k, each output block split over 4
+// CTAs of 16 rows (blockIdx.y): Cold_b = M_bk and Cn_b = M_bk P (column
+// panel, blockIdx.x < nb), R_b = P M_kb (row panel).  M_bk and M_kb come from
+// the stored lower tiles by the sign rule.
 __global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, int N, int k,
                                                   const float2* __restrict__ P,
                                                   float2* __restrict__ Cold,
@@ -852,15 +905,19 @@ __global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, 
   float2* sP = gsm;
   float2* sX = gsm + GJB * GJS;
   const int nb = N / GJB;
-  const int b = blockIdx.x % nb, col_panel = blockIdx.x < nb;
+  const int b = blockIdx.x % nb, col_panel = blockIdx.x < nb, r0 = 16 * blockIdx.y;
   if (b == k) return;
+  // stored tile read row by row; a transposed source is read along its rows
+  // (r fastest) so that the global loads stay coalesced
+  const bool transposed = col_panel ? (b < k) : (b > k);
+#pragma unroll
   for (int q = threadIdx.x; q < GJB * GJB; q += 256) {
-    const int r = q / GJB, c = q % GJB;
-    sP[r * GJS + c] = P[q];
+    sP[(q / GJB) * GJS + q % GJB] = P[q];
+    const int r = transposed ? q % GJB : q / GJB, c = transposed ? q / GJB : q % GJB;
     float2 x;
     if (col_panel) {
       // M_bk: stored for b > k; for b < k it is -(M_kb)^H (swept row, unswept column)
-      if (b > k) {
+      if (!transposed) {
         x = M[(long long)(b * GJB + r) * N + k * GJB + c];
       } else {
         const float2 v = M[(long long)(k * GJB + c) * N + b * GJB + r];
@@ -868,7 +925,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, 
       }
     } else {
       // M_kb: stored for b < k; for b > k it is (M_bk)^H (both unswept)
-      if (b < k) {
+      if (!transposed) {
         x = M[(long long)(k * GJB + r) * N + b * GJB + c];
       } else {
         const float2 v = M[(long long)(b * GJB + c) * N + k * GJB + r];
@@ -878,19 +935,19 @@ __global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, 
     sX[r * GJS + c] = x;
   }
   __syncthreads();
-  const int r = threadIdx.x >> 2, c0 = threadIdx.x & 3;
-  float2 acc[16];
+  const int r = r0 + (threadIdx.x >> 4), c0 = threadIdx.x & 15;
+  float2 acc[4];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
+  for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
   if (col_panel) {
     for (int q = 0; q < GJB; ++q) {
       const float2 xv = sX[r * GJS + q];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) cfma(acc[u], xv, sP[q * GJS + c0 + 4 * u]);
+      for (int u = 0; u < 4; ++u) cfma(acc[u], xv, sP[q * GJS + c0 + 16 * u]);
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int c = c0 + 4 * u;
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + 16 * u;
       Cold[(long long)(b * GJB + r) * GJB + c] = sX[r * GJS + c];
       Cn[(long long)(b * GJB + r) * GJB + c] = acc[u];
     }
@@ -898,18 +955,44 @@ __global__ void __launch_bounds__(256) k_gj_panel(const float2* __restrict__ M, 
     for (int q = 0; q < GJB; ++q) {
       const float2 pv = sP[r * GJS + q];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) cfma(acc[u], pv, sX[q * GJS + c0 + 4 * u]);
+      for (int u = 0; u < 4; ++u) cfma(acc[u], pv, sX[q * GJS + c0 + 16 * u]);
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) Rp[(long long)r * N + b * GJB + c0 + 4 * u] = acc[u];
+    for (int u = 0; u < 4; ++u) Rp[(long long)r * N + b * GJB + c0 + 16 * u] = acc[u];
   }
 }
 
 // Lower tiles (I, J) for pivot block k: M_IJ -= Cold_I R_J for I, J != k, and
 // the sweep's write-back: M_kJ = R_J (J < k), M_Ik = -Cn_I (I > k), M_kk = P.
-// 4 x 4 complex outputs per thread.  CTA 0 takes tile (k+1, k+1) and, after
-// updating it, inverts it into Pnext (the next pivot block), overlapping that
-// sweep with the other tiles.
+// CTA 0 takes tile (k+1, k+1) and, after updating it, inverts it into Pnext
+// (the next pivot block), overlapping that sweep with the other tiles.
+//
+// The complex product runs on the tensor cores as a real GEMM: with complex
+// entries interleaved (re, im), Out (64 x 128) = C (64 x 128) B (128 x 128),
+// where B realifies R: B[2k][2j] = Re R_kj, B[2k][2j+1] = Im R_kj,
+// B[2k+1][2j] = -Im R_kj, B[2k+1][2j+1] = Re R_kj.  mma.sync m16n8k8 TF32 with
+// each operand split x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) and three
+// products hi hi + hi lo + lo hi, FP32 accumulation: about FP32 accuracy.
+// 8 warps in a 2 x 4 grid, 32 x 32 real outputs each; lane (g, t) = (lane/4,
+// lane%4) holds complex outputs (row g or g + 8, column t) of each 16 x 4
+// complex sub-tile, so the epilogue works on whole complex numbers.
+static constexpr int GJC = 66;                   // sC row stride (float2), conflict-free A loads
+static constexpr int GJR = 68;                   // sR row stride (float2), conflict-free B loads
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(lo) : "f"(r));
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N, int k,
                                                    const float2* __restrict__ P,
                                                    float2* __restrict__ Pnext,
@@ -944,47 +1027,93 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
     }
     return;
   }
-  float2* sC = gsm;                                    // Cold_I [64][GJS]
-  float2* sR = gsm + GJB * GJS;                        // R_J    [64][GJS]
-  for (int q = tid; q < GJB * GJB; q += 256) {
-    const int r = q / GJB, c = q % GJB;
-    sC[r * GJS + c] = Cold[(long long)(I * GJB + r) * GJB + c];
-    sR[r * GJS + c] = Rp[(long long)r * N + J * GJB + c];
+  float2* sC = gsm;                                    // Cold_I [64][GJC]
+  float2* sR = gsm + GJB * GJC;                        // R_J    [64][GJR]
+  {                                                    // two complex per 16-byte load,
+    float4 vc[8], vr[8];                               // all 16 loads in flight first
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = tid + 256 * u, r = q / (GJB / 2), c = 2 * (q % (GJB / 2));
+      vc[u] = *(const float4*)&Cold[(long long)(I * GJB + r) * GJB + c];
+      vr[u] = *(const float4*)&Rp[(long long)r * N + J * GJB + c];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = tid + 256 * u, r = q / (GJB / 2), c = 2 * (q % (GJB / 2));
+      *(float4*)&sC[r * GJC + c] = vc[u];
+      *(float4*)&sR[r * GJR + c] = vr[u];
+    }
   }
   __syncthreads();
-  const int tr = tid >> 4, tc = tid & 15;              // rows tr + 16 u, cols tc + 16 v
-  float2 acc[4][4];
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;             // rows 32 wm.., complex cols 16 wn..
+  const float* sCf = (const float*)sC;
+  float acc[2][4][4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
-#pragma unroll 4
-  for (int q = 0; q < GJB; ++q) {
-    float2 cv[4], rv[4];
+    for (int n = 0; n < 4; ++n)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) cv[u] = sC[(tr + 16 * u) * GJS + q];
+      for (int e = 0; e < 4; ++e) acc[mt][n][e] = 0.f;
+#pragma unroll 2
+  for (int kk = 0; kk < 2 * GJB / 8; ++kk) {           // 16 real k-steps of 8
+    uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) rv[v] = sR[q * GJS + tc + 16 * v];
+    for (int mt = 0; mt < 2; ++mt) {
+      const int row = 32 * wm + 16 * mt + g;
+      const float* r0 = sCf + row * 2 * GJC + 8 * kk;
+      const float* r8 = r0 + 8 * 2 * GJC;
+      split_tf32(r0[tq], ah[mt][0], al[mt][0]);
+      split_tf32(r8[tq], ah[mt][1], al[mt][1]);
+      split_tf32(r0[tq + 4], ah[mt][2], al[mt][2]);
+      split_tf32(r8[tq + 4], ah[mt][3], al[mt][3]);
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int n = 0; n < 4; ++n) {
+      // B[8kk + tq][8n' + g] and B[8kk + tq + 4][8n' + g], n' = 4 wn + n
+      const int j = 16 * wn + 4 * n + (g >> 1), d = g & 1;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) cfma(acc[u][v], cv[u], rv[v]);
+      for (int h = 0; h < 2; ++h) {
+        const int kr = 8 * kk + tq + 4 * h;            // real row of B
+        const float2 v = sR[(kr >> 1) * GJR + j];
+        const float x = (kr & 1) ? (d ? v.x : -v.y) : (d ? v.y : v.x);
+        split_tf32(x, bh[n][h], bl[n][h]);
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        mma_tf32(acc[mt][n], al[mt], bh[n]);
+        mma_tf32(acc[mt][n], ah[mt], bl[n]);
+        mma_tf32(acc[mt][n], ah[mt], bh[n]);
+      }
   }
   const bool next_pivot = (long long)t == kp;
   if (next_pivot) __syncthreads();                     // sC is reused for the new tile
+  float2 old[2][4][2];                                 // all tile loads before the stores
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int r = tr + 16 * u, c = tc + 16 * v;
-      float2* p = tile + (long long)r * N + c;
-      const float2 nv = csub(*p, acc[u][v]);
-      *p = nv;
-      if (next_pivot) sC[r * GJS + c] = nv;
-    }
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        old[mt][n][h] = tile[(long long)(32 * wm + 16 * mt + g + 8 * h) * N + 16 * wn + 4 * n + tq];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = 32 * wm + 16 * mt + g + 8 * h, c = 16 * wn + 4 * n + tq;
+        const float2 o = old[mt][n][h];
+        const float2 nv = make_float2(o.x - acc[mt][n][2 * h], o.y - acc[mt][n][2 * h + 1]);
+        tile[(long long)r * N + c] = nv;
+        if (next_pivot) sC[r * GJS + c] = nv;
+      }
   if (next_pivot) {
     __syncthreads();
-    sweep_block64(sC);
+    sweep_block64(sC, sR);
     for (int q = tid; q < GJB * GJB; q += 256) Pnext[q] = sC[(q / GJB) * GJS + q % GJB];
   }
 }
@@ -998,17 +1127,20 @@ cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s
   float2* Rp = Cn + (long long)N * GJB;
   const int nb = N / GJB;
   const size_t sm = 2 * GJB * GJS * sizeof(float2);
+  const size_t smu = GJB * (GJC + GJR) * sizeof(float2);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu);
     attr = true;
   }
-  k_gj_pivot0<<<1, 256, GJB * GJS * sizeof(float2), s>>>(M, N, Pb[0]); count_launch();
+  k_gj_pivot0<<<1, 256, (GJB * GJS + 2 * 16 * 48) * sizeof(float2), s>>>(M, N, Pb[0]);
+  count_launch();
   const int ntiles = nb * (nb + 1) / 2;
   for (int k = 0; k < nb; ++k) {
-    k_gj_panel<<<2 * nb, 256, sm, s>>>(M, N, k, Pb[k & 1], Cold, Cn, Rp); count_launch();
-    k_gj_update<<<ntiles, 256, sm, s>>>(M, N, k, Pb[k & 1], Pb[(k + 1) & 1], Cold, Cn, Rp);
+    k_gj_panel<<<dim3(2 * nb, GJB / 16), 256, sm, s>>>(M, N, k, Pb[k & 1], Cold, Cn, Rp);
+    count_launch();
+    k_gj_update<<<ntiles, 256, smu, s>>>(M, N, k, Pb[k & 1], Pb[(k + 1) & 1], Cold, Cn, Rp);
     count_launch();
   }
   return cudaGetLastError();
