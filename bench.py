@@ -49,9 +49,11 @@ def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured",
-                "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "sm_max_mhz": 2070.0}
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "src": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "src": "fallback", "sm_max_mhz": 2070.0}
 
 
 def workload_inputs(name):
@@ -148,14 +150,20 @@ def gpu_bench(args):
                             setup_sweeps=wl["setup_sweeps"])
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
 
-    def step(solver, record=None, profile=False):
-        h = mg.mg_setup(U_d, masses[0], params, stream)
+    def step(solver, record=None, profile=False, phases=None):
+        p = params
+        if profile:                        # per-kernel-family event timing from the setup on
+            p = type(params).from_buffer_copy(params)
+            p.profile = 1
+        h = mg.mg_setup(U_d, masses[0], p, stream)
+        mark = (lambda what: phases.append((what, mg.mg_kernel_launches()))) if phases is not None \
+            else (lambda what: None)
+        mark("setup")
         try:
-            if profile:
-                mg.mg_profile_enable(h, True)
             for m in masses:
                 if m != masses[0]:
                     mg.mg_set_mass(h, m)
+                    mark(f"set_mass {m}")
                 mg.mg_apply_D(h, chi_d, b_d, 1, 1, mg.PREC_F64)
                 e0, e1 = ev(), ev()
                 e0.record(stream)
@@ -166,14 +174,15 @@ def gpu_bench(args):
                                        f"residual {info[0].true_residual}: {mg.mg_last_error(h)}")
                 if record is not None:
                     record.append((m, e0, e1, info[0]))
+                mark(f"solve {m}")
             prof = None
             if profile:
-                prof = {f: mg.mg_profile_read(h, f) for f in range(8)}
+                prof = {f: mg.mg_profile_read(h, f) for f in range(mg.KF_COUNT)}
             return prof
         finally:
             mg.mg_destroy(h)
 
-    def timed(solver, K, clocks=None):
+    def timed(solver, K, clocks=None, phases=None):
         recs, steps = [], []
         torch.cuda.synchronize()
         if world > 1:
@@ -181,11 +190,11 @@ def gpu_bench(args):
         if clocks:
             clocks.start()
         launches0 = mg.mg_kernel_launches()
-        for _ in range(K):
+        for i in range(K):
             flush.zero_()                      # L2 flush between timed steps
             s0, s1 = ev(), ev()
             s0.record(stream)
-            step(solver, recs)
+            step(solver, recs, phases=phases if i == 0 else None)
             s1.record(stream)
             steps.append((s0, s1))
         torch.cuda.synchronize()
@@ -216,7 +225,9 @@ def gpu_bench(args):
     for _ in range(args.warmup):
         step(mg.SOLVER_MGCG_MIXED)
     clocks = Clocks(local) if rank == 0 else None
-    res = timed(mg.SOLVER_MGCG_MIXED, args.steps, clocks)
+    phases = [] if args.phase_launches else None
+    base = mg.mg_kernel_launches()
+    res = timed(mg.SOLVER_MGCG_MIXED, args.steps, clocks, phases)
     solves = len(masses) * args.steps * world
     value = solves / (res["total_ms"] / 1000.0)
 
@@ -226,6 +237,7 @@ def gpu_bench(args):
                               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": round(res["total_ms"] / args.steps, 3),
                               "per_mass": res["per_mass"], "gpu_launches": int(res["launches"]),
+                              "phase_launches": [(w, n - base) for w, n in phases] if phases else None,
                               "note": "timed-only profiling run"}))
         return
     # plain FP64 MG-CG, same step
@@ -285,19 +297,24 @@ def gpu_bench(args):
         dist.destroy_process_group()
 
 
-FAM_NAMES = ["fine_A_f32", "coarse_apply", "transfer", "coarsest_solve", "coarsest_inverse",
-             "galerkin", "fine_A_f64", "coarsest_dense_gemv"]
+FAM_NAMES = ["fine_A_f32", "coarse_apply_f32_bf16", "transfer", "coarsest_solve",
+             "coarsest_inverse", "galerkin", "fine_A_f64", "coarsest_gemv_tiles", "gj_update",
+             "coarse_apply_f64"]
+
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel source (summaries and commands under profiles/); a kernel changed
+# since its capture has no entry.
+NCU_TRAFFIC = {"gj_update": 71368192 + 13786368}
 
 
 def roofline(prof, wl, peaks):
-    """Dominant kernel family by device time in one profiled (eager) step, the
-    coarsest-solve family split into its dense GEMV and the rest; achieved =
-    algorithmic bytes (or flops) per call / average call duration."""
-    prof = dict(prof)
-    # the coarsest-solve family contains the dense GEMV calls: count the rest only
-    prof[3] = (max(prof[3][0] - prof[7][0], 0.0), prof[3][1])
-    fam = max(prof, key=lambda f: prof[f][0])
-    ms, calls = prof[fam]
+    """Roofline of the dominant kernel of one profiled (eager) step, and of
+    the other candidates.  The candidates are the profiling families that time
+    one kind of kernel each (CUDA events recorded on the library's stream
+    around each launch, set-up included): the tensor-core Gauss-Jordan update
+    of the coarsest inverse, the fused FP32 and FP64 fine stencils, the tile
+    kernel of the packed Hermitian GEMV and the BF16 coarse apply; achieved =
+    algorithmic bytes (or flops) per launch / average launch duration."""
     Lx, Lt = wl["Lx"], wl["Lt"]
     V = Lx * Lt
     Nv1, Nv2 = wl["Nv"]
@@ -306,37 +323,49 @@ def roofline(prof, wl, peaks):
     V3 = V2 // (b2[0] * b2[1])
     N3 = V3 * 2 * Nv2
     ld = (N3 + 63) // 64 * 64
-    ntiles = (ld // 64) * (ld // 64 + 1) // 2
-    shares = {FAM_NAMES[f]: round(prof[f][0], 3) for f in prof}
-    per_call_s = ms / 1000.0 / max(calls, 1)
-    out = {"kernel": FAM_NAMES[fam], "calls": calls, "avg_us": round(per_call_s * 1e6, 3),
-           "family_ms_in_step": shares, "traffic": None,
-           "timing": "CUDA events around each call in one eager (non-graph) step"}
-    if fam == 4:       # Hermitian Gauss-Jordan: 4 ld^3 real flops (lower triangle)
-        flops = 4.0 * ld ** 3
-        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        out.update({"bound": "alu", "achieved": round(flops / per_call_s / 1e12, 3),
-                    "peak": round(peak, 1), "unit": "TFLOP/s",
-                    "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"})
-    else:
-        if fam == 0:
-            byts = 48.0 * V                              # psi in/out + links, FP32
-        elif fam == 6:
-            byts = 96.0 * V
-        elif fam == 1:      # BF16 V-cycle applies on level 2 dominate
-            byts = V2 * (9 * (2 * Nv1) ** 2 * 4 + 2 * 2 * Nv1 * 8)
-        elif fam == 2:
-            byts = V * (2 * 8 + 2 * Nv1 * 8) + V2 * 2 * Nv1 * 8
-        elif fam == 7:      # packed lower-triangular tiles of the FP32 inverse
-            byts = ntiles * 64 * 64 * 8.0 + ntiles * 2 * 64 * 8 * 2
-        elif fam == 3:
-            byts = V3 * 9 * (2 * Nv2) ** 2 * 16.0
+    nt = ld // 64
+    ntiles = nt * (nt + 1) // 2
+    cand = {8: "gj_update", 7: "coarsest_gemv_tiles", 1: "coarse_apply_bf16", 0: "fine_A_f32",
+            6: "fine_A_f64"}
+    total = sum(prof[f][0] for f in cand)
+
+    def one(fam):
+        ms, calls = prof[fam]
+        per_call_s = ms / 1000.0 / max(calls, 1)
+        o = {"kernel": cand[fam], "launches": calls, "avg_us": round(per_call_s * 1e6, 3),
+             "ms_in_step": round(ms, 3)}
+        if fam == 8:
+            # complex rank-64 update of the lower 64 x 64 tiles outside the pivot
+            # row and column: 64^3 complex multiply-adds (8 real flops) per tile
+            flops = (ntiles - nt) * 64.0 ** 3 * 8.0
+            peak = peaks["bf16_tflops_sustained"] * 1.1 / 2.25   # nominal TF32 / BF16 ratio
+            o.update({"bound": "tensor", "achieved": round(flops / per_call_s / 1e12, 3),
+                      "peak": round(peak, 1), "unit": "TFLOP/s", "flops_per_launch": flops,
+                      "peak_note": f"of {peaks['src']}: sustained bf16 x nominal tf32/bf16 1.1/2.25",
+                      "tensor_flops_issued_per_launch": 3 * flops,
+                      "note": "mma.sync m16n8k8 TF32, three products per FP32-accurate product",
+                      "traffic": NCU_TRAFFIC.get("gj_update")})
         else:
-            byts = 16.0 * V2 * 9 * (2 * Nv1) ** 2
-        out.update({"bound": "hbm", "achieved": round(byts / per_call_s / 1e9, 1),
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes_per_call": int(byts)})
-    out["frac"] = round(out["achieved"] / out["peak"], 4)
-    out["peak_note"] = f"of {peaks['src']}"
+            if fam == 0:
+                byts = 48.0 * V                          # psi in/out + links, FP32
+            elif fam == 6:
+                byts = 96.0 * V
+            elif fam == 1:      # level-2 BF16 blocks + FP32 input and output vectors
+                byts = V2 * (9 * (2 * Nv1) ** 2 * 4.0 + 2 * 2 * Nv1 * 8.0)
+            else:               # packed lower tiles of the inverse + per-tile partial sums
+                byts = ntiles * 64 * 64 * 8.0 + ntiles * 2 * 64 * 8.0
+            o.update({"bound": "hbm", "achieved": round(byts / per_call_s / 1e9, 1),
+                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes_per_launch": int(byts),
+                      "peak_note": f"of {peaks['src']}", "traffic": NCU_TRAFFIC.get(cand[fam])})
+        o["frac"] = round(o["achieved"] / o["peak"], 4)
+        o["share_of_candidates"] = round(ms / total, 3) if total else None
+        return o
+
+    fam = max(cand, key=lambda f: prof[f][0])
+    out = one(fam)
+    out["timing"] = "CUDA events on the library stream around each launch, one eager step"
+    out["family_ms_in_step"] = {FAM_NAMES[f]: round(prof[f][0], 3) for f in prof}
+    out["other_candidates"] = [one(f) for f in cand if f != fam]
     return out
 
 
@@ -560,7 +589,9 @@ def ncu_case(args):
                benchmark workload, one right-hand side; coarse_mma -- the same
                with 64 right-hand sides (tensor cores); coarsest -- the
                coarsest solve (packed FP32 GEMV + FP64 refinement) of the
-               benchmark workload; vcycle -- one FP32 V-cycle."""
+               benchmark workload; vcycle -- one FP32 V-cycle; setup -- the
+               set-up of the benchmark workload alone (its Gauss-Jordan
+               inverse of the 4096-unknown coarsest operator included)."""
     import torch
     from paper_0710_3612_gb300 import mg
     dev = torch.device("cuda", 0)
@@ -587,6 +618,8 @@ def ncu_case(args):
             y = torch.empty_like(x)
             for _ in range(4):
                 mg.mg_apply_coarse(h, 2, x, y, nrhs, mg.PREC_BF16)
+        elif args.ncu_case == "setup":
+            pass
         elif args.ncu_case == "coarsest":
             Lx, Lt, n, _ = mg.mg_get_level(h, len(wl["blocks"]) + 1)
             x = torch.randn(Lx * Lt * n, dtype=torch.complex128, device=dev)
@@ -619,7 +652,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
-    ap.add_argument("--ncu-case", choices=["stencil", "coarse", "coarse_mma", "coarsest", "vcycle"],
+    ap.add_argument("--phase-launches", action="store_true",
+                    help="with --timed-only: library kernel launches counted at the end of each "
+                         "phase (setup, re-mass, solve) of the first timed step")
+    ap.add_argument("--ncu-case", choices=["stencil", "coarse", "coarse_mma", "coarsest", "vcycle",
+                                           "setup"],
                     help="run a small kernel case for an ncu capture and exit")
     args = ap.parse_args()
     if args.ncu_case:

@@ -98,6 +98,9 @@ typedef struct {
   int max_rhs;                          /* right-hand sides solved together by
                                            mg_solve, 1..64 (1); work memory
                                            scales with it                        */
+  int profile;                          /* nonzero: per-kernel-family event
+                                           timing (mg_profile_enable) from the
+                                           start of mg_setup (0)                 */
 } mg_params;
 
 typedef struct {
@@ -210,16 +213,20 @@ unsigned long long mg_kernel_launches(void);
  * device time and the number of calls since the last enable. */
 typedef enum {
   MG_KF_FINE_A = 0,     /* fused A = D^dagger D on the fine lattice            */
-  MG_KF_COARSE = 1,     /* coarse stencil apply, any level and precision       */
+  MG_KF_COARSE = 1,     /* coarse stencil apply in FP32 or BF16 weights        */
   MG_KF_TRANSFER = 2,   /* restriction and prolongation                        */
   MG_KF_COARSEST = 3,   /* coarsest solve (GEMV + FP64 refinement)             */
   MG_KF_INVERSE = 4,    /* coarsest dense inverse (Gauss-Jordan)               */
   MG_KF_GALERKIN = 5,   /* Galerkin coarse-operator build                      */
   MG_KF_FINE_A64 = 6,   /* A = D^dagger D on the fine lattice in FP64 (MG_KF_FINE_A
                            counts the FP32 applications)                        */
-  MG_KF_DENSE = 7,      /* coarsest-level packed Hermitian GEMV (part of
-                           MG_KF_COARSEST)                                      */
-  MG_KF_COUNT = 8
+  MG_KF_DENSE = 7,      /* the tile kernel of the coarsest-level packed
+                           Hermitian GEMV (part of MG_KF_COARSEST)              */
+  MG_KF_GJ_UPDATE = 8,  /* the rank-64 tensor-core update kernel of the dense
+                           inverse, one call per pivot block (part of
+                           MG_KF_INVERSE)                                       */
+  MG_KF_COARSE64 = 9,   /* coarse stencil apply in FP64                         */
+  MG_KF_COUNT = 10
 } mg_kernel_family;
 mg_status mg_profile_enable(mg_handle* h, int on);
 mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long* calls);

@@ -153,8 +153,11 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 // In-place blocked Gauss-Jordan inversion of a Hermitian positive definite
 // complex64 N x N matrix (N multiple of 64), lower triangle kept (the upper
 // halves of diagonal 64 x 64 tiles are rebuilt by pack_hermitian).
-// work: 3 * N * 64 + 2 * 64 * 64 complex64.
-cudaError_t gauss_jordan_inverse_f32(void* M, int N, void* work, cudaStream_t s);
+// work: 3 * N * 64 + 2 * 64 * 64 complex64.  Launch sequence: begin (inverts
+// the first pivot block), then for k = 0 .. N/64 - 1: panel(k), update(k).
+cudaError_t gauss_jordan_begin(void* M, int N, void* work, cudaStream_t s);
+cudaError_t gauss_jordan_panel(void* M, int N, int k, void* work, cudaStream_t s);
+cudaError_t gauss_jordan_update(void* M, int N, int k, void* work, cudaStream_t s);
 // y = B x, or y += B x when accumulate (complex64 B, leading dimension ld);
 // x complex128 (N) -> y complex128 (N); FP32 products and accumulation, result
 // widened to FP64.  xtmp: ld complex64.
@@ -170,6 +173,12 @@ cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s);
 // FP32 products and accumulation; each tile is read once for all vectors.
 cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
                                void* part, bool accumulate, cudaStream_t s);
+// The two launches of hermitian_gemv_f32: partial products per stored tile,
+// then their fixed-order sum per row into y.
+cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
+                                 void* part, cudaStream_t s);
+cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
+                                  bool accumulate, cudaStream_t s);
 
 // index map for tests
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,

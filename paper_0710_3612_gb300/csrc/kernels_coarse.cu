@@ -6,6 +6,8 @@
 //    levels >= 2 from the block formula P(i)^dagger A_l[i, e] P(i + e)
 //  * coarsest level: dense FP32 Gauss-Jordan inverse and GEMV (the FP64
 //    refinement around them lives in the host orchestration)
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -62,7 +64,7 @@ template <> struct row_dot<float> {
 };
 
 template <typename R, typename WT>
-__global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restrict__ in,
+__global__ void __launch_bounds__(576, 2) k_coarse_apply(const cplx_t<R>* __restrict__ in,
                                                       cplx_t<R>* out,
                                                       const WT* __restrict__ A, int Lx, int Lt,
                                                       int n, Epilogue ep) {
@@ -73,6 +75,28 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
   const int j = blockIdx.x;
   const int x = j % Lx, t = j / Lx;
   const cplx_t<R>* vin = in + (long long)blockIdx.y * V * n;
+  // BF16 rows of up to 24 entries are loaded into registers before the
+  // neighbour vectors are staged, so the two global reads overlap
+  constexpr bool kBf16 = std::is_same<WT, __nv_bfloat162>::value;
+  constexpr int PRE = 6;                         // 16-byte chunks (4 entries each)
+  const bool pre = kBf16 && n <= 4 * PRE && n % 4 == 0;
+  uint4 rv[PRE];
+  if constexpr (kBf16) {
+    if (pre && threadIdx.x < 9 * n) {
+      const int d = threadIdx.x / n, r = threadIdx.x % n;
+      const uint4* row4 = (const uint4*)(A + (((long long)j * 9 + d) * n + r) * n);
+#pragma unroll
+      for (int k = 0; k < PRE; ++k)
+        if (k < n / 4) rv[k] = __ldg(row4 + k);
+    }
+  }
+  // epilogue operands are read up front as well (off the critical path)
+  cplx_t<R> eu = mk((R)0, (R)0), ew = mk((R)0, (R)0);
+  if (threadIdx.x < n) {
+    const long long o = ((long long)blockIdx.y * V + j) * n + threadIdx.x;
+    if (ep.U) eu = ((const cplx_t<R>*)ep.U)[o];
+    if (ep.W) ew = ((const cplx_t<R>*)ep.W)[o];
+  }
   for (int q = threadIdx.x; q < 9 * n; q += blockDim.x) {
     const int d = q / n, c = q % n;
     int xn = x + d % 3 - 1, tn = t + d / 3 - 1;
@@ -84,8 +108,29 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
   const int q = threadIdx.x;
   if (q < 9 * n) {
     const int d = q / n, r = q % n;
-    const WT* row = A + (((long long)j * 9 + d) * n + r) * n;
-    part[q] = row_dot<R>::run(row, xs + d * n, n);
+    bool done = false;
+    if constexpr (kBf16 && sizeof(R) == 4) {
+      if (pre) {
+        const float2* xv = xs + d * n;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < PRE; ++k) {
+          if (k < n / 4) {
+            const uint4 w = rv[k];
+            cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.x), xv[4 * k]);
+            cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.y), xv[4 * k + 1]);
+            cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.z), xv[4 * k + 2]);
+            cfma(acc, bf2_to_f2(*(const __nv_bfloat162*)&w.w), xv[4 * k + 3]);
+          }
+        }
+        part[q] = acc;
+        done = true;
+      }
+    }
+    if (!done) {
+      const WT* row = A + (((long long)j * 9 + d) * n + r) * n;
+      part[q] = row_dot<R>::run(row, xs + d * n, n);
+    }
   }
   __syncthreads();
   if (q < n) {
@@ -94,14 +139,8 @@ __global__ void __launch_bounds__(576) k_coarse_apply(const cplx_t<R>* __restric
     for (int d = 1; d < 9; ++d) acc = cadd(acc, part[d * n + q]);
     const long long o = ((long long)blockIdx.y * V + j) * n + q;
     acc = mk((R)ep.ca * acc.x, (R)ep.ca * acc.y);
-    if (ep.U) {
-      const cplx_t<R> u = ((const cplx_t<R>*)ep.U)[o];
-      acc = mk(acc.x + (R)ep.cu * u.x, acc.y + (R)ep.cu * u.y);
-    }
-    if (ep.W) {
-      const cplx_t<R> w = ((const cplx_t<R>*)ep.W)[o];
-      acc = mk(acc.x + (R)ep.cw * w.x, acc.y + (R)ep.cw * w.y);
-    }
+    if (ep.U) acc = mk(acc.x + (R)ep.cu * eu.x, acc.y + (R)ep.cu * eu.y);
+    if (ep.W) acc = mk(acc.x + (R)ep.cw * ew.x, acc.y + (R)ep.cw * ew.y);
     out[o] = acc;
   }
 }
@@ -1118,31 +1157,50 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
   }
 }
 
-cudaError_t gauss_jordan_inverse_f32(void* Mv, int N, void* work, cudaStream_t s) {
+// Work layout: P[2][64 x 64] (pivot inverse, double-buffered by pivot parity),
+// Cold [N][64], Cn [N][64], Rp [64][N].
+static void gj_work_split(void* work, int N, float2** Pb, float2** Cold, float2** Cn, float2** Rp) {
+  Pb[0] = (float2*)work;
+  Pb[1] = Pb[0] + GJB * GJB;
+  *Cold = Pb[1] + GJB * GJB;
+  *Cn = *Cold + (long long)N * GJB;
+  *Rp = *Cn + (long long)N * GJB;
+}
+
+cudaError_t gauss_jordan_begin(void* M, int N, void* work, cudaStream_t s) {
   if (N % GJB != 0) return cudaErrorInvalidValue;
-  float2* M = (float2*)Mv;
-  float2* Pb[2] = {(float2*)work, (float2*)work + GJB * GJB};
-  float2* Cold = Pb[1] + GJB * GJB;
-  float2* Cn = Cold + (long long)N * GJB;
-  float2* Rp = Cn + (long long)N * GJB;
-  const int nb = N / GJB;
-  const size_t sm = 2 * GJB * GJS * sizeof(float2);
-  const size_t smu = GJB * (GJC + GJR) * sizeof(float2);
+  float2 *Pb[2], *Cold, *Cn, *Rp;
+  gj_work_split(work, N, Pb, &Cold, &Cn, &Rp);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu);
+    cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * GJB * GJS * sizeof(float2)));
+    cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(GJB * (GJC + GJR) * sizeof(float2)));
     attr = true;
   }
-  k_gj_pivot0<<<1, 256, (GJB * GJS + 2 * 16 * 48) * sizeof(float2), s>>>(M, N, Pb[0]);
+  k_gj_pivot0<<<1, 256, (GJB * GJS + 2 * 16 * 48) * sizeof(float2), s>>>((const float2*)M, N, Pb[0]);
   count_launch();
-  const int ntiles = nb * (nb + 1) / 2;
-  for (int k = 0; k < nb; ++k) {
-    k_gj_panel<<<dim3(2 * nb, GJB / 16), 256, sm, s>>>(M, N, k, Pb[k & 1], Cold, Cn, Rp);
-    count_launch();
-    k_gj_update<<<ntiles, 256, smu, s>>>(M, N, k, Pb[k & 1], Pb[(k + 1) & 1], Cold, Cn, Rp);
-    count_launch();
-  }
+  return cudaGetLastError();
+}
+
+cudaError_t gauss_jordan_panel(void* M, int N, int k, void* work, cudaStream_t s) {
+  float2 *Pb[2], *Cold, *Cn, *Rp;
+  gj_work_split(work, N, Pb, &Cold, &Cn, &Rp);
+  const int nb = N / GJB;
+  k_gj_panel<<<dim3(2 * nb, GJB / 16), 256, 2 * GJB * GJS * sizeof(float2), s>>>(
+      (const float2*)M, N, k, Pb[k & 1], Cold, Cn, Rp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gauss_jordan_update(void* M, int N, int k, void* work, cudaStream_t s) {
+  float2 *Pb[2], *Cold, *Cn, *Rp;
+  gj_work_split(work, N, Pb, &Cold, &Cn, &Rp);
+  const int nb = N / GJB;
+  k_gj_update<<<nb * (nb + 1) / 2, 256, GJB * (GJC + GJR) * sizeof(float2), s>>>(
+      (float2*)M, N, k, Pb[k & 1], Pb[(k + 1) & 1], Cold, Cn, Rp);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -1285,13 +1343,14 @@ __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ 
   }
 }
 
-// Warp-per-tile variant for up to four right-hand sides: each warp streams
-// one stored tile straight from global memory in four chunks of 16 rows, lane
-// l holding columns 2l and 2l + 1 of every row (one 16-byte load per row).
-// The row products B_IJ x_J are summed across the warp by a transposing
-// butterfly (after it, lanes 2r and 2r + 1 hold row r of the chunk); the column
-// products B_IJ^H x_I stay in registers for the whole tile.  The partial sums
-// use the buffer layout of k_hgemv_tiles.
+// Variant for up to four right-hand sides: two warps per stored tile, each
+// streaming two chunks of 16 rows straight from global memory, lane l holding
+// columns 2l and 2l + 1 of every row (one 16-byte load per row).  The row
+// products B_IJ x_J are summed across the warp by a transposing butterfly
+// (after it, lanes 2r and 2r + 1 hold row r of the chunk); the column
+// products B_IJ^H x_I stay in registers and the two warps' sums are added
+// through shared memory.  The partial sums use the buffer layout of
+// k_hgemv_tiles.
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
@@ -1300,13 +1359,13 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 }
 
 template <int NR>
-__global__ void __launch_bounds__(128) k_hgemv_warp(const float2* __restrict__ P,
-                                                    const double2* __restrict__ x, int N,
-                                                    int ntiles, int nrhs,
-                                                    float2* __restrict__ part) {
-  const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (k >= ntiles) return;                               // whole warp
+__global__ void __launch_bounds__(64) k_hgemv_warp(const float2* __restrict__ P,
+                                                   const double2* __restrict__ x, int N,
+                                                   int ntiles, int nrhs,
+                                                   float2* __restrict__ part) {
+  __shared__ float4 colsum[NR][32];                      // column partials of warp 1
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x;                              // one tile, rows split by warp
   int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
   while ((I + 1) * (I + 2) / 2 <= k) ++I;
   while (I * (I + 1) / 2 > k) --I;
@@ -1326,8 +1385,9 @@ __global__ void __launch_bounds__(128) k_hgemv_warp(const float2* __restrict__ P
         if (ri + 32 < N) xi1[q] = make_float2((float)xr[ri + 32].x, (float)xr[ri + 32].y);
       }
     }
-#pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
+#pragma unroll(NR == 1 ? 2 : 1)
+    for (int cc = 0; cc < 2; ++cc) {
+      const int ch = 2 * w + cc;                         // rows 16 ch .. 16 ch + 15
       float4 t[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) t[i] = __ldg(src + (ch * 16 + i) * (HT / 2));
@@ -1340,7 +1400,7 @@ __global__ void __launch_bounds__(128) k_hgemv_warp(const float2* __restrict__ P
           p[i] = make_float2(0.f, 0.f);
           cfma(p[i], a, xj0[q]);
           cfma(p[i], b, xj1[q]);
-          const float2 xr = shfl2(ch < 2 ? xi0[q] : xi1[q], (ch * 16 + i) & 31);
+          const float2 xr = shfl2(w == 0 ? xi0[q] : xi1[q], (ch * 16 + i) & 31);
           cfmac(ac0[q], a, xr);
           cfmac(ac1[q], b, xr);
         }
@@ -1364,12 +1424,22 @@ __global__ void __launch_bounds__(128) k_hgemv_warp(const float2* __restrict__ P
           part[(long long)(q0 + q) * ntiles * 2 * HT + 2LL * k * HT + ch * 16 + (lane >> 1)] = v;
       }
     }
-    if (I != J) {
+    if (I != J) {                                        // column partials: warp 0 + warp 1
+      if (w == 1) {
 #pragma unroll
-      for (int q = 0; q < NR; ++q)
-        if (q0 + q < nrhs)
-          *(float4*)(part + (long long)(q0 + q) * ntiles * 2 * HT + (2LL * k + 1) * HT + 2 * lane) =
-              make_float4(ac0[q].x, ac0[q].y, ac1[q].x, ac1[q].y);
+        for (int q = 0; q < NR; ++q) colsum[q][lane] = make_float4(ac0[q].x, ac0[q].y, ac1[q].x, ac1[q].y);
+      }
+      __syncthreads();
+      if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const float4 o = colsum[q][lane];
+          if (q0 + q < nrhs)
+            *(float4*)(part + (long long)(q0 + q) * ntiles * 2 * HT + (2LL * k + 1) * HT + 2 * lane) =
+                make_float4(ac0[q].x + o.x, ac0[q].y + o.y, ac1[q].x + o.z, ac1[q].y + o.w);
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -1402,30 +1472,44 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
   }
 }
 
-cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
-                               void* part, bool accumulate, cudaStream_t s) {
+cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
+                                 void* part, cudaStream_t s) {
   if (ld % HT || ld < N) return cudaErrorInvalidValue;
   const int nt = ld / HT, ntiles = nt * (nt + 1) / 2;
   if (nrhs <= 4) {                               // streamed from global, one warp per tile
-    const dim3 grid((ntiles + 3) / 4);
+    const dim3 grid(ntiles);
     if (nrhs == 1)
-      k_hgemv_warp<1><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+      k_hgemv_warp<1><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
                                            (float2*)part);
     else if (nrhs == 2)
-      k_hgemv_warp<2><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+      k_hgemv_warp<2><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
                                            (float2*)part);
     else
-      k_hgemv_warp<4><<<grid, 128, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
+      k_hgemv_warp<4><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
                                            (float2*)part);
   } else {
     k_hgemv_tiles<<<ntiles, 256, 0, s>>>((const float2*)P, (const double2*)x, N, nrhs,
                                          (float2*)part);
   }
   count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
+                                  bool accumulate, cudaStream_t s) {
+  if (ld % HT || ld < N) return cudaErrorInvalidValue;
+  const int nt = ld / HT;
   k_hgemv_reduce<<<dim3(nt, nrhs), 256, 0, s>>>((const float2*)part, (double2*)y, N, nt,
                                                 accumulate);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
+                               void* part, bool accumulate, cudaStream_t s) {
+  cudaError_t e = hermitian_gemv_tiles(P, x, N, ld, nrhs, part, s);
+  if (e != cudaSuccess) return e;
+  return hermitian_gemv_reduce(part, y, N, ld, nrhs, accumulate, s);
 }
 
 __global__ void k_block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset) {

@@ -387,6 +387,8 @@ bool wilson_A_streamed(int Lx, int Lt) {
   return Lx >= 64 && Lt >= 2 * SROWS && warps >= 4LL * 152;
 }
 
+// Tile choice of the fused kernel: 32 x 8 (FP64) or 32 x 16 (FP32) when that
+// gives two CTAs per SM, else 16 x 8 (smaller tiles measured slower: more halo).
 int wilson_A_ctas(int Lx, int Lt, bool f64) {
   const int big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16));
   if (big >= 2 * 152) return big;

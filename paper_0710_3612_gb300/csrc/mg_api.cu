@@ -175,7 +175,8 @@ template <typename R>
 void apply_level(mg_handle* h, int l, const void* in, void* out, int nrhs, int weights,
                  const Epilogue& ep = Epilogue()) {
   Level& L = h->lv[l];
-  ProfScope prof(h, l == 0 ? (sizeof(R) == 8 ? MG_KF_FINE_A64 : MG_KF_FINE_A) : MG_KF_COARSE);
+  ProfScope prof(h, l == 0 ? (sizeof(R) == 8 ? MG_KF_FINE_A64 : MG_KF_FINE_A)
+                          : (weights == W_F64 ? MG_KF_COARSE64 : MG_KF_COARSE));
   if (l == 0) {
     const double diag = 4.0 + h->mass;
     const void* U = sizeof(R) == 8 ? (const void*)h->U64 : (const void*)h->U32;
@@ -202,16 +203,19 @@ Epilogue ep_lincomb(double ca, const void* U, double cu, const void* W = nullptr
 // nrhs vectors [nrhs][N].
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs) {
   ProfScope prof(h, MG_KF_COARSEST);
-  {
-    ProfScope pd(h, MG_KF_DENSE);
-    ck(h, hermitian_gemv_f32(h->Bpk, b, x, h->Nc, h->ldc, nrhs, h->gemv_part, false, h->s),
-       "coarsest gemv");
-  }
+  auto gemv = [&](const double2* in, bool accumulate) {
+    {
+      ProfScope pd(h, MG_KF_DENSE);
+      ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s),
+         "coarsest gemv");
+    }
+    ck(h, hermitian_gemv_reduce(h->gemv_part, x, h->Nc, h->ldc, nrhs, accumulate, h->s),
+       "coarsest gemv reduce");
+  };
+  gemv(b, false);
   for (int it = 0; it < steps; ++it) {
     apply_level<double>(h, h->L - 1, x, h->cr, nrhs, W_F64, ep_lincomb(-1.0, b, 1.0));
-    ProfScope pd(h, MG_KF_DENSE);
-    ck(h, hermitian_gemv_f32(h->Bpk, h->cr, x, h->Nc, h->ldc, nrhs, h->gemv_part, true, h->s),
-       "coarsest gemv");
+    gemv(h->cr, true);
   }
 }
 
@@ -320,7 +324,12 @@ void build_coarsest(mg_handle* h) {
   ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
   {
     ProfScope prof(h, MG_KF_INVERSE);
-    ck(h, gauss_jordan_inverse_f32(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+    ck(h, gauss_jordan_begin(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
+    for (int k = 0; k < h->ldc / 64; ++k) {
+      ck(h, gauss_jordan_panel(h->Binv, h->ldc, k, h->gj_work, h->s), "gauss-jordan panel");
+      ProfScope pu(h, MG_KF_GJ_UPDATE);
+      ck(h, gauss_jordan_update(h->Binv, h->ldc, k, h->gj_work, h->s), "gauss-jordan update");
+    }
     ck(h, pack_hermitian(h->Binv, h->Bpk, h->ldc, h->s), "pack");
   }
   // Refinement count: smallest number of FP64 correction steps that brings a
@@ -725,6 +734,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->inner_coarsest_refine = 1;
   p->vcycle_coarse_bf16 = 1;
   p->max_rhs = 1;
+  p->profile = 0;
   return MG_OK;
 }
 
@@ -755,6 +765,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
   h->s = (cudaStream_t)stream;
   h->L = params->nlevels;
   h->R = params->max_rhs;
+  h->prof_on = params->profile != 0;
   mg_status st = guarded(h, [&]() {
     const mg_params& P = h->p;
     // geometry

@@ -34,7 +34,7 @@ class MgParams(ctypes.Structure):
                 ("omega_mr", ctypes.c_double), ("setup_noise", ctypes.c_void_p),
                 ("coarsest_tol", ctypes.c_double), ("coarsest_refine_max", ctypes.c_int),
                 ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int),
-                ("max_rhs", ctypes.c_int)]
+                ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):
@@ -219,7 +219,9 @@ def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
                               _stream_ptr(stream)))
 
 
-KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64, KF_DENSE = range(8)
+KF_FINE_A, KF_COARSE, KF_TRANSFER, KF_COARSEST, KF_INVERSE, KF_GALERKIN, KF_FINE_A64, KF_DENSE, \
+    KF_GJ_UPDATE, KF_COARSE64 = range(10)
+KF_COUNT = 10
 
 
 def mg_apply_A_dot_noalloc(h, inp, out, xAx):
