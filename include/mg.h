@@ -101,6 +101,11 @@ typedef struct {
   int profile;                          /* nonzero: per-kernel-family event
                                            timing (mg_profile_enable) from the
                                            start of mg_setup (0)                 */
+  int coarsest_dense_max;               /* coarsest levels with at most this
+                                           many unknowns use the dense FP32
+                                           inverse with FP64 refinement; larger
+                                           ones FP64 CG on the coarsest stencil
+                                           (16384, the largest dense size)      */
 } mg_params;
 
 typedef struct {
@@ -178,7 +183,10 @@ mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_
 mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision);
 
 /* Coarsest-level solve A_L x = b (FP64, complex128 level-L vectors): FP32
- * explicit inverse refined in FP64 to coarsest_tol. */
+ * explicit inverse refined in FP64 to coarsest_tol, or, when the level has
+ * more than coarsest_dense_max unknowns, FP64 CG on the coarsest stencil for
+ * the iteration count fixed at set-up (the count at which a test vector
+ * reaches coarsest_tol, times 1.25 plus 4). */
 mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out);
 
 /* Level geometry: extents and dof per site; Nv of the blocking below it

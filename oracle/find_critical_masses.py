@@ -29,6 +29,7 @@ CONFIGS = {
     "L128_b6_s1": (128, 6.0, 200, 1),
     "L128_b6_s2": (128, 6.0, 200, 2),
     "L256_b10_s1": (256, 10.0, 500, 1),
+    "L1024_b10_s1": (1024, 10.0, 500, 1),
 }
 
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mg.h"
@@ -58,6 +59,9 @@ struct mg_handle {
   float2* gemv_part = nullptr;  // partial products of the packed GEMV
   int n_refine = 0;
   double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
+  bool dense = true;            // dense inverse (else CG on the coarsest stencil)
+  int ccg_iters = 0;            // CG iterations of one coarsest solve (fixed at set-up)
+  double2 *cp = nullptr, *cq = nullptr;                  // coarsest CG vectors
   // CUDA graphs of the Krylov loop (one per preconditioner mode), launched on
   // the internal stream gs and fenced to the user's stream with events
   cudaStream_t gs = nullptr;
@@ -96,7 +100,7 @@ constexpr long long MG_DENSE_MAX = 16384;
 
 // scalar slots (each a double2)
 // scalar slots: slot k holds one double2 per right-hand side
-enum { S_RZ = 0, S_RZN, S_PQ, S_RR, S_T0, S_T1, S_BN, S_NR, S_STOP, S_COUNT };
+enum { S_RZ = 0, S_RZN, S_PQ, S_RR, S_T0, S_T1, S_BN, S_NR, S_STOP, S_CA, S_CB, S_CPQ, S_COUNT };
 
 struct Fail {
   mg_status st;
@@ -198,11 +202,38 @@ Epilogue ep_lincomb(double ca, const void* U, double cu, const void* W = nullptr
   return e;
 }
 
-// ----- coarsest solve: FP32 explicit inverse refined in FP64 ----------------
-// x = B b; then `steps` times: r = b - A_L x (FP64 stencil), x += B r; for
-// nrhs vectors [nrhs][N].
+// ----- coarsest solve ---------------------------------------------------------
+// Coarsest levels above coarsest_dense_max unknowns: CG on the coarsest
+// stencil in FP64, x0 = 0, a fixed number `iters` of iterations (chosen at
+// set-up so that a test vector reaches coarsest_tol), so that the whole solve
+// can be captured in a graph.  The two r.r slots alternate between iterations.
+void coarsest_cg(mg_handle* h, const double2* b, double2* x, int iters, int nrhs) {
+  const long long n = h->Nc;
+  double* rz = slot(h, S_CA);
+  double* rn = slot(h, S_CB);
+  ck(h, cudaMemsetAsync(x, 0, n * nrhs * sizeof(double2), h->s), "memset");
+  ck(h, cudaMemcpyAsync(h->cr, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, cudaMemcpyAsync(h->cp, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, norm2<double>(h->cr, n, nrhs, h->partials, rz, h->s), "norm");
+  for (int it = 0; it < iters; ++it) {
+    apply_level<double>(h, h->L - 1, h->cp, h->cq, nrhs, W_F64);
+    ck(h, dot<double>(h->cp, h->cq, n, nrhs, h->partials, slot(h, S_CPQ), h->s), "dot");
+    ck(h, cg_xr<double>(x, h->cr, h->cp, h->cq, rz, slot(h, S_CPQ), nullptr, n, nrhs,
+                        h->partials, rn, h->s), "cg update");
+    if (it + 1 < iters)
+      ck(h, cg_p<double>(h->cp, h->cr, rn, rz, nullptr, n, nrhs, h->s), "cg direction");
+    std::swap(rz, rn);
+  }
+}
+
+// Dense path: FP32 explicit inverse refined in FP64.  x = B b; then `steps`
+// times: r = b - A_L x (FP64 stencil), x += B r; for nrhs vectors [nrhs][N].
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs) {
   ProfScope prof(h, MG_KF_COARSEST);
+  if (!h->dense) {
+    coarsest_cg(h, b, x, h->ccg_iters, nrhs);
+    return;
+  }
   auto gemv = [&](const double2* in, bool accumulate) {
     {
       ProfScope pd(h, MG_KF_DENSE);
@@ -319,7 +350,48 @@ void build_coarse_ops(mg_handle* h) {
   }
 }
 
+// Iterations of the coarsest CG: the first count at which the test vector
+// (all ones) reaches coarsest_tol, times 1.25 plus 4 for other right-hand
+// sides; at most coarsest_cg_max.
+constexpr int COARSEST_CG_MAX = 5000;
+
+void build_coarsest_cg(mg_handle* h) {
+  const long long n = h->Nc;
+  std::vector<double2> ones(n, make_double2(1.0, 0.0));
+  ck(h, cudaMemcpyAsync(h->cb, ones.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, h->s),
+     "upload");
+  ck(h, norm2<double>(h->cb, n, 1, h->partials, slot(h, S_T1), h->s), "norm");
+  const double bn = read_scalar(h, S_T1);
+  const double stop = h->p.coarsest_tol * h->p.coarsest_tol * bn;
+  double* rz = slot(h, S_CA);
+  double* rn = slot(h, S_CB);
+  ck(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double2), h->s), "memset");
+  ck(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, cudaMemcpyAsync(h->cp, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+  ck(h, norm2<double>(h->cr, n, 1, h->partials, rz, h->s), "norm");
+  int it = 0;
+  for (; it < COARSEST_CG_MAX; ++it) {
+    apply_level<double>(h, h->L - 1, h->cp, h->cq, 1, W_F64);
+    ck(h, dot<double>(h->cp, h->cq, n, 1, h->partials, slot(h, S_CPQ), h->s), "dot");
+    ck(h, cg_xr<double>(h->cx, h->cr, h->cp, h->cq, rz, slot(h, S_CPQ), nullptr, n, 1,
+                        h->partials, rn, h->s), "cg update");
+    ck(h, cg_p<double>(h->cp, h->cr, rn, rz, nullptr, n, 1, h->s), "cg direction");
+    std::swap(rz, rn);
+    double rr = 0.0;
+    ck(h, cudaMemcpyAsync(&rr, rz, sizeof(double), cudaMemcpyDeviceToHost, h->s), "read");
+    sync(h);
+    if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest CG is not finite");
+    if (rr <= stop) break;
+  }
+  if (it == COARSEST_CG_MAX) fail(h, MG_ERR_NOCONV, "coarsest CG did not reach coarsest_tol");
+  h->ccg_iters = std::min(COARSEST_CG_MAX, (it + 1) + (it + 1) / 4 + 4);
+}
+
 void build_coarsest(mg_handle* h) {
+  if (!h->dense) {
+    build_coarsest_cg(h);
+    return;
+  }
   Level& L = h->lv[h->L - 1];
   ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
   {
@@ -389,8 +461,8 @@ mg_status validate(const mg_params* p, std::string& msg) {
   if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
   if (p->max_rhs < 1 || p->max_rhs > 64) { msg = "max_rhs must be in [1, 64]"; return MG_ERR_ARG; }
   if (p->nlevels > 1 && !p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
-  if (p->nlevels > 1 && (long long)lx * lt * n > MG_DENSE_MAX) {
-    msg = "coarsest level has more than " + std::to_string(MG_DENSE_MAX) + " unknowns";
+  if (p->coarsest_dense_max < 0 || p->coarsest_dense_max > MG_DENSE_MAX) {
+    msg = "coarsest_dense_max must be in [0, " + std::to_string(MG_DENSE_MAX) + "]";
     return MG_ERR_ARG;
   }
   return MG_OK;
@@ -735,6 +807,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->vcycle_coarse_bf16 = 1;
   p->max_rhs = 1;
   p->profile = 0;
+  p->coarsest_dense_max = (int)MG_DENSE_MAX;
   return MG_OK;
 }
 
@@ -835,12 +908,18 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       const Level& C = h->lv[h->L - 1];
       h->Nc = (int)C.count();
       h->ldc = (h->Nc + 63) / 64 * 64;
-      h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
-      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
-      h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
-      const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
-      h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
-      h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
+      h->dense = h->Nc <= P.coarsest_dense_max;
+      if (h->dense) {
+        h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
+        h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
+        h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
+        const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
+        h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
+        h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
+      } else {
+        h->cp = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+        h->cq = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+      }
       h->cb = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
       h->cx = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
       h->cr = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
