@@ -304,7 +304,9 @@ FAM_NAMES = ["fine_A_f32", "coarse_apply_f32_bf16", "transfer", "coarsest_solve"
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel source (summaries and commands under profiles/); a kernel changed
 # since its capture has no entry.
-NCU_TRAFFIC = {"gj_update": 71368192 + 13786368}
+NCU_TRAFFIC = {"gj_update": 71368192 + 13786368,           # profiles/gj_update_L128.md
+               "coarsest_gemv_tiles": 68242688 + 337664,  # profiles/hgemv_warp_L128.md
+               "coarse_apply_bf16": 9581824 + 0}          # profiles/coarse_bf16_L128.md
 
 
 def roofline(prof, wl, peaks):
