@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import critical
 from oracle import krylov as okr
 from oracle import multigrid as omg
 from oracle import wilson as ow
@@ -93,3 +94,52 @@ def test_cfg_256x256_batched_64_rhs_near_critical(mg):
         assert res <= TOL, f"rhs {k}: true residual {res:.3e}"
         assert infos[k].true_residual <= TOL
         assert abs(infos[k].true_residual - res) <= 1e-3 * TOL
+
+
+def test_cfg_128x128_mass_sweep(mg):
+    """The benchmark workload: set-up at the near-critical mass, re-mass to
+    m = 0.1.  At 0.1 both solvers are compared with the oracle's solve of the
+    same hierarchy; at m_nc (814 oracle iterations, too slow to repeat here)
+    the FP64 iteration count is compared with the oracle's stored count and
+    every solution's true residual is recomputed by the oracle."""
+    wl = W.BENCH_WORKLOADS["L128_b6_massweep"]
+    crit = json.load(open(os.path.join(ROOT, "workloads", "critical_masses.json")))[wl["critical_key"]]
+    stored = json.load(open(os.path.join(ROOT, "workloads", "oracle_iterations.json")))
+    stored = stored["L128_b6_massweep"]["masses"]
+    L, blocks, Nv = wl["Lx"], wl["blocks"], wl["Nv"]
+    th = W.quenched_u1_angles(L, L, wl["beta"], wl["sweeps"], wl["seed"])
+    assert W.mean_plaquette(th) == pytest.approx(crit["plaquette"], abs=1e-12)
+    U = W.links_from_angles(th)
+    noise = W.setup_noise(L, L, blocks, Nv, wl["noise_seed"])
+    chi = W.gaussian_field((L, L, 2), wl["chi_seed"])
+    m_nc = crit["m_nc"]
+    with mg.Multigrid(dev(U), m_nc, blocks, Nv, dev(noise), setup_sweeps=wl["setup_sweeps"]) as s:
+        b = ow.apply_D(U, m_nc, chi, dagger=True)
+        for solver in (mg.SOLVER_MGCG_FP64, mg.SOLVER_MGCG_MIXED):
+            x, infos = s.solve(dev(b), tol=TOL, maxiter=20000, solver=solver)
+            got = host(x).reshape(b.shape)
+            res = np.linalg.norm(b - ow.apply_A(U, m_nc, got)) / np.linalg.norm(b)
+            assert res <= TOL and infos[0].true_residual <= TOL
+            if solver == mg.SOLVER_MGCG_FP64:
+                assert abs(infos[0].iterations - stored[repr(m_nc)]["iterations"]) <= 1
+        m = 0.1
+        s.set_mass(m)
+        H = omg.setup(U, m_nc, blocks, Nv, noise, sweeps=wl["setup_sweeps"])
+        H = omg.set_mass(H, m)
+        b = ow.apply_D(U, m, chi, dagger=True)
+        _, it10, _ = okr.mgcg(H, b, TOL)
+        assert it10 == stored[repr(m)]["iterations"]
+        x_ora, _, _ = okr.mgcg(H, b, 1e-13)
+        # kappa(A) bound: lambda_max(A) = |D|^2 <= (|4 + m| + 4)^2 (each of the four
+        # hop terms has norm <= 1); lambda_min(A) = sigma_min(D)^2 = (eigenvalue of
+        # the Hermitian sigma_3 D nearest zero)^2
+        lam_h, _ = critical.nearest_eig_H(U, m)
+        kappa = (abs(4.0 + m) + 4.0) ** 2 / lam_h ** 2
+        for solver in (mg.SOLVER_MGCG_FP64, mg.SOLVER_MGCG_MIXED):
+            x, infos = s.solve(dev(b), tol=TOL, maxiter=1000, solver=solver)
+            got = host(x).reshape(b.shape)
+            res = np.linalg.norm(b - ow.apply_A(U, m, got)) / np.linalg.norm(b)
+            assert res <= TOL and infos[0].true_residual <= TOL
+            assert np.linalg.norm(got - x_ora) <= (kappa * TOL + 1e-12) * np.linalg.norm(x_ora)
+            if solver == mg.SOLVER_MGCG_FP64:
+                assert abs(infos[0].iterations - it10) <= 1
