@@ -56,6 +56,24 @@ def load_peaks():
             "src": "fallback", "sm_max_mhz": 2070.0}
 
 
+def max_over_ranks(x, device=None):
+    """The largest value of x over the ranks of the job (the slowest rank's
+    time); x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, slowest_seconds):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return units_per_rank * world / slowest_seconds
+
+
 def workload_inputs(name):
     wl = W.BENCH_WORKLOADS[name]
     crit = json.load(open(os.path.join(ROOT, "workloads", "critical_masses.json")))[wl["critical_key"]]
@@ -204,10 +222,7 @@ def gpu_bench(args):
         ck = clocks.stop() if clocks else None
         step_ms = [a.elapsed_time(b) for a, b in steps]
         total = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(total, dev)
         solve_ms = [a.elapsed_time(b) for _, a, b, _ in recs]
         per_mass = {}
         for (m, a, b, info), t in zip(recs, solve_ms):
@@ -228,8 +243,7 @@ def gpu_bench(args):
     phases = [] if args.phase_launches else None
     base = mg.mg_kernel_launches()
     res = timed(mg.SOLVER_MGCG_MIXED, args.steps, clocks, phases)
-    solves = len(masses) * args.steps * world
-    value = solves / (res["total_ms"] / 1000.0)
+    value = job_rate(len(masses) * args.steps, world, res["total_ms"] / 1000.0)
 
     if args.timed_only:
         if rank == 0:
@@ -244,7 +258,7 @@ def gpu_bench(args):
     kp = max(1, min(args.steps, args.plain_steps))
     step(mg.SOLVER_MGCG_FP64)
     plain = timed(mg.SOLVER_MGCG_FP64, kp)
-    plain_value = len(masses) * kp * world / (plain["total_ms"] / 1000.0)
+    plain_value = job_rate(len(masses) * kp, world, plain["total_ms"] / 1000.0)
 
     # batched mixed-precision MG-CG: many right-hand sides of the same
     # configuration at the near-critical mass in one Krylov loop
@@ -431,8 +445,8 @@ def batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
             if st != 0 or max(i.true_residual for i in info) > tol:
                 raise RuntimeError("batched solve did not converge")
             reps.append(e0.elapsed_time(e1))
-        ms = statistics.median(reps)
-        out.update({"value": round(world * nrhs / (ms / 1000.0), 3), "unit": UNIT,
+        ms = max_over_ranks(statistics.median(reps), dev)
+        out.update({"value": round(job_rate(nrhs, world, ms / 1000.0), 3), "unit": UNIT,
                     "ms_per_batch": round(ms, 3),
                     "iterations_max": max(i.iterations for i in info),
                     "max_true_residual": max(i.true_residual for i in info)})
@@ -481,8 +495,8 @@ def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, wor
                 if not info[0].true_residual <= wl["tol"]:
                     raise RuntimeError("e2e solve did not converge")
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    return {"value": round(len(masses) * K * world / dt, 3), "unit": UNIT, "steps": K,
+    dt = max_over_ranks(time.perf_counter() - t0, dev)
+    return {"value": round(job_rate(len(masses) * K, world, dt), 3), "unit": UNIT, "steps": K,
             "h2d_bytes_per_step": int(Uh.nbytes + nh.nbytes + ch.nbytes),
             "d2h_bytes_per_step": int(len(masses) * xh.nbytes)}
 
