@@ -135,8 +135,8 @@ size_t mg_setup_noise_len(const mg_params* p);
  * stream: cudaStream_t to use (NULL: the legacy default stream).
  * Validation: Lx, Lt even; each extent divisible by its block; every coarse
  *   extent >= 2; blocks >= 2 x 2; 1 <= Nv_l <= (bx * bt * n_l / 2);
- *   1 <= nlevels <= MG_MAX_LEVELS; the coarsest level has at most 16384
- *   unknowns (dense inverse).  MG_ERR_ARG otherwise.  With nlevels = 1 no
+ *   1 <= nlevels <= MG_MAX_LEVELS; 0 <= coarsest_dense_max <= 16384.
+ *   MG_ERR_ARG otherwise.  With nlevels = 1 no
  *   hierarchy is built and setup_noise may be NULL.
  * On success *out owns all device memory of the hierarchy. */
 mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void* stream,
@@ -145,6 +145,15 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
 /* Reuse the setup's vectors at another mass (Sec. 4): rebuilds every
  * Galerkin operator, the smoothers and the coarsest inverse. */
 mg_status mg_set_mass(mg_handle* h, double mass);
+
+/* Device memory of a set-up, before making it (no device work): *resident =
+ * the bytes mg_setup allocates and keeps (equal to mg_device_bytes of the
+ * handle it returns), *peak = resident + the set-up's temporary relaxation
+ * vectors.  Either pointer may be NULL.  MG_ERR_ARG for invalid params. */
+mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long* peak);
+
+/* Device bytes currently owned by the handle. */
+mg_status mg_device_bytes(const mg_handle* h, long long* bytes);
 
 /* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
  * b, x: device complex128 [nrhs][Lt][Lx][2].  Right-hand sides are solved in

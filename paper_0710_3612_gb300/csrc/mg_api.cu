@@ -85,6 +85,9 @@ struct mg_handle {
   double* hscal = nullptr;      // pinned host mirror
   int* dflag = nullptr;
   std::vector<void*> allocs;
+  long long bytes = 0;          // device bytes currently allocated by the handle
+  long long peak_bytes = 0;     // largest value of `bytes` so far
+  bool dry = false;             // size-only pass: dalloc counts bytes, allocates nothing
   std::string err;
   long long fine_applies = 0, vcycles = 0;
   // optional per-family event timing
@@ -120,9 +123,13 @@ template <typename T = void>
 T* dalloc(mg_handle* h, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
+  h->bytes += (long long)bytes;
+  h->peak_bytes = std::max(h->peak_bytes, h->bytes);
+  if (h->dry) return (T*)(uintptr_t)256;        // never dereferenced in a size-only pass
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    h->bytes -= (long long)bytes;
     fail(h, MG_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
   h->allocs.push_back(p);
@@ -145,7 +152,7 @@ double read_scalar(mg_handle* h, int k) {
 void ensure_partials(mg_handle* h, int nrhs) {
   if (h->partial_rhs >= nrhs) return;
   h->partials = dalloc<double>(h, sizeof(double) * (64 + 2 * 608 * (size_t)nrhs));
-  ck(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 64, h->s), "memset tickets");
+  if (!h->dry) ck(h, cudaMemsetAsync(h->partials, 0, sizeof(double) * 64, h->s), "memset tickets");
   h->partial_rhs = nrhs;
 }
 
@@ -783,6 +790,95 @@ mg_status solve_batch(mg_handle* h, const void* b, void* x, int nrhs, double tol
   return st;
 }
 
+// Level geometry from the parameters (no device work).
+void set_geometry(mg_handle* h) {
+  const mg_params& P = h->p;
+    h->lv.resize(h->L);
+    int lx = P.Lx, lt = P.Lt, n = 2;
+    for (int l = 0; l < h->L; ++l) {
+      Level& L = h->lv[l];
+      L.Lx = lx; L.Lt = lt; L.V = lx * lt; L.n = n;
+      if (l + 1 < h->L) {
+        L.bx = P.block[l][0]; L.bt = P.block[l][1]; L.Nv = P.Nv[l];
+        lx /= L.bx; lt /= L.bt; n = 2 * L.Nv;
+      }
+    }
+}
+
+// Every device allocation that outlives mg_setup, in one place, so that a
+// size-only pass (h->dry) gives the handle's device footprint exactly.
+void allocate_storage(mg_handle* h) {
+  const mg_params& P = h->p;
+  h->scal = dalloc<double>(h, (size_t)S_COUNT * 2 * h->R * sizeof(double));
+  h->dflag = dalloc<int>(h, sizeof(int));
+  h->dctrl = dalloc<int>(h, (4 + 2 * h->R) * sizeof(int));
+  int max_nv = h->R;
+  for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
+  ensure_partials(h, max_nv);
+  const long long V = h->lv[0].V;
+  h->U64 = dalloc<double2>(h, 2 * V * sizeof(double2));
+  h->U32 = dalloc<float2>(h, 2 * V * sizeof(float2));
+  // per-level storage
+  for (int l = 0; l < h->L; ++l) {
+    Level& L = h->lv[l];
+    const size_t c = (size_t)L.count();
+    for (int k = 0; k < 4; ++k) {
+      L.w64[k] = dalloc(h, c * h->R * sizeof(double2));
+      L.w32[k] = dalloc(h, c * h->R * sizeof(float2));
+    }
+    if (l > 0) {
+      const size_t ab = (size_t)L.V * 9 * L.n * L.n;
+      L.A64 = dalloc<double2>(h, ab * sizeof(double2));
+      L.A32 = dalloc<float2>(h, ab * sizeof(float2));
+      L.A16 = dalloc(h, ab * 4);
+    }
+    if (l + 1 < h->L) {
+      L.Vst64 = dalloc<double2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(double2));
+      L.Vst32 = dalloc<float2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(float2));
+      L.eta = dalloc<double2>(h, c * sizeof(double2));
+    }
+  }
+  for (int k = 0; k < 6; ++k) {
+    h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(double2));
+    h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(float2));
+  }
+  if (h->L > 1) {
+    const Level& L0 = h->lv[0];
+    const size_t Vc = (size_t)(L0.Lx / L0.bx) * (L0.Lt / L0.bt);
+    h->Wbuf = dalloc(h, Vc * 2 * L0.Nv * (L0.bx + 2) * (L0.bt + 2) * 2 * sizeof(double2));
+  }
+  // coarsest dense storage
+  if (h->L > 1) {
+    const Level& C = h->lv[h->L - 1];
+    h->Nc = (int)C.count();
+    h->ldc = (h->Nc + 63) / 64 * 64;
+    h->dense = h->Nc <= P.coarsest_dense_max;
+    if (h->dense) {
+      h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
+      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
+      h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
+      const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
+      h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
+      h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
+    } else {
+      h->cp = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+      h->cq = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+    }
+    h->cb = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+    h->cx = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+    h->cr = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
+  }
+}
+
+// Device bytes of the set-up's temporary relaxation vectors (E and T of the
+// largest level), allocated and freed inside mg_setup.
+long long setup_temp_bytes(const mg_handle* h) {
+  long long t = 0;
+  for (int l = 0; l + 1 < h->L; ++l)
+    t = std::max(t, 2LL * h->lv[l].Nv * h->lv[l].count() * (long long)sizeof(double2));
+  return t;
+}
+
 }  // namespace
 
 // =============================================================================
@@ -841,89 +937,22 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
   h->prof_on = params->profile != 0;
   mg_status st = guarded(h, [&]() {
     const mg_params& P = h->p;
-    // geometry
-    h->lv.resize(h->L);
-    int lx = P.Lx, lt = P.Lt, n = 2;
-    for (int l = 0; l < h->L; ++l) {
-      Level& L = h->lv[l];
-      L.Lx = lx; L.Lt = lt; L.V = lx * lt; L.n = n;
-      if (l + 1 < h->L) {
-        L.bx = P.block[l][0]; L.bt = P.block[l][1]; L.Nv = P.Nv[l];
-        lx /= L.bx; lt /= L.bt; n = 2 * L.Nv;
-      }
-    }
+    set_geometry(h);
     ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
-    h->scal = dalloc<double>(h, (size_t)S_COUNT * 2 * h->R * sizeof(double));
-    h->dflag = dalloc<int>(h, sizeof(int));
-    h->dctrl = dalloc<int>(h, (4 + 2 * h->R) * sizeof(int));
     ck(h, cudaMallocHost((void**)&h->hctrl, (4 + 2 * h->R) * sizeof(int)), "pinned alloc");
     ck(h, cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream create");
     ck(h, cudaEventCreateWithFlags(&h->fence[0], cudaEventDisableTiming), "event create");
     ck(h, cudaEventCreateWithFlags(&h->fence[1], cudaEventDisableTiming), "event create");
     if (const char* e = std::getenv("MG_NO_GRAPHS")) h->use_graphs = e[0] == '0';
-    int max_nv = h->R;
-    for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
-    ensure_partials(h, max_nv);
+    allocate_storage(h);
     // links
     const long long V = h->lv[0].V;
-    h->U64 = dalloc<double2>(h, 2 * V * sizeof(double2));
-    h->U32 = dalloc<float2>(h, 2 * V * sizeof(float2));
     ck(h, link_unitarity(gauge, 2 * V, slot(h, S_T0), h->s), "unitarity");
     const double dev = read_scalar(h, S_T0);
     if (!(dev <= 1e-12)) fail(h, MG_ERR_ARG, "gauge links are not unit modulus (|U|-1 = " + std::to_string(dev) + ")");
     ck(h, fold_links<double>(gauge, h->U64, P.Lx, P.Lt, h->s), "fold");
     ck(h, fold_links<float>(gauge, h->U32, P.Lx, P.Lt, h->s), "fold");
     h->mass = mass;
-    // per-level storage
-    for (int l = 0; l < h->L; ++l) {
-      Level& L = h->lv[l];
-      const size_t c = (size_t)L.count();
-      for (int k = 0; k < 4; ++k) {
-        L.w64[k] = dalloc(h, c * h->R * sizeof(double2));
-        L.w32[k] = dalloc(h, c * h->R * sizeof(float2));
-      }
-      if (l > 0) {
-        const size_t ab = (size_t)L.V * 9 * L.n * L.n;
-        L.A64 = dalloc<double2>(h, ab * sizeof(double2));
-        L.A32 = dalloc<float2>(h, ab * sizeof(float2));
-        L.A16 = dalloc(h, ab * 4);
-      }
-      if (l + 1 < h->L) {
-        L.Vst64 = dalloc<double2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(double2));
-        L.Vst32 = dalloc<float2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(float2));
-        L.eta = dalloc<double2>(h, c * sizeof(double2));
-      }
-    }
-    for (int k = 0; k < 6; ++k) {
-      h->sv64[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(double2));
-      h->sv32[k] = dalloc(h, (size_t)h->lv[0].count() * h->R * sizeof(float2));
-    }
-    if (h->L > 1) {
-      const Level& L0 = h->lv[0];
-      const size_t Vc = (size_t)(L0.Lx / L0.bx) * (L0.Lt / L0.bt);
-      h->Wbuf = dalloc(h, Vc * 2 * L0.Nv * (L0.bx + 2) * (L0.bt + 2) * 2 * sizeof(double2));
-    }
-    // coarsest dense storage
-    if (h->L > 1) {
-      const Level& C = h->lv[h->L - 1];
-      h->Nc = (int)C.count();
-      h->ldc = (h->Nc + 63) / 64 * 64;
-      h->dense = h->Nc <= P.coarsest_dense_max;
-      if (h->dense) {
-        h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
-        h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
-        h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
-        const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
-        h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
-        h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
-      } else {
-        h->cp = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
-        h->cq = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
-      }
-      h->cb = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
-      h->cx = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
-      h->cr = dalloc<double2>(h, (size_t)h->Nc * h->R * sizeof(double2));
-    }
     // adaptive setup, level by level (Sec. 3)
     const double2* noise = (const double2*)P.setup_noise;
     size_t pos = 0;
@@ -968,6 +997,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
         if (a == E || a == T) a = nullptr;
       cudaFree(E);
       cudaFree(T);
+      h->bytes -= 2LL * L.Nv * c * (long long)sizeof(double2);
     }
     set_mass_internal(h, mass);
   });
@@ -978,6 +1008,28 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
     return st;
   }
   *out = h;
+  return MG_OK;
+}
+
+mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long* peak) {
+  std::string msg;
+  mg_status v = validate(params, msg);
+  if (v != MG_OK) { g_last_error = msg; return v; }
+  mg_handle tmp;
+  tmp.p = *params;
+  tmp.L = params->nlevels;
+  tmp.R = params->max_rhs;
+  tmp.dry = true;
+  set_geometry(&tmp);
+  allocate_storage(&tmp);
+  if (resident) *resident = tmp.bytes;
+  if (peak) *peak = tmp.bytes + setup_temp_bytes(&tmp);
+  return MG_OK;
+}
+
+mg_status mg_device_bytes(const mg_handle* h, long long* bytes) {
+  if (!h || !bytes) return MG_ERR_ARG;
+  *bytes = h->bytes;
   return MG_OK;
 }
 

@@ -44,8 +44,19 @@ class MgSolveInfo(ctypes.Structure):
                 ("vcycles", ctypes.c_longlong), ("milliseconds", ctypes.c_double)]
 
 
+class MgServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong),
+                ("batched_rhs", ctypes.c_longlong), ("builds", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("remasses", ctypes.c_longlong),
+                ("resident_bytes", ctypes.c_longlong), ("peak_resident_bytes", ctypes.c_longlong),
+                ("budget_bytes", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _lib = None
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_ll = ctypes.c_longlong
 _SIGS = {
     "mg_params_default": (_i, [ctypes.POINTER(MgParams), _i, _i]),
     "mg_setup_noise_len": (ctypes.c_size_t, [ctypes.POINTER(MgParams)]),
@@ -66,6 +77,14 @@ _SIGS = {
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "mg_apply_A_dot_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mg_setup_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "mg_server_create": (_i, [_ll, _i, _i, ctypes.POINTER(_vp)]),
+    "mg_server_add_config": (_i, [_vp, _vp, ctypes.POINTER(MgParams), _d, ctypes.POINTER(_i)]),
+    "mg_server_submit": (_i, [_vp, _i, _d, _vp, _vp, _i, _d, _i, ctypes.POINTER(_ll)]),
+    "mg_server_wait": (_i, [_vp, _ll, _vp, ctypes.POINTER(_d)]),
+    "mg_server_get_stats": (_i, [_vp, ctypes.POINTER(MgServerStats)]),
+    "mg_server_destroy": (None, [_vp]),
+    "mg_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -137,6 +156,18 @@ def mg_setup(gauge, mass, params: MgParams, stream=None):
     _check(lib().mg_setup(_ptr(gauge, torch.complex128), float(mass), ctypes.byref(params),
                           _stream_ptr(stream), ctypes.byref(h)))
     return h
+
+
+def mg_setup_bytes(params: MgParams):
+    res, peak = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().mg_setup_bytes(ctypes.byref(params), ctypes.byref(res), ctypes.byref(peak)))
+    return res.value, peak.value
+
+
+def mg_device_bytes(h) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().mg_device_bytes(h, ctypes.byref(v)), h)
+    return v.value
 
 
 def mg_set_mass(h, mass):
@@ -297,3 +328,57 @@ class Multigrid:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Serving engine (include/mg_server.h): configurations registered once,
+    solve requests queued and batched by the library's worker threads."""
+
+    def __init__(self, budget_bytes, max_rhs=16, workers=2):
+        self.s = ctypes.c_void_p()
+        _check(lib().mg_server_create(int(budget_bytes), int(max_rhs), int(workers),
+                                      ctypes.byref(self.s)))
+        self._keep = {}
+
+    def add_config(self, gauge, params: MgParams, setup_mass, noise=None) -> int:
+        """gauge (and noise, which sets params.setup_noise) are copied by the call."""
+        import torch
+        if noise is not None:
+            params.setup_noise = _ptr(noise, torch.complex128).value
+        cid = ctypes.c_int()
+        _check(lib().mg_server_add_config(self.s, _ptr(gauge, torch.complex128),
+                                          ctypes.byref(params), float(setup_mass),
+                                          ctypes.byref(cid)))
+        return cid.value
+
+    def submit(self, config_id, mass, b, x, nrhs, tol=1e-10, solver=0) -> int:
+        import torch
+        rid = ctypes.c_longlong()
+        _check(lib().mg_server_submit(self.s, int(config_id), float(mass), _ptr(b, torch.complex128),
+                                      _ptr(x, torch.complex128), int(nrhs), float(tol), int(solver),
+                                      ctypes.byref(rid)))
+        self._keep[rid.value] = (b, x)
+        return rid.value
+
+    def wait(self, request_id, nrhs):
+        infos = (MgSolveInfo * nrhs)()
+        lat = ctypes.c_double()
+        st = lib().mg_server_wait(self.s, int(request_id), infos, ctypes.byref(lat))
+        self._keep.pop(request_id, None)
+        return st, list(infos), lat.value
+
+    def stats(self) -> MgServerStats:
+        out = MgServerStats()
+        _check(lib().mg_server_get_stats(self.s, ctypes.byref(out)))
+        return out
+
+    def close(self):
+        if self.s:
+            lib().mg_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,5 +1,5 @@
 """The C ABI library builds for sm_103a, loads without a GPU, and exports every
-function that include/mg.h declares; the Python binding declares the same set.
+function that include/*.h declare; the Python binding declares the same set.
 No compute call is made here (no GPU needed)."""
 import ctypes
 import os
@@ -11,7 +11,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mg.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                    if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mg_\w+)\s*\(", src, flags=re.M)))
 
@@ -52,3 +54,15 @@ def test_param_struct_layout_matches(lib_path):
     assert mg.mg_setup_noise_len(p) == W.setup_noise_len(32, 16, [(4, 4), (2, 2)], [3, 5])
     bad = mg.make_params(30, 16, [(4, 4)], [3])
     assert mg.mg_setup_noise_len(bad) == 0
+
+
+def test_setup_bytes_is_host_only(lib_path):
+    """mg_setup_bytes sizes a hierarchy without touching a device."""
+    from paper_0710_3612_gb300 import mg
+    p = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8])
+    p.setup_noise = 1                    # never dereferenced by the size-only pass
+    res, peak = mg.mg_setup_bytes(p)
+    assert 0 < res < peak
+    p8 = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8], max_rhs=8)
+    p8.setup_noise = 1
+    assert mg.mg_setup_bytes(p8)[0] > res
