@@ -89,6 +89,124 @@ def workload_inputs(name):
 
 
 # ---------------------------------------------------------------------------
+# serving workload: Poisson arrivals over 8 configurations
+# ---------------------------------------------------------------------------
+# (key, L, beta, sweeps, seed, blocks, Nv): 64^2 beta 3, 128^2 beta 6, 256^2 and
+# 512^2 beta 10, two seeds each; three levels (four at 512^2, so that the
+# coarsest level keeps 16384 unknowns).
+SERVING_CONFIGS = [
+    ("L64_b3_s1", 64, 3.0, 200, 1, [(4, 4), (2, 2)], [8, 8]),
+    ("L64_b3_s2", 64, 3.0, 200, 2, [(4, 4), (2, 2)], [8, 8]),
+    ("L128_b6_s1", 128, 6.0, 200, 1, [(4, 4), (2, 2)], [8, 8]),
+    ("L128_b6_s2", 128, 6.0, 200, 2, [(4, 4), (2, 2)], [8, 8]),
+    ("L256_b10_s1", 256, 10.0, 500, 1, [(4, 4), (2, 2)], [8, 8]),
+    ("L256_b10_s2", 256, 10.0, 500, 2, [(4, 4), (2, 2)], [8, 8]),
+    ("L512_b10_s1", 512, 10.0, 500, 1, [(4, 4), (2, 2), (2, 2)], [8, 8, 8]),
+    ("L512_b10_s2", 512, 10.0, 500, 2, [(4, 4), (2, 2), (2, 2)], [8, 8, 8]),
+]
+
+
+def _gauge_angles(args):
+    L, beta, sweeps, seed = args
+    return W.quenched_u1_angles(L, L, beta, sweeps, seed)
+
+
+def critical_table():
+    out = {}
+    for f in ("critical_masses.json", "critical_masses_serving.json"):
+        p = os.path.join(ROOT, "workloads", f)
+        if os.path.exists(p):
+            out.update(json.load(open(p)))
+    return out
+
+
+def serving_leg(args, mg, torch, dev):
+    """Requests arrive as a Poisson stream over the 8 configurations (config
+    uniform, mass uniform over {0.05, 0.0, m_nc}, 1-16 Gaussian right-hand
+    sides, tol 1e-10, mixed solver) at a rate set to `--serve-load` times the
+    capacity estimated from a warm-up pass that builds every hierarchy and
+    solves one right-hand side per (config, mass).  Reported: right-hand
+    sides solved per second over the stream, and the submit-to-completion
+    latency percentiles of its requests."""
+    import multiprocessing as mp
+    crit = critical_table()
+    with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
+        thetas = pool.map(_gauge_angles, [(L, beta, sw, seed) for _, L, beta, sw, seed, _, _ in SERVING_CONFIGS])
+    rng = np.random.default_rng(2024)
+    gen = torch.Generator(device=dev).manual_seed(2024)
+    masses, missing = [], []
+    with mg.Server(budget_bytes=args.serve_budget_gb << 30, max_rhs=16, workers=4) as srv:
+        ids = []
+        for (key, L, beta, sw, seed, blocks, Nv), th in zip(SERVING_CONFIGS, thetas):
+            ms = [0.05, 0.0]
+            if key in crit and abs(W.mean_plaquette(th) - crit[key]["plaquette"]) <= 1e-12:
+                ms.append(crit[key]["m_nc"])
+            else:
+                missing.append(key)
+            masses.append(ms)
+            U = torch.from_numpy(W.links_from_angles(th)).to(dev)
+            noise = torch.from_numpy(W.setup_noise(L, L, blocks, Nv, 7)).to(dev)
+            ids.append(srv.add_config(U, mg.make_params(L, L, blocks, Nv, setup_sweeps=8), min(ms),
+                                      noise=noise))
+
+        def rhs(c, n):
+            L = SERVING_CONFIGS[c][1]
+            return torch.randn((n, L, L, 2), dtype=torch.complex128, device=dev, generator=gen)
+
+        # warm-up: every hierarchy built, one solve per (config, mass)
+        warm = []
+        for c in range(len(SERVING_CONFIGS)):
+            for m in masses[c]:
+                b = rhs(c, 1)
+                x = torch.empty_like(b)
+                torch.cuda.synchronize()
+                warm.append((srv.submit(ids[c], m, b, x, 1, 1e-10, mg.SOLVER_MGCG_MIXED), b, x))
+        service = [srv.wait(r, 1)[2] for r, _, _ in warm]
+        mean_service_s = statistics.mean(service) / 1000.0
+        rate = args.serve_load / mean_service_s        # requests per second
+        # the stream
+        reqs = []
+        for _ in range(args.serve_requests):
+            c = int(rng.integers(len(SERVING_CONFIGS)))
+            reqs.append((c, masses[c][int(rng.integers(len(masses[c])))], int(rng.integers(1, 17))))
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        bufs = [(rhs(c, n), None) for c, _, n in reqs]
+        bufs = [(b, torch.empty_like(b)) for b, _ in bufs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        submit_t, rids = [], []
+        for (c, m, n), (b, x), gap in zip(reqs, bufs, gaps):
+            t0 += gap
+            delay = t0 - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            submit_t.append(time.perf_counter())
+            rids.append(srv.submit(ids[c], m, b, x, n, 1e-10, mg.SOLVER_MGCG_MIXED))
+        lat, worst, failed = [], 0.0, 0
+        for r, (c, m, n) in zip(rids, reqs):
+            st, infos, ms = srv.wait(r, n)
+            failed += st != 0
+            lat.append(ms)
+            worst = max([worst] + [i.true_residual for i in infos])
+        end = max(t + l / 1000.0 for t, l in zip(submit_t, lat))
+        wall = end - submit_t[0]
+        stats = srv.stats()
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]   # noqa: E731
+    total_rhs = sum(n for _, _, n in reqs)
+    return {"configs": [k for k, *_ in SERVING_CONFIGS], "requests": len(reqs), "rhs": total_rhs,
+            "offered_load": args.serve_load, "arrival_rate_per_s": round(rate, 3),
+            "value": round(total_rhs / wall, 3), "unit": "solves/s (right-hand sides)",
+            "wall_s": round(wall, 3), "p50_ms": round(pct(0.50), 3), "p99_ms": round(pct(0.99), 3),
+            "failed": failed, "max_true_residual": worst,
+            "mean_batch_rhs": round(stats.batched_rhs / max(stats.batches, 1), 2),
+            "builds": stats.builds, "evictions": stats.evictions, "remasses": stats.remasses,
+            "peak_resident_gb": round(stats.peak_resident_bytes / 2 ** 30, 2),
+            "budget_gb": args.serve_budget_gb, "masses_without_m_nc": missing,
+            "warmup_mean_service_ms": round(mean_service_s * 1000.0, 3)}
+
+
+# ---------------------------------------------------------------------------
 # clocks sampler
 # ---------------------------------------------------------------------------
 class Clocks:
@@ -271,6 +389,9 @@ def gpu_bench(args):
     # end-to-end through the public API with host buffers
     e2e = e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, world)
 
+    # serving: Poisson request stream over 8 configurations through the serving engine
+    serving = serving_leg(args, mg, torch, dev) if args.serve_requests > 0 else None
+
     if rank == 0:
         sm = sorted(res["solve_ms"])
         pct = lambda q: sm[min(len(sm) - 1, int(math.ceil(q * len(sm))) - 1)]   # noqa: E731
@@ -299,6 +420,7 @@ def gpu_bench(args):
                            "per_mass": plain["per_mass"]},
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
             "batched": batched,
+            "serving": serving,
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
             "e2e": e2e,
@@ -666,6 +788,11 @@ def main():
                     help="right-hand sides of the batched leg (0 skips it)")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests in the serving stream (0 skips the serving leg)")
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="offered load of the serving stream (fraction of estimated capacity)")
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
     ap.add_argument("--phase-launches", action="store_true",

@@ -11,10 +11,12 @@
  *
  * Scheduling.  A pool of host worker threads; each takes the configuration
  * whose oldest pending request is the oldest overall (FIFO across
- * configurations) among those no other worker holds.  It packs that request
- * and every other pending request of the same configuration, mass, solver and
- * tolerance (up to max_rhs right-hand sides) into one batched mg_solve on the
- * configuration's own CUDA stream.  Requests that arrive while a batch is on
+ * configurations) among those no other worker holds.  Within it, requests at
+ * the hierarchy's current mass go first (a re-mass rebuilds the Galerkin
+ * operators and the coarsest inverse), else the oldest request; the worker
+ * packs that request and every other pending request of the same mass, solver
+ * and tolerance (up to max_rhs right-hand sides) into one batched mg_solve on
+ * the configuration's own CUDA stream.  Requests that arrive while a batch is on
  * the GPU join the next batch of their configuration (continuous batching);
  * batches of different configurations run concurrently on their streams.
  *

@@ -199,11 +199,18 @@ void worker_main(mg_server* s) {
       s->resident += c->resident - c->need;
       ++s->builds;
     }
-    // one batch: the oldest request and every pending request of the same
+    // one batch: the oldest pending request at the hierarchy's current mass
+    // (re-massing rebuilds the Galerkin operators and the coarsest inverse),
+    // else the oldest request; with it every pending request of the same
     // mass, solver and tolerance that fits in max_rhs
     std::vector<Request*> batch;
     int total = 0;
     const Request* head = c->queue.front();
+    for (const Request* r : c->queue)
+      if (r->mass == c->cur_mass) {
+        head = r;
+        break;
+      }
     const double mass = head->mass, tol = head->tol;
     const int solver = head->solver;
     for (auto it = c->queue.begin(); it != c->queue.end();) {
