@@ -124,8 +124,9 @@ def serving_leg(args, mg, torch, dev):
     """Requests arrive as a Poisson stream over the 8 configurations (config
     uniform, mass uniform over {0.05, 0.0, m_nc}, 1-16 Gaussian right-hand
     sides, tol 1e-10, mixed solver) at a rate set to `--serve-load` times the
-    capacity estimated from a warm-up pass that builds every hierarchy and
-    solves one right-hand side per (config, mass).  Reported: right-hand
+    capacity estimated from a warm-up that builds every (config, mass)
+    hierarchy and then times one 8-right-hand-side request per (config, mass),
+    one at a time (8.5 is the mean request size).  Reported: right-hand
     sides solved per second over the stream, and the submit-to-completion
     latency percentiles of its requests."""
     import multiprocessing as mp
@@ -153,15 +154,24 @@ def serving_leg(args, mg, torch, dev):
             L = SERVING_CONFIGS[c][1]
             return torch.randn((n, L, L, 2), dtype=torch.complex128, device=dev, generator=gen)
 
-        # warm-up: every hierarchy built, one solve per (config, mass)
-        warm = []
-        for c in range(len(SERVING_CONFIGS)):
+        # warm-up: every (config, mass) hierarchy built, then one timed solve each
+        def one_each():
+            warm = []
+            for c in range(len(SERVING_CONFIGS)):
+                for m in masses[c]:
+                    b = rhs(c, 1)
+                    x = torch.empty_like(b)
+                    torch.cuda.synchronize()
+                    warm.append((srv.submit(ids[c], m, b, x, 1, 1e-10, mg.SOLVER_MGCG_MIXED), b, x))
+            return [srv.wait(r, 1)[2] for r, _, _ in warm]
+        one_each()
+        service = []
+        for c in range(len(SERVING_CONFIGS)):     # one at a time: service time of a mean-size request
             for m in masses[c]:
-                b = rhs(c, 1)
+                b = rhs(c, 8)
                 x = torch.empty_like(b)
                 torch.cuda.synchronize()
-                warm.append((srv.submit(ids[c], m, b, x, 1, 1e-10, mg.SOLVER_MGCG_MIXED), b, x))
-        service = [srv.wait(r, 1)[2] for r, _, _ in warm]
+                service.append(srv.wait(srv.submit(ids[c], m, b, x, 8, 1e-10, mg.SOLVER_MGCG_MIXED), 8)[2])
         mean_service_s = statistics.mean(service) / 1000.0
         rate = args.serve_load / mean_service_s        # requests per second
         # the stream
@@ -200,7 +210,8 @@ def serving_leg(args, mg, torch, dev):
             "wall_s": round(wall, 3), "p50_ms": round(pct(0.50), 3), "p99_ms": round(pct(0.99), 3),
             "failed": failed, "max_true_residual": worst,
             "mean_batch_rhs": round(stats.batched_rhs / max(stats.batches, 1), 2),
-            "builds": stats.builds, "evictions": stats.evictions, "remasses": stats.remasses,
+            "builds": stats.builds, "clones": stats.clones, "evictions": stats.evictions,
+            "remasses": stats.remasses,
             "peak_resident_gb": round(stats.peak_resident_bytes / 2 ** 30, 2),
             "budget_gb": args.serve_budget_gb, "masses_without_m_nc": missing,
             "warmup_mean_service_ms": round(mean_service_s * 1000.0, 3)}
@@ -792,7 +803,7 @@ def main():
                     help="requests in the serving stream (0 skips the serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the serving stream (fraction of estimated capacity)")
-    ap.add_argument("--serve-budget-gb", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
     ap.add_argument("--phase-launches", action="store_true",

@@ -155,6 +155,15 @@ mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long
 /* Device bytes currently owned by the handle. */
 mg_status mg_device_bytes(const mg_handle* h, long long* bytes);
 
+/* A second hierarchy at another mass from the same set-up (Sec. 4: the
+ * vectors of the set-up reused at other masses): the gauge field, the block
+ * vectors of every level and the smoother start vectors are copied from src
+ * (device to device, on `stream`), then the Galerkin operators, smoothers and
+ * coarsest solver are built at `mass`.  The result equals mg_set_mass(src,
+ * mass) without changing src, and owns as much device memory as src.  src
+ * may be in use on another thread meanwhile (it is only read). */
+mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** out);
+
 /* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
  * b, x: device complex128 [nrhs][Lt][Lx][2].  Right-hand sides are solved in
  * batches of params->max_rhs that share one Krylov loop (one operator and

@@ -9,25 +9,30 @@
  * coarsest inverse) resident on the device while it fits in the budget and
  * solves the requests of one configuration and mass together.
  *
- * Scheduling.  A pool of host worker threads; each takes the configuration
- * whose oldest pending request is the oldest overall (FIFO across
- * configurations) among those no other worker holds.  Within it, requests at
- * the hierarchy's current mass go first (a re-mass rebuilds the Galerkin
- * operators and the coarsest inverse), else the oldest request; the worker
- * packs that request and every other pending request of the same mass, solver
- * and tolerance (up to max_rhs right-hand sides) into one batched mg_solve on
- * the configuration's own CUDA stream.  Requests that arrive while a batch is on
- * the GPU join the next batch of their configuration (continuous batching);
- * batches of different configurations run concurrently on their streams.
+ * Hierarchies.  Each (configuration, mass) pair that has requests is served
+ * by its own resident hierarchy with its own CUDA stream: the first one of a
+ * configuration by mg_setup at its set-up mass (then mg_set_mass), the others
+ * by mg_clone of a resident one (the set-up's vectors are shared by every
+ * mass, Sec. 4), so that requests at different masses neither re-mass nor
+ * wait for each other.
  *
- * Admission.  A configuration's hierarchy is built when a worker first takes
- * one of its requests, if its peak set-up memory (mg_setup_bytes plus the
- * batch buffers) fits the budget together with the resident hierarchies,
- * after destroying idle hierarchies (no pending request, not being solved),
- * least recently used first.  If it cannot fit yet, its requests wait and the
- * workers serve resident configurations meanwhile (a waiting worker holds
- * nothing, so the pool cannot deadlock).  A configuration larger than the
- * whole budget fails its requests with MG_ERR_NOMEM.
+ * Scheduling.  A pool of host worker threads.  A worker takes the (configuration,
+ * mass) group whose oldest pending request is the oldest overall among those
+ * whose hierarchy no other worker holds, and packs that request and every
+ * other pending request of the group with the same solver and tolerance (up
+ * to max_rhs right-hand sides) into one batched mg_solve.  Requests that
+ * arrive while a batch is on the GPU join the next batch of their group
+ * (continuous batching); batches of different groups run concurrently.
+ *
+ * Admission.  A new hierarchy is made only if its memory (mg_setup_bytes peak
+ * for a set-up, resident bytes for a clone, plus the batch buffers) fits the
+ * budget together with the resident ones, after destroying idle hierarchies
+ * (not held, no pending request at their mass), least recently used first.
+ * Otherwise an idle hierarchy of the same configuration is re-massed
+ * (mg_set_mass), or the group waits while the workers serve others (a waiting
+ * worker holds nothing, so the pool cannot deadlock).  A configuration whose
+ * set-up is larger than the whole budget fails its requests with
+ * MG_ERR_NOMEM.
  *
  * Results.  A request's solution is the same as a solve of it alone with
  * the same solver, within the solver's tolerance (batched right-hand sides
@@ -51,7 +56,7 @@ typedef struct mg_server mg_server;
 typedef struct {
   long long submitted, completed, failed;
   long long batches, batched_rhs;    /* batched_rhs / batches = mean batch size   */
-  long long builds, evictions, remasses;
+  long long builds, clones, evictions, remasses;
   long long resident_bytes, peak_resident_bytes, budget_bytes;
   double p50_ms, p99_ms, max_ms;     /* submit-to-completion latency, completed   */
 } mg_server_stats;

@@ -870,6 +870,16 @@ void allocate_storage(mg_handle* h) {
   }
 }
 
+// Pinned host mirrors, the internal graph stream and its fences.
+void init_runtime(mg_handle* h) {
+  ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
+  ck(h, cudaMallocHost((void**)&h->hctrl, (4 + 2 * h->R) * sizeof(int)), "pinned alloc");
+  ck(h, cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream create");
+  ck(h, cudaEventCreateWithFlags(&h->fence[0], cudaEventDisableTiming), "event create");
+  ck(h, cudaEventCreateWithFlags(&h->fence[1], cudaEventDisableTiming), "event create");
+  if (const char* e = std::getenv("MG_NO_GRAPHS")) h->use_graphs = e[0] == '0';
+}
+
 // Device bytes of the set-up's temporary relaxation vectors (E and T of the
 // largest level), allocated and freed inside mg_setup.
 long long setup_temp_bytes(const mg_handle* h) {
@@ -938,12 +948,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
   mg_status st = guarded(h, [&]() {
     const mg_params& P = h->p;
     set_geometry(h);
-    ck(h, cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)), "pinned alloc");
-    ck(h, cudaMallocHost((void**)&h->hctrl, (4 + 2 * h->R) * sizeof(int)), "pinned alloc");
-    ck(h, cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream create");
-    ck(h, cudaEventCreateWithFlags(&h->fence[0], cudaEventDisableTiming), "event create");
-    ck(h, cudaEventCreateWithFlags(&h->fence[1], cudaEventDisableTiming), "event create");
-    if (const char* e = std::getenv("MG_NO_GRAPHS")) h->use_graphs = e[0] == '0';
+    init_runtime(h);
     allocate_storage(h);
     // links
     const long long V = h->lv[0].V;
@@ -1030,6 +1035,48 @@ mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long
 mg_status mg_device_bytes(const mg_handle* h, long long* bytes) {
   if (!h || !bytes) return MG_ERR_ARG;
   *bytes = h->bytes;
+  return MG_OK;
+}
+
+mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** out) {
+  if (!src || !out) return MG_ERR_ARG;
+  *out = nullptr;
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) { g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
+  h->p = src->p;
+  h->p.profile = 0;
+  h->s = (cudaStream_t)stream;
+  h->L = src->L;
+  h->R = src->R;
+  mg_status st = guarded(h, [&]() {
+    set_geometry(h);
+    init_runtime(h);
+    allocate_storage(h);
+    const long long V = h->lv[0].V;
+    auto copy = [&](void* d, const void* sp, size_t bytes) {
+      ck(h, cudaMemcpyAsync(d, sp, bytes, cudaMemcpyDeviceToDevice, h->s), "clone copy");
+    };
+    copy(h->U64, src->U64, 2 * V * sizeof(double2));
+    copy(h->U32, src->U32, 2 * V * sizeof(float2));
+    for (int l = 0; l + 1 < h->L; ++l) {
+      Level& L = h->lv[l];
+      const Level& S = src->lv[l];
+      const size_t nv = (size_t)L.V * 2 * L.Nv * (L.n / 2);
+      copy(L.Vst64, S.Vst64, nv * sizeof(double2));
+      copy(L.Vst32, S.Vst32, nv * sizeof(float2));
+      copy(L.eta, S.eta, (size_t)L.count() * sizeof(double2));
+      L.lambda_max = S.lambda_max;
+      L.omega_relax = S.omega_relax;
+    }
+    set_mass_internal(h, mass);
+  });
+  if (st != MG_OK) {
+    g_last_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
   return MG_OK;
 }
 

@@ -39,6 +39,21 @@ struct Request {
   double latency_ms = 0.0;
 };
 
+// One resident hierarchy of a configuration at one mass, with its own
+// stream and batch buffers.
+struct Hier {
+  double mass = 0.0;
+  mg_handle* h = nullptr;
+  cudaStream_t stream = nullptr;
+  void* bbuf = nullptr;          // batch staging, [max_rhs][Lt][Lx][2] complex128 each
+  void* xbuf = nullptr;
+  long long bytes = 0;           // device bytes while resident
+  bool busy = false;             // held by a worker (solving, or being built)
+  bool ready = false;            // built (set under the lock when the build returns)
+  int readers = 0;               // clones being made from it (not evictable meanwhile)
+  long long last_used = 0;
+};
+
 struct Config {
   int id = 0;
   mg_params p{};
@@ -46,16 +61,10 @@ struct Config {
   int Lx = 0, Lt = 0;
   void* gauge = nullptr;         // device copies owned by the server
   void* noise = nullptr;
-  long long need = 0;            // peak bytes of a set-up + the batch buffers
-  long long resident = 0;        // bytes while resident
-  mg_handle* h = nullptr;
-  double cur_mass = 0.0;
-  cudaStream_t stream = nullptr;
-  void* bbuf = nullptr;          // batch staging, [max_rhs][Lt][Lx][2] complex128 each
-  void* xbuf = nullptr;
+  long long need_setup = 0;      // peak bytes of a set-up + batch buffers
+  long long need_clone = 0;      // resident bytes of a hierarchy + batch buffers
+  std::vector<std::unique_ptr<Hier>> hs;
   std::deque<Request*> queue;
-  bool busy = false;             // held by a worker
-  long long last_used = 0;
 };
 
 }  // namespace
@@ -71,62 +80,11 @@ struct mg_server {
   bool stop = false;
   long long next_id = 1, tick = 0;
   long long submitted = 0, completed = 0, failed = 0, batches = 0, batched_rhs = 0;
-  long long builds = 0, evictions = 0, remasses = 0;
+  long long builds = 0, clones = 0, evictions = 0, remasses = 0;
   std::vector<double> latencies;
 };
 
 namespace {
-
-// Releases a configuration's hierarchy and batch buffers (the caller holds
-// the lock and the configuration is idle).
-void evict(mg_server* s, Config* c) {
-  mg_destroy(c->h);
-  c->h = nullptr;
-  cudaFree(c->bbuf);
-  cudaFree(c->xbuf);
-  c->bbuf = c->xbuf = nullptr;
-  s->resident -= c->resident;
-  c->resident = 0;
-  ++s->evictions;
-}
-
-// Chooses the next configuration to run (the lock is held; never waits):
-// candidates are the configurations no worker holds that have pending
-// requests, oldest pending request first.  A resident candidate runs; one
-// larger than the whole budget is returned to fail its requests; otherwise a
-// candidate runs if idle hierarchies (no pending request, not held) can be
-// evicted, least recently used first, to fit its set-up -- then *build is set
-// and its peak is reserved.  nullptr if nothing can run now.
-Config* choose(mg_server* s, bool* build) {
-  *build = false;
-  std::vector<Config*> cand;
-  for (auto& c : s->cfgs)
-    if (!c->busy && !c->queue.empty()) cand.push_back(c.get());
-  std::sort(cand.begin(), cand.end(),
-            [](const Config* a, const Config* b) { return a->queue.front()->id < b->queue.front()->id; });
-  for (Config* c : cand) {
-    if (c->h || c->need > s->budget) return c;
-    std::vector<Config*> idle;
-    long long freeable = 0;
-    for (auto& o : s->cfgs)
-      if (o->h && !o->busy && o->queue.empty()) {
-        idle.push_back(o.get());
-        freeable += o->resident;
-      }
-    if (s->resident - freeable + c->need > s->budget) continue;
-    std::sort(idle.begin(), idle.end(),
-              [](const Config* a, const Config* b) { return a->last_used < b->last_used; });
-    for (Config* o : idle) {
-      if (s->resident + c->need <= s->budget) break;
-      evict(s, o);
-    }
-    s->resident += c->need;                   // reserve the set-up's peak
-    s->peak_resident = std::max(s->peak_resident, s->resident);
-    *build = true;
-    return c;
-  }
-  return nullptr;
-}
 
 void finish(mg_server* s, std::vector<Request*>& batch, mg_status st,
             const std::vector<mg_solve_info>* infos) {
@@ -147,77 +105,211 @@ void finish(mg_server* s, std::vector<Request*>& batch, mg_status st,
   }
 }
 
+void erase_hier(Config* c, const Hier* r) {
+  for (auto it = c->hs.begin(); it != c->hs.end(); ++it)
+    if (it->get() == r) {
+      c->hs.erase(it);
+      return;
+    }
+}
+
+void free_hier(Hier* r) {
+  mg_destroy(r->h);
+  cudaFree(r->bbuf);
+  cudaFree(r->xbuf);
+  if (r->stream) cudaStreamDestroy(r->stream);
+  r->h = nullptr;
+  r->bbuf = r->xbuf = nullptr;
+  r->stream = nullptr;
+}
+
+bool pending_at(const Config* c, double mass) {
+  for (const Request* q : c->queue)
+    if (q->mass == mass) return true;
+  return false;
+}
+
+// Destroys idle hierarchies (not held, not a clone source, no pending request
+// at their mass), least recently used first, until `need` more bytes fit;
+// false if they cannot.  The lock is held.
+bool make_room(mg_server* s, long long need) {
+  if (s->resident + need <= s->budget) return true;
+  std::vector<std::pair<Config*, Hier*>> idle;
+  long long freeable = 0;
+  for (auto& c : s->cfgs)
+    for (auto& r : c->hs)
+      if (!r->busy && !r->readers && !pending_at(c.get(), r->mass)) {
+        idle.push_back({c.get(), r.get()});
+        freeable += r->bytes;
+      }
+  if (s->resident - freeable + need > s->budget) return false;
+  std::sort(idle.begin(), idle.end(),
+            [](const auto& a, const auto& b) { return a.second->last_used < b.second->last_used; });
+  for (auto& cr : idle) {
+    if (s->resident + need <= s->budget) break;
+    free_hier(cr.second);
+    s->resident -= cr.second->bytes;
+    ++s->evictions;
+    erase_hier(cr.first, cr.second);
+  }
+  return true;
+}
+
+Hier* find_hier(Config* c, double mass) {
+  for (auto& r : c->hs)
+    if (r->mass == mass) return r.get();
+  return nullptr;
+}
+
+// What a worker does next (chosen with the lock held; never waits).
+struct Job {
+  Config* c = nullptr;
+  Hier* r = nullptr;             // the hierarchy that serves the batch
+  double mass = 0.0;
+  enum { RUN, BUILD, CLONE, REMASS, FAIL } kind = RUN;
+  Hier* src = nullptr;           // clone source
+};
+
+// Pending (configuration, mass) groups in the order of their oldest request.
+// A group whose hierarchy exists and is free runs.  One without a hierarchy
+// gets a new one if memory allows (after evicting idle ones): a clone of a
+// resident hierarchy of its configuration, else a set-up; otherwise an idle
+// hierarchy of the same configuration is re-massed.  A configuration larger
+// than the whole budget fails.
+bool choose(mg_server* s, Job* job) {
+  struct G { long long id; Config* c; double mass; };
+  std::vector<G> groups;
+  for (auto& c : s->cfgs)
+    for (const Request* q : c->queue) {
+      bool seen = false;
+      for (const G& g : groups)
+        if (g.c == c.get() && g.mass == q->mass) seen = true;
+      if (!seen) groups.push_back({q->id, c.get(), q->mass});
+    }
+  std::sort(groups.begin(), groups.end(), [](const G& a, const G& b) { return a.id < b.id; });
+  for (const G& g : groups) {
+    Config* c = g.c;
+    job->c = c;
+    job->mass = g.mass;
+    if (Hier* r = find_hier(c, g.mass)) {
+      if (r->busy) continue;
+      job->r = r;
+      job->kind = Job::RUN;
+      return true;
+    }
+    Hier* src = nullptr;
+    for (auto& r : c->hs)
+      if (r->ready && (!src || r->last_used > src->last_used)) src = r.get();
+    if (!src && !c->hs.empty()) continue;      // its first hierarchy is being built: clone later
+    const long long need = src ? c->need_clone : c->need_setup;
+    if (!src && c->need_setup > s->budget) {
+      job->kind = Job::FAIL;
+      return true;
+    }
+    if (make_room(s, need)) {
+      auto r = std::make_unique<Hier>();
+      r->mass = g.mass;
+      r->busy = true;
+      r->bytes = need;                          // reserved; exact after the build
+      s->resident += need;
+      s->peak_resident = std::max(s->peak_resident, s->resident);
+      job->r = r.get();
+      job->src = src;
+      job->kind = src ? Job::CLONE : Job::BUILD;
+      if (src) ++src->readers;
+      c->hs.push_back(std::move(r));
+      return true;
+    }
+    for (auto& r : c->hs)                        // re-mass an idle hierarchy instead
+      if (r->ready && !r->busy && !r->readers && !pending_at(c, r->mass)) {
+        r->mass = g.mass;                          // serves this group from now on
+        r->busy = true;
+        job->r = r.get();
+        job->kind = Job::REMASS;
+        return true;
+      }
+  }
+  return false;
+}
+
+void fail_queue(mg_server* s, Config* c, mg_status st) {
+  std::vector<Request*> all(c->queue.begin(), c->queue.end());
+  c->queue.clear();
+  finish(s, all, st, nullptr);
+}
+
 void worker_main(mg_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    bool build = false;
-    Config* c = choose(s, &build);
-    if (!c) {
+    Job job;
+    if (!choose(s, &job)) {
       if (s->stop) return;
       s->cv_work.wait(lk);
       continue;
     }
-    if (!c->h && !build) {                    // larger than the whole budget
-      std::vector<Request*> all(c->queue.begin(), c->queue.end());
-      c->queue.clear();
-      finish(s, all, MG_ERR_NOMEM, nullptr);
+    Config* c = job.c;
+    Hier* r = job.r;
+    if (job.kind == Job::FAIL) {
+      fail_queue(s, c, MG_ERR_NOMEM);
       s->cv_done.notify_all();
       continue;
     }
-    c->busy = true;
-    if (build) {
+    r->busy = true;
+    const size_t vb = (size_t)s->max_rhs * c->Lx * c->Lt * 2 * 16;
+    if (job.kind == Job::BUILD || job.kind == Job::CLONE) {
       lk.unlock();
-      const size_t vb = (size_t)s->max_rhs * c->Lx * c->Lt * 2 * 16;
-      mg_handle* h = nullptr;
-      mg_status st = mg_setup(c->gauge, c->setup_mass, &c->p, c->stream, &h);
-      if (st == MG_OK && (cudaMalloc(&c->bbuf, vb) != cudaSuccess ||
-                          cudaMalloc(&c->xbuf, vb) != cudaSuccess)) {
+      mg_status st = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess
+                         ? MG_OK : MG_ERR_CUDA;
+      if (st == MG_OK) {
+        if (job.kind == Job::CLONE) {
+          st = mg_clone(job.src->h, job.mass, r->stream, &r->h);
+        } else {
+          st = mg_setup(c->gauge, c->setup_mass, &c->p, r->stream, &r->h);
+          if (st == MG_OK && job.mass != c->setup_mass) st = mg_set_mass(r->h, job.mass);
+        }
+      }
+      if (st == MG_OK && (cudaMalloc(&r->bbuf, vb) != cudaSuccess ||
+                          cudaMalloc(&r->xbuf, vb) != cudaSuccess)) {
         cudaGetLastError();
         st = MG_ERR_NOMEM;
       }
       long long bytes = 0;
-      if (st == MG_OK) mg_device_bytes(h, &bytes);
+      if (st == MG_OK) mg_device_bytes(r->h, &bytes);
       lk.lock();
+      if (job.src) --job.src->readers;
       if (st != MG_OK) {
-        if (h) mg_destroy(h);
-        cudaFree(c->bbuf);
-        cudaFree(c->xbuf);
-        c->bbuf = c->xbuf = nullptr;
-        s->resident -= c->need;
-        std::vector<Request*> all(c->queue.begin(), c->queue.end());
-        c->queue.clear();
-        finish(s, all, st, nullptr);
-        c->busy = false;
+        free_hier(r);
+        s->resident -= r->bytes;
+        erase_hier(c, r);
+        fail_queue(s, c, st);
         s->cv_done.notify_all();
         s->cv_work.notify_all();
         continue;
       }
-      c->h = h;
-      c->cur_mass = c->setup_mass;
-      c->resident = bytes + 2 * (long long)vb;  // the set-up's temporaries are freed
-      s->resident += c->resident - c->need;
-      ++s->builds;
+      s->resident += bytes + 2 * (long long)vb - r->bytes;
+      r->bytes = bytes + 2 * (long long)vb;
+      r->ready = true;
+      if (job.kind == Job::CLONE) ++s->clones; else ++s->builds;
     }
-    // one batch: the oldest pending request at the hierarchy's current mass
-    // (re-massing rebuilds the Galerkin operators and the coarsest inverse),
-    // else the oldest request; with it every pending request of the same
-    // mass, solver and tolerance that fits in max_rhs
+    // one batch: the oldest pending request at this mass and every other one
+    // with the same solver and tolerance that fits in max_rhs
     std::vector<Request*> batch;
     int total = 0;
-    const Request* head = c->queue.front();
-    for (const Request* r : c->queue)
-      if (r->mass == c->cur_mass) {
-        head = r;
+    const Request* head = nullptr;
+    for (const Request* q : c->queue)
+      if (q->mass == job.mass) {
+        head = q;
         break;
       }
-    const double mass = head->mass, tol = head->tol;
+    const double tol = head->tol;
     const int solver = head->solver;
     for (auto it = c->queue.begin(); it != c->queue.end();) {
-      Request* r = *it;
-      if (r->mass == mass && r->tol == tol && r->solver == solver && total + r->nrhs <= s->max_rhs) {
-        batch.push_back(r);
-        total += r->nrhs;
+      Request* q = *it;
+      if (q->mass == job.mass && q->tol == tol && q->solver == solver &&
+          total + q->nrhs <= s->max_rhs) {
+        batch.push_back(q);
+        total += q->nrhs;
         it = c->queue.erase(it);
       } else {
         ++it;
@@ -225,14 +317,7 @@ void worker_main(mg_server* s) {
     }
     lk.unlock();
     mg_status st = MG_OK;
-    bool remassed = false;
-    if (c->cur_mass != mass) {
-      st = mg_set_mass(c->h, mass);
-      if (st == MG_OK) {
-        c->cur_mass = mass;
-        remassed = true;
-      }
-    }
+    if (job.kind == Job::REMASS) st = mg_set_mass(r->h, job.mass);
     std::vector<mg_solve_info> infos(total);
     if (st == MG_OK) {
       const size_t n = (size_t)c->Lx * c->Lt * 2 * 16;     // bytes of one right-hand side
@@ -240,32 +325,37 @@ void worker_main(mg_server* s) {
       void* x = batch[0]->x;
       if (batch.size() > 1) {
         size_t off = 0;
-        for (Request* r : batch) {
-          cudaMemcpyAsync((char*)c->bbuf + off, r->b, r->nrhs * n, cudaMemcpyDeviceToDevice,
-                          c->stream);
-          off += r->nrhs * n;
+        for (Request* q : batch) {
+          cudaMemcpyAsync((char*)r->bbuf + off, q->b, q->nrhs * n, cudaMemcpyDeviceToDevice,
+                          r->stream);
+          off += q->nrhs * n;
         }
-        b = c->bbuf;
-        x = c->xbuf;
+        b = r->bbuf;
+        x = r->xbuf;
       }
-      st = mg_solve(c->h, b, x, total, tol, 1000000, solver, infos.data());
+      st = mg_solve(r->h, b, x, total, tol, 1000000, solver, infos.data());
       if (batch.size() > 1 && (st == MG_OK || st == MG_ERR_NOCONV)) {
         size_t off = 0;
-        for (Request* r : batch) {
-          cudaMemcpyAsync(r->x, (char*)c->xbuf + off, r->nrhs * n, cudaMemcpyDeviceToDevice,
-                          c->stream);
-          off += r->nrhs * n;
+        for (Request* q : batch) {
+          cudaMemcpyAsync(q->x, (char*)r->xbuf + off, q->nrhs * n, cudaMemcpyDeviceToDevice,
+                          r->stream);
+          off += q->nrhs * n;
         }
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = MG_ERR_CUDA;
+        if (cudaStreamSynchronize(r->stream) != cudaSuccess) st = MG_ERR_CUDA;
       }
     }
     lk.lock();
-    if (remassed) ++s->remasses;
+    if (job.kind == Job::REMASS && st == MG_OK) ++s->remasses;
     ++s->batches;
     s->batched_rhs += total;
     finish(s, batch, st, &infos);
-    c->busy = false;
-    c->last_used = ++s->tick;
+    r->busy = false;
+    r->last_used = ++s->tick;
+    if (job.kind == Job::REMASS && st != MG_OK) {   // state of a failed re-mass is unknown
+      free_hier(r);
+      s->resident -= r->bytes;
+      erase_hier(c, r);
+    }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
   }
@@ -302,13 +392,15 @@ mg_status mg_server_add_config(mg_server* s, const void* gauge, const mg_params*
   auto c = std::make_unique<Config>();
   c->p = *params;
   c->p.max_rhs = s->max_rhs;
-  long long peak = 0;
-  mg_status st = mg_setup_bytes(&c->p, nullptr, &peak);
+  long long resident = 0, peak = 0;
+  mg_status st = mg_setup_bytes(&c->p, &resident, &peak);
   if (st != MG_OK) return st;
   c->Lx = params->Lx;
   c->Lt = params->Lt;
   c->setup_mass = setup_mass;
-  c->need = peak + 2LL * s->max_rhs * c->Lx * c->Lt * 2 * 16;
+  const long long vb = 2LL * s->max_rhs * c->Lx * c->Lt * 2 * 16;
+  c->need_setup = peak + vb;
+  c->need_clone = resident + vb;
   const size_t gb = (size_t)2 * c->Lx * c->Lt * 16;
   const size_t nb = (size_t)mg_setup_noise_len(params) * 16;
   if (cudaMalloc(&c->gauge, gb) != cudaSuccess) { cudaGetLastError(); return MG_ERR_NOMEM; }
@@ -318,8 +410,7 @@ mg_status mg_server_add_config(mg_server* s, const void* gauge, const mg_params*
     return MG_ERR_NOMEM;
   }
   if (cudaMemcpy(c->gauge, gauge, gb, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-      (nb && cudaMemcpy(c->noise, params->setup_noise, nb, cudaMemcpyDeviceToDevice) != cudaSuccess) ||
-      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      (nb && cudaMemcpy(c->noise, params->setup_noise, nb, cudaMemcpyDeviceToDevice) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(c->gauge);
     cudaFree(c->noise);
@@ -380,6 +471,7 @@ mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out) {
   out->batches = s->batches;
   out->batched_rhs = s->batched_rhs;
   out->builds = s->builds;
+  out->clones = s->clones;
   out->evictions = s->evictions;
   out->remasses = s->remasses;
   out->resident_bytes = s->resident;
@@ -396,8 +488,11 @@ void mg_server_destroy(mg_server* s) {
   {
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_done.wait(lk, [&] {
-      for (auto& c : s->cfgs)
-        if (c->busy || !c->queue.empty()) return false;
+      for (auto& c : s->cfgs) {
+        if (!c->queue.empty()) return false;
+        for (auto& r : c->hs)
+          if (r->busy) return false;
+      }
       return true;
     });
     s->stop = true;
@@ -405,10 +500,9 @@ void mg_server_destroy(mg_server* s) {
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
   for (auto& c : s->cfgs) {
-    if (c->h) evict(s, c.get());
+    for (auto& r : c->hs) free_hier(r.get());
     cudaFree(c->gauge);
     cudaFree(c->noise);
-    if (c->stream) cudaStreamDestroy(c->stream);
   }
   delete s;
 }

@@ -48,7 +48,7 @@ class MgServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
                 ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong),
                 ("batched_rhs", ctypes.c_longlong), ("builds", ctypes.c_longlong),
-                ("evictions", ctypes.c_longlong), ("remasses", ctypes.c_longlong),
+                ("clones", ctypes.c_longlong), ("evictions", ctypes.c_longlong), ("remasses", ctypes.c_longlong),
                 ("resident_bytes", ctypes.c_longlong), ("peak_resident_bytes", ctypes.c_longlong),
                 ("budget_bytes", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
@@ -85,6 +85,7 @@ _SIGS = {
     "mg_server_get_stats": (_i, [_vp, ctypes.POINTER(MgServerStats)]),
     "mg_server_destroy": (None, [_vp]),
     "mg_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "mg_clone": (_i, [_vp, _d, _vp, ctypes.POINTER(_vp)]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -168,6 +169,12 @@ def mg_device_bytes(h) -> int:
     v = ctypes.c_longlong()
     _check(lib().mg_device_bytes(h, ctypes.byref(v)), h)
     return v.value
+
+
+def mg_clone(h, mass, stream=None):
+    out = ctypes.c_void_p()
+    _check(lib().mg_clone(h, float(mass), _stream_ptr(stream), ctypes.byref(out)), h)
+    return out
 
 
 def mg_set_mass(h, mass):

@@ -53,6 +53,31 @@ def test_setup_bytes_equal_the_allocations(mg, kw):
         assert peak > res
 
 
+def test_clone_equals_set_mass(mg):
+    """mg_clone(h, m) builds the same hierarchy as mg_set_mass(h, m) (bit for
+    bit: same vectors, same deterministic kernels) and leaves h unchanged."""
+    L, beta, sweeps, seed, m0, blocks, Nv, ms = CONFIGS[0]
+    U = dev(W.quenched_u1(L, L, beta, sweeps, seed))
+    noise = dev(W.setup_noise(L, L, blocks, Nv, 5))
+    m1 = ms[1]
+    with mg.Multigrid(U, m0, blocks, Nv, noise) as a, mg.Multigrid(U, m0, blocks, Nv, noise) as b:
+        c = mg.mg_clone(a.h, m1)
+        try:
+            b.set_mass(m1)
+            for lvl in range(2, len(blocks) + 2):
+                Lx, Lt, n, _ = mg.mg_get_level(a.h, lvl)
+                shape = (Lt * Lx * 9 * n * n,)
+                oa, ob, oc = (torch.empty(shape, dtype=torch.complex128, device=DEV) for _ in range(3))
+                mg.mg_get_coarse_op(a.h, lvl, oa)
+                mg.mg_get_coarse_op(b.h, lvl, ob)
+                mg.mg_get_coarse_op(c, lvl, oc)
+                assert torch.equal(ob, oc)                     # clone == re-massed copy
+                assert not torch.equal(oa, oc)                 # the source kept its mass
+            assert mg.mg_device_bytes(c) == mg.mg_device_bytes(a.h)
+        finally:
+            mg.mg_destroy(c)
+
+
 def _requests():
     """Mixed stream: (config, mass, nrhs, source seeds), interleaved."""
     rng = np.random.default_rng(11)
@@ -116,7 +141,8 @@ def test_results_same_alone_and_in_the_mix(mg, solver):
         st = srv.stats()
         assert st.completed == len(reqs) and st.failed == 0
         assert st.batches < len(reqs)              # some requests shared a batch
-        assert st.builds == 2 and st.p99_ms >= st.p50_ms > 0
+        assert st.builds == 2 and st.clones == 2      # one set-up per config, one clone per other mass
+        assert st.remasses == 0 and st.p99_ms >= st.p50_ms > 0
     for k, ((c, m, nrhs, _), b) in enumerate(zip(reqs, bs)):
         status, infos, lat = results[k]
         assert status == 0 and lat > 0
