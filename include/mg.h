@@ -106,6 +106,11 @@ typedef struct {
                                            inverse with FP64 refinement; larger
                                            ones FP64 CG on the coarsest stencil
                                            (16384, the largest dense size)      */
+  int coarsest_gj_tcgen05;              /* rank-64 updates of the dense inverse
+                                           on tcgen05 tensor cores (TMEM
+                                           accumulator, 1) or with mma.sync
+                                           (0, default: measured faster at 4096
+                                           unknowns)                            */
 } mg_params;
 
 typedef struct {

@@ -158,6 +158,10 @@ cudaError_t coarse_to_dense_f32(const void* A, void* dense, int Lx, int Lt, int 
 cudaError_t gauss_jordan_begin(void* M, int N, void* work, cudaStream_t s);
 cudaError_t gauss_jordan_panel(void* M, int N, int k, void* work, cudaStream_t s);
 cudaError_t gauss_jordan_update(void* M, int N, int k, void* work, cudaStream_t s);
+// The same update on tcgen05 tensor cores (TMEM accumulator); needs 16 more
+// bytes of work: an int error flag after the row panel, zero before the first
+// call, set if a completion wait runs out (the inverse is then invalid).
+cudaError_t gauss_jordan_update_tc(void* M, int N, int k, void* work, cudaStream_t s);
 // y = B x, or y += B x when accumulate (complex64 B, leading dimension ld);
 // x complex128 (N) -> y complex128 (N); FP32 products and accumulation, result
 // widened to FP64.  xtmp: ld complex64.

@@ -6,6 +6,7 @@
 //    levels >= 2 from the block formula P(i)^dagger A_l[i, e] P(i + e)
 //  * coarsest level: dense FP32 Gauss-Jordan inverse and GEMV (the FP64
 //    refinement around them lives in the host orchestration)
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1157,6 +1158,269 @@ __global__ void __launch_bounds__(256) k_gj_update(float2* __restrict__ M, int N
   }
 }
 
+// ---- tcgen05 variant of the update ---------------------------------------
+// The same update, M_IJ -= Cold_I R_J, on the 5th-generation tensor cores:
+// one CTA per "tall tile" of two 64-row blocks (2p, 2p+1) and one 64-column
+// block J, an M = 128, N = 128 (realified), K = 8 tcgen05.mma of kind::tf32
+// per step with the FP32 accumulator in tensor memory (row r of the tile in
+// TMEM lane r).  The 64 complex pivot columns (K = 128 real) are staged in four
+// quarters of 16; each stage writes A = Cold rows (complex entries interleaved
+// (re, im) along K) and B = R_J realified (B[n][k], n = 2j + d, k = 2q + c:
+// Re R for c = d, Im R for (c, d) = (0, 1), -Im R for (c, d) = (1, 0)) into
+// shared memory in the K-major no-swizzle core-matrix layout (8 rows x 16 B
+// per core matrix), as TF32 hi/lo splits; three MMAs per step (lo hi, hi lo,
+// hi hi).  One elected thread issues the MMAs and commits them to an
+// mbarrier; every thread waits on it (bounded: a wait that runs out sets
+// *err and the CTA gives up) before reusing shared memory or reading the
+// accumulator with tcgen05.ld.  Warps w and w + 4 read TMEM lanes 32 (w % 4)
+// .. + 31, columns split in halves.
+static constexpr int TC_K = 32;                  // real K per stage (16 complex pivot columns)
+static constexpr int TC_OPF = 128 * TC_K;        // floats per operand split (16 KB)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// float offset of element (row, k) of a [128][TC_K] operand, core matrices
+// (row / 8, k / 4) of 32 floats, K fastest
+__device__ __forceinline__ int tc_off(int row, int k) {
+  return ((row >> 3) * (TC_K / 4) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+// shared-memory matrix descriptor: start address and offsets in 16-byte
+// units; leading-dimension offset = next core matrix along K (128 B), stride
+// offset = next 8-row group (TC_K / 4 core matrices), version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)((TC_K / 4 * 128u) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 128, M = 128
+constexpr uint32_t TC_IDESC =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      :: "r"(dtmem), "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int* err) {
+  const uint32_t a = smem_u32(m);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    if (ok) return true;
+    __nanosleep(64);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// number of tall tiles of row pair p: column blocks 0 .. min(2p + 1, nt - 1)
+__device__ __forceinline__ int tc_tiles_of_pair(int p, int nt) { return min(2 * p + 2, nt); }
+
+__global__ void __launch_bounds__(256, 2) k_gj_update_tc(float2* __restrict__ M, int N, int k,
+                                                         const float2* __restrict__ P,
+                                                         float2* __restrict__ Pnext,
+                                                         const float2* __restrict__ Cold,
+                                                         const float2* __restrict__ Cn,
+                                                         const float2* __restrict__ Rp,
+                                                         int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char tc_dyn[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_sh;
+  const int nt = N / GJB, npairs = (nt + 1) / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tall tile of this CTA; CTA 0 takes the one holding block (k+1, k+1)
+  long long target = -1;
+  if (k + 1 < nt) {
+    long long cum = 0;
+    for (int q = 0; q < (k + 1) / 2; ++q) cum += tc_tiles_of_pair(q, nt);
+    target = cum + (k + 1);
+  }
+  long long t = blockIdx.x;
+  if (target >= 0) t = (t == 0) ? target : (t <= target ? t - 1 : t);
+  int p = 0;
+  for (; p < npairs; ++p) {
+    const int c = tc_tiles_of_pair(p, nt);
+    if (t < c) break;
+    t -= c;
+  }
+  const int J = (int)t;
+  // role of each 64-row half: 0 skip, 1 update, 2 copy R_J (pivot row),
+  // 3 copy P (pivot block), 4 copy -Cn_I (pivot column)
+  int role[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int I = 2 * p + h;
+    if (I >= nt || J > I) role[h] = 0;
+    else if (I == k && J == k) role[h] = 3;
+    else if (I == k) role[h] = 2;
+    else if (J == k) role[h] = 4;
+    else role[h] = 1;
+  }
+  // copies (no MMA involved)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (role[h] < 2) continue;
+    const int I = 2 * p + h;
+    float2* tile = M + (long long)I * GJB * N + J * GJB;
+    for (int q = tid; q < GJB * GJB; q += 256) {
+      const int r = q / GJB, c = q % GJB;
+      float2 v;
+      if (role[h] == 3) v = P[q];
+      else if (role[h] == 2) v = Rp[(long long)r * N + J * GJB + c];
+      else {
+        const float2 w = Cn[(long long)(I * GJB + r) * GJB + c];
+        v = make_float2(-w.x, -w.y);
+      }
+      tile[(long long)r * N + c] = v;
+    }
+  }
+  if (role[0] != 1 && role[1] != 1) return;             // CTA-uniform
+  // operands from a 1024-byte aligned base (the allocation has 1 KB of slack)
+  unsigned char* tc_raw = tc_dyn + ((1024u - (smem_u32(tc_dyn) & 1023u)) & 1023u);
+  float* Ahi = (float*)tc_raw;
+  float* Alo = Ahi + TC_OPF;
+  float* Bhi = Alo + TC_OPF;
+  float* Blo = Bhi + TC_OPF;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n"
+                 :: "r"(smem_u32(&tmem_sh)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  bool ok = true;
+  constexpr int KC = TC_K / 2;                           // complex pivot columns per stage
+  constexpr int PER = 128 * KC / 256;                    // operand slots per thread and stage
+  // A: 128 rows x KC complex pivot columns of Cold (rows of a missing second
+  // block, when nt is odd, are zero).  Thread e writes float2 slot e % 16 of
+  // core matrix e / 16 (consecutive threads, consecutive slots: no bank
+  // conflicts); slot w holds row w / 2, complex column w % 2 of it.
+  // B: R_J realified, rows q of the pivot block; slot w of core matrix cm
+  // (8 n x 4 k) holds n = 2 j + d with j = 4 (cm / 8) + w / 4, d = (w / 2) % 2,
+  // k = 2 q .. 2 q + 1 with q = 2 (cm % 8) + w % 2: (Re, -Im) for d = 0,
+  // (Im, Re) for d = 1.  The next stage's entries are loaded into registers
+  // while the tensor cores work on the current one.
+  float2 va[PER], vb[PER];
+  auto load_stage = [&](int kh) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = tid + 256 * i, cm = e >> 4, w = e & 15;
+      const int row = 8 * (cm / (TC_K / 4)) + (w >> 1), c = 2 * (cm % (TC_K / 4)) + (w & 1);
+      const int I = 2 * p + (row >> 6);
+      va[i] = I < nt ? Cold[((long long)I * GJB + (row & 63)) * GJB + KC * kh + c]
+                     : make_float2(0.f, 0.f);
+      const int j = 4 * (cm / (TC_K / 4)) + (w >> 2);
+      const int ql = 2 * (cm % (TC_K / 4)) + (w & 1);
+      vb[i] = Rp[(long long)(KC * kh + ql) * N + J * GJB + j];
+    }
+  };
+  auto store_stage = [&]() {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = tid + 256 * i, w = e & 15;
+      const int o = (e >> 4) * 32 + 2 * w;                 // == tc_off of the slot
+      uint32_t h0, l0, h1, l1;
+      split_tf32(va[i].x, h0, l0);
+      split_tf32(va[i].y, h1, l1);
+      *(float2*)(Ahi + o) = make_float2(__uint_as_float(h0), __uint_as_float(h1));
+      *(float2*)(Alo + o) = make_float2(__uint_as_float(l0), __uint_as_float(l1));
+      const int d = (w >> 1) & 1;
+      const float b0 = d ? vb[i].y : vb[i].x, b1 = d ? vb[i].x : -vb[i].y;
+      split_tf32(b0, h0, l0);
+      split_tf32(b1, h1, l1);
+      *(float2*)(Bhi + o) = make_float2(__uint_as_float(h0), __uint_as_float(h1));
+      *(float2*)(Blo + o) = make_float2(__uint_as_float(l0), __uint_as_float(l1));
+    }
+  };
+  load_stage(0);
+  for (int kh = 0; kh < GJB / KC && ok; ++kh) {
+    store_stage();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll 1
+      for (int kk = 0; kk < TC_K / 8; ++kk) {
+        const uint32_t off = kk * 2 * 128;          // two core matrices along K per step
+        tc_mma(tmem, tc_desc(al + off), tc_desc(bh + off), (kh | kk) ? 1u : 0u);
+        tc_mma(tmem, tc_desc(ah + off), tc_desc(bl + off), 1u);
+        tc_mma(tmem, tc_desc(ah + off), tc_desc(bh + off), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                   :: "r"(smem_u32(&mbar)) : "memory");
+    }
+    if (kh + 1 < GJB / KC) load_stage(kh + 1);          // overlaps the MMAs of stage kh
+    ok = mbar_wait(&mbar, (uint32_t)(kh & 1), err);
+    ok = __syncthreads_and(ok);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  // epilogue: row r = 32 (warp % 4) + lane of the tall tile, columns split by warp / 4
+  const int quarter = warp & 3, chalf = warp >> 2;
+  const int r = 32 * quarter + lane, h = r >> 6, rr = r & 63, I = 2 * p + h;
+  const bool next_pivot = (I == k + 1 && J == k + 1);
+  float2* sw = (float2*)tc_raw;            // the new pivot block [64][GJS] + sweep scratch
+  if (ok) {
+    float v[32];
+#pragma unroll 1
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int col0 = 64 * chalf + 32 * c2;             // real column of the chunk
+      tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0, v);
+      if (role[h] == 1) {
+        float2* rowp = M + ((long long)I * GJB + rr) * N + J * GJB + col0 / 2;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float2 o = rowp[i];
+          const float2 nv = make_float2(o.x - v[2 * i], o.y - v[2 * i + 1]);
+          rowp[i] = nv;
+          if (next_pivot) sw[rr * GJS + col0 / 2 + i] = nv;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" :: "r"(tmem));
+  if (ok && (role[0] == 1 && 2 * p == k + 1 && J == k + 1 || role[1] == 1 && 2 * p + 1 == k + 1 && J == k + 1)) {
+    sweep_block64(sw, sw + GJB * GJS);
+    for (int q = tid; q < GJB * GJB; q += 256) Pnext[q] = sw[(q / GJB) * GJS + q % GJB];
+  }
+}
+
 // Work layout: P[2][64 x 64] (pivot inverse, double-buffered by pivot parity),
 // Cold [N][64], Cn [N][64], Rp [64][N].
 static void gj_work_split(void* work, int N, float2** Pb, float2** Cold, float2** Cn, float2** Rp) {
@@ -1190,6 +1454,29 @@ cudaError_t gauss_jordan_panel(void* M, int N, int k, void* work, cudaStream_t s
   const int nb = N / GJB;
   k_gj_panel<<<dim3(2 * nb, GJB / 16), 256, 2 * GJB * GJS * sizeof(float2), s>>>(
       (const float2*)M, N, k, Pb[k & 1], Cold, Cn, Rp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Tall tiles of a pivot step: sum over row pairs p of min(2p + 2, nt).
+static int tc_tile_count(int nt) {
+  int c = 0;
+  for (int p = 0; p < (nt + 1) / 2; ++p) c += std::min(2 * p + 2, nt);
+  return c;
+}
+
+cudaError_t gauss_jordan_update_tc(void* M, int N, int k, void* work, cudaStream_t s) {
+  float2 *Pb[2], *Cold, *Cn, *Rp;
+  gj_work_split(work, N, Pb, &Cold, &Cn, &Rp);
+  const int nb = N / GJB;
+  const size_t sm = 4 * TC_OPF * sizeof(float) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  k_gj_update_tc<<<tc_tile_count(nb), 256, sm, s>>>((float2*)M, N, k, Pb[k & 1], Pb[(k + 1) & 1],
+                                                    Cold, Cn, Rp, (int*)(Rp + (long long)GJB * N));
   count_launch();
   return cudaGetLastError();
 }

@@ -403,11 +403,21 @@ void build_coarsest(mg_handle* h) {
   ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
   {
     ProfScope prof(h, MG_KF_INVERSE);
+    const bool tc = h->p.coarsest_gj_tcgen05 != 0;
+    int* gj_err = (int*)(h->gj_work + (size_t)3 * h->ldc * 64 + 2 * 64 * 64);
+    if (tc) ck(h, cudaMemsetAsync(gj_err, 0, sizeof(int), h->s), "memset");
     ck(h, gauss_jordan_begin(h->Binv, h->ldc, h->gj_work, h->s), "gauss-jordan");
     for (int k = 0; k < h->ldc / 64; ++k) {
       ck(h, gauss_jordan_panel(h->Binv, h->ldc, k, h->gj_work, h->s), "gauss-jordan panel");
       ProfScope pu(h, MG_KF_GJ_UPDATE);
-      ck(h, gauss_jordan_update(h->Binv, h->ldc, k, h->gj_work, h->s), "gauss-jordan update");
+      ck(h, tc ? gauss_jordan_update_tc(h->Binv, h->ldc, k, h->gj_work, h->s)
+               : gauss_jordan_update(h->Binv, h->ldc, k, h->gj_work, h->s), "gauss-jordan update");
+    }
+    if (tc) {
+      int e = 0;
+      ck(h, cudaMemcpyAsync(&e, gj_err, sizeof(int), cudaMemcpyDeviceToHost, h->s), "read");
+      sync(h);
+      if (e) fail(h, MG_ERR_TIMEOUT, "tensor-core Gauss-Jordan update: completion wait ran out");
     }
     ck(h, pack_hermitian(h->Binv, h->Bpk, h->ldc, h->s), "pack");
   }
@@ -855,7 +865,7 @@ void allocate_storage(mg_handle* h) {
     h->dense = h->Nc <= P.coarsest_dense_max;
     if (h->dense) {
       h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
-      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64) * sizeof(float2));
+      h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64 + 2) * sizeof(float2));
       h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
       const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
       h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
@@ -914,6 +924,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->max_rhs = 1;
   p->profile = 0;
   p->coarsest_dense_max = (int)MG_DENSE_MAX;
+  p->coarsest_gj_tcgen05 = 0;
   return MG_OK;
 }
 

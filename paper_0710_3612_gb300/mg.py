@@ -35,7 +35,7 @@ class MgParams(ctypes.Structure):
                 ("coarsest_tol", ctypes.c_double), ("coarsest_refine_max", ctypes.c_int),
                 ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int),
-                ("coarsest_dense_max", ctypes.c_int)]
+                ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):
