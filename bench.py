@@ -759,7 +759,8 @@ def ncu_case(args):
         nd = torch.from_numpy(noise).to(dev)
         h = mg.mg_setup(torch.from_numpy(U).to(dev), masses[0],
                         mg.make_params(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], nd,
-                                       setup_sweeps=wl["setup_sweeps"]), stream)
+                                       setup_sweeps=wl["setup_sweeps"],
+                                       coarsest_gj_tcgen05=int(args.gj_tcgen05)), stream)
         if args.ncu_case in ("coarse", "coarse_mma"):
             nrhs = 64 if args.ncu_case == "coarse_mma" else 1
             Lx, Lt, n, _ = mg.mg_get_level(h, 2)
@@ -806,6 +807,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
+    ap.add_argument("--gj-tcgen05", action="store_true",
+                    help="with --ncu-case: coarsest inverse updates on tcgen05 tensor cores")
     ap.add_argument("--phase-launches", action="store_true",
                     help="with --timed-only: library kernel launches counted at the end of each "
                          "phase (setup, re-mass, solve) of the first timed step")
