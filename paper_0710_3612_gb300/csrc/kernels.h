@@ -181,8 +181,9 @@ cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int
 // then their fixed-order sum per row into y.
 cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
                                  void* part, cudaStream_t s);
+// y32 (optional, complex64 [nrhs][N]) receives an FP32 copy of y.
 cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
-                                  bool accumulate, cudaStream_t s);
+                                  bool accumulate, cudaStream_t s, void* y32 = nullptr);
 
 // index map for tests
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,

@@ -1735,15 +1735,18 @@ __global__ void __launch_bounds__(64) k_hgemv_warp(const float2* __restrict__ P,
 // 64-wide tile row in order; the quarters are added in a fixed order.
 __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__ part,
                                                       double2* __restrict__ y, int N, int nt,
-                                                      bool accumulate) {
+                                                      bool accumulate,
+                                                      float2* __restrict__ y32) {
   __shared__ float2 red[4][HT];
   const int I = blockIdx.x, rr = threadIdx.x % HT, g = threadIdx.x / HT;
   part += (long long)blockIdx.y * (nt * (nt + 1) / 2) * 2 * HT;
   y += (long long)blockIdx.y * N;
   float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
   for (int J = g; J < nt; J += 4) {
-    if (J <= I) acc = cadd(acc, part[(2LL * (I * (I + 1) / 2 + J)) * HT + rr]);
-    else acc = cadd(acc, part[(2LL * (J * (J + 1) / 2 + I) + 1) * HT + rr]);
+    const long long o = J <= I ? (2LL * (I * (I + 1) / 2 + J)) * HT + rr
+                               : (2LL * (J * (J + 1) / 2 + I) + 1) * HT + rr;
+    acc = cadd(acc, part[o]);
   }
   red[g][rr] = acc;
   __syncthreads();
@@ -1756,6 +1759,7 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
     double2 v = make_double2(a.x, a.y);
     if (accumulate) { v.x += y[row].x; v.y += y[row].y; }
     y[row] = v;
+    if (y32) y32[(long long)blockIdx.y * N + row] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -1783,11 +1787,11 @@ cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, in
 }
 
 cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
-                                  bool accumulate, cudaStream_t s) {
+                                  bool accumulate, cudaStream_t s, void* y32) {
   if (ld % HT || ld < N) return cudaErrorInvalidValue;
   const int nt = ld / HT;
   k_hgemv_reduce<<<dim3(nt, nrhs), 256, 0, s>>>((const float2*)part, (double2*)y, N, nt,
-                                                accumulate);
+                                                accumulate, (float2*)y32);
   count_launch();
   return cudaGetLastError();
 }

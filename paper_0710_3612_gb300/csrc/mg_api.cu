@@ -235,25 +235,28 @@ void coarsest_cg(mg_handle* h, const double2* b, double2* x, int iters, int nrhs
 
 // Dense path: FP32 explicit inverse refined in FP64.  x = B b; then `steps`
 // times: r = b - A_L x (FP64 stencil), x += B r; for nrhs vectors [nrhs][N].
-void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs) {
+// x32 (optional): an FP32 copy of the result, written by the last step.
+void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs,
+                      void* x32 = nullptr) {
   ProfScope prof(h, MG_KF_COARSEST);
   if (!h->dense) {
     coarsest_cg(h, b, x, h->ccg_iters, nrhs);
+    if (x32) ck(h, convert_f64_f32(x, x32, (long long)h->Nc * nrhs, h->s), "coarsest out");
     return;
   }
-  auto gemv = [&](const double2* in, bool accumulate) {
+  auto gemv = [&](const double2* in, bool accumulate, void* out32) {
     {
       ProfScope pd(h, MG_KF_DENSE);
       ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s),
          "coarsest gemv");
     }
-    ck(h, hermitian_gemv_reduce(h->gemv_part, x, h->Nc, h->ldc, nrhs, accumulate, h->s),
+    ck(h, hermitian_gemv_reduce(h->gemv_part, x, h->Nc, h->ldc, nrhs, accumulate, h->s, out32),
        "coarsest gemv reduce");
   };
-  gemv(b, false);
+  gemv(b, false, steps == 0 ? x32 : nullptr);
   for (int it = 0; it < steps; ++it) {
     apply_level<double>(h, h->L - 1, x, h->cr, nrhs, W_F64, ep_lincomb(-1.0, b, 1.0));
-    gemv(h->cr, true);
+    gemv(h->cr, true, it + 1 == steps ? x32 : nullptr);
   }
 }
 
@@ -269,8 +272,7 @@ void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
     } else {
       const long long c = (long long)h->Nc * nrhs;
       ck(h, convert_f32_f64(b, h->cb, c, h->s), "coarsest in");
-      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs);
-      ck(h, convert_f64_f32(h->cx, x, c, h->s), "coarsest out");
+      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs, x);
     }
     return;
   }
