@@ -143,3 +143,31 @@ def test_cfg_128x128_mass_sweep(mg):
             assert np.linalg.norm(got - x_ora) <= (kappa * TOL + 1e-12) * np.linalg.norm(x_ora)
             if solver == mg.SOLVER_MGCG_FP64:
                 assert abs(infos[0].iterations - it10) <= 1
+
+
+def test_cfg_1024x1024_four_level_16_rhs(mg):
+    """1024 x 1024, beta = 10 (500 checkerboard sweeps), four levels (4x4, 2x2,
+    2x2), Nv = 12, 16 right-hand sides in one batched mixed solve; the
+    coarsest level (64 x 64 x 24 = 98304 unknowns) is solved by FP64 CG.  At
+    m = -1.9 (between the heavy masses and the critical region; the
+    near-critical mass needs about 200 ms per outer iteration here, too slow
+    for a test).  The oracle checks D^dagger per element on two right-hand
+    sides and every solution's true residual."""
+    L, blocks, Nv, nrhs, m = 1024, [(4, 4), (2, 2), (2, 2)], [12, 12, 12], 16, -1.9
+    U = W.quenched_u1(L, L, 10.0, 500, 1)
+    noise = W.setup_noise(L, L, blocks, Nv, 7)
+    chis = np.stack([W.gaussian_field((L, L, 2), 1101 + k) for k in range(nrhs)])
+    with mg.Multigrid(dev(U), m, blocks, Nv, dev(noise), setup_sweeps=8, max_rhs=nrhs) as s:
+        assert s.level(4)[0] * s.level(4)[1] * s.level(4)[2] == 98304
+        b_d = torch.empty((nrhs, L, L, 2), dtype=torch.complex128, device=DEV)
+        mg.mg_apply_D(s.h, dev(chis), b_d, nrhs, 1, mg.PREC_F64)
+        b = host(b_d)
+        for k in (0, nrhs - 1):
+            want = ow.apply_D(U, m, chis[k], dagger=True)
+            assert np.max(np.abs(b[k] - want)) <= 1e-12 * np.max(np.abs(want))
+        x, infos = s.solve(b_d, tol=TOL, maxiter=5000, solver=mg.SOLVER_MGCG_MIXED)
+        got = host(x).reshape(b.shape)
+    for k in range(nrhs):
+        res = np.linalg.norm(b[k] - ow.apply_A(U, m, got[k])) / np.linalg.norm(b[k])
+        assert res <= TOL and infos[k].true_residual <= TOL
+        assert abs(infos[k].true_residual - res) <= 1e-3 * TOL
