@@ -179,8 +179,10 @@ cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int
                                void* part, bool accumulate, cudaStream_t s);
 // The two launches of hermitian_gemv_f32: partial products per stored tile,
 // then their fixed-order sum per row into y.
+// xscratch (optional, nrhs * ld complex64): with 16..64 vectors the tile
+// products run on tensor cores from an FP32 copy of x held there.
 cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
-                                 void* part, cudaStream_t s);
+                                 void* part, cudaStream_t s, void* xscratch = nullptr);
 // y32 (optional, complex64 [nrhs][N]) receives an FP32 copy of y.
 cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
                                   bool accumulate, cudaStream_t s, void* y32 = nullptr);

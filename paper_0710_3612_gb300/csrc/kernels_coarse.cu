@@ -1566,6 +1566,125 @@ cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Tensor-core variant for 16..64 right-hand sides: per stored tile T (64 x 64
+// complex) the row products T X_J and, off the diagonal, the column products
+// T^H X_I, as realified GEMMs on mma.sync m16n8k8 TF32 with three products per
+// FP32-accurate product (the layout and fragment mapping of k_gj_update: A =
+// T rows, or T^H built from T's columns with the imaginary part negated; B =
+// X realified, rows k of the tile, columns = right-hand sides).  X comes as an
+// FP32 copy xs [nrhs][ld] (zero beyond N); right-hand sides are padded to a
+// multiple of 16 with zeros (warps whose 16 columns are all padding skip the
+// products).  Partial sums go to the buffer layout of k_hgemv_tiles.
+__global__ void __launch_bounds__(256) k_hgemv_mma(const float2* __restrict__ P,
+                                                   const float2* __restrict__ xs, int ld,
+                                                   int ntiles, int nrhs,
+                                                   float2* __restrict__ part) {
+  extern __shared__ float2 hsm[];
+  float2* sT = hsm;                                      // [64][GJC]
+  float2* sXJ = sT + HT * GJC;                           // [64 k][GJR]: X_J[k][rhs]
+  float2* sXI = sXJ + HT * GJR;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= k) ++I;
+  while (I * (I + 1) / 2 > k) --I;
+  const int J = k - I * (I + 1) / 2;
+  {
+    const float4* src = (const float4*)(P + (long long)k * HT * HT);
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = src[tid + 256 * u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = 2 * (tid + 256 * u), r = e / HT, c = e % HT;
+      *(float4*)&sT[r * GJC + c] = v[u];
+    }
+  }
+  for (int e = tid; e < HT * HT; e += 256) {             // rhs r = e / 64, row kk = e % 64
+    const int r = e / HT, kk = e % HT;
+    float2 xj = make_float2(0.f, 0.f), xi = make_float2(0.f, 0.f);
+    if (r < nrhs) {
+      xj = xs[(long long)r * ld + J * HT + kk];
+      xi = xs[(long long)r * ld + I * HT + kk];
+    }
+    sXJ[kk * GJR + r] = xj;
+    sXI[kk * GJR + r] = xi;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;
+  const bool active = 16 * wn < nrhs;                    // warp-uniform: its 16 RHS exist
+  const float* sTf = (const float*)sT;
+  for (int pass = 0; pass < (I == J ? 1 : 2) && active; ++pass) {  // 0: T X_J, 1: T^H X_I
+    const float2* sX = pass ? sXI : sXJ;
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[mt][n][e] = 0.f;
+#pragma unroll 2
+    for (int kk = 0; kk < 2 * HT / 8; ++kk) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int m = 32 * wm + 16 * mt + g;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int mm = m + 8 * (f & 1), kr = 8 * kk + tq + 4 * (f >> 1);
+          float a;
+          if (pass == 0) {
+            a = sTf[mm * 2 * GJC + kr];                      // T[m][kr/2], (re, im) along K
+          } else {
+            const float2 t = sT[(kr >> 1) * GJC + mm];       // conj(T[kr/2][m])
+            a = (kr & 1) ? -t.y : t.x;
+          }
+          split_tf32(a, ah[mt][f], al[mt][f]);
+        }
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const int j = 16 * wn + 4 * n + (g >> 1), d = g & 1;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int kr = 8 * kk + tq + 4 * hh;
+          const float2 v = sX[(kr >> 1) * GJR + j];
+          const float x = (kr & 1) ? (d ? v.x : -v.y) : (d ? v.y : v.x);
+          split_tf32(x, bh[n][hh], bl[n][hh]);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          mma_tf32(acc[mt][n], al[mt], bh[n]);
+          mma_tf32(acc[mt][n], ah[mt], bl[n]);
+          mma_tf32(acc[mt][n], ah[mt], bh[n]);
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int m = 32 * wm + 16 * mt + g + 8 * hh, r = 16 * wn + 4 * n + tq;
+          if (r < nrhs)
+            part[(long long)r * ntiles * 2 * HT + (2LL * k + pass) * HT + m] =
+                make_float2(acc[mt][n][2 * hh], acc[mt][n][2 * hh + 1]);
+        }
+  }
+}
+
+__global__ void k_x32_pad(const double2* __restrict__ x, float2* __restrict__ xs, int N, int ld,
+                          int nrhs) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ld * nrhs) return;
+  const int r = (int)(i / ld), c = (int)(i % ld);
+  const double2 v = c < N ? x[(long long)r * N + c] : make_double2(0.0, 0.0);
+  xs[i] = make_float2((float)v.x, (float)v.y);
+}
+
 __global__ void __launch_bounds__(256) k_hgemv_tiles(const float2* __restrict__ P,
                                                      const double2* __restrict__ x, int N,
                                                      int nrhs, float2* __restrict__ part) {
@@ -1764,9 +1883,25 @@ __global__ void __launch_bounds__(256) k_hgemv_reduce(const float2* __restrict__
 }
 
 cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
-                                 void* part, cudaStream_t s) {
+                                 void* part, cudaStream_t s, void* xscratch) {
   if (ld % HT || ld < N) return cudaErrorInvalidValue;
   const int nt = ld / HT, ntiles = nt * (nt + 1) / 2;
+  if (nrhs >= 16 && nrhs <= 64 && xscratch) {   // tensor cores
+    const long long n = (long long)ld * nrhs;
+    k_x32_pad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2*)x, (float2*)xscratch, N,
+                                                        ld, nrhs);
+    count_launch();
+    const size_t sm = (size_t)HT * (GJC + 2 * GJR) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_hgemv_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_hgemv_mma<<<ntiles, 256, sm, s>>>((const float2*)P, (const float2*)xscratch, ld, ntiles,
+                                        nrhs, (float2*)part);
+    count_launch();
+    return cudaGetLastError();
+  }
   if (nrhs <= 4) {                               // streamed from global, one warp per tile
     const dim3 grid(ntiles);
     if (nrhs == 1)
@@ -1798,7 +1933,7 @@ cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int 
 
 cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int ld, int nrhs,
                                void* part, bool accumulate, cudaStream_t s) {
-  cudaError_t e = hermitian_gemv_tiles(P, x, N, ld, nrhs, part, s);
+  cudaError_t e = hermitian_gemv_tiles(P, x, N, ld, nrhs, part, s, nullptr);
   if (e != cudaSuccess) return e;
   return hermitian_gemv_reduce(part, y, N, ld, nrhs, accumulate, s);
 }

@@ -247,7 +247,7 @@ void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int
   auto gemv = [&](const double2* in, bool accumulate, void* out32) {
     {
       ProfScope pd(h, MG_KF_DENSE);
-      ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s),
+      ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s, h->gemv_x),
          "coarsest gemv");
     }
     ck(h, hermitian_gemv_reduce(h->gemv_part, x, h->Nc, h->ldc, nrhs, accumulate, h->s, out32),
@@ -868,7 +868,7 @@ void allocate_storage(mg_handle* h) {
     if (h->dense) {
       h->Binv = dalloc<float2>(h, (size_t)h->ldc * h->ldc * sizeof(float2));
       h->gj_work = dalloc<float2>(h, ((size_t)3 * h->ldc * 64 + 2 * 64 * 64 + 2) * sizeof(float2));
-      h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * sizeof(float2));
+      h->gemv_x = dalloc<float2>(h, (size_t)h->ldc * h->R * sizeof(float2));
       const size_t nt = h->ldc / 64, ntiles = nt * (nt + 1) / 2;
       h->Bpk = dalloc<float2>(h, ntiles * 64 * 64 * sizeof(float2));
       h->gemv_part = dalloc<float2>(h, ntiles * 2 * 64 * h->R * sizeof(float2));
