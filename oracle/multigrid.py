@@ -30,7 +30,7 @@ Readings of the paper taken here (each listed in the design notes):
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 import scipy.linalg as sla
@@ -293,29 +293,49 @@ def setup(U: np.ndarray, m: float, blocks, Nv, noise: np.ndarray, sweeps: int = 
     """
     _, Lt, Lx = U.shape
     levels = [Level(WilsonNormalOp(U, m), Lx, Lt, 2)]
+    _build_levels(levels, blocks, Nv, noise, sweeps, power_iters)
+    H = Hierarchy(levels, float(m), U, omega_mr=omega_mr, coarsest_dense_max=coarsest_dense_max)
+    _finish_levels(H)
+    return H
+
+
+def _build_levels(levels, blocks, Nv, noise, sweeps, power_iters, given=None):
+    """Level-by-level body of the setup, from level len(levels) - 1 down.
+    With `given` = (E, omega_relax, eta) the first level built takes the
+    vectors E instead of relaxing random starts and keeps the given relaxation
+    step and smoother start.  `noise` keeps the layout of
+    ``workloads.setup_noise`` for the full (blocks, Nv); the parts of the
+    levels not relaxed here are skipped."""
+    first = len(levels) - 1
     pos = 0
     for l, ((bx, bt), nv) in enumerate(zip(blocks, Nv)):
+        if l < first:
+            lv = levels[l]
+            pos += (nv + 2) * lv.Lt * lv.Lx * lv.n
+            continue
         lv = levels[l]
         size = lv.Lt * lv.Lx * lv.n
-        starts = noise[pos:pos + nv * size].reshape(nv, lv.Lt, lv.Lx, lv.n)
-        pos += nv * size
-        pw = noise[pos:pos + size].reshape(lv.Lt, lv.Lx, lv.n)
-        pos += size
-        lv.eta = noise[pos:pos + size].reshape(lv.Lt, lv.Lx, lv.n).copy()
-        pos += size
-        lam = power_lambda_max(lv.op.apply, pw, power_iters)
-        lv.omega_relax = 1.0 / lam
-        E = starts.copy()
-        for _ in range(sweeps):
-            E = E - lv.omega_relax * lv.op.apply(E)
+        if l == first and given is not None:
+            pos += (nv + 2) * size
+            E, lv.omega_relax, eta = given
+            lv.eta = eta.copy()
+        else:
+            starts = noise[pos:pos + nv * size].reshape(nv, lv.Lt, lv.Lx, lv.n)
+            pos += nv * size
+            pw = noise[pos:pos + size].reshape(lv.Lt, lv.Lx, lv.n)
+            pos += size
+            lv.eta = noise[pos:pos + size].reshape(lv.Lt, lv.Lx, lv.n).copy()
+            pos += size
+            lam = power_lambda_max(lv.op.apply, pw, power_iters)
+            lv.omega_relax = 1.0 / lam
+            E = starts.copy()
+            for _ in range(sweeps):
+                E = E - lv.omega_relax * lv.op.apply(E)
         lv.E = E
         lv.V = block_orthonormalise(E, bx, bt)
         lv.bx, lv.bt, lv.Nv = bx, bt, nv
         coarse = galerkin(lv.op, lv.V, bx, bt)
         levels.append(Level(coarse, lv.Lx // bx, lv.Lt // bt, 2 * nv))
-    H = Hierarchy(levels, float(m), U, omega_mr=omega_mr, coarsest_dense_max=coarsest_dense_max)
-    _finish_levels(H)
-    return H
 
 
 def _finish_levels(H: Hierarchy):
@@ -374,3 +394,58 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     x = x + prolong(lv.V, lv.bx, lv.bt, ec)
     x = x + smooth(lv, b - lv.op.apply(x))
     return x
+
+
+# ---------------------------------------------------------------------------
+# Adaptive refinement by V-cycles (Sec. 3, the adaptive step after the first
+# vector set)
+# ---------------------------------------------------------------------------
+def vcycle_error_propagation(H: Hierarchy, e0: np.ndarray, ncycles: int, level: int = 0) -> np.ndarray:
+    """The V-cycle of level `level` applied to an error with no source,
+    `ncycles` times (Sec. 3): one cycle on A_l x = 0 from x = -e leaves the
+    error e <- e - V_l(A_l e), with V_l the V-cycle of Sec. 2 from level l down
+    as a linear map of its right-hand side."""
+    A = H.levels[level].op.apply
+    e = e0.copy()
+    for _ in range(ncycles):
+        e = e - vcycle(H, A(e), level)
+    return e
+
+
+def energy_norm(H: Hierarchy, e: np.ndarray, level: int = 0) -> float:
+    """|e|_A = sqrt(<e, A_l e>)."""
+    return float(np.sqrt(vdot(e, H.levels[level].op.apply(e)).real))
+
+
+def refine(H: Hierarchy, e0: np.ndarray, ncycles: int, noise: np.ndarray, level: int = 0,
+           sweeps: int = 8, power_iters: int = 30):
+    """One adaptive pass on level `level` (Sec. 3; recursive for coarser
+    levels): run `ncycles` V-cycles of that level on the random error e0; the
+    error e'' that survives is restricted to every block S_j, made orthogonal
+    there (per chirality) to the block's current vectors, normalised, and
+    appended as vector Nv_l + 1 of the level.  Finer levels are kept; the level
+    keeps its relaxation step and smoother start; the Galerkin operators below
+    it, the coarser levels' vectors (first-pass setup on the new coarse
+    operators, from `noise` laid out as ``workloads.setup_noise`` for the
+    refined Nv), the smoothers and the coarsest factor are rebuilt.
+
+    Returns (H', e'', rho) with rho = (|e''|_A / |e0|_A)^(1/ncycles), the
+    measured error reduction per cycle of the level's V-cycle in H.
+    """
+    if not 0 <= level < H.L - 1:
+        raise ValueError("level must have a coarser level below it")
+    e = vcycle_error_propagation(H, e0, ncycles, level)
+    rho = (energy_norm(H, e, level) / energy_norm(H, e0, level)) ** (1.0 / ncycles)
+    blocks = [(lv.bx, lv.bt) for lv in H.levels[:-1]]
+    Nv = [lv.Nv for lv in H.levels[:-1]]
+    Nv[level] += 1
+    lv = H.levels[level]
+    E = np.concatenate([lv.V, e[None]], axis=0)
+    levels = [replace(x) for x in H.levels[:level]]
+    levels.append(Level(lv.op if level > 0 else WilsonNormalOp(H.U, H.m), lv.Lx, lv.Lt, lv.n))
+    _build_levels(levels, blocks, Nv, noise, sweeps, power_iters,
+                  given=(E, lv.omega_relax, lv.eta))
+    H2 = Hierarchy(levels, H.m, H.U, omega_mr=H.omega_mr,
+                   coarsest_dense_max=H.coarsest_dense_max, coarsest_tol=H.coarsest_tol)
+    _finish_levels(H2)
+    return H2, e, float(rho)
