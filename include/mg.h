@@ -169,6 +169,36 @@ mg_status mg_device_bytes(const mg_handle* h, long long* bytes);
  * may be in use on another thread meanwhile (it is only read). */
 mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** out);
 
+/* Adaptive refinement by V-cycles (Sec. 3, the adaptive step that follows the
+ * first vector set), one pass on `level` (1 = finest .. nlevels - 1).
+ * The V-cycle of that level (FP64, the preconditioner of MG_SOLVER_MGCG_FP64
+ * from that level down) is applied `ncycles` times to the error e0 with no
+ * source: e <- e - V_l(A_l e).  The error e'' that survives becomes one more
+ * vector of the level: restricted to each block, made orthogonal there (per
+ * chirality, modified Gram-Schmidt) to the block's current vectors and
+ * normalised.  *out receives a new hierarchy at src's mass and parameters
+ * with Nv[level - 1] + 1: finer levels copied from src, the level's vectors
+ * extended by e'', the Galerkin operators below rebuilt, the coarser levels'
+ * vectors set up again by relaxation (Eq. relax) on the new coarse operators
+ * from `noise`, then the smoothers and the coarsest solver.
+ *   e0:     device complex128 level vector [Lt_l][Lx_l][ndof_l], read only.
+ *   noise:  device complex128, laid out as mg_params.setup_noise for the
+ *           refined Nv (mg_setup_noise_len of the refined parameters); the
+ *           parts of levels <= `level` are not read.  May be NULL when
+ *           level = nlevels - 1 (nothing below is relaxed).
+ *   rho:    (host, may be NULL) (|e''|_A / |e0|_A)^(1 / ncycles), the measured
+ *           error reduction per cycle of src's V-cycle on that level.
+ *   e_out:  (device, may be NULL) receives e''.
+ * src is not changed but its stream and work vectors are used (no concurrent
+ * use of src); the new handle runs on `stream` and owns its memory (free with
+ * mg_destroy).  The scratch (Nv + 3 level vectors and Nv coarse vectors) is
+ * allocated and freed inside the call.  MG_ERR_ARG on a bad level, ncycles < 1
+ * or an Nv above the limits of mg_setup; MG_ERR_BREAKDOWN when e'' lies in the
+ * span of the current vectors on some block (Gram-Schmidt breakdown) or
+ * |e0|_A = 0. */
+mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, const void* noise,
+                    void* stream, mg_handle** out, double* rho, void* e_out);
+
 /* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
  * b, x: device complex128 [nrhs][Lt][Lx][2].  Right-hand sides are solved in
  * batches of params->max_rhs that share one Krylov loop (one operator and

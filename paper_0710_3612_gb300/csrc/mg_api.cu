@@ -901,6 +901,66 @@ long long setup_temp_bytes(const mg_handle* h) {
   return t;
 }
 
+// Galerkin operator of level l + 1 from the vectors of level l (FP64 master only).
+void galerkin_next(mg_handle* h, int l) {
+  Level& L = h->lv[l];
+  Level& C = h->lv[l + 1];
+  if (l == 0)
+    ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin_fine");
+  else
+    ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin_coarse");
+}
+
+// One level of the adaptive setup (Sec. 3): with E = NULL, Nv random starts
+// from `noise` (then the power-iteration start and the smoother start) are
+// relaxed with Eq. relax; with E given (Nv full level vectors), the level takes
+// them as they are and keeps the relaxation step and smoother start it holds.
+// The vectors are split by chirality and block-orthonormalised (FP64), and the
+// Galerkin operator of the next level is built from them.
+void build_level(mg_handle* h, int l, const double2* noise, const void* Egiven) {
+  Level& L = h->lv[l];
+  const long long c = L.count();
+  void* E = nullptr;
+  void* T = nullptr;
+  if (!Egiven) {
+    const double2* starts = noise;
+    const double2* pw = noise + (size_t)L.Nv * c;
+    ck(h, cudaMemcpyAsync(L.eta, pw + c, c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy eta");
+    // relaxation step from lambda_max (power iteration)
+    L.lambda_max = power_lambda_max(h, l, pw, L.w64[1], L.w64[2]);
+    if (!(L.lambda_max > 0.0)) fail(h, MG_ERR_BREAKDOWN, "power iteration gave lambda_max <= 0");
+    L.omega_relax = 1.0 / L.lambda_max;
+    // Eq. relax: e <- (1 - omega A) e, nu sweeps, all Nv vectors at once
+    E = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
+    T = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
+    ck(h, cudaMemcpyAsync(E, starts, (size_t)L.Nv * c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    for (int sw = 0; sw < h->p.setup_sweeps; ++sw) {
+      apply_level<double>(h, l, E, T, L.Nv, W_F64);
+      ck(h, axpby<double>(-L.omega_relax, T, 1.0, E, c, L.Nv, h->s), "relax");
+    }
+  }
+  // chirality split + block Gram-Schmidt (FP64)
+  ck(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s), "memset");
+  ck(h, block_gram_schmidt(Egiven ? Egiven : E, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1e-14,
+                           h->dflag, h->s), "gram-schmidt");
+  int flag = 0;
+  ck(h, cudaMemcpyAsync(h->hscal, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+  sync(h);
+  std::memcpy(&flag, h->hscal, sizeof(int));
+  if (flag) fail(h, MG_ERR_BREAKDOWN, "block Gram-Schmidt breakdown at level " + std::to_string(l + 1));
+  ck(h, convert_f64_f32(L.Vst64, L.Vst32, (long long)L.V * 2 * L.Nv * (L.n / 2), h->s), "convert");
+  // Galerkin operator of the next level (needed before relaxing on it)
+  galerkin_next(h, l);
+  sync(h);
+  if (E) {
+    for (auto& a : h->allocs)
+      if (a == E || a == T) a = nullptr;
+    cudaFree(E);
+    cudaFree(T);
+    h->bytes -= 2LL * L.Nv * c * (long long)sizeof(double2);
+  }
+}
+
 }  // namespace
 
 // =============================================================================
@@ -975,47 +1035,8 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
     const double2* noise = (const double2*)P.setup_noise;
     size_t pos = 0;
     for (int l = 0; l + 1 < h->L; ++l) {
-      Level& L = h->lv[l];
-      const long long c = L.count();
-      const double2* starts = noise + pos;
-      pos += (size_t)L.Nv * c;
-      const double2* pw = noise + pos;
-      pos += c;
-      ck(h, cudaMemcpyAsync(L.eta, noise + pos, c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy eta");
-      pos += c;
-      // relaxation step from lambda_max (power iteration)
-      L.lambda_max = power_lambda_max(h, l, pw, L.w64[1], L.w64[2]);
-      if (!(L.lambda_max > 0.0)) fail(h, MG_ERR_BREAKDOWN, "power iteration gave lambda_max <= 0");
-      L.omega_relax = 1.0 / L.lambda_max;
-      // Eq. relax: e <- (1 - omega A) e, nu sweeps, all Nv vectors at once
-      void* E = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
-      void* T = dalloc(h, (size_t)L.Nv * c * sizeof(double2));
-      ck(h, cudaMemcpyAsync(E, starts, (size_t)L.Nv * c * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-      for (int sw = 0; sw < P.setup_sweeps; ++sw) {
-        apply_level<double>(h, l, E, T, L.Nv, W_F64);
-        ck(h, axpby<double>(-L.omega_relax, T, 1.0, E, c, L.Nv, h->s), "relax");
-      }
-      // chirality split + block Gram-Schmidt (FP64)
-      ck(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->s), "memset");
-      ck(h, block_gram_schmidt(E, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, 1e-14, h->dflag, h->s), "gram-schmidt");
-      int flag = 0;
-      ck(h, cudaMemcpyAsync(h->hscal, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
-      sync(h);
-      std::memcpy(&flag, h->hscal, sizeof(int));
-      if (flag) fail(h, MG_ERR_BREAKDOWN, "block Gram-Schmidt breakdown at level " + std::to_string(l + 1));
-      ck(h, convert_f64_f32(L.Vst64, L.Vst32, (long long)L.V * 2 * L.Nv * (L.n / 2), h->s), "convert");
-      // Galerkin operator of the next level (needed before relaxing on it)
-      Level& C = h->lv[l + 1];
-      if (l == 0)
-        ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin_fine");
-      else
-        ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin_coarse");
-      sync(h);
-      for (auto& a : h->allocs)
-        if (a == E || a == T) a = nullptr;
-      cudaFree(E);
-      cudaFree(T);
-      h->bytes -= 2LL * L.Nv * c * (long long)sizeof(double2);
+      build_level(h, l, noise + pos, nullptr);
+      pos += (size_t)(h->lv[l].Nv + 2) * h->lv[l].count();
     }
     set_mass_internal(h, mass);
   });
@@ -1083,6 +1104,129 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
     }
     set_mass_internal(h, mass);
   });
+  if (st != MG_OK) {
+    g_last_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return MG_OK;
+}
+
+mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, const void* noise,
+                    void* stream, mg_handle** out, double* rho, void* e_out) {
+  if (!out) { g_last_error = "out is NULL"; return MG_ERR_ARG; }
+  *out = nullptr;
+  if (!src || !e0 || ncycles < 1 || level < 1 || level >= src->L) {
+    g_last_error = "invalid refine arguments (level must be in [1, nlevels - 1], ncycles >= 1)";
+    return MG_ERR_ARG;
+  }
+  const int lr = level - 1;
+  if (!noise && lr + 2 < src->L) { g_last_error = "noise is NULL but coarser levels are relaxed"; return MG_ERR_ARG; }
+  mg_params P = src->p;
+  P.Nv[lr] += 1;
+  P.profile = 0;
+  P.setup_noise = noise ? noise : (const void*)src;   // not read when NULL was allowed
+  std::string msg;
+  mg_status v = validate(&P, msg);
+  if (v != MG_OK) { g_last_error = msg; return v; }
+  const Level& S = src->lv[lr];
+  const long long c = S.count();
+  const int nv0 = S.Nv;
+  const Level& SC = src->lv[lr + 1];
+  const long long cc = SC.count();
+  // scratch: E = the nv0 current vectors of the level, then the surviving
+  // error e''; then two level vectors, then nv0 coarse indicator vectors
+  void* E = nullptr;
+  if (cudaMalloc(&E, ((size_t)(nv0 + 3) * c + (size_t)nv0 * cc) * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "device allocation failed (refine scratch)";
+    return MG_ERR_NOMEM;
+  }
+  double2* Ek = (double2*)E;
+  double2* e = Ek + (size_t)nv0 * c;
+  double2* t = e + c;
+  double2* z = t + c;
+  double2* dind = z + c;
+  // 1. V-cycles of the level on the error, no source (Sec. 3)
+  double a0 = 0.0, a1 = 0.0;
+  mg_status st = guarded(src, [&]() {
+    ck(src, cudaMemcpyAsync(e, e0, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e0");
+    apply_level<double>(src, lr, e, t, 1, W_F64);
+    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
+    a0 = read_scalar(src, S_T0);
+    for (int k = 0; k < ncycles; ++k) {
+      if (k) apply_level<double>(src, lr, e, t, 1, W_F64);
+      vcycle<double>(src, lr, t, z, 1);
+      ck(src, axpby<double>(-1.0, z, 1.0, e, c, 1, src->s), "e -= V A e");
+    }
+    apply_level<double>(src, lr, e, t, 1, W_F64);
+    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
+    a1 = read_scalar(src, S_T0);
+    if (!(a0 > 0.0) || !(a1 == a1)) fail(src, MG_ERR_BREAKDOWN, "refine: |e0|_A = 0 or non-finite error");
+    if (e_out) ck(src, cudaMemcpyAsync(e_out, e, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e''");
+    // the level's current vectors as full level vectors: v_k = P (1_{s=k} + 1_{s=Nv+k})
+    std::vector<double2> ind((size_t)nv0 * cc, make_double2(0.0, 0.0));
+    for (int k = 0; k < nv0; ++k)
+      for (long long j = 0; j < SC.V; ++j) {
+        ind[(size_t)k * cc + j * SC.n + k] = make_double2(1.0, 0.0);
+        ind[(size_t)k * cc + j * SC.n + nv0 + k] = make_double2(1.0, 0.0);
+      }
+    ck(src, cudaMemcpyAsync(dind, ind.data(), ind.size() * sizeof(double2), cudaMemcpyHostToDevice, src->s), "upload");
+    ck(src, prolong_op<double>(dind, Ek, S.Vst64, S.Lx, S.Lt, S.bx, S.bt, S.n / 2, nv0, nv0, false, src->s), "unpack");
+    sync(src);
+  });
+  if (st != MG_OK) {
+    g_last_error = src->err;
+    cudaFree(E);
+    return st;
+  }
+  if (rho) *rho = std::pow(std::sqrt(a1 / a0), 1.0 / ncycles);
+  // 2. the refined hierarchy: finer levels copied, this level from E, coarser
+  //    levels set up again on the new coarse operators
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) { cudaFree(E); g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
+  h->p = P;
+  h->s = (cudaStream_t)stream;
+  h->L = src->L;
+  h->R = src->R;
+  st = guarded(h, [&]() {
+    set_geometry(h);
+    init_runtime(h);
+    allocate_storage(h);
+    h->mass = src->mass;
+    const long long V = h->lv[0].V;
+    auto copy = [&](void* d, const void* sp, size_t bytes) {
+      ck(h, cudaMemcpyAsync(d, sp, bytes, cudaMemcpyDeviceToDevice, h->s), "refine copy");
+    };
+    copy(h->U64, src->U64, 2 * V * sizeof(double2));
+    copy(h->U32, src->U32, 2 * V * sizeof(float2));
+    const double2* nz = (const double2*)noise;
+    size_t pos = 0;
+    for (int l = 0; l + 1 < h->L; ++l) {
+      Level& L = h->lv[l];
+      const Level& Sl = src->lv[l];
+      if (l <= lr) {
+        copy(L.eta, Sl.eta, (size_t)L.count() * sizeof(double2));
+        L.lambda_max = Sl.lambda_max;
+        L.omega_relax = Sl.omega_relax;
+      }
+      if (l < lr) {
+        const size_t nvs = (size_t)L.V * 2 * L.Nv * (L.n / 2);
+        copy(L.Vst64, Sl.Vst64, nvs * sizeof(double2));
+        copy(L.Vst32, Sl.Vst32, nvs * sizeof(float2));
+        galerkin_next(h, l);
+      } else if (l == lr) {
+        build_level(h, l, nullptr, E);
+      } else {
+        build_level(h, l, nz + pos, nullptr);
+      }
+      pos += (size_t)(L.Nv + 2) * L.count();
+    }
+    set_mass_internal(h, src->mass);
+  });
+  cudaFree(E);
   if (st != MG_OK) {
     g_last_error = h->err;
     free_all(h);

@@ -86,6 +86,7 @@ _SIGS = {
     "mg_server_destroy": (None, [_vp]),
     "mg_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_clone": (_i, [_vp, _d, _vp, ctypes.POINTER(_vp)]),
+    "mg_refine": (_i, [_vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_d), _vp]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -175,6 +176,17 @@ def mg_clone(h, mass, stream=None):
     out = ctypes.c_void_p()
     _check(lib().mg_clone(h, float(mass), _stream_ptr(stream), ctypes.byref(out)), h)
     return out
+
+
+def mg_refine(h, level, e0, ncycles, noise=None, stream=None, e_out=None):
+    """One adaptive pass on `level` (1 = finest); returns (new handle, rho)."""
+    import torch
+    out, rho = ctypes.c_void_p(), ctypes.c_double()
+    _check(lib().mg_refine(h, int(level), _ptr(e0, torch.complex128), int(ncycles),
+                           None if noise is None else _ptr(noise, torch.complex128),
+                           _stream_ptr(stream), ctypes.byref(out), ctypes.byref(rho),
+                           None if e_out is None else _ptr(e_out, torch.complex128)), h)
+    return out, rho.value
 
 
 def mg_set_mass(h, mass):
@@ -308,6 +320,18 @@ class Multigrid:
 
     def level(self, level):
         return mg_get_level(self.h, level)
+
+    def refine(self, level, e0, ncycles, noise=None, e_out=None):
+        """Replace the hierarchy by its adaptive refinement on `level` (mg_refine);
+        returns rho, the error reduction per cycle measured before refining."""
+        h, rho = mg_refine(self.h, level, e0, ncycles, noise, e_out=e_out)
+        mg_destroy(self.h)
+        self.h = h
+        self.params.Nv[level - 1] += 1
+        if noise is not None:
+            self.params.setup_noise = noise.data_ptr()
+            self._noise = noise
+        return rho
 
     def solve(self, b, tol=1e-10, maxiter=10000, solver=SOLVER_MGCG_MIXED, x=None):
         import torch
