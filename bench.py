@@ -393,6 +393,9 @@ def gpu_bench(args):
     # configuration at the near-critical mass in one Krylov loop
     batched = batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world)
 
+    # adaptive refinement by V-cycles at the near-critical mass
+    adaptive = adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world)
+
     # roofline: one profiled step, dominant kernel family by device time
     prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
     roof = roofline(prof, wl, load_peaks())
@@ -431,6 +434,7 @@ def gpu_bench(args):
                            "per_mass": plain["per_mass"]},
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
             "batched": batched,
+            "adaptive": adaptive,
             "serving": serving,
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
@@ -598,6 +602,74 @@ def batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
             ts.append(e0.elapsed_time(e1))
         out["plain_fp64_single_rhs"] = round(1000.0 / statistics.median(ts), 3)
         out["vs_plain_fp64_single_rhs"] = round(out["value"] / world / out["plain_fp64_single_rhs"], 2)
+    return out
+
+
+def adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
+    """Adaptive refinement by V-cycles (Sec. 3) on the workload's hierarchy at
+    the near-critical mass: `plan` lists the level refined by each pass
+    (args.adaptive_cycles V-cycles on a Gaussian error, seeds noise_seed + 100 + p;
+    coarser levels set up again from setup noise of seed noise_seed + 1 + p).
+    Reports the refinement time, and the single-RHS and batched mixed solves
+    at m_nc before and after it (the headline step keeps the relaxation-only
+    set-up of the workload definition)."""
+    plan = [int(c) for c in args.adaptive_plan]
+    if not plan:
+        return None
+    L, Lt, blocks, tol, m = wl["Lx"], wl["Lt"], wl["blocks"], wl["tol"], masses[0]
+    nrhs = max(1, args.batch_rhs)
+    chis = np.stack([W.gaussian_field((Lt, L, 2), wl["chi_seed"] + 1000 + k) for k in range(nrhs)])
+    chi_d = torch.from_numpy(chis).to(dev)
+    b_d = torch.empty_like(chi_d)
+    x_d = torch.empty_like(chi_d)
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+
+    def timed_solve(h, n):
+        mg.mg_solve(h, b_d, x_d, n, tol, 200000, mg.SOLVER_MGCG_MIXED)       # warm-up
+        reps = []
+        for _ in range(3):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            st, info = mg.mg_solve(h, b_d, x_d, n, tol, 200000, mg.SOLVER_MGCG_MIXED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != 0 or max(i.true_residual for i in info) > tol:
+                raise RuntimeError("adaptive leg: solve did not converge")
+            reps.append(e0.elapsed_time(e1))
+        ms = max_over_ranks(statistics.median(reps), dev)
+        return {"iterations_max": max(i.iterations for i in info), "ms": round(ms, 3),
+                "max_true_residual": max(i.true_residual for i in info)}
+
+    Nv = list(wl["Nv"])
+    out = {"plan": args.adaptive_plan, "ncycles": args.adaptive_cycles, "mass": m}
+    with mg.Multigrid(U_d, m, blocks, Nv, noise_d, setup_sweeps=wl["setup_sweeps"],
+                      max_rhs=nrhs) as s:
+        mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
+        before1, beforeB = timed_solve(s.h, 1), timed_solve(s.h, nrhs)
+        rhos, keep = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p, lvl in enumerate(plan):
+            Nv[lvl - 1] += 1
+            Lx_l, Lt_l, n_l, _ = mg.mg_get_level(s.h, lvl)
+            e0 = torch.from_numpy(W.gaussian_field((Lt_l, Lx_l, n_l), wl["noise_seed"] + 100 + p)).to(dev)
+            nz = torch.from_numpy(W.setup_noise(L, Lt, blocks, Nv, wl["noise_seed"] + 1 + p)).to(dev)
+            keep.append(nz)
+            rhos.append(round(s.refine(lvl, e0, args.adaptive_cycles, nz), 4))
+        torch.cuda.synchronize()
+        refine_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, dev)
+        after1, afterB = timed_solve(s.h, 1), timed_solve(s.h, nrhs)
+        coarsest = mg.mg_get_level(s.h, len(blocks) + 1)
+    out.update({"Nv_after": Nv, "rho_per_pass": rhos, "refine_ms": round(refine_ms, 1),
+                "coarsest_unknowns": coarsest[0] * coarsest[1] * coarsest[2],
+                "single_rhs": {"relaxation_only": before1, "refined": after1,
+                               "speedup": round(before1["ms"] / after1["ms"], 2)},
+                "batched": {"nrhs": nrhs,
+                            "relaxation_only": dict(beforeB, value=round(job_rate(nrhs, world, beforeB["ms"] / 1e3), 3)),
+                            "refined": dict(afterB, value=round(job_rate(nrhs, world, afterB["ms"] / 1e3), 3)),
+                            "unit": UNIT,
+                            "speedup": round(beforeB["ms"] / afterB["ms"], 2)},
+                "breakeven_solves": round(refine_ms / max(1e-9, before1["ms"] - after1["ms"]), 1)})
     return out
 
 
@@ -799,6 +871,9 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64,
                     help="right-hand sides of the batched leg (0 skips it)")
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--adaptive-plan", default="112222",
+                    help="levels refined by the adaptive passes of the adaptive leg ('' skips it)")
+    ap.add_argument("--adaptive-cycles", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests in the serving stream (0 skips the serving leg)")
