@@ -653,7 +653,7 @@ def adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
             Nv[lvl - 1] += 1
             Lx_l, Lt_l, n_l, _ = mg.mg_get_level(s.h, lvl)
             e0 = torch.from_numpy(W.gaussian_field((Lt_l, Lx_l, n_l), wl["noise_seed"] + 100 + p)).to(dev)
-            nz = torch.from_numpy(W.setup_noise(L, Lt, blocks, Nv, wl["noise_seed"] + 1 + p)).to(dev)
+            nz = torch.from_numpy(W.refine_noise(L, Lt, blocks, Nv, lvl - 1, wl["noise_seed"] + 1 + p)).to(dev)
             keep.append(nz)
             rhos.append(round(s.refine(lvl, e0, args.adaptive_cycles, nz), 4))
         torch.cuda.synchronize()

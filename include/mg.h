@@ -49,6 +49,7 @@ extern "C" {
 #endif
 
 #define MG_MAX_LEVELS 5
+#define MG_MAX_REFINE 16                /* adaptive passes made by mg_setup      */
 
 typedef struct mg_handle mg_handle;
 
@@ -111,6 +112,16 @@ typedef struct {
                                            accumulator, 1) or with mma.sync
                                            (0, default: measured faster at 4096
                                            unknowns)                            */
+  int refine_levels[MG_MAX_REFINE];     /* adaptive refinement by V-cycles made
+                                           by mg_setup after the first pass
+                                           (Sec. 3): the level (1 .. nlevels-1)
+                                           refined by each pass, in order, ended
+                                           by 0 or by the array's end; levels
+                                           must not decrease.  Nv above is the
+                                           first-pass set; each pass adds one
+                                           vector per chirality to its level
+                                           (all 0: no refinement)              */
+  int refine_cycles;                    /* V-cycles per adaptive pass (30)      */
 } mg_params;
 
 typedef struct {
@@ -129,7 +140,10 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt);
  * l < nlevels (finest first): Nv_l start vectors for the relaxation of
  * Eq. relax, then one start vector for the power iteration that sets the
  * relaxation step 1/lambda_max(A_l), then one start vector for the two MR
- * steps that fix the smoother (Sec. 4).  Each is a level-l vector.
+ * steps that fix the smoother (Sec. 4).  Each is a level-l vector.  Then,
+ * for each adaptive pass p on level l (refine_levels), its random error e0
+ * (a level-l vector) followed by the random starts of every level below l
+ * for the Nv after pass p, in the per-level layout above.
  * Returns 0 for invalid parameters and for nlevels = 1 (no noise needed). */
 size_t mg_setup_noise_len(const mg_params* p);
 
@@ -140,8 +154,12 @@ size_t mg_setup_noise_len(const mg_params* p);
  * stream: cudaStream_t to use (NULL: the legacy default stream).
  * Validation: Lx, Lt even; each extent divisible by its block; every coarse
  *   extent >= 2; blocks >= 2 x 2; 1 <= Nv_l <= (bx * bt * n_l / 2);
- *   1 <= nlevels <= MG_MAX_LEVELS; 0 <= coarsest_dense_max <= 16384.
- *   MG_ERR_ARG otherwise.  With nlevels = 1 no
+ *   1 <= nlevels <= MG_MAX_LEVELS; 0 <= coarsest_dense_max <= 16384;
+ *   refine_levels in [1, nlevels - 1], not decreasing, with refine_cycles
+ *   >= 1, and the Nv limits holding after every pass.
+ *   MG_ERR_ARG otherwise.  With refine_levels set, the first pass is followed
+ *   by the adaptive passes of mg_refine, made in place (the handle then has
+ *   the refined Nv; mg_get_level reports it).  With nlevels = 1 no
  *   hierarchy is built and setup_noise may be NULL.
  * On success *out owns all device memory of the hierarchy. */
 mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void* stream,
@@ -153,8 +171,9 @@ mg_status mg_set_mass(mg_handle* h, double mass);
 
 /* Device memory of a set-up, before making it (no device work): *resident =
  * the bytes mg_setup allocates and keeps (equal to mg_device_bytes of the
- * handle it returns), *peak = resident + the set-up's temporary relaxation
- * vectors.  Either pointer may be NULL.  MG_ERR_ARG for invalid params. */
+ * handle it returns), *peak = an upper bound of what the set-up holds at
+ * once (resident + its temporary relaxation vectors; with adaptive passes,
+ * also the hierarchy being replaced and the pass's scratch).  Either pointer may be NULL.  MG_ERR_ARG for invalid params. */
 mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long* peak);
 
 /* Device bytes currently owned by the handle. */
@@ -180,12 +199,14 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
  * with Nv[level - 1] + 1: finer levels copied from src, the level's vectors
  * extended by e'', the Galerkin operators below rebuilt, the coarser levels'
  * vectors set up again by relaxation (Eq. relax) on the new coarse operators
- * from `noise`, then the smoothers and the coarsest solver.
+ * from `noise`, then the smoothers and the coarsest solver.  mg_setup makes
+ * the same passes when mg_params.refine_levels asks for them.
  *   e0:     device complex128 level vector [Lt_l][Lx_l][ndof_l], read only.
- *   noise:  device complex128, laid out as mg_params.setup_noise for the
- *           refined Nv (mg_setup_noise_len of the refined parameters); the
- *           parts of levels <= `level` are not read.  May be NULL when
- *           level = nlevels - 1 (nothing below is relaxed).
+ *   noise:  device complex128: the random starts of the levels below
+ *           `level` only, for the refined Nv, each level laid out as in
+ *           mg_params.setup_noise (Nv_k starts, power-iteration start,
+ *           smoother start).  May be NULL when level = nlevels - 1 (nothing
+ *           below is relaxed).
  *   rho:    (host, may be NULL) (|e''|_A / |e0|_A)^(1 / ncycles), the measured
  *           error reduction per cycle of src's V-cycle on that level.
  *   e_out:  (device, may be NULL) receives e''.
@@ -198,6 +219,10 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
  * |e0|_A = 0. */
 mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, const void* noise,
                     void* stream, mg_handle** out, double* rho, void* e_out);
+
+/* The measured rho of each adaptive pass mg_setup made (see mg_refine), in
+ * pass order: up to `max` values into rho (host), their number into *count. */
+mg_status mg_get_refine_rho(const mg_handle* h, double* rho, int max, int* count);
 
 /* Solve A x = b for nrhs right-hand sides (Sec. 4, MG-CG), x_0 = 0.
  * b, x: device complex128 [nrhs][Lt][Lx][2].  Right-hand sides are solved in

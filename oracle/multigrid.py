@@ -282,41 +282,65 @@ class Hierarchy:
 
 def setup(U: np.ndarray, m: float, blocks, Nv, noise: np.ndarray, sweeps: int = 8,
           power_iters: int = 30, omega_mr: float = 0.8,
-          coarsest_dense_max: int = 4096) -> Hierarchy:
-    """Adaptive setup, first pass (Sec. 3, Eq. relax, Eq. P1, Eq. Galerkin), recursively.
+          coarsest_dense_max: int = 4096, refine_levels=(), refine_cycles: int = 30) -> Hierarchy:
+    """Adaptive setup (Sec. 3, Eq. relax, Eq. P1, Eq. Galerkin), recursively.
 
-    For each level l < L-1: omega = 1/lambda_max(A_l); Nv random vectors are
-    relaxed with e <- (1 - omega A_l) e, `sweeps` times; split by chirality and
-    block-orthonormalised; A_{l+1} = P^dagger A_l P.  The smoother is then
-    fixed on each level, and the coarsest operator factored.  `noise` is the
-    flat buffer of random starts (layout in ``workloads.setup_noise``).
+    First pass, for each level l < L-1: omega = 1/lambda_max(A_l); Nv random
+    vectors are relaxed with e <- (1 - omega A_l) e, `sweeps` times; split by
+    chirality and block-orthonormalised; A_{l+1} = P^dagger A_l P.  The
+    smoother is then fixed on each level, and the coarsest operator factored.
+    Then one adaptive pass (``refine``, `refine_cycles` V-cycles) for each
+    entry of `refine_levels` (0 = finest), in order.  `noise` is the flat
+    buffer of random starts (layout in ``workloads.setup_noise``): the first
+    pass's, then for each adaptive pass its random error and the starts of
+    the levels below it.
     """
     _, Lt, Lx = U.shape
     levels = [Level(WilsonNormalOp(U, m), Lx, Lt, 2)]
-    _build_levels(levels, blocks, Nv, noise, sweeps, power_iters)
+    shapes = _level_shapes(Lx, Lt, blocks, Nv)
+    first = sum((nv + 2) * lx * lt * n for (lx, lt, n), nv in zip(shapes[:-1], Nv))
+    _build_levels(levels, blocks, Nv, noise[:first], sweeps, power_iters)
     H = Hierarchy(levels, float(m), U, omega_mr=omega_mr, coarsest_dense_max=coarsest_dense_max)
     _finish_levels(H)
+    pos, Nv = first, list(Nv)
+    for level in refine_levels:
+        Nv[level] += 1
+        lx, lt, n = _level_shapes(Lx, Lt, blocks, Nv)[level]
+        e0 = noise[pos:pos + lx * lt * n].reshape(lt, lx, n)
+        pos += lx * lt * n
+        shapes = _level_shapes(Lx, Lt, blocks, Nv)
+        tail = sum((nv + 2) * a * b * c for (a, b, c), nv in zip(shapes[level + 1:-1], Nv[level + 1:]))
+        H, _, rho = refine(H, e0, refine_cycles, noise[pos:pos + tail], level, sweeps, power_iters)
+        H.stats.setdefault("refine_rho", []).append(rho)
+        pos += tail
+    if pos != noise.size:
+        raise ValueError(f"noise has {noise.size} entries, the set-up reads {pos}")
     return H
+
+
+def _level_shapes(Lx, Lt, blocks, Nv):
+    """(Lx_l, Lt_l, n_l) of every level."""
+    out = [(Lx, Lt, 2)]
+    for (bx, bt), nv in zip(blocks, Nv):
+        lx, lt, _ = out[-1]
+        out.append((lx // bx, lt // bt, 2 * nv))
+    return out
 
 
 def _build_levels(levels, blocks, Nv, noise, sweeps, power_iters, given=None):
     """Level-by-level body of the setup, from level len(levels) - 1 down.
     With `given` = (E, omega_relax, eta) the first level built takes the
     vectors E instead of relaxing random starts and keeps the given relaxation
-    step and smoother start.  `noise` keeps the layout of
-    ``workloads.setup_noise`` for the full (blocks, Nv); the parts of the
-    levels not relaxed here are skipped."""
+    step and smoother start.  `noise` holds the random starts of the relaxed
+    levels only, each in the per-level layout of ``workloads.setup_noise``."""
     first = len(levels) - 1
     pos = 0
     for l, ((bx, bt), nv) in enumerate(zip(blocks, Nv)):
         if l < first:
-            lv = levels[l]
-            pos += (nv + 2) * lv.Lt * lv.Lx * lv.n
             continue
         lv = levels[l]
         size = lv.Lt * lv.Lx * lv.n
         if l == first and given is not None:
-            pos += (nv + 2) * size
             E, lv.omega_relax, eta = given
             lv.eta = eta.copy()
         else:
@@ -426,8 +450,9 @@ def refine(H: Hierarchy, e0: np.ndarray, ncycles: int, noise: np.ndarray, level:
     appended as vector Nv_l + 1 of the level.  Finer levels are kept; the level
     keeps its relaxation step and smoother start; the Galerkin operators below
     it, the coarser levels' vectors (first-pass setup on the new coarse
-    operators, from `noise` laid out as ``workloads.setup_noise`` for the
-    refined Nv), the smoothers and the coarsest factor are rebuilt.
+    operators, from `noise`: the random starts of the levels below `level`
+    for the refined Nv, as laid out by ``workloads.refine_noise``), the
+    smoothers and the coarsest factor are rebuilt.
 
     Returns (H', e'', rho) with rho = (|e''|_A / |e0|_A)^(1/ncycles), the
     measured error reduction per cycle of the level's V-cycle in H.
@@ -446,6 +471,7 @@ def refine(H: Hierarchy, e0: np.ndarray, ncycles: int, noise: np.ndarray, level:
     _build_levels(levels, blocks, Nv, noise, sweeps, power_iters,
                   given=(E, lv.omega_relax, lv.eta))
     H2 = Hierarchy(levels, H.m, H.U, omega_mr=H.omega_mr,
-                   coarsest_dense_max=H.coarsest_dense_max, coarsest_tol=H.coarsest_tol)
+                   coarsest_dense_max=H.coarsest_dense_max, coarsest_tol=H.coarsest_tol,
+                   stats={k: list(v) if isinstance(v, list) else v for k, v in H.stats.items()})
     _finish_levels(H2)
     return H2, e, float(rho)

@@ -90,6 +90,7 @@ struct mg_handle {
   bool dry = false;             // size-only pass: dalloc counts bytes, allocates nothing
   std::string err;
   long long fine_applies = 0, vcycles = 0;
+  std::vector<double> refine_rho;   // rho of each adaptive pass made by mg_setup
   // optional per-family event timing
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev[MG_KF_COUNT];
@@ -462,6 +463,39 @@ void set_mass_internal(mg_handle* h, double mass) {
   sync(h);
 }
 
+// Adaptive passes asked for by p (refine_levels up to the first 0).
+int refine_count(const mg_params* p) {
+  int k = 0;
+  while (k < MG_MAX_REFINE && p->refine_levels[k] != 0) ++k;
+  return k;
+}
+
+// Complex entries of one level-l vector (geometry already validated).
+long long level_size(const mg_params* p, int l) {
+  long long lx = p->Lx, lt = p->Lt, n = 2;
+  for (int k = 0; k < l; ++k) {
+    lx /= p->block[k][0];
+    lt /= p->block[k][1];
+    n = 2 * p->Nv[k];
+  }
+  return lx * lt * n;
+}
+
+// Entries of the random starts of levels first .. nlevels - 2.
+size_t noise_len_from(const mg_params* p, int first) {
+  size_t t = 0;
+  for (int l = first; l + 1 < p->nlevels; ++l) t += (size_t)(p->Nv[l] + 2) * level_size(p, l);
+  return t;
+}
+
+// The parameters after the first `passes` adaptive passes, with no plan left.
+mg_params after_passes(const mg_params* p, int passes) {
+  mg_params q = *p;
+  for (int k = 0; k < passes; ++k) q.Nv[p->refine_levels[k] - 1] += 1;
+  std::memset(q.refine_levels, 0, sizeof(q.refine_levels));
+  return q;
+}
+
 mg_status validate(const mg_params* p, std::string& msg) {
   if (!p) { msg = "params is NULL"; return MG_ERR_ARG; }
   if (p->Lx < 4 || p->Lt < 4 || p->Lx % 2 || p->Lt % 2) { msg = "Lx, Lt must be even and >= 4"; return MG_ERR_ARG; }
@@ -483,6 +517,20 @@ mg_status validate(const mg_params* p, std::string& msg) {
   if (p->coarsest_dense_max < 0 || p->coarsest_dense_max > MG_DENSE_MAX) {
     msg = "coarsest_dense_max must be in [0, " + std::to_string(MG_DENSE_MAX) + "]";
     return MG_ERR_ARG;
+  }
+  const int np = refine_count(p);
+  if (np) {
+    if (p->refine_cycles < 1) { msg = "refine_cycles must be >= 1"; return MG_ERR_ARG; }
+    for (int k = 0; k < np; ++k) {
+      const int lv = p->refine_levels[k];
+      if (lv < 1 || lv >= p->nlevels || (k && lv < p->refine_levels[k - 1])) {
+        msg = "refine_levels must be in [1, nlevels - 1] and not decrease";
+        return MG_ERR_ARG;
+      }
+    }
+    // Nv only grows, so the limits hold after every pass if they hold after the last
+    const mg_params q = after_passes(p, np);
+    if (validate(&q, msg) != MG_OK) { msg = "after the adaptive passes: " + msg; return MG_ERR_ARG; }
   }
   return MG_OK;
 }
@@ -961,6 +1009,121 @@ void build_level(mg_handle* h, int l, const double2* noise, const void* Egiven) 
   }
 }
 
+// One adaptive pass on level lr of src (Sec. 3; the contract is mg_refine's).
+// noise: the random starts of the levels below lr for the refined Nv.  The
+// arguments are validated by the caller.
+mg_status refine_core(mg_handle* src, int lr, const void* e0, int ncycles, const double2* noise,
+                      cudaStream_t stream, mg_handle** out, double* rho, void* e_out) {
+  *out = nullptr;
+  mg_params P = src->p;
+  P.Nv[lr] += 1;
+  std::memset(P.refine_levels, 0, sizeof(P.refine_levels));
+  const Level& S = src->lv[lr];
+  const long long c = S.count();
+  const int nv0 = S.Nv;
+  const Level& SC = src->lv[lr + 1];
+  const long long cc = SC.count();
+  // scratch: E = the nv0 current vectors of the level, then the surviving
+  // error e''; then two level vectors, then nv0 coarse indicator vectors
+  void* E = nullptr;
+  if (cudaMalloc(&E, ((size_t)(nv0 + 3) * c + (size_t)nv0 * cc) * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "device allocation failed (refine scratch)";
+    return MG_ERR_NOMEM;
+  }
+  double2* Ek = (double2*)E;
+  double2* e = Ek + (size_t)nv0 * c;
+  double2* t = e + c;
+  double2* z = t + c;
+  double2* dind = z + c;
+  // 1. V-cycles of the level on the error, no source (Sec. 3)
+  double a0 = 0.0, a1 = 0.0;
+  mg_status st = guarded(src, [&]() {
+    ck(src, cudaMemcpyAsync(e, e0, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e0");
+    apply_level<double>(src, lr, e, t, 1, W_F64);
+    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
+    a0 = read_scalar(src, S_T0);
+    for (int k = 0; k < ncycles; ++k) {
+      if (k) apply_level<double>(src, lr, e, t, 1, W_F64);
+      vcycle<double>(src, lr, t, z, 1);
+      ck(src, axpby<double>(-1.0, z, 1.0, e, c, 1, src->s), "e -= V A e");
+    }
+    apply_level<double>(src, lr, e, t, 1, W_F64);
+    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
+    a1 = read_scalar(src, S_T0);
+    if (!(a0 > 0.0) || !(a1 == a1)) fail(src, MG_ERR_BREAKDOWN, "refine: |e0|_A = 0 or non-finite error");
+    if (e_out) ck(src, cudaMemcpyAsync(e_out, e, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e''");
+    // the level's current vectors as full level vectors: v_k = P (1_{s=k} + 1_{s=Nv+k})
+    std::vector<double2> ind((size_t)nv0 * cc, make_double2(0.0, 0.0));
+    for (int k = 0; k < nv0; ++k)
+      for (long long j = 0; j < SC.V; ++j) {
+        ind[(size_t)k * cc + j * SC.n + k] = make_double2(1.0, 0.0);
+        ind[(size_t)k * cc + j * SC.n + nv0 + k] = make_double2(1.0, 0.0);
+      }
+    ck(src, cudaMemcpyAsync(dind, ind.data(), ind.size() * sizeof(double2), cudaMemcpyHostToDevice, src->s), "upload");
+    ck(src, prolong_op<double>(dind, Ek, S.Vst64, S.Lx, S.Lt, S.bx, S.bt, S.n / 2, nv0, nv0, false, src->s), "unpack");
+    sync(src);
+  });
+  if (st != MG_OK) {
+    g_last_error = src->err;
+    cudaFree(E);
+    return st;
+  }
+  if (rho) *rho = std::pow(std::sqrt(a1 / a0), 1.0 / ncycles);
+  // 2. the refined hierarchy: finer levels copied, this level from E, coarser
+  //    levels set up again on the new coarse operators
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) { cudaFree(E); g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
+  h->p = P;
+  h->s = stream;
+  h->L = src->L;
+  h->R = src->R;
+  h->prof_on = src->prof_on;
+  st = guarded(h, [&]() {
+    set_geometry(h);
+    init_runtime(h);
+    allocate_storage(h);
+    h->mass = src->mass;
+    const long long V = h->lv[0].V;
+    auto copy = [&](void* d, const void* sp, size_t bytes) {
+      ck(h, cudaMemcpyAsync(d, sp, bytes, cudaMemcpyDeviceToDevice, h->s), "refine copy");
+    };
+    copy(h->U64, src->U64, 2 * V * sizeof(double2));
+    copy(h->U32, src->U32, 2 * V * sizeof(float2));
+    size_t pos = 0;
+    for (int l = 0; l + 1 < h->L; ++l) {
+      Level& L = h->lv[l];
+      const Level& Sl = src->lv[l];
+      if (l <= lr) {
+        copy(L.eta, Sl.eta, (size_t)L.count() * sizeof(double2));
+        L.lambda_max = Sl.lambda_max;
+        L.omega_relax = Sl.omega_relax;
+      }
+      if (l < lr) {
+        const size_t nvs = (size_t)L.V * 2 * L.Nv * (L.n / 2);
+        copy(L.Vst64, Sl.Vst64, nvs * sizeof(double2));
+        copy(L.Vst32, Sl.Vst32, nvs * sizeof(float2));
+        galerkin_next(h, l);
+      } else if (l == lr) {
+        build_level(h, l, nullptr, E);
+      } else {
+        build_level(h, l, noise + pos, nullptr);
+        pos += (size_t)(L.Nv + 2) * L.count();
+      }
+    }
+    set_mass_internal(h, src->mass);
+  });
+  cudaFree(E);
+  if (st != MG_OK) {
+    g_last_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return MG_OK;
+}
+
 }  // namespace
 
 // =============================================================================
@@ -987,18 +1150,25 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->profile = 0;
   p->coarsest_dense_max = (int)MG_DENSE_MAX;
   p->coarsest_gj_tcgen05 = 0;
+  p->refine_cycles = 30;
   return MG_OK;
 }
 
 size_t mg_setup_noise_len(const mg_params* p) {
   if (!p || p->nlevels < 1 || p->nlevels > MG_MAX_LEVELS) return 0;
-  size_t tot = 0;
-  long long lx = p->Lx, lt = p->Lt, n = 2;
+  long long lx = p->Lx, lt = p->Lt;
   for (int l = 0; l + 1 < p->nlevels; ++l) {
     const int bx = p->block[l][0], bt = p->block[l][1];
     if (bx <= 0 || bt <= 0 || lx % bx || lt % bt) return 0;
-    tot += (size_t)(p->Nv[l] + 2) * lx * lt * n;
-    lx /= bx; lt /= bt; n = 2 * p->Nv[l];
+    lx /= bx; lt /= bt;
+  }
+  size_t tot = noise_len_from(p, 0);
+  const int np = refine_count(p);
+  for (int k = 0; k < np; ++k) {
+    const int lr = p->refine_levels[k] - 1;
+    if (lr < 0 || lr + 1 >= p->nlevels) return 0;
+    const mg_params q = after_passes(p, k + 1);
+    tot += (size_t)level_size(&q, lr) + noise_len_from(&q, lr + 1);
   }
   return tot;
 }
@@ -1039,6 +1209,26 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       pos += (size_t)(h->lv[l].Nv + 2) * h->lv[l].count();
     }
     set_mass_internal(h, mass);
+    // adaptive passes (Sec. 3), each replacing the hierarchy in place
+    std::vector<double> rhos;
+    const int np = refine_count(params);
+    for (int k = 0; k < np; ++k) {
+      const int lr = params->refine_levels[k] - 1;
+      const mg_params q = after_passes(params, k + 1);
+      const double2* e0 = noise + pos;
+      pos += (size_t)level_size(&q, lr);
+      const double2* tail = noise + pos;
+      pos += noise_len_from(&q, lr + 1);
+      mg_handle* nh = nullptr;
+      double rho = 0.0;
+      const mg_status rs = refine_core(h, lr, e0, params->refine_cycles, tail, h->s, &nh, &rho, nullptr);
+      if (rs != MG_OK) fail(h, rs, "adaptive pass " + std::to_string(k + 1) + ": " + g_last_error);
+      std::swap(*h, *nh);
+      free_all(nh);
+      delete nh;
+      rhos.push_back(rho);
+    }
+    h->refine_rho = rhos;
   });
   if (st != MG_OK) {
     g_last_error = h->err;
@@ -1054,15 +1244,34 @@ mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long
   std::string msg;
   mg_status v = validate(params, msg);
   if (v != MG_OK) { g_last_error = msg; return v; }
-  mg_handle tmp;
-  tmp.p = *params;
-  tmp.L = params->nlevels;
-  tmp.R = params->max_rhs;
-  tmp.dry = true;
-  set_geometry(&tmp);
-  allocate_storage(&tmp);
-  if (resident) *resident = tmp.bytes;
-  if (peak) *peak = tmp.bytes + setup_temp_bytes(&tmp);
+  auto dry = [](const mg_params& q, long long* temp) {
+    mg_handle tmp;
+    tmp.p = q;
+    tmp.L = q.nlevels;
+    tmp.R = q.max_rhs;
+    tmp.dry = true;
+    set_geometry(&tmp);
+    allocate_storage(&tmp);
+    *temp = setup_temp_bytes(&tmp);
+    return tmp.bytes;
+  };
+  long long temp = 0;
+  long long res = dry(after_passes(params, 0), &temp);
+  long long top = res + temp;
+  const int np = refine_count(params);
+  for (int k = 0; k < np; ++k) {
+    // the pass holds the previous hierarchy, the new one with its set-up
+    // temporaries, and its scratch (Nv + 3 level vectors, Nv coarse vectors)
+    const int lr = params->refine_levels[k] - 1;
+    const mg_params prev = after_passes(params, k);
+    const long long res_k = dry(after_passes(params, k + 1), &temp);
+    const long long scratch = ((long long)(prev.Nv[lr] + 3) * level_size(&prev, lr) +
+                               (long long)prev.Nv[lr] * level_size(&prev, lr + 1)) * 16;
+    top = std::max(top, res + res_k + temp + scratch);
+    res = res_k;
+  }
+  if (resident) *resident = res;
+  if (peak) *peak = top;
   return MG_OK;
 }
 
@@ -1126,114 +1335,20 @@ mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, cons
   if (!noise && lr + 2 < src->L) { g_last_error = "noise is NULL but coarser levels are relaxed"; return MG_ERR_ARG; }
   mg_params P = src->p;
   P.Nv[lr] += 1;
-  P.profile = 0;
-  P.setup_noise = noise ? noise : (const void*)src;   // not read when NULL was allowed
+  std::memset(P.refine_levels, 0, sizeof(P.refine_levels));
+  P.setup_noise = noise ? noise : (const void*)src;   // a non-NULL placeholder when nothing is read
   std::string msg;
   mg_status v = validate(&P, msg);
   if (v != MG_OK) { g_last_error = msg; return v; }
-  const Level& S = src->lv[lr];
-  const long long c = S.count();
-  const int nv0 = S.Nv;
-  const Level& SC = src->lv[lr + 1];
-  const long long cc = SC.count();
-  // scratch: E = the nv0 current vectors of the level, then the surviving
-  // error e''; then two level vectors, then nv0 coarse indicator vectors
-  void* E = nullptr;
-  if (cudaMalloc(&E, ((size_t)(nv0 + 3) * c + (size_t)nv0 * cc) * sizeof(double2)) != cudaSuccess) {
-    cudaGetLastError();
-    g_last_error = "device allocation failed (refine scratch)";
-    return MG_ERR_NOMEM;
-  }
-  double2* Ek = (double2*)E;
-  double2* e = Ek + (size_t)nv0 * c;
-  double2* t = e + c;
-  double2* z = t + c;
-  double2* dind = z + c;
-  // 1. V-cycles of the level on the error, no source (Sec. 3)
-  double a0 = 0.0, a1 = 0.0;
-  mg_status st = guarded(src, [&]() {
-    ck(src, cudaMemcpyAsync(e, e0, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e0");
-    apply_level<double>(src, lr, e, t, 1, W_F64);
-    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
-    a0 = read_scalar(src, S_T0);
-    for (int k = 0; k < ncycles; ++k) {
-      if (k) apply_level<double>(src, lr, e, t, 1, W_F64);
-      vcycle<double>(src, lr, t, z, 1);
-      ck(src, axpby<double>(-1.0, z, 1.0, e, c, 1, src->s), "e -= V A e");
-    }
-    apply_level<double>(src, lr, e, t, 1, W_F64);
-    ck(src, dot<double>(e, t, c, 1, src->partials, slot(src, S_T0), src->s), "dot");
-    a1 = read_scalar(src, S_T0);
-    if (!(a0 > 0.0) || !(a1 == a1)) fail(src, MG_ERR_BREAKDOWN, "refine: |e0|_A = 0 or non-finite error");
-    if (e_out) ck(src, cudaMemcpyAsync(e_out, e, c * sizeof(double2), cudaMemcpyDeviceToDevice, src->s), "copy e''");
-    // the level's current vectors as full level vectors: v_k = P (1_{s=k} + 1_{s=Nv+k})
-    std::vector<double2> ind((size_t)nv0 * cc, make_double2(0.0, 0.0));
-    for (int k = 0; k < nv0; ++k)
-      for (long long j = 0; j < SC.V; ++j) {
-        ind[(size_t)k * cc + j * SC.n + k] = make_double2(1.0, 0.0);
-        ind[(size_t)k * cc + j * SC.n + nv0 + k] = make_double2(1.0, 0.0);
-      }
-    ck(src, cudaMemcpyAsync(dind, ind.data(), ind.size() * sizeof(double2), cudaMemcpyHostToDevice, src->s), "upload");
-    ck(src, prolong_op<double>(dind, Ek, S.Vst64, S.Lx, S.Lt, S.bx, S.bt, S.n / 2, nv0, nv0, false, src->s), "unpack");
-    sync(src);
-  });
-  if (st != MG_OK) {
-    g_last_error = src->err;
-    cudaFree(E);
-    return st;
-  }
-  if (rho) *rho = std::pow(std::sqrt(a1 / a0), 1.0 / ncycles);
-  // 2. the refined hierarchy: finer levels copied, this level from E, coarser
-  //    levels set up again on the new coarse operators
-  mg_handle* h = new (std::nothrow) mg_handle();
-  if (!h) { cudaFree(E); g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
-  h->p = P;
-  h->s = (cudaStream_t)stream;
-  h->L = src->L;
-  h->R = src->R;
-  st = guarded(h, [&]() {
-    set_geometry(h);
-    init_runtime(h);
-    allocate_storage(h);
-    h->mass = src->mass;
-    const long long V = h->lv[0].V;
-    auto copy = [&](void* d, const void* sp, size_t bytes) {
-      ck(h, cudaMemcpyAsync(d, sp, bytes, cudaMemcpyDeviceToDevice, h->s), "refine copy");
-    };
-    copy(h->U64, src->U64, 2 * V * sizeof(double2));
-    copy(h->U32, src->U32, 2 * V * sizeof(float2));
-    const double2* nz = (const double2*)noise;
-    size_t pos = 0;
-    for (int l = 0; l + 1 < h->L; ++l) {
-      Level& L = h->lv[l];
-      const Level& Sl = src->lv[l];
-      if (l <= lr) {
-        copy(L.eta, Sl.eta, (size_t)L.count() * sizeof(double2));
-        L.lambda_max = Sl.lambda_max;
-        L.omega_relax = Sl.omega_relax;
-      }
-      if (l < lr) {
-        const size_t nvs = (size_t)L.V * 2 * L.Nv * (L.n / 2);
-        copy(L.Vst64, Sl.Vst64, nvs * sizeof(double2));
-        copy(L.Vst32, Sl.Vst32, nvs * sizeof(float2));
-        galerkin_next(h, l);
-      } else if (l == lr) {
-        build_level(h, l, nullptr, E);
-      } else {
-        build_level(h, l, nz + pos, nullptr);
-      }
-      pos += (size_t)(L.Nv + 2) * L.count();
-    }
-    set_mass_internal(h, src->mass);
-  });
-  cudaFree(E);
-  if (st != MG_OK) {
-    g_last_error = h->err;
-    free_all(h);
-    delete h;
-    return st;
-  }
-  *out = h;
+  return refine_core(src, lr, e0, ncycles, (const double2*)noise, (cudaStream_t)stream, out, rho,
+                     e_out);
+}
+
+mg_status mg_get_refine_rho(const mg_handle* h, double* rho, int max, int* count) {
+  if (!h || (max > 0 && !rho)) return MG_ERR_ARG;
+  const int n = (int)h->refine_rho.size();
+  for (int k = 0; k < n && k < max; ++k) rho[k] = h->refine_rho[k];
+  if (count) *count = n;
   return MG_OK;
 }
 

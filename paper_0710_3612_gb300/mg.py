@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmg.so")
 
 MG_MAX_LEVELS = 5
+MG_MAX_REFINE = 16
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 SOLVER_MGCG_FP64, SOLVER_MGCG_MIXED, SOLVER_CG_FP64 = 0, 1, 2
 STATUS = {0: "MG_OK", 1: "MG_ERR_ARG", 2: "MG_ERR_NOMEM", 3: "MG_ERR_CUDA", 4: "MG_ERR_NOCONV",
@@ -35,7 +36,8 @@ class MgParams(ctypes.Structure):
                 ("coarsest_tol", ctypes.c_double), ("coarsest_refine_max", ctypes.c_int),
                 ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int),
-                ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int)]
+                ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
+                ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):
@@ -87,6 +89,7 @@ _SIGS = {
     "mg_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_clone": (_i, [_vp, _d, _vp, ctypes.POINTER(_vp)]),
     "mg_refine": (_i, [_vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_d), _vp]),
+    "mg_get_refine_rho": (_i, [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -142,7 +145,11 @@ def make_params(Lx, Lt, blocks, Nv, noise=None, **kw) -> MgParams:
         p.block[l][0], p.block[l][1] = bx, bt
         p.Nv[l] = nv
     for k, v in kw.items():
-        setattr(p, k, v)
+        if k == "refine_levels":            # 1-based levels of the adaptive passes
+            for j, lv in enumerate(v):
+                p.refine_levels[j] = lv
+        else:
+            setattr(p, k, v)
     if noise is not None:
         p.setup_noise = _ptr(noise).value
     return p
@@ -187,6 +194,14 @@ def mg_refine(h, level, e0, ncycles, noise=None, stream=None, e_out=None):
                            _stream_ptr(stream), ctypes.byref(out), ctypes.byref(rho),
                            None if e_out is None else _ptr(e_out, torch.complex128)), h)
     return out, rho.value
+
+
+def mg_get_refine_rho(h):
+    """rho of each adaptive pass mg_setup made."""
+    buf = (ctypes.c_double * 16)()
+    n = ctypes.c_int()
+    _check(lib().mg_get_refine_rho(h, buf, 16, ctypes.byref(n)), h)
+    return list(buf[:n.value])
 
 
 def mg_set_mass(h, mass):
@@ -328,9 +343,6 @@ class Multigrid:
         mg_destroy(self.h)
         self.h = h
         self.params.Nv[level - 1] += 1
-        if noise is not None:
-            self.params.setup_noise = noise.data_ptr()
-            self._noise = noise
         return rho
 
     def solve(self, b, tol=1e-10, maxiter=10000, solver=SOLVER_MGCG_MIXED, x=None):

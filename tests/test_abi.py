@@ -54,6 +54,10 @@ def test_param_struct_layout_matches(lib_path):
     assert mg.mg_setup_noise_len(p) == W.setup_noise_len(32, 16, [(4, 4), (2, 2)], [3, 5])
     bad = mg.make_params(30, 16, [(4, 4)], [3])
     assert mg.mg_setup_noise_len(bad) == 0
+    # with adaptive passes (1-based levels in the library, 0-based in workloads)
+    r = mg.make_params(32, 16, [(4, 4), (2, 2)], [3, 5], refine_levels=[1, 2, 2])
+    assert r.refine_cycles == 30 and list(r.refine_levels[:4]) == [1, 2, 2, 0]
+    assert mg.mg_setup_noise_len(r) == W.setup_noise_len(32, 16, [(4, 4), (2, 2)], [3, 5], [0, 1, 1])
 
 
 def test_setup_bytes_is_host_only(lib_path):
@@ -66,3 +70,22 @@ def test_setup_bytes_is_host_only(lib_path):
     p8 = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8], max_rhs=8)
     p8.setup_noise = 1
     assert mg.mg_setup_bytes(p8)[0] > res
+    # adaptive passes: resident = the refined hierarchy's, the peak holds two
+    pr = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8], refine_levels=[1, 2])
+    pr.setup_noise = 1
+    ref = mg.make_params(128, 128, [(4, 4), (2, 2)], [9, 9])
+    ref.setup_noise = 1
+    res_r, peak_r = mg.mg_setup_bytes(pr)
+    assert res_r == mg.mg_setup_bytes(ref)[0] and peak_r > res_r + res
+    for bad in ([2, 1], [3], [0, 1]):
+        q = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8], refine_levels=bad)
+        q.setup_noise = 1
+        if bad == [0, 1]:                  # a leading 0 ends the plan: no passes
+            assert mg.mg_setup_bytes(q)[0] == res
+            continue
+        with pytest.raises(mg.MgError):
+            mg.mg_setup_bytes(q)
+    q = mg.make_params(128, 128, [(4, 4), (2, 2)], [16, 8], refine_levels=[1])
+    q.setup_noise = 1
+    with pytest.raises(mg.MgError):      # 4x4 blocks of 2 components hold 16 vectors at most
+        mg.mg_setup_bytes(q)

@@ -66,7 +66,7 @@ def test_refine_matches_oracle(mg, near_critical_32, level):
     e0 = W.gaussian_field((lv.Lt, lv.Lx, lv.n), 20 + level)
     Nv2 = list(Nv)
     Nv2[level - 1] += 1
-    noise2 = W.setup_noise(L, L, BLOCKS, Nv2, 8)
+    noise2 = W.refine_noise(L, L, BLOCKS, Nv2, level - 1, 8)
     H2, e_want, rho_want = omg.refine(H, e0, 6, noise2, level=level - 1)
     with mg.Multigrid(dev(U), m, BLOCKS, Nv, dev(W.setup_noise(L, L, BLOCKS, Nv, 7))) as s:
         e_out = torch.empty(e0.shape, dtype=torch.complex128, device=DEV)
@@ -119,7 +119,7 @@ def test_refinement_on_the_near_critical_64_hierarchy(mg):
                 Nv[level - 1] += 1
                 Lx, Lt, n, _ = mg.mg_get_level(s.h, level)
                 e0 = dev(W.gaussian_field((Lt, Lx, n), 100 + p))
-                rho = s.refine(level, e0, 30, dev(W.setup_noise(L, L, BLOCKS, Nv, 8 + p)))
+                rho = s.refine(level, e0, 30, dev(W.refine_noise(L, L, BLOCKS, Nv, level - 1, 8 + p)))
                 assert 0 < rho < 1
             x, infos = s.solve(dev(b), tol=TOL, maxiter=5000, solver=mg.SOLVER_MGCG_MIXED)
             assert rel(ow.apply_A(U, m, host(x)), b) <= TOL
@@ -158,3 +158,75 @@ def test_refine_argument_checks(mg, near_critical_32):
             assert torch.equal(before, after)
         finally:
             mg.mg_destroy(h2)
+
+
+def test_setup_with_a_refinement_plan_matches_oracle(mg, near_critical_32):
+    """mg_setup with refine_levels = 1, 2, 2 (the passes made in place, every
+    random input from the one setup_noise buffer) against the oracle's setup
+    with the same plan: the rho of each pass, every level's vectors and
+    coarse operators, the exact memory accounting, solves, and a clone of the
+    refined hierarchy at another mass."""
+    L, U, m = near_critical_32
+    Nv, plan = [3, 3], [1, 2, 2]
+    noise = W.setup_noise(L, L, BLOCKS, Nv, 9, refine_levels=[lv - 1 for lv in plan])
+    H = omg.setup(U, m, BLOCKS, Nv, noise, refine_levels=[lv - 1 for lv in plan], refine_cycles=5)
+    with mg.Multigrid(dev(U), m, BLOCKS, Nv, dev(noise), refine_levels=plan, refine_cycles=5) as s:
+        assert mg.mg_get_refine_rho(s.h) == pytest.approx(H.stats["refine_rho"], rel=1e-9)
+        res, peak = mg.mg_setup_bytes(s.params)
+        assert res == mg.mg_device_bytes(s.h) and peak > res
+        for l in range(H.L - 1):
+            ref = H.levels[l]
+            Lx, Lt, n, nv = mg.mg_get_level(s.h, l + 1)
+            assert (Lx, Lt, n, nv) == (ref.Lx, ref.Lt, ref.n, ref.Nv)
+            out = torch.empty((nv, Lt, Lx, n), dtype=torch.complex128, device=DEV)
+            mg.mg_get_null_vectors(s.h, l + 1, out)
+            assert np.max(np.abs(host(out) - ref.V)) <= 1e-8, f"vectors of level {l + 1}"
+        for l in range(1, H.L):
+            op = H.levels[l].op
+            out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
+            mg.mg_get_coarse_op(s.h, l + 1, out)
+            assert np.max(np.abs(host(out) - op.M)) <= 1e-8 * np.max(np.abs(op.M)), f"A_c level {l + 1}"
+        b = ow.apply_D(U, m, W.gaussian_field((L, L, 2), 3), dagger=True)
+        _, it_want, _ = krylov.mgcg(H, b, TOL, 5000)
+        x, infos = s.solve(dev(b), tol=TOL, maxiter=5000, solver=mg.SOLVER_MGCG_FP64)
+        assert rel(ow.apply_A(U, m, host(x)), b) <= TOL and abs(infos[0].iterations - it_want) <= 1
+        # a clone at another mass keeps the refined vectors
+        m2 = m + 0.5
+        c = mg.mg_clone(s.h, m2)
+        try:
+            assert mg.mg_get_level(c, 2)[3] == 5 and mg.mg_device_bytes(c) == res
+            H2 = omg.set_mass(H, m2)
+            op = H2.levels[1].op
+            out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
+            mg.mg_get_coarse_op(c, 2, out)
+            assert np.max(np.abs(host(out) - op.M)) <= 1e-8 * np.max(np.abs(op.M))
+        finally:
+            mg.mg_destroy(c)
+
+
+def test_server_with_a_refined_configuration(mg, near_critical_32):
+    """The serving engine builds a configuration whose parameters ask for
+    adaptive passes (its set-up makes them; the other masses are clones of the
+    refined hierarchy); every request reaches its tolerance."""
+    L, U, m = near_critical_32
+    Nv, plan = [3, 3], [1, 2]
+    noise = dev(W.setup_noise(L, L, BLOCKS, Nv, 9, refine_levels=[lv - 1 for lv in plan]))
+    masses = [m, m + 0.3]
+    with mg.Server(budget_bytes=4 << 30, max_rhs=4, workers=2) as srv:
+        p = mg.make_params(L, L, BLOCKS, Nv, refine_levels=plan, refine_cycles=10)
+        cid = srv.add_config(dev(U), p, m, noise=noise)
+        rids, bufs = [], []
+        for k in range(6):
+            mk = masses[k % 2]
+            b = dev(ow.apply_D(U, mk, W.gaussian_field((L, L, 2), 700 + k), dagger=True))
+            x = torch.empty_like(b)
+            torch.cuda.synchronize()
+            rids.append(srv.submit(cid, mk, b, x, 1, TOL, mg.SOLVER_MGCG_MIXED))
+            bufs.append((mk, b, x))
+        for r in rids:
+            st, infos, _ = srv.wait(r, 1)
+            assert st == 0 and infos[0].true_residual <= TOL
+        stats = srv.stats()
+        assert stats.builds == 1 and stats.clones == 1 and stats.failed == 0
+    for mk, b, x in bufs:
+        assert rel(ow.apply_A(U, mk, host(x)), host(b)) <= TOL

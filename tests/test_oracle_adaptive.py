@@ -79,7 +79,7 @@ def test_energy_norm_never_grows_and_rho_is_the_measured_ratio():
         e = mg.vcycle_error_propagation(H, e, 1)
         norms.append(mg.energy_norm(H, e))
     assert all(b < a for a, b in zip(norms, norms[1:]))
-    noise = W.setup_noise(16, 16, [(4, 4)], [3], 8)
+    noise = W.refine_noise(16, 16, [(4, 4)], [3], 0, 8)
     _, e6, rho = mg.refine(H, W.gaussian_field((16, 16, 2), 7), 6, noise)
     assert abs(rho - (norms[-1] / norms[0]) ** (1 / 6)) <= 1e-12
     assert np.linalg.norm(e6 - e) <= 1e-14 * np.linalg.norm(e) + 1e-300
@@ -101,7 +101,7 @@ def test_refined_vectors_append_the_orthogonal_block_component(level):
     Nv = [2, 3]
     Nv[level] += 1
     e0 = W.gaussian_field((lv.Lt, lv.Lx, lv.n), 9)
-    H2, e, _ = mg.refine(H, e0, 4, W.setup_noise(16, 16, [(4, 4), (2, 2)], Nv, 10), level=level)
+    H2, e, _ = mg.refine(H, e0, 4, W.refine_noise(16, 16, [(4, 4), (2, 2)], Nv, level, 10), level=level)
     new = H2.levels[level]
     assert new.Nv == lv.Nv + 1 and [x.Nv for x in H2.levels[:-1]] == Nv
     assert np.max(np.abs(new.V[:lv.Nv] - lv.V)) <= 1e-13
@@ -141,9 +141,38 @@ def test_refinement_removes_critical_slowing_down():
     for p in range(2):
         Nv = [H.levels[0].Nv + 1]
         H, _, rho = mg.refine(H, W.gaussian_field((L, L, 2), 100 + p), 20,
-                              W.setup_noise(L, L, [(4, 4)], Nv, 8 + p))
+                              W.refine_noise(L, L, [(4, 4)], Nv, 0, 8 + p))
         assert 0 < rho < 1
         counts.append(iters(H))
     relax4 = iters(mg.setup(U, m, [(4, 4)], [4], W.setup_noise(L, L, [(4, 4)], [4], 7)))
     assert counts[2] < counts[1] < counts[0]
     assert 1.5 * counts[2] <= relax4
+
+
+def test_setup_with_a_refinement_plan_reads_the_extended_noise():
+    """setup(refine_levels=...) = the first pass followed by refine() on each
+    level of the plan, with every random input taken from one buffer in the
+    order of ``workloads.setup_noise``; the buffer is read to its end."""
+    L, blocks, Nv, plan = 16, [(4, 4), (2, 2)], [2, 2], [0, 1, 1]
+    U = W.links_from_angles(W.quenched_u1_angles(L, L, 3.0, 20, 1))
+    noise = W.setup_noise(L, L, blocks, Nv, 4, refine_levels=plan)
+    assert noise.size == W.setup_noise_len(L, L, blocks, Nv, plan)
+    H = mg.setup(U, -0.7, blocks, Nv, noise, refine_levels=plan, refine_cycles=3)
+    pos = W.setup_noise_len(L, L, blocks, Nv)
+    G = mg.setup(U, -0.7, blocks, Nv, noise[:pos])
+    nv = list(Nv)
+    for level in plan:
+        nv[level] += 1
+        lx, lt, n = W.level_shapes(L, L, blocks, nv)[level]
+        e0 = noise[pos:pos + lx * lt * n].reshape(lt, lx, n)
+        pos += lx * lt * n
+        tail = W.setup_noise_len(L, L, blocks, nv) - W.setup_noise_len(L, L, blocks[:level + 1], nv[:level + 1])
+        G, _, _ = mg.refine(G, e0, 3, noise[pos:pos + tail], level)
+        pos += tail
+    assert pos == noise.size
+    assert [lv.Nv for lv in H.levels[:-1]] == [3, 4]
+    for a, b in zip(H.levels, G.levels):
+        assert np.array_equal(a.op.dense(), b.op.dense())
+    assert len(H.stats["refine_rho"]) == 3
+    with pytest.raises(ValueError):
+        mg.setup(U, -0.7, blocks, Nv, noise[:-1], refine_levels=plan, refine_cycles=3)

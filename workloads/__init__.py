@@ -148,22 +148,43 @@ def level_shapes(Lx: int, Lt: int, blocks, Nv):
     return shapes
 
 
-def setup_noise_len(Lx: int, Lt: int, blocks, Nv) -> int:
-    """Number of complex entries of the setup noise buffer (see setup_noise)."""
+def _noise_len_from(Lx: int, Lt: int, blocks, Nv, first: int) -> int:
+    """Entries of the per-level random starts of levels first .. L-2."""
     shapes = level_shapes(Lx, Lt, blocks, Nv)
-    return sum((nv + 2) * lx * lt * n for (lx, lt, n), nv in zip(shapes[:-1], Nv))
+    return sum((nv + 2) * lx * lt * n
+               for (lx, lt, n), nv in list(zip(shapes[:-1], Nv))[first:])
 
 
-def setup_noise(Lx: int, Lt: int, blocks, Nv, seed: int) -> np.ndarray:
+def setup_noise_len(Lx: int, Lt: int, blocks, Nv, refine_levels=()) -> int:
+    """Number of complex entries of the setup noise buffer (see setup_noise)."""
+    tot = _noise_len_from(Lx, Lt, blocks, Nv, 0)
+    Nv = list(Nv)
+    for level in refine_levels:
+        Nv[level] += 1
+        lx, lt, n = level_shapes(Lx, Lt, blocks, Nv)[level]
+        tot += lx * lt * n + _noise_len_from(Lx, Lt, blocks, Nv, level + 1)
+    return tot
+
+
+def setup_noise(Lx: int, Lt: int, blocks, Nv, seed: int, refine_levels=()) -> np.ndarray:
     """Random vectors drawn by the adaptive setup, flattened complex128.
 
     For each non-coarsest level l (finest first) the buffer holds, in order,
     Nv_l starting vectors for the null-space relaxation, one start for the
     power iteration that sets the relaxation step, and one start for the two
     minimum-residual steps that fix the smoother; each is a level-l vector in
-    [t][x][dof] order.
+    [t][x][dof] order.  Then, for each adaptive pass on level refine_levels[p]
+    (0 = finest), the random error it starts from (a level vector) and the
+    starts of every level below it for the Nv after the pass, laid out as
+    above (see refine_noise).
     """
-    return gaussian_field((setup_noise_len(Lx, Lt, blocks, Nv),), seed)
+    return gaussian_field((setup_noise_len(Lx, Lt, blocks, Nv, refine_levels),), seed)
+
+
+def refine_noise(Lx: int, Lt: int, blocks, Nv, level: int, seed: int) -> np.ndarray:
+    """Random starts of the levels below `level` (0 = finest) for the vector
+    counts Nv (after the pass), as an adaptive pass on `level` reads them."""
+    return gaussian_field((_noise_len_from(Lx, Lt, blocks, Nv, level + 1),), seed)
 
 
 # ---------------------------------------------------------------------------
