@@ -438,6 +438,7 @@ def gpu_bench(args):
             "serving": serving,
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
+            "autotune": mg.stencil_tunings(),
             "e2e": e2e,
             "gpu_launches": int(res["launches"]),
             "clocks": res["clocks"],

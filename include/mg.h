@@ -122,6 +122,13 @@ typedef struct {
                                            vector per chirality to its level
                                            (all 0: no refinement)              */
   int refine_cycles;                    /* V-cycles per adaptive pass (30)      */
+  int autotune;                         /* nonzero: mg_setup times the launch
+                                           shapes of the fused fine A (FP32 and
+                                           FP64, 1 and max_rhs right-hand
+                                           sides) once per process and shape
+                                           and keeps the fastest whose output
+                                           is bit-identical to the default
+                                           shape's (1)                          */
 } mg_params;
 
 typedef struct {
@@ -132,6 +139,22 @@ typedef struct {
   long long vcycles;          /* V-cycles applied                               */
   double milliseconds;        /* wall time of the call                          */
 } mg_solve_info;
+
+/* One launch shape picked by the stencil autotuner (mg_params.autotune). */
+typedef struct {
+  int precision;              /* MG_PREC_F64 or MG_PREC_F32                    */
+  int Lx, Lt, nrhs;           /* the launch it serves                          */
+  int tx, ty, rows_per_thread;/* tile of the fused A; 0 x 0 = the streaming
+                                 kernel (one warp per strip)                   */
+  int tried, admitted;        /* shapes timed / shapes bit-identical to the
+                                 default shape (only those may be chosen)      */
+  double us_chosen;           /* microseconds per launch of the chosen shape   */
+  double us_default;          /* microseconds per launch of the default shape  */
+} mg_stencil_tuning;
+
+/* The shapes tuned so far in this process: up to max records into out (host,
+ * may be NULL with max = 0); returns the number of records. */
+int mg_stencil_tunings(mg_stencil_tuning* out, int max);
 
 /* Fill *p with the defaults listed above for an Lx x Lt lattice (no levels). */
 mg_status mg_params_default(mg_params* p, int Lx, int Lt);

@@ -105,6 +105,27 @@ cudaError_t wilson_D(const void* in, void* out, const void* U, double diag, int 
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, const Epilogue& ep, cudaStream_t s);
+
+// Launch shape chosen by the autotuner for one (precision, Lx, Lt, nrhs):
+// tile tx x ty with rpt rows per thread (0 x 0: the streaming kernel), timed
+// against the default shape; only shapes whose output is bit-identical to
+// the default's are admitted.
+struct StencilTuning {
+  int precision;        // 0 = FP64, 1 = FP32
+  int Lx, Lt, nrhs;
+  int variant, tx, ty, rpt;
+  int tried, admitted;
+  double us_best, us_default;
+};
+// Times every launch shape of the fused A on (in, U) once per process and
+// shape, writing into out and ref (nrhs fine vectors each) and using dflag (one
+// device int); later wilson_A launches without the dot epilogue use the
+// fastest admitted shape.
+template <typename R>
+cudaError_t wilson_A_tune(const void* in, void* out, void* ref, const void* U, double diag,
+                          int Lx, int Lt, int nrhs, int* dflag, cudaStream_t s);
+// Copies up to max tuned shapes into out; returns how many exist.
+int stencil_tunings(StencilTuning* out, int max);
 // Thread blocks wilson_A launches per right-hand side (the fused <x, A x>
 // needs at most 608).
 int wilson_A_ctas(int Lx, int Lt, bool f64);

@@ -7,6 +7,10 @@
 // (1 - s sigma_2) phi = (phi0 + i s phi1) (1, -i s)^T, so each hop is one
 // complex projection, one link multiply and a rank-1 reconstruction.
 // D uses s = +1 forward (x + mu) and s = -1 backward; D^dagger swaps them.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -398,29 +402,172 @@ int wilson_A_ctas(int Lx, int Lt, bool f64) {
 template <typename R, int TX, int TY, int RPT>
 static void launch_wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                             int nrhs, const Epilogue& ep, cudaStream_t s) {
+  static_assert(sizeof(R) * 4 * ((TY * RPT + 4) * (TX + 4) + (TY * RPT + 2) * (TX + 2)) +
+                        sizeof(R) * 4 * (TY * RPT + 3) * (TX + 3) <= 48 * 1024,
+                "tile above the static shared-memory limit");
   dim3 grid((Lx + TX - 1) / TX, (Lt + TY * RPT - 1) / (TY * RPT), nrhs);
   k_wilson_A<R, TX, TY, RPT><<<grid, TX * TY, 0, s>>>((const cplx_t<R>*)in, (cplx_t<R>*)out,
                                                       (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
 }
 
+// ---------------------------------------------------------------------------
+// Launch shapes of the fused A and their autotuner.  Every shape runs the same
+// per-site arithmetic (wilson_site order), so a shape is admitted by the
+// tuner only if it reproduces the default shape's output bit for bit; the
+// tuner then keeps the fastest admitted shape per (precision, Lx, Lt, nrhs).
+// Launches with the fused <in, A in> epilogue keep the default shape (their
+// partial sums depend on the tiling).
+// ---------------------------------------------------------------------------
+enum { WV_STREAM = 0, WV_16x8, WV_32x8, WV_32x8x2, WV_16x16, WV_64x4, WV_64x4x2, WV_COUNT };
+static const int WV_SHAPE[WV_COUNT][3] = {{0, 0, 0}, {16, 8, 1}, {32, 8, 1}, {32, 8, 2},
+                                          {16, 16, 1}, {64, 4, 1}, {64, 4, 2}};
+
+// The default shape (the choice made before any tuning).
+template <typename R>
+static int wilson_default_variant(int Lx, int Lt, bool dot) {
+  const bool f64 = sizeof(R) == 8;
+  if (!dot && wilson_A_streamed(Lx, Lt)) return WV_STREAM;
+  const bool big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16)) >= 2 * 152;
+  if (!big) return WV_16x8;
+  return f64 ? WV_32x8 : WV_32x8x2;
+}
+
+template <typename R>
+static bool wilson_variant_ok(int v, int Lx, int Lt) {
+  if (v == WV_STREAM) return wilson_A_streamed(Lx, Lt);
+  if (sizeof(R) == 8 && (v == WV_32x8x2 || v == WV_64x4x2)) return false;   // shared memory
+  return true;
+}
+
+template <typename R>
+static void launch_variant(int v, const void* in, void* out, const void* U, double diag, int Lx,
+                           int Lt, int nrhs, const Epilogue& ep, cudaStream_t s) {
+  switch (v) {
+    case WV_STREAM: {
+      const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);
+      k_wilson_A_stream<R><<<dim3((unsigned)((warps + 3) / 4), nrhs), 128, 0, s>>>(
+          (const cplx_t<R>*)in, (cplx_t<R>*)out, (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
+      break;
+    }
+    case WV_16x8: launch_wilson_A<R, 16, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s); break;
+    case WV_32x8: launch_wilson_A<R, 32, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s); break;
+    case WV_16x16: launch_wilson_A<R, 16, 16, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s); break;
+    case WV_64x4: launch_wilson_A<R, 64, 4, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s); break;
+    default:
+      if constexpr (sizeof(R) == 4) {
+        if (v == WV_32x8x2) launch_wilson_A<R, 32, 8, 2>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
+        else launch_wilson_A<R, 64, 4, 2>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
+      }
+      break;
+  }
+}
+
+struct TuneKey {
+  int prec, Lx, Lt, nrhs;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(prec, Lx, Lt, nrhs) < std::tie(o.prec, o.Lx, o.Lt, o.nrhs);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, StencilTuning> g_tune;
+
+template <typename R>
+static int tuned_variant(int Lx, int Lt, int nrhs) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find({(int)sizeof(R), Lx, Lt, nrhs});
+  return it == g_tune.end() ? -1 : it->second.variant;
+}
+
+__global__ void k_count_diff(const unsigned long long* __restrict__ a,
+                             const unsigned long long* __restrict__ b, long long n, int* diff) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) atomicAdd(diff, 1);
+}
+
+template <typename R>
+cudaError_t wilson_A_tune(const void* in, void* out, void* ref, const void* U, double diag,
+                          int Lx, int Lt, int nrhs, int* dflag, cudaStream_t s) {
+  const TuneKey key{(int)sizeof(R), Lx, Lt, nrhs};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    if (g_tune.count(key)) return cudaSuccess;
+  }
+  const Epilogue none{};
+  const int def = wilson_default_variant<R>(Lx, Lt, false);
+  const long long words = (long long)Lx * Lt * nrhs * 2 * sizeof(cplx_t<R>) / 8;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  StencilTuning t{};
+  t.precision = sizeof(R) == 8 ? 0 : 1;
+  t.Lx = Lx; t.Lt = Lt; t.nrhs = nrhs;
+  t.variant = def;
+  float best = 0.f;
+  launch_variant<R>(def, in, ref, U, diag, Lx, Lt, nrhs, none, s);
+  for (int v = 0; v < WV_COUNT; ++v) {
+    if (!wilson_variant_ok<R>(v, Lx, Lt)) continue;
+    ++t.tried;
+    launch_variant<R>(v, in, out, U, diag, Lx, Lt, nrhs, none, s);
+    int diff = 0;
+    cudaMemsetAsync(dflag, 0, sizeof(int), s);
+    k_count_diff<<<152, 256, 0, s>>>((const unsigned long long*)out,
+                                     (const unsigned long long*)ref, words, dflag);
+    cudaMemcpyAsync(&diff, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return err;
+    }
+    if (diff) continue;                                    // not bit-identical: never used
+    ++t.admitted;
+    for (int w = 0; w < 2; ++w) launch_variant<R>(v, in, out, U, diag, Lx, Lt, nrhs, none, s);
+    constexpr int REPS = 10;
+    cudaEventRecord(e0, s);
+    for (int w = 0; w < REPS; ++w) launch_variant<R>(v, in, out, U, diag, Lx, Lt, nrhs, none, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double us = 1000.0 * ms / REPS;
+    if (v == def) t.us_default = us;
+    if (t.admitted == 1 || ms < best) {
+      best = ms;
+      t.variant = v;
+      t.us_best = us;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  t.tx = WV_SHAPE[t.variant][0];
+  t.ty = WV_SHAPE[t.variant][1];
+  t.rpt = WV_SHAPE[t.variant][2];
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = t;
+  }
+  return cudaGetLastError();
+}
+
+int stencil_tunings(StencilTuning* out, int max) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  int k = 0;
+  for (const auto& kv : g_tune) {
+    if (k < max && out) out[k] = kv.second;
+    ++k;
+  }
+  return k;
+}
+
 template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, const Epilogue& ep, cudaStream_t s) {
-  const bool f64 = sizeof(R) == 8;
-  const int ctas = wilson_A_ctas(Lx, Lt, f64);
-  if (ep.dot_out && (nrhs > 64 || ctas > 608)) return cudaErrorInvalidValue;
-  const bool big = ((Lx + 31) / 32) * ((Lt + (f64 ? 7 : 15)) / (f64 ? 8 : 16)) >= 2 * 152;
-  if (!ep.dot_out && wilson_A_streamed(Lx, Lt)) {
-    const long long warps = (long long)((Lx + SOUT - 1) / SOUT) * ((Lt + SROWS - 1) / SROWS);
-    k_wilson_A_stream<R><<<dim3((unsigned)((warps + 3) / 4), nrhs), 128, 0, s>>>(
-        (const cplx_t<R>*)in, (cplx_t<R>*)out, (const cplx_t<R>*)U, (R)diag, Lx, Lt, ep);
-  } else if (!big) {
-    launch_wilson_A<R, 16, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
-  } else if constexpr (sizeof(R) == 8) {
-    launch_wilson_A<R, 32, 8, 1>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
-  } else {
-    launch_wilson_A<R, 32, 8, 2>(in, out, U, diag, Lx, Lt, nrhs, ep, s);
-  }
+  const bool dot = ep.dot_out != nullptr;
+  if (dot && (nrhs > 64 || wilson_A_ctas(Lx, Lt, sizeof(R) == 8) > 608)) return cudaErrorInvalidValue;
+  int v = dot ? -1 : tuned_variant<R>(Lx, Lt, nrhs);
+  if (v < 0) v = wilson_default_variant<R>(Lx, Lt, dot);
+  launch_variant<R>(v, in, out, U, diag, Lx, Lt, nrhs, ep, s);
   count_launch();
   return cudaGetLastError();
 }
@@ -475,6 +622,8 @@ cudaError_t link_unitarity(const void* gauge, long long count, double* out, cuda
                                    bool, cudaStream_t);                                       \
   template cudaError_t wilson_A<R>(const void*, void*, const void*, double, int, int, int,    \
                                    const Epilogue&, cudaStream_t);                            \
+  template cudaError_t wilson_A_tune<R>(const void*, void*, void*, const void*, double, int,   \
+                                        int, int, int*, cudaStream_t);                        \
   template cudaError_t fold_links<R>(const void*, void*, int, int, cudaStream_t);
 INST(double)
 INST(float)

@@ -1009,6 +1009,28 @@ void build_level(mg_handle* h, int l, const double2* noise, const void* Egiven) 
   }
 }
 
+// Autotuning of the fused fine A for this handle's launches (FP32 and FP64,
+// 1 and max_rhs right-hand sides), on the idle solver vectors.  The input is
+// the link field read as a fine vector (2 V unit-modulus entries, the size of
+// one fine vector), repeated.
+void autotune_fine(mg_handle* h) {
+  const Level& F = h->lv[0];
+  const long long c = F.count();
+  const double diag = 4.0 + h->mass;
+  for (int k = 0; k < h->R; ++k)
+    ck(h, cudaMemcpyAsync((double2*)h->sv64[0] + k * c, h->U64, c * sizeof(double2),
+                          cudaMemcpyDeviceToDevice, h->s), "tune input");
+  ck(h, convert_f64_f32(h->sv64[0], h->sv32[0], c * h->R, h->s), "tune input");
+  for (int nrhs : {1, h->R}) {
+    ck(h, wilson_A_tune<double>(h->sv64[0], h->sv64[1], h->sv64[2], h->U64, diag, F.Lx, F.Lt,
+                                nrhs, h->dflag, h->s), "tune f64");
+    ck(h, wilson_A_tune<float>(h->sv32[0], h->sv32[1], h->sv32[2], h->U32, diag, F.Lx, F.Lt,
+                               nrhs, h->dflag, h->s), "tune f32");
+    if (h->R == 1) break;
+  }
+  sync(h);
+}
+
 // One adaptive pass on level lr of src (Sec. 3; the contract is mg_refine's).
 // noise: the random starts of the levels below lr for the refined Nv.  The
 // arguments are validated by the caller.
@@ -1151,6 +1173,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->coarsest_dense_max = (int)MG_DENSE_MAX;
   p->coarsest_gj_tcgen05 = 0;
   p->refine_cycles = 30;
+  p->autotune = 1;
   return MG_OK;
 }
 
@@ -1229,6 +1252,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
       rhos.push_back(rho);
     }
     h->refine_rho = rhos;
+    if (params->autotune) autotune_fine(h);
   });
   if (st != MG_OK) {
     g_last_error = h->err;
@@ -1342,6 +1366,20 @@ mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, cons
   if (v != MG_OK) { g_last_error = msg; return v; }
   return refine_core(src, lr, e0, ncycles, (const double2*)noise, (cudaStream_t)stream, out, rho,
                      e_out);
+}
+
+int mg_stencil_tunings(mg_stencil_tuning* out, int max) {
+  std::vector<StencilTuning> t(std::max(0, max));
+  const int n = stencil_tunings(t.data(), max);
+  for (int k = 0; k < n && k < max && out; ++k) {
+    mg_stencil_tuning& o = out[k];
+    o.precision = t[k].precision == 0 ? MG_PREC_F64 : MG_PREC_F32;
+    o.Lx = t[k].Lx; o.Lt = t[k].Lt; o.nrhs = t[k].nrhs;
+    o.tx = t[k].tx; o.ty = t[k].ty; o.rows_per_thread = t[k].rpt;
+    o.tried = t[k].tried; o.admitted = t[k].admitted;
+    o.us_chosen = t[k].us_best; o.us_default = t[k].us_default;
+  }
+  return n;
 }
 
 mg_status mg_get_refine_rho(const mg_handle* h, double* rho, int max, int* count) {

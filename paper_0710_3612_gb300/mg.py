@@ -37,7 +37,16 @@ class MgParams(ctypes.Structure):
                 ("inner_coarsest_refine", ctypes.c_int), ("vcycle_coarse_bf16", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int),
                 ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
-                ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int)]
+                ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+
+class MgStencilTuning(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("Lx", ctypes.c_int), ("Lt", ctypes.c_int),
+                ("nrhs", ctypes.c_int), ("tx", ctypes.c_int), ("ty", ctypes.c_int),
+                ("rows_per_thread", ctypes.c_int), ("tried", ctypes.c_int),
+                ("admitted", ctypes.c_int), ("us_chosen", ctypes.c_double),
+                ("us_default", ctypes.c_double)]
 
 
 class MgSolveInfo(ctypes.Structure):
@@ -90,6 +99,7 @@ _SIGS = {
     "mg_clone": (_i, [_vp, _d, _vp, ctypes.POINTER(_vp)]),
     "mg_refine": (_i, [_vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_d), _vp]),
     "mg_get_refine_rho": (_i, [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)]),
+    "mg_stencil_tunings": (_i, [_vp, _i]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -194,6 +204,21 @@ def mg_refine(h, level, e0, ncycles, noise=None, stream=None, e_out=None):
                            _stream_ptr(stream), ctypes.byref(out), ctypes.byref(rho),
                            None if e_out is None else _ptr(e_out, torch.complex128)), h)
     return out, rho.value
+
+
+def stencil_tunings():
+    """Launch shapes of the fused fine A picked by the autotuner in this process."""
+    n = lib().mg_stencil_tunings(None, 0)
+    buf = (MgStencilTuning * max(1, n))()
+    n = lib().mg_stencil_tunings(buf, n)
+    out = []
+    for t in buf[:n]:
+        out.append({"precision": "f64" if t.precision == PREC_F64 else "f32",
+                    "lattice": [t.Lx, t.Lt], "nrhs": t.nrhs,
+                    "tile": "stream" if t.tx == 0 else f"{t.tx}x{t.ty}x{t.rows_per_thread}",
+                    "tried": t.tried, "admitted": t.admitted,
+                    "us_chosen": round(t.us_chosen, 3), "us_default": round(t.us_default, 3)})
+    return out
 
 
 def mg_get_refine_rho(h):

@@ -57,6 +57,8 @@ def test_param_struct_layout_matches(lib_path):
     # with adaptive passes (1-based levels in the library, 0-based in workloads)
     r = mg.make_params(32, 16, [(4, 4), (2, 2)], [3, 5], refine_levels=[1, 2, 2])
     assert r.refine_cycles == 30 and list(r.refine_levels[:4]) == [1, 2, 2, 0]
+    assert p.autotune == 1
+    assert mg.lib().mg_stencil_tunings(None, 0) == 0        # nothing tuned without a device
     assert mg.mg_setup_noise_len(r) == W.setup_noise_len(32, 16, [(4, 4), (2, 2)], [3, 5], [0, 1, 1])
 
 
