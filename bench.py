@@ -439,6 +439,7 @@ def gpu_bench(args):
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
             "autotune": mg.stencil_tunings(),
+            "gauge_gen": gauge_gen_leg(mg, torch, dev, stream),
             "e2e": e2e,
             "gpu_launches": int(res["launches"]),
             "clocks": res["clocks"],
@@ -552,6 +553,27 @@ def stencil_gbs(mg, torch, dev, stream):
                 "bytes_per_site": 48}
     finally:
         mg.mg_destroy(h)
+
+
+def gauge_gen_leg(mg, torch, dev, stream):
+    """Quenched U(1) field of the largest serving lattice on the device
+    (checkerboard Metropolis, counter-based uniforms): 512 x 512, beta = 10,
+    500 sweeps from a cold start, CUDA-event time."""
+    L, beta, sweeps = 512, 10.0, 500
+    th = torch.zeros((2, L, L), dtype=torch.float64, device=dev)
+    mg.gauge_metropolis(th, beta, 5, 1, stream=stream)            # warm-up (discarded)
+    th.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    acc = mg.gauge_metropolis(th, beta, sweeps, 1, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"lattice": [L, L], "beta": beta, "sweeps": sweeps, "ms": round(ms, 2),
+            "link_updates_per_s": round(2 * L * L * sweeps / (ms / 1000.0), 1),
+            "acceptance": round(acc / (2 * L * L * sweeps), 4),
+            "mean_plaquette": round(float(torch.cos(th[0] + torch.roll(th[1], -1, 1)
+                                                    - torch.roll(th[0], -1, 0) - th[1]).mean()), 6)}
 
 
 def batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):

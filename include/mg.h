@@ -152,6 +152,27 @@ typedef struct {
   double us_default;          /* microseconds per launch of the default shape  */
 } mg_stencil_tuning;
 
+/* Quenched U(1) gauge field on the device (the paper's gauge ensembles,
+ * Sec. 4: Wilson plaquette action S = -beta sum_p Re U_p): checkerboard
+ * Metropolis sweeps first_sweep .. first_sweep + sweeps - 1 on the link angles
+ * theta (device float64 [2][Lt][Lx], x links then t links), updated in place.
+ * One sweep visits direction 0 then 1, each in two halves by the parity of
+ * the other coordinate; proposal theta' = theta + eps (2 u - 1), accepted
+ * when u' < exp(-dS); accepted angles are mapped to [-pi, pi).  The uniforms
+ * are Philox4x32-10 (Salmon et al., SC'11) at counter (t Lx + x,
+ * 4 sweep + 2 mu + parity as two 32-bit words, 0) and key (seed low 32 bits,
+ * seed high 32 bits): u from words 0, 1 and u' from words 2, 3, each
+ * (w0 >> 5) 2^-27 + (w1 >> 6) 2^-53.  Lx, Lt even and >= 2.  accepted (host,
+ * may be NULL) receives the number of accepted proposals.  Synchronises the
+ * stream. */
+mg_status mg_gauge_metropolis(double* theta, int Lx, int Lt, double beta, double eps, int sweeps,
+                              long long first_sweep, unsigned long long seed, void* stream,
+                              long long* accepted);
+
+/* Gauge links U = exp(i theta) (device complex128 [2][Lt][Lx], the layout
+ * mg_setup takes) from the angles of mg_gauge_metropolis. */
+mg_status mg_gauge_links(const double* theta, void* U, int Lx, int Lt, void* stream);
+
 /* The shapes tuned so far in this process: up to max records into out (host,
  * may be NULL with max = 0); returns the number of records. */
 int mg_stencil_tunings(mg_stencil_tuning* out, int max);

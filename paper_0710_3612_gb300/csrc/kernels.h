@@ -212,4 +212,13 @@ cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int 
 cudaError_t block_map(int Lx, int Lt, int bx, int bt, int32_t* coarse, int32_t* offset,
                       cudaStream_t s);
 
+// Checkerboard Metropolis sweeps first_sweep .. first_sweep + sweeps - 1 of the
+// U(1) plaquette action on angles theta[2][Lt][Lx] (counter-based uniforms
+// keyed by seed); accepted (device, may be NULL) accumulates the accepted
+// proposals.  U = exp(i theta) for n angles.
+cudaError_t gauge_metropolis(double* theta, int Lx, int Lt, double beta, double eps, int sweeps,
+                             long long first_sweep, unsigned long long seed,
+                             unsigned long long* accepted, cudaStream_t s);
+cudaError_t links_from_angles(const double* theta, void* U, long long n, cudaStream_t s);
+
 }  // namespace mgk

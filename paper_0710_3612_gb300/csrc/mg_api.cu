@@ -1368,6 +1368,42 @@ mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, cons
                      e_out);
 }
 
+mg_status mg_gauge_metropolis(double* theta, int Lx, int Lt, double beta, double eps, int sweeps,
+                              long long first_sweep, unsigned long long seed, void* stream,
+                              long long* accepted) {
+  if (!theta || Lx < 2 || Lt < 2 || Lx % 2 || Lt % 2 || sweeps < 0 || first_sweep < 0 ||
+      !(eps > 0.0) || (long long)Lx * Lt > (1LL << 31)) {
+    g_last_error = "invalid Metropolis arguments";
+    return MG_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "device allocation failed";
+    return MG_ERR_NOMEM;
+  }
+  unsigned long long n = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(n), s);
+  if (e == cudaSuccess) e = gauge_metropolis(theta, Lx, Lt, beta, eps, sweeps, first_sweep, seed, d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, d, sizeof(n), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("Metropolis: ") + cudaGetErrorString(e);
+    return MG_ERR_CUDA;
+  }
+  if (accepted) *accepted = (long long)n;
+  return MG_OK;
+}
+
+mg_status mg_gauge_links(const double* theta, void* U, int Lx, int Lt, void* stream) {
+  if (!theta || !U || Lx < 1 || Lt < 1) { g_last_error = "invalid arguments"; return MG_ERR_ARG; }
+  cudaError_t e = links_from_angles(theta, U, 2LL * Lx * Lt, (cudaStream_t)stream);
+  if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return MG_ERR_CUDA; }
+  return MG_OK;
+}
+
 int mg_stencil_tunings(mg_stencil_tuning* out, int max) {
   std::vector<StencilTuning> t(std::max(0, max));
   const int n = stencil_tunings(t.data(), max);

@@ -100,6 +100,9 @@ _SIGS = {
     "mg_refine": (_i, [_vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(_vp), ctypes.POINTER(_d), _vp]),
     "mg_get_refine_rho": (_i, [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)]),
     "mg_stencil_tunings": (_i, [_vp, _i]),
+    "mg_gauge_metropolis": (_i, [_vp, _i, _i, _d, _d, _i, _ll, ctypes.c_ulonglong, _vp,
+                                 ctypes.POINTER(_ll)]),
+    "mg_gauge_links": (_i, [_vp, _vp, _i, _i, _vp]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -204,6 +207,28 @@ def mg_refine(h, level, e0, ncycles, noise=None, stream=None, e_out=None):
                            _stream_ptr(stream), ctypes.byref(out), ctypes.byref(rho),
                            None if e_out is None else _ptr(e_out, torch.complex128)), h)
     return out, rho.value
+
+
+def gauge_metropolis(theta, beta, sweeps, seed, first_sweep=0, eps=1.0, stream=None):
+    """Checkerboard Metropolis on device angles theta[2][Lt][Lx] (float64), in
+    place; returns the number of accepted proposals."""
+    import torch
+    _, Lt, Lx = theta.shape
+    acc = ctypes.c_longlong()
+    _check(lib().mg_gauge_metropolis(_ptr(theta, torch.float64), Lx, Lt, float(beta), float(eps),
+                                     int(sweeps), int(first_sweep), int(seed),
+                                     _stream_ptr(stream), ctypes.byref(acc)))
+    return acc.value
+
+
+def gauge_links(theta, stream=None):
+    """U = exp(i theta) as a device complex128 [2][Lt][Lx] tensor."""
+    import torch
+    _, Lt, Lx = theta.shape
+    U = torch.empty(theta.shape, dtype=torch.complex128, device=theta.device)
+    _check(lib().mg_gauge_links(_ptr(theta, torch.float64), _ptr(U, torch.complex128), Lx, Lt,
+                                _stream_ptr(stream)))
+    return U
 
 
 def stencil_tunings():

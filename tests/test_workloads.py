@@ -73,3 +73,50 @@ def test_noise_layout_length():
     # level 1: 16x8 sites x 2 dof x (3+2); level 2: 4x2 sites x 6 dof x (5+2)
     assert n == 16 * 8 * 2 * 5 + 4 * 2 * 6 * 7
     assert W.setup_noise(16, 8, [(4, 4), (2, 2)], [3, 5], 1).shape == (n,)
+
+
+def test_counter_uniforms_are_uniform_and_independent():
+    """Philox4x32-10 uniforms of the counter-based generator: moments of U(0, 1),
+    a flat histogram, no correlation between the two draws of a site, between
+    neighbouring sites or between half-sweeps, and distinct seeds differ."""
+    u, a = W.metropolis_uniforms(512, 512, 5, 3, 1, 0)
+    n = u.size
+    for v in (u, a):
+        assert np.all((v >= 0) & (v < 1))
+        assert abs(v.mean() - 0.5) < 5 * np.sqrt(1 / 12 / n)
+        assert abs(v.var() - 1 / 12) < 5 * np.sqrt(1 / 180 / n)
+        h, _ = np.histogram(v, bins=64, range=(0, 1))
+        chi2 = ((h - n / 64) ** 2 / (n / 64)).sum()
+        assert chi2 < 63 + 5 * np.sqrt(2 * 63)
+    u2, _ = W.metropolis_uniforms(512, 512, 5, 3, 1, 1)
+    u3, _ = W.metropolis_uniforms(512, 512, 6, 3, 1, 0)
+    for x, y in ((u, a), (u.ravel()[:-1], u.ravel()[1:]), (u, u2), (u, u3)):
+        assert abs(np.corrcoef(x.ravel(), y.ravel())[0, 1]) < 5 / np.sqrt(n)
+    assert not np.array_equal(u, u3)
+    # the 53-bit construction is exact: every value is a multiple of 2^-53
+    assert np.all(np.floor(u * 2.0 ** 53) == u * 2.0 ** 53)
+
+
+def test_counter_metropolis_chunks_and_range():
+    """Sweeps are functions of (seed, sweep): 6 sweeps at once equal 2 + 4 from
+    the intermediate field; angles stay in [-pi, pi); Lx != Lt works."""
+    full = W.quenched_u1_angles_counter(12, 8, 2.0, 6, 9)
+    part = W.quenched_u1_angles_counter(12, 8, 2.0, 2, 9)
+    part = W.quenched_u1_angles_counter(12, 8, 2.0, 4, 9, theta=part, first_sweep=2)
+    assert np.array_equal(full, part)
+    assert np.all((full >= -np.pi) & (full < np.pi))
+    assert not np.array_equal(full, W.quenched_u1_angles_counter(12, 8, 2.0, 6, 10))
+
+
+@pytest.mark.parametrize("beta", [3.0, 6.0])
+def test_counter_metropolis_plaquette_matches_bessel_ratio(beta):
+    L, therm, meas = 32, 100, 200
+    theta = W.quenched_u1_angles_counter(L, L, beta, therm, seed=31)
+    samples = []
+    for k in range(meas):
+        theta = W.quenched_u1_angles_counter(L, L, beta, 1, 31, theta=theta, first_sweep=therm + k)
+        samples.append(W.mean_plaquette(theta))
+    samples = np.array(samples)
+    bins = samples.reshape(20, -1).mean(axis=1)
+    err = bins.std(ddof=1) / np.sqrt(len(bins))
+    assert abs(samples.mean() - plaquette_exact(beta)) < 5 * err + 2e-4

@@ -67,6 +67,15 @@ def _metropolis_half(theta, mu, parity, beta, eps, rng):
     """Update every link of direction mu whose other coordinate has the given
     parity.  Such links share no plaquette, so they are updated at once."""
     Lt, Lx = theta.shape[1:]
+    u_prop = rng.random((Lt, Lx))
+    u_acc = rng.random((Lt, Lx))
+    return _metropolis_half_u(theta, mu, parity, beta, eps, u_prop, u_acc)
+
+
+def _metropolis_half_u(theta, mu, parity, beta, eps, u_prop, u_acc):
+    """The half-sweep of _metropolis_half with its uniforms given: u_prop
+    proposes theta' = theta + eps (2 u_prop - 1), u_acc accepts (per site)."""
+    Lt, Lx = theta.shape[1:]
     th0, th1 = theta[0], theta[1]
     if mu == 0:
         # link theta0(x,t) enters p(x,t) with + and p(x,t-1) with -.
@@ -82,8 +91,6 @@ def _metropolis_half(theta, mu, parity, beta, eps, rng):
              - np.roll(th1, 1, axis=1))                                           # p(x-1,t) = b + th1
         mask = (np.arange(Lx)[None, :] % 2 == parity) & np.ones((Lt, 1), bool)
         cur = th1
-    u_prop = rng.random((Lt, Lx))
-    u_acc = rng.random((Lt, Lx))
     new = cur + eps * (2.0 * u_prop - 1.0)
     if mu == 0:
         s_old = np.cos(cur + a) + np.cos(b - cur)
@@ -114,6 +121,72 @@ def quenched_u1_angles(Lx: int, Lt: int, beta: float, sweeps: int, seed: int,
         for mu in (0, 1):
             for parity in (0, 1):
                 _metropolis_half(theta, mu, parity, float(beta), float(eps), rng)
+    return theta
+
+
+# ---------------------------------------------------------------------------
+# Counter-based uniforms (Philox4x32-10, Salmon, Moraes, Dror, Shaw, SC'11) for
+# the Metropolis generator that has a GPU twin: every uniform is a function of
+# (seed, sweep, direction, parity, site), so both sides draw the same numbers
+# without sharing a stream.
+# ---------------------------------------------------------------------------
+PHILOX_M = (0xD2511F53, 0xCD9E8D57)      # round multipliers
+PHILOX_W = (0x9E3779B9, 0xBB67AE85)      # key increments (golden ratio, sqrt(3) - 1)
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32(ctr, key, rounds: int = 10):
+    """Philox4x32 block function on uint32 counters ctr[..., 4] with key (k0, k1):
+    each round multiplies counter words 0 and 2 by M0 and M1 into 64-bit
+    products (hi, lo) and forms (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the
+    key is advanced by (W0, W1) before every round but the first."""
+    c = [np.asarray(ctr[..., i], dtype=np.uint64) for i in range(4)]
+    k0, k1 = np.uint64(key[0]), np.uint64(key[1])
+    for r in range(rounds):
+        if r:
+            k0 = (k0 + np.uint64(PHILOX_W[0])) & _M32
+            k1 = (k1 + np.uint64(PHILOX_W[1])) & _M32
+        p0 = np.uint64(PHILOX_M[0]) * c[0]
+        p1 = np.uint64(PHILOX_M[1]) * c[2]
+        c = [((p1 >> np.uint64(32)) ^ c[1] ^ k0) & _M32, p1 & _M32,
+             ((p0 >> np.uint64(32)) ^ c[3] ^ k1) & _M32, p0 & _M32]
+    return np.stack(c, axis=-1).astype(np.uint32)
+
+
+def uniform53(hi, lo):
+    """A double in [0, 1) from two uint32 words: 27 + 26 bits, exact."""
+    return ((np.asarray(hi, np.uint64) >> np.uint64(5)).astype(np.float64) * 67108864.0
+            + (np.asarray(lo, np.uint64) >> np.uint64(6)).astype(np.float64)) * 2.0 ** -53
+
+
+def metropolis_uniforms(Lx: int, Lt: int, seed: int, sweep: int, mu: int, parity: int):
+    """(u_prop, u_acc)[Lt][Lx] of one half-sweep: Philox4x32-10 at counter
+    (t Lx + x, 4 sweep + 2 mu + parity (low, high 32 bits), 0), key (seed low,
+    seed high); u_prop from words 0, 1 and u_acc from words 2, 3."""
+    half = 4 * int(sweep) + 2 * int(mu) + int(parity)
+    ctr = np.zeros((Lt * Lx, 4), dtype=np.uint64)
+    ctr[:, 0] = np.arange(Lt * Lx, dtype=np.uint64)
+    ctr[:, 1] = half & 0xFFFFFFFF
+    ctr[:, 2] = half >> 32
+    out = philox4x32(ctr, (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF))
+    u_prop = uniform53(out[:, 0], out[:, 1]).reshape(Lt, Lx)
+    u_acc = uniform53(out[:, 2], out[:, 3]).reshape(Lt, Lx)
+    return u_prop, u_acc
+
+
+def quenched_u1_angles_counter(Lx: int, Lt: int, beta: float, sweeps: int, seed: int,
+                               eps: float = 1.0, theta=None, first_sweep: int = 0) -> np.ndarray:
+    """The checkerboard Metropolis of quenched_u1_angles with counter-based
+    uniforms (metropolis_uniforms): sweeps first_sweep .. first_sweep + sweeps - 1
+    from theta (cold start theta = 0 when None).  Returns the angles."""
+    if Lx % 2 or Lt % 2:
+        raise ValueError("Lx and Lt must be even")
+    theta = np.zeros((2, Lt, Lx), dtype=np.float64) if theta is None else np.array(theta, np.float64)
+    for sw in range(int(first_sweep), int(first_sweep) + int(sweeps)):
+        for mu in (0, 1):
+            for parity in (0, 1):
+                u_prop, u_acc = metropolis_uniforms(Lx, Lt, seed, sw, mu, parity)
+                _metropolis_half_u(theta, mu, parity, float(beta), float(eps), u_prop, u_acc)
     return theta
 
 
