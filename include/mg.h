@@ -129,6 +129,14 @@ typedef struct {
                                            and keeps the fastest whose output
                                            is bit-identical to the default
                                            shape's (1)                          */
+  int remass_quadratic;                 /* nonzero: keep G0_l and G1_l with
+                                           A_l(m) = G0_l + m G1_l + m^2 I on
+                                           every coarse level (A(m) = A0 +
+                                           m (D0 + D0^dagger) + m^2 and
+                                           P^dagger P = I), so a new mass is one
+                                           combination per level instead of the
+                                           Galerkin products; two more FP64
+                                           copies of each coarse operator (1)   */
 } mg_params;
 
 typedef struct {

@@ -142,6 +142,9 @@ enum CoarseWeights { W_F64 = 0, W_F32 = 1, W_BF16 = 2 };
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
                          int n, int nrhs, const Epilogue& ep, cudaStream_t s);
 // A (complex128) -> float2 or bf16x2 copy
+// out = a X + b Y + c I for coarse operators of `sites` sites and n dof (FP64).
+cudaError_t coarse_lincomb(double a, const void* X, double b, const void* Y, double c, void* out,
+                           long long sites, int n, cudaStream_t s);
 cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
                            cudaStream_t s);
 

@@ -303,6 +303,29 @@ cudaError_t coarse_convert(const void* A64, void* out, int weights, long long co
   return cudaGetLastError();
 }
 
+// out = a X + b Y + c I on 9-point block stencils [site][d][r][s] (I: the
+// identity blocks of the d = 4 displacement); out may alias X or Y.
+__global__ void k_coarse_lincomb(double a, const double2* X, double b, const double2* Y, double c,
+                                 double2* out, long long count, int n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int q = (int)(i % ((long long)9 * n * n));
+  const int d = q / (n * n), r = (q / n) % n, sc = q % n;
+  const double2 x = X[i], y = Y[i];
+  double re = a * x.x + b * y.x, im = a * x.y + b * y.y;
+  if (d == 4 && r == sc) re += c;
+  out[i] = make_double2(re, im);
+}
+
+cudaError_t coarse_lincomb(double a, const void* X, double b, const void* Y, double c, void* out,
+                           long long sites, int n, cudaStream_t s) {
+  const long long count = sites * 9 * n * n;
+  k_coarse_lincomb<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+      a, (const double2*)X, b, (const double2*)Y, c, (double2*)out, count, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Restriction and prolongation.  Vst[i][c][k][a]: component c*h + a of vector
 // k at fine site i, orthonormal per (block, chirality).

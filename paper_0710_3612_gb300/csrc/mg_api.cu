@@ -29,6 +29,8 @@ struct Level {
   double2* A64 = nullptr;
   float2* A32 = nullptr;
   void* A16 = nullptr;
+  double2* G0 = nullptr;                 // A(m) = G0 + m G1 + m^2 I (remass_quadratic)
+  double2* G1 = nullptr;
   // transfer to the next level
   int bx = 0, bt = 0, Nv = 0;
   double2* Vst64 = nullptr;
@@ -91,6 +93,7 @@ struct mg_handle {
   std::string err;
   long long fine_applies = 0, vcycles = 0;
   std::vector<double> refine_rho;   // rho of each adaptive pass made by mg_setup
+  bool g_built = false;             // G0, G1 of every coarse level hold the current vectors
   // optional per-family event timing
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev[MG_KF_COUNT];
@@ -342,7 +345,40 @@ void smoother_coefficients(mg_handle* h, int l, void* q, void* r1) {
   L.c1 = -om * om * a0 * a1;
 }
 
+// G0 and G1 of every coarse level from the vectors: on level 2, G0 = the
+// Galerkin product at m = 0 and G1 = (the product at m = 1) - G0 - I; below,
+// both pass through P^dagger . P like the operator itself.
+void build_quadratic(mg_handle* h) {
+  for (int l = 0; l + 1 < h->L; ++l) {
+    Level& L = h->lv[l];
+    Level& C = h->lv[l + 1];
+    ProfScope prof(h, MG_KF_GALERKIN);
+    if (l == 0) {
+      ck(h, galerkin_fine(h->U64, 4.0, L.Vst64, h->Wbuf, C.G0, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin G0");
+      ck(h, galerkin_fine(h->U64, 5.0, L.Vst64, h->Wbuf, C.G1, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin A(1)");
+      ck(h, coarse_lincomb(1.0, C.G1, -1.0, C.G0, -1.0, C.G1, C.V, C.n, h->s), "G1");
+    } else {
+      ck(h, galerkin_coarse(L.G0, L.Vst64, C.G0, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin G0");
+      ck(h, galerkin_coarse(L.G1, L.Vst64, C.G1, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin G1");
+    }
+  }
+  h->g_built = true;
+}
+
 void build_coarse_ops(mg_handle* h) {
+  if (h->p.remass_quadratic) {
+    if (!h->g_built) build_quadratic(h);
+    const double m = h->mass;
+    for (int l = 1; l < h->L; ++l) {
+      Level& C = h->lv[l];
+      ProfScope prof(h, MG_KF_GALERKIN);
+      ck(h, coarse_lincomb(1.0, C.G0, m, C.G1, m * m, C.A64, C.V, C.n, h->s), "A(m)");
+      const long long cnt = (long long)C.V * 9 * C.n * C.n;
+      ck(h, coarse_convert(C.A64, C.A32, W_F32, cnt, h->s), "convert f32");
+      ck(h, coarse_convert(C.A64, C.A16, W_BF16, cnt, h->s), "convert bf16");
+    }
+    return;
+  }
   for (int l = 0; l + 1 < h->L; ++l) {
     Level& L = h->lv[l];
     Level& C = h->lv[l + 1];
@@ -891,6 +927,10 @@ void allocate_storage(mg_handle* h) {
       L.A64 = dalloc<double2>(h, ab * sizeof(double2));
       L.A32 = dalloc<float2>(h, ab * sizeof(float2));
       L.A16 = dalloc(h, ab * 4);
+      if (h->p.remass_quadratic) {
+        L.G0 = dalloc<double2>(h, ab * sizeof(double2));
+        L.G1 = dalloc<double2>(h, ab * sizeof(double2));
+      }
     }
     if (l + 1 < h->L) {
       L.Vst64 = dalloc<double2>(h, (size_t)L.V * 2 * L.Nv * (L.n / 2) * sizeof(double2));
@@ -1174,6 +1214,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->coarsest_gj_tcgen05 = 0;
   p->refine_cycles = 30;
   p->autotune = 1;
+  p->remass_quadratic = 1;
   return MG_OK;
 }
 
@@ -1334,6 +1375,14 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
       copy(L.eta, S.eta, (size_t)L.count() * sizeof(double2));
       L.lambda_max = S.lambda_max;
       L.omega_relax = S.omega_relax;
+    }
+    if (h->p.remass_quadratic && src->g_built) {
+      for (int l = 1; l < h->L; ++l) {
+        const size_t ab = (size_t)h->lv[l].V * 9 * h->lv[l].n * h->lv[l].n * sizeof(double2);
+        copy(h->lv[l].G0, src->lv[l].G0, ab);
+        copy(h->lv[l].G1, src->lv[l].G1, ab);
+      }
+      h->g_built = true;
     }
     set_mass_internal(h, mass);
   });

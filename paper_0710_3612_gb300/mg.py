@@ -38,7 +38,7 @@ class MgParams(ctypes.Structure):
                 ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int),
                 ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
                 ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("remass_quadratic", ctypes.c_int)]
 
 
 class MgStencilTuning(ctypes.Structure):

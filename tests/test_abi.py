@@ -57,7 +57,7 @@ def test_param_struct_layout_matches(lib_path):
     # with adaptive passes (1-based levels in the library, 0-based in workloads)
     r = mg.make_params(32, 16, [(4, 4), (2, 2)], [3, 5], refine_levels=[1, 2, 2])
     assert r.refine_cycles == 30 and list(r.refine_levels[:4]) == [1, 2, 2, 0]
-    assert p.autotune == 1
+    assert p.autotune == 1 and p.remass_quadratic == 1
     assert mg.lib().mg_stencil_tunings(None, 0) == 0        # nothing tuned without a device
     assert mg.mg_setup_noise_len(r) == W.setup_noise_len(32, 16, [(4, 4), (2, 2)], [3, 5], [0, 1, 1])
 
@@ -87,6 +87,11 @@ def test_setup_bytes_is_host_only(lib_path):
             continue
         with pytest.raises(mg.MgError):
             mg.mg_setup_bytes(q)
+    # the quadratic re-mass keeps two more FP64 copies of each coarse operator
+    p0 = mg.make_params(128, 128, [(4, 4), (2, 2)], [8, 8], remass_quadratic=0)
+    p0.setup_noise = 1
+    coarse = (32 * 32 * 9 * 16 * 16 + 16 * 16 * 9 * 16 * 16) * 16
+    assert res - mg.mg_setup_bytes(p0)[0] == 2 * coarse
     q = mg.make_params(128, 128, [(4, 4), (2, 2)], [16, 8], refine_levels=[1])
     q.setup_noise = 1
     with pytest.raises(mg.MgError):      # 4x4 blocks of 2 components hold 16 vectors at most

@@ -445,3 +445,30 @@ def test_argument_errors(mg):
         with pytest.raises(mg.MgError) as e:
             s.solve(b, solver=mg.SOLVER_MGCG_FP64)
         assert e.value.status == 5
+
+
+def test_quadratic_remass_equals_galerkin_products(mg):
+    """With remass_quadratic (default) every coarse operator after mg_set_mass
+    is G0 + m G1 + m^2 I; it matches the Galerkin products of the same vectors
+    at that mass (remass_quadratic = 0) to rounding, and the oracle's."""
+    Lx, Lt, beta, sweeps, seed, m, blocks, Nv = CASES[list(CASES)[-1]]
+    U = W.links_from_angles(W.quenched_u1_angles(Lx, Lt, beta, sweeps, seed))
+    noise = W.setup_noise(Lx, Lt, blocks, Nv, seed + 100)
+    H = omg.setup(U, m, blocks, Nv, noise)
+    with mg.Multigrid(dev(U), m, blocks, Nv, dev(noise)) as q, \
+            mg.Multigrid(dev(U), m, blocks, Nv, dev(noise), remass_quadratic=0) as g:
+        assert mg.mg_device_bytes(q.h) > mg.mg_device_bytes(g.h)
+        for m2 in (m + 0.3, -0.05, m):
+            q.set_mass(m2)
+            g.set_mass(m2)
+            omg.set_mass(H, m2)
+            for l in range(1, H.L):
+                op = H.levels[l].op
+                oq, og = (torch.empty(op.M.shape, dtype=torch.complex128, device=DEV) for _ in range(2))
+                mg.mg_get_coarse_op(q.h, l + 1, oq)
+                mg.mg_get_coarse_op(g.h, l + 1, og)
+                a, b = host(oq), host(og)
+                scale = np.max(np.abs(op.M))
+                assert np.max(np.abs(a - b)) <= 1e-13 * scale, f"level {l + 1} at m = {m2}"
+                rowmax = np.max(np.abs(op.M), axis=(2, 4), keepdims=True)
+                check(a, op.M, rowmax, 1e-11, f"A_c level {l + 1} at m = {m2}")

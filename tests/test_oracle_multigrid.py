@@ -225,3 +225,23 @@ def test_set_mass_matches_fresh_galerkin():
     mg.set_mass(H, 0.25)
     A = mg.WilsonNormalOp(U, 0.25).dense()
     assert np.max(np.abs(H.levels[1].op.dense() - P.conj().T @ A @ P)) < 1e-13 * np.max(np.abs(A))
+
+
+def test_coarse_operators_are_quadratic_in_the_mass():
+    """A(m) = A0 + m (D0 + D0^dagger) + m^2 and P^dagger P = I on every level,
+    so each coarse operator is G0 + m G1 + m^2 I with G0 = A_c(0) and
+    G1 = A_c(1) - A_c(0) - I (the identity behind re-massing by combination)."""
+    U, H = make(L=(16, 16), blocks=((4, 4), (2, 2)), Nv=(3, 2), m=-0.4)
+    ops = {}
+    for m in (0.0, 1.0, -0.4, 0.37, -2.1):
+        mg.set_mass(H, m)
+        ops[m] = [lv.op.dense() for lv in H.levels[1:]]
+    for l in range(len(ops[0.0])):
+        G0 = ops[0.0][l]
+        I = np.eye(G0.shape[0])
+        G1 = ops[1.0][l] - G0 - I
+        for m in (-0.4, 0.37, -2.1):
+            want = ops[m][l]
+            assert np.max(np.abs(G0 + m * G1 + m * m * I - want)) <= 1e-12 * np.max(np.abs(want))
+        # G1 is Hermitian (P^dagger (D0 + D0^dagger) P)
+        assert np.max(np.abs(G1 - G1.conj().T)) <= 1e-12 * np.max(np.abs(G1))
