@@ -160,6 +160,31 @@ typedef struct {
   double us_default;          /* microseconds per launch of the default shape  */
 } mg_stencil_tuning;
 
+/* Critical mass m_crit (the mass gap m - m_crit of Sec. 4): the heaviest
+ * mass below m_hi at which D(m) is singular, i.e. at which an eigenvalue of the
+ * Hermitian H(m) = sigma_3 D(m) crosses zero.  Spectral-flow scan: every
+ * eigenvalue of H moves by at most |dm| (dH/dm = sigma_3), so
+ * mu(m) = min |eig H(m)| is 1-Lipschitz and no crossing lies within mu(m) of
+ * m; from m_hi the scan steps down by safety * mu(m).  mu(m) and the signed
+ * eigenvalue lam come from inverse iteration with H^-1 = A^-1 D^dagger
+ * sigma_3 (FP64 MG-CG solves on h, re-massed as the scan goes; warm-started
+ * from the previous eigenvector), dlam/dm = <v, sigma_3 v>.  Once mu <
+ * newton_below, Newton steps aimed at |lam| = newton_floor (never closer,
+ * where the solves lose accuracy) bring m near the crossing; there the
+ * eigenvalue lam_D of D(m) nearest zero is found by inverse iteration with
+ * D^-1 = A^-1 D^dagger, and since D(m) = D_0 + m shifts every eigenvalue by m
+ * exactly, m_crit = m - lam_D when lam_D is real (|Im| <= 1e-8 |Re|) and
+ * agrees with the cubic Hermite interpolant of the last two (lam, dlam/dm)
+ * points; otherwise that interpolant's root is returned.
+ *   v0:  device complex128 fine vector, the first inverse-iteration start.
+ *   *m_crit, *slope (dlam/dm there, may be NULL), *evals (eigen-solves
+ *   made, may be NULL).  h is left at the last mass evaluated.
+ * MG_ERR_NOCONV when no crossing is found above m_lo within max_evals
+ * eigen-solves; MG_ERR_ARG for invalid arguments or nlevels < 2. */
+mg_status mg_critical_mass(mg_handle* h, double m_hi, double m_lo, const void* v0, double safety,
+                           double newton_below, double newton_floor, int max_evals,
+                           double* m_crit, double* slope, int* evals);
+
 /* Quenched U(1) gauge field on the device (the paper's gauge ensembles,
  * Sec. 4: Wilson plaquette action S = -beta sum_p Re U_p): checkerboard
  * Metropolis sweeps first_sweep .. first_sweep + sweeps - 1 on the link angles

@@ -106,6 +106,9 @@ template <typename R>
 cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int Lx, int Lt,
                      int nrhs, const Epilogue& ep, cudaStream_t s);
 
+// out = sigma_3 in for V fine two-spinors (FP64); out may alias in.
+cudaError_t sigma3_mul(const void* in, void* out, long long V, cudaStream_t s);
+
 // Launch shape chosen by the autotuner for one (precision, Lx, Lt, nrhs):
 // tile tx x ty with rpt rows per thread (0 x 0: the streaming kernel), timed
 // against the default shape; only shapes whose output is bit-identical to

@@ -579,6 +579,21 @@ cudaError_t wilson_A(const void* in, void* out, const void* U, double diag, int 
   return cudaGetLastError();
 }
 
+// out = sigma_3 in on V two-spinors (FP64): spin component 1 negated.
+__global__ void k_sigma3(const double2* __restrict__ in, double2* out, long long V) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  const double2 a = in[2 * i], b = in[2 * i + 1];
+  out[2 * i] = a;
+  out[2 * i + 1] = make_double2(-b.x, -b.y);
+}
+
+cudaError_t sigma3_mul(const void* in, void* out, long long V, cudaStream_t s) {
+  k_sigma3<<<(unsigned)((V + 255) / 256), 256, 0, s>>>((const double2*)in, (double2*)out, V);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void k_fold_links(const double2* __restrict__ g, cplx_t<R>* __restrict__ U, int Lx,
                              int Lt) {

@@ -1071,6 +1071,98 @@ void autotune_fine(mg_handle* h) {
   sync(h);
 }
 
+// ----- critical mass (the mass gap m - m_crit of Sec. 4) ----------------------
+struct EigH {
+  double lam = 0.0, slope = 0.0;
+  int its = 0;
+};
+
+// Eigenvalue of the Hermitian H(m) = sigma_3 D(m) nearest zero, by inverse
+// iteration with H^-1 = A^-1 D^dagger sigma_3 (one MG-CG solve per step,
+// warm-started from v, which holds the unit eigenvector on return): lam =
+// <v, sigma_3 D v>, and its derivative dlam/dm = <v, sigma_3 v> (dH/dm =
+// sigma_3, first-order perturbation theory).  w, t: scratch fine vectors.
+EigH nearest_eig_H(mg_handle* h, double m, void* v, void* w, void* t, int solver, double solve_tol,
+                   int max_inv, double conv) {
+  if (m != h->mass) set_mass_internal(h, m);
+  const Level& F = h->lv[0];
+  const long long c = F.count();
+  const double diag = 4.0 + m;
+  EigH e;
+  double prev = 0.0;
+  for (int k = 0; k < max_inv; ++k) {
+    ck(h, sigma3_mul(v, t, F.V, h->s), "sigma3");
+    ck(h, wilson_D<double>(t, w, h->U64, diag, F.Lx, F.Lt, 1, true, h->s), "D dagger");
+    mg_solve_info info{};
+    solve_batch(h, w, t, 1, solve_tol, 100000, solver, &info);   // an inexact solve still iterates
+    ck(h, norm2<double>(t, c, 1, h->partials, slot(h, S_T0), h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(t, v, slot(h, S_T0), c, 1, h->s), "normalise");
+    ck(h, wilson_D<double>(v, w, h->U64, diag, F.Lx, F.Lt, 1, false, h->s), "D");
+    ck(h, sigma3_mul(w, w, F.V, h->s), "sigma3");
+    ck(h, dot<double>(v, w, c, 1, h->partials, slot(h, S_T1), h->s), "dot");
+    e.lam = read_scalar(h, S_T1);
+    e.its = k + 1;
+    if (k && std::fabs(e.lam - prev) <= conv * std::fabs(e.lam)) break;
+    prev = e.lam;
+  }
+  ck(h, sigma3_mul(v, w, F.V, h->s), "sigma3");
+  ck(h, dot<double>(v, w, c, 1, h->partials, slot(h, S_T1), h->s), "dot");
+  e.slope = read_scalar(h, S_T1);
+  return e;
+}
+
+// Eigenvalue of D(m) nearest zero, by inverse iteration with D^-1 =
+// A^-1 D^dagger (warm-started from v, which holds the unit right eigenvector
+// on return): lam = <v, D v>.  Since D(m) = D_0 + m, an eigenvalue of D(m) is
+// lam_0 + m exactly, so a real one gives the mass at which it vanishes.
+double2 nearest_eig_D(mg_handle* h, double m, void* v, void* w, void* t, int solver,
+                      double solve_tol, int max_inv, double conv) {
+  if (m != h->mass) set_mass_internal(h, m);
+  const Level& F = h->lv[0];
+  const long long c = F.count();
+  const double diag = 4.0 + m;
+  double2 lam = make_double2(0.0, 0.0), prev = lam;
+  for (int k = 0; k < max_inv; ++k) {
+    ck(h, wilson_D<double>(v, w, h->U64, diag, F.Lx, F.Lt, 1, true, h->s), "D dagger");
+    mg_solve_info info{};
+    solve_batch(h, w, t, 1, solve_tol, 100000, solver, &info);
+    ck(h, norm2<double>(t, c, 1, h->partials, slot(h, S_T0), h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(t, v, slot(h, S_T0), c, 1, h->s), "normalise");
+    ck(h, wilson_D<double>(v, w, h->U64, diag, F.Lx, F.Lt, 1, false, h->s), "D");
+    ck(h, dot<double>(v, w, c, 1, h->partials, slot(h, S_T1), h->s), "dot");
+    lam.x = read_scalar(h, S_T1);
+    lam.y = h->hscal[1];
+    if (k && std::hypot(lam.x - prev.x, lam.y - prev.y) <= conv * std::hypot(lam.x, lam.y)) break;
+    prev = lam;
+  }
+  return lam;
+}
+
+// Root of the cubic Hermite interpolant of (m0, f0, d0), (m1, f1, d1) nearest
+// m1 (Newton on the cubic from the Newton step of the second point).
+double hermite_root(double m0, double f0, double d0, double m1, double f1, double d1) {
+  const double hh = m1 - m0;
+  auto p = [&](double x, double* dp) {
+    const double u = (x - m0) / hh, u2 = u * u, u3 = u2 * u;
+    const double h00 = 2 * u3 - 3 * u2 + 1, h10 = u3 - 2 * u2 + u, h01 = -2 * u3 + 3 * u2,
+                 h11 = u3 - u2;
+    const double g00 = 6 * u2 - 6 * u, g10 = 3 * u2 - 4 * u + 1, g01 = -6 * u2 + 6 * u,
+                 g11 = 3 * u2 - 2 * u;
+    *dp = (g00 * f0 + g01 * f1) / hh + g10 * d0 + g11 * d1;
+    return h00 * f0 + hh * h10 * d0 + h01 * f1 + hh * h11 * d1;
+  };
+  double x = m1 - f1 / d1;
+  for (int k = 0; k < 60; ++k) {
+    double dp = 0.0;
+    const double f = p(x, &dp);
+    if (!(dp != 0.0)) break;
+    const double dx = f / dp;
+    x -= dx;
+    if (std::fabs(dx) <= 1e-16 * std::fabs(x)) break;
+  }
+  return x;
+}
+
 // One adaptive pass on level lr of src (Sec. 3; the contract is mg_refine's).
 // noise: the random starts of the levels below lr for the refined Nv.  The
 // arguments are validated by the caller.
@@ -1450,6 +1542,88 @@ mg_status mg_gauge_links(const double* theta, void* U, int Lx, int Lt, void* str
   if (!theta || !U || Lx < 1 || Lt < 1) { g_last_error = "invalid arguments"; return MG_ERR_ARG; }
   cudaError_t e = links_from_angles(theta, U, 2LL * Lx * Lt, (cudaStream_t)stream);
   if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return MG_ERR_CUDA; }
+  return MG_OK;
+}
+
+mg_status mg_critical_mass(mg_handle* h, double m_hi, double m_lo, const void* v0, double safety,
+                           double newton_below, double newton_floor, int max_evals,
+                           double* m_crit, double* slope, int* evals) {
+  if (!h || !v0 || !m_crit || !(m_hi > m_lo) || !(safety > 0.0 && safety < 1.0) ||
+      !(newton_below > newton_floor && newton_floor > 0.0) || max_evals < 1 || h->L < 2) {
+    if (h) h->err = "invalid critical-mass arguments";
+    g_last_error = "invalid critical-mass arguments";
+    return MG_ERR_ARG;
+  }
+  const long long c = h->lv[0].count();
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 3 * c * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "device allocation failed (critical-mass scratch)";
+    return MG_ERR_NOMEM;
+  }
+  double2* v = (double2*)buf;
+  double2* w = v + c;
+  double2* t = w + c;
+  int n_ev = 0;
+  bool found = false;
+  double root = 0.0, root_slope = 0.0;
+  const int solver = MG_SOLVER_MGCG_FP64;
+  const double solve_tol = 1e-9, conv = 1e-10;
+  const int max_inv = 60;
+  mg_status st = guarded(h, [&]() {
+    ck(h, norm2<double>(v0, c, 1, h->partials, slot(h, S_T0), h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(v0, v, slot(h, S_T0), c, 1, h->s), "normalise");
+    double m = m_hi;
+    while (m > m_lo && n_ev < max_evals && !found) {
+      const EigH e = nearest_eig_H(h, m, v, w, t, solver, solve_tol, max_inv, conv);
+      ++n_ev;
+      const double mu = std::fabs(e.lam);
+      if (mu < newton_below && std::fabs(e.slope) > 1e-3) {
+        // Newton steps aimed at |lam| = newton_floor on the same side (no
+        // solve closer to the singular point), then the root of the cubic
+        // Hermite interpolant of the last two points
+        double pm = m, pl = e.lam, ps = e.slope, qm = m, ql = e.lam, qs = e.slope;
+        int npts = 1;
+        bool ok = true;
+        for (int k = 0; k < 40 && std::fabs(ql) > 1.5 * newton_floor && n_ev < max_evals; ++k) {
+          const double target = ql > 0 ? newton_floor : -newton_floor;
+          const double mn = qm - (ql - target) / qs;
+          if (!(m - 4.0 * mu / std::fabs(e.slope) <= mn && mn <= m + 1e-15)) { ok = false; break; }
+          const EigH f = nearest_eig_H(h, mn, v, w, t, solver, solve_tol, max_inv, conv);
+          ++n_ev;
+          if (std::fabs(f.lam) > 0.75 * std::fabs(ql) || std::fabs(f.slope) < 1e-3) { ok = false; break; }
+          const bool crossed = (f.lam > 0) != (ql > 0);   // the root is now bracketed
+          pm = qm; pl = ql; ps = qs;
+          qm = mn; ql = f.lam; qs = f.slope;
+          ++npts;
+          if (crossed) break;
+        }
+        if (ok) {
+          root = npts >= 2 ? hermite_root(pm, pl, ps, qm, ql, qs) : qm - ql / qs;
+          root_slope = qs;
+          // the exact shift: a real eigenvalue lam_D of D(qm) vanishes at qm - lam_D
+          const double2 ld = nearest_eig_D(h, qm, v, w, t, solver, solve_tol, max_inv, 1e-13);
+          ++n_ev;
+          if (std::fabs(ld.y) <= 1e-8 * std::fabs(ld.x) + 1e-13 &&
+              std::fabs(qm - ld.x - root) <= 0.5 * std::fabs(qm - root) + 1e-12)
+            root = qm - ld.x;
+          found = root <= m + 1e-15 && root >= m - 4.0 * mu / std::fabs(e.slope);
+          if (found) break;
+        }
+      }
+      m -= safety * mu;
+    }
+  });
+  cudaFree(buf);
+  if (evals) *evals = n_ev;
+  if (st != MG_OK) { g_last_error = h->err; return st; }
+  if (!found) {
+    h->err = "no crossing above m_lo within max_evals";
+    g_last_error = h->err;
+    return MG_ERR_NOCONV;
+  }
+  *m_crit = root;
+  if (slope) *slope = root_slope;
   return MG_OK;
 }
 

@@ -103,6 +103,8 @@ _SIGS = {
     "mg_gauge_metropolis": (_i, [_vp, _i, _i, _d, _d, _i, _ll, ctypes.c_ulonglong, _vp,
                                  ctypes.POINTER(_ll)]),
     "mg_gauge_links": (_i, [_vp, _vp, _i, _i, _vp]),
+    "mg_critical_mass": (_i, [_vp, _d, _d, _vp, _d, _d, _d, _i, ctypes.POINTER(_d),
+                              ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "mg_kernel_launches": (ctypes.c_ulonglong, []),
     "mg_profile_enable": (_i, [_vp, _i]),
     "mg_profile_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]),
@@ -207,6 +209,18 @@ def mg_refine(h, level, e0, ncycles, noise=None, stream=None, e_out=None):
                            _stream_ptr(stream), ctypes.byref(out), ctypes.byref(rho),
                            None if e_out is None else _ptr(e_out, torch.complex128)), h)
     return out, rho.value
+
+
+def critical_mass(h, v0, m_hi=-1.9, m_lo=-2.4, safety=0.9, newton_below=1e-2,
+                  newton_floor=1e-3, max_evals=200):
+    """m_crit by the spectral-flow scan on the GPU; returns (m_crit, slope, evals)."""
+    import torch
+    m, sl, ev = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().mg_critical_mass(h, float(m_hi), float(m_lo), _ptr(v0, torch.complex128),
+                                  float(safety), float(newton_below), float(newton_floor),
+                                  int(max_evals), ctypes.byref(m), ctypes.byref(sl),
+                                  ctypes.byref(ev)), h)
+    return m.value, sl.value, ev.value
 
 
 def gauge_metropolis(theta, beta, sweeps, seed, first_sweep=0, eps=1.0, stream=None):
