@@ -18,10 +18,14 @@ Contents, each following the paper (Brannick, Brower, Clark, Osborn, Rebbi,
                    Galerkin coarse operator P^dagger A P (Eq. Galerkin), the
                    frozen two-step minimum-residual smoother (Sec. 4), the
                    five-step V-cycle (Sec. 2), the exact coarsest solve, and
-                   the adaptive setup relaxation (Eq. relax).
+                   the adaptive setup relaxation (Eq. relax) and the adaptive
+                   refinement by V-cycles (Sec. 3).
 * ``krylov``    -- plain CG and MG-preconditioned CG (Sec. 4).
 * ``critical``  -- the critical-mass finder used to choose near-critical
                    masses (Sec. 4, mass gap m - m_crit).
+* ``smoothed``  -- smoothed aggregation: the Richardson step on the vectors
+                   before the prolongator is formed, its damping minimising
+                   the condition number of the coarse operator (Sec. 3).
 
 Every function states the passage it follows.  Pins against the paper and
 the mathematics live in ``tests/test_oracle_*.py``; parity of any function
