@@ -96,3 +96,22 @@ def test_setup_bytes_is_host_only(lib_path):
     q.setup_noise = 1
     with pytest.raises(mg.MgError):      # 4x4 blocks of 2 components hold 16 vectors at most
         mg.mg_setup_bytes(q)
+
+
+def test_new_entry_points_reject_arguments_on_the_host(lib_path):
+    """mg_refine, mg_critical_mass, mg_gauge_metropolis and mg_gauge_links
+    validate their arguments before any device work (no GPU needed)."""
+    import ctypes
+    from paper_0710_3612_gb300 import mg
+    L = mg.lib()
+    out, rho = ctypes.c_void_p(), ctypes.c_double()
+    assert L.mg_refine(None, 1, None, 1, None, None, ctypes.byref(out), ctypes.byref(rho), None) == 1
+    assert L.mg_refine(None, 1, None, 1, None, None, None, None, None) == 1
+    m = ctypes.c_double()
+    assert L.mg_critical_mass(None, -1.9, -2.4, None, 0.9, 1e-2, 1e-3, 10, ctypes.byref(m), None, None) == 1
+    acc = ctypes.c_longlong()
+    assert L.mg_gauge_metropolis(None, 8, 8, 1.0, 1.0, 1, 0, 1, None, ctypes.byref(acc)) == 1
+    assert L.mg_gauge_links(None, None, 8, 8, None) == 1
+    rr = (ctypes.c_double * 4)()
+    n = ctypes.c_int()
+    assert L.mg_get_refine_rho(None, rr, 4, ctypes.byref(n)) == 1
