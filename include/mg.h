@@ -324,6 +324,16 @@ mg_status mg_apply_A(mg_handle* h, const void* in, void* out, int nrhs, int prec
 mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, int nrhs,
                           int precision);
 
+/* Tensor-core kernel of the multi-right-hand-side BF16 coarse apply (Eq.
+ * Galerkin at every coarse level of the FP32 V-cycle; 8 .. 64 right-hand
+ * sides): 0 = tcgen05.mma with the accumulator in tensor memory (coarse
+ * levels with 2Nv = 16 or 24 dof per site, the others use 1), 1 = mma.sync
+ * (default).  Both
+ * compute with the stored BF16 blocks and X carried as two BF16 parts, FP32
+ * accumulation.  Process-wide; takes effect for launches (and CUDA graphs)
+ * made after the call.  MG_ERR_ARG for other values. */
+mg_status mg_set_coarse_tensor_kernel(int kind);
+
 /* Restriction P^dagger from level `level` to level+1 (Sec. 2 step 2) and
  * prolongation P from level+1 to `level` (Sec. 2 step 4), 1 <= level < nlevels.
  * precision F64 or F32. */
@@ -343,6 +353,20 @@ mg_status mg_vcycle(mg_handle* h, const void* in, void* out, int precision);
  * the iteration count fixed at set-up (the count at which a test vector
  * reaches coarsest_tol, times 1.25 plus 4). */
 mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out);
+
+/* The coarsest solve fixed at set-up (Sec. 2: exact solve on the coarsest
+ * level).  *dense: 1 = FP32 explicit inverse refined in FP64, 0 = FP64 CG on
+ * the coarsest stencil; *steps: FP64 refinement steps, or CG iterations, of
+ * one coarsest solve; *test_residual: the largest relative residual the
+ * set-up's test vectors (two seeded complex Gaussian vectors) reached with
+ * that count (<= coarsest_tol).  mg_setup / mg_set_mass fail with
+ * MG_ERR_NOCONV, and say what they reached, when a test vector does not reach
+ * coarsest_tol within coarsest_refine_max refinement steps (the coarsest
+ * operator's condition number is too close to 1/eps of FP32 for the dense
+ * inverse: use a larger coarsest_tol or coarsest_dense_max = 0, the CG path)
+ * or within 5000 CG iterations.  Any output pointer may be NULL; MG_ERR_ARG
+ * when h has one level. */
+mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, double* test_residual);
 
 /* Level geometry: extents and dof per site; Nv of the blocking below it
  * (0 on the coarsest).  Any output pointer may be NULL. */
@@ -403,11 +427,16 @@ mg_status mg_profile_read(mg_handle* h, int family, double* total_ms, long long*
  * <in, A in>, deterministic) are written with the same fused kernel as
  * mg_apply_A; its reduction scratch lives in a 10 KB array inside the library
  * (every GPU that loads the library keeps it until exit) instead of the
- * handle's workspace.  Maximum size: lattices needing at most 608 thread
- * blocks (Lx * Lt <= 155648 sites, e.g. 384 x 384); larger ones get
- * MG_ERR_ARG.  The first call on a device looks up the array's device address
- * (make that call before any stream capture).  Calls share the array: calls
- * whose kernels overlap on the GPU race and must be ordered by the caller. */
+ * handle's workspace.  Maximum size: 608 thread blocks of the fused kernel,
+ * counted as B = ceil(Lx/32) * ceil(Lt/8) when B >= 304, otherwise
+ * ceil(Lx/16) * ceil(Lt/8) (so 155648 sites for lattices that are multiples of
+ * 32 x 8, e.g. 608 x 256; 384 x 384 takes 576); larger lattices get
+ * MG_ERR_ARG and a message with their block count.  The first call on a
+ * device looks up the array's device address, with that device current (make
+ * that call before any stream capture); the address is cached per device
+ * ordinal for the life of the process's CUDA context.  Calls share the array
+ * and leave their partial sums in it: calls whose kernels overlap on the GPU
+ * race and must be ordered by the caller. */
 mg_status mg_apply_A_dot_noalloc(mg_handle* h, const void* in, void* out, double* xAx);
 
 /* Message of the last error on h (h == NULL: last mg_setup / mg_block_map

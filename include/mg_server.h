@@ -94,6 +94,13 @@ mg_status mg_server_wait(mg_server* s, long long request_id, mg_solve_info* info
 
 mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out);
 
+/* Failure injection on the host, for tests of the failure path: the next
+ * `count` hierarchy builds or clones report MG_ERR_CUDA (after 50 ms, without
+ * touching the device) instead of running.  A failed build or clone fails
+ * the queued requests of its own (configuration, mass) group only; requests
+ * at other masses, and builds of other groups in flight meanwhile, go on. */
+mg_status mg_server_inject_build_failures(mg_server* s, int count);
+
 /* Waits for every queued request, then frees everything.  NULL is allowed. */
 void mg_server_destroy(mg_server* s);
 

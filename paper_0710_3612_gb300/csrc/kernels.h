@@ -144,6 +144,17 @@ cudaError_t link_unitarity(const void* gauge, long long count, double* out, cuda
 enum CoarseWeights { W_F64 = 0, W_F32 = 1, W_BF16 = 2 };
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
                          int n, int nrhs, const Epilogue& ep, cudaStream_t s);
+// Multi-RHS BF16 coarse apply on tcgen05 tensor cores (TMEM accumulator):
+// n in {16, 24}, 1 <= nrhs <= 64, FP32 vectors [nrhs][V][n], bf16x2 blocks.
+bool coarse_apply_tcgen05_ok(int n, int nrhs);
+cudaError_t coarse_apply_tcgen05(const void* in, void* out, const void* A, int Lx, int Lt, int n,
+                                 int nrhs, const Epilogue& ep, cudaStream_t s);
+// Reads and clears the process-wide flag set when a bounded completion wait
+// of the tcgen05 coarse apply ran out (its results are then invalid).
+cudaError_t coarse_tc_take_error(int* flag);
+// Tensor-core kernel of coarse_apply for BF16 blocks and >= 8 right-hand
+// sides: 0 = tcgen05 where the shape allows it (default), 1 = mma.sync.
+void set_coarse_tensor_kernel(int kind);
 // A (complex128) -> float2 or bf16x2 copy
 // out = a X + b Y + c I for coarse operators of `sites` sites and n dof (FP64).
 cudaError_t coarse_lincomb(double a, const void* X, double b, const void* Y, double c, void* out,

@@ -7,6 +7,7 @@
 //  * coarsest level: dense FP32 Gauss-Jordan inverse and GEMV (the FP64
 //    refinement around them lives in the host orchestration)
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "common.cuh"
@@ -253,9 +254,16 @@ bool coarse_apply_tensor(int weights, int n, int nrhs) {
   return weights == W_BF16 && nrhs >= 8 && n % 8 == 0 && n <= 32 && nrhs <= 64;
 }
 
+static std::atomic<int> g_coarse_tensor_kernel{1};
+
+void set_coarse_tensor_kernel(int kind) { g_coarse_tensor_kernel.store(kind); }
+
 cudaError_t coarse_apply(const void* in, void* out, const void* A, int weights, int Lx, int Lt,
                          int n, int nrhs, const Epilogue& ep, cudaStream_t s) {
   if (n % 2 || 9 * n > 576) return cudaErrorInvalidValue;
+  if (coarse_apply_tensor(weights, n, nrhs) && g_coarse_tensor_kernel.load() == 0 &&
+      coarse_apply_tcgen05_ok(n, nrhs))
+    return coarse_apply_tcgen05(in, out, A, Lx, Lt, n, nrhs, ep, s);
   if (coarse_apply_tensor(weights, n, nrhs)) {
     const size_t smem = (size_t)2 * 9 * n * (MMA_RC + 8) * sizeof(__nv_bfloat162);
     static bool attr = false;

@@ -3,6 +3,7 @@
 // frozen MR smoother (Sec. 4), five-step V-cycle (Sec. 2), MG-CG (Sec. 4).
 // All arithmetic runs in the kernels of this library; the host only sequences
 // launches and reads back the few scalars the Krylov loops branch on.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -63,6 +64,8 @@ struct mg_handle {
   double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
   bool dense = true;            // dense inverse (else CG on the coarsest stencil)
   int ccg_iters = 0;            // CG iterations of one coarsest solve (fixed at set-up)
+  double coarsest_test_res = 0; // worst relative residual of the set-up's test vectors
+  bool poisoned = false;        // a bounded device wait ran out: device state undefined
   double2 *cp = nullptr, *cq = nullptr;                  // coarsest CG vectors
   // CUDA graphs of the Krylov loop (one per preconditioner mode), launched on
   // the internal stream gs and fenced to the user's stream with events
@@ -396,44 +399,77 @@ void build_coarse_ops(mg_handle* h) {
   }
 }
 
-// Iterations of the coarsest CG: the first count at which the test vector
-// (all ones) reaches coarsest_tol, times 1.25 plus 4 for other right-hand
-// sides; at most coarsest_cg_max.
+// Test vectors of the coarsest solve's set-up: complex Gaussian entries (Re,
+// Im ~ N(0, 1/2)) from splitmix64 (Steele, Lea, Flood, OOPSLA'14) by the
+// Box-Muller transform, seeded per vector.  A random vector has components on
+// every eigenvector, so the iteration counts fixed with it hold for other
+// right-hand sides too (an all-ones vector can miss the slow modes).
+constexpr int COARSEST_TEST_VECTORS = 2;
+
+std::vector<double2> coarsest_test_vector(long long n, uint64_t seed) {
+  uint64_t st = 0x5eed0000c0a25e57ULL ^ (seed * 0x9E3779B97F4A7C15ULL);
+  auto next = [&st]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  };
+  std::vector<double2> v(n);
+  for (long long i = 0; i < n; ++i) {
+    const double u1 = ((next() >> 11) + 1.0) * 0x1.0p-53;     // (0, 1]
+    const double u2 = (next() >> 11) * 0x1.0p-53;             // [0, 1)
+    const double r = std::sqrt(-std::log(u1));                // E|z|^2 = 1
+    v[i] = make_double2(r * std::cos(6.283185307179586 * u2), r * std::sin(6.283185307179586 * u2));
+  }
+  return v;
+}
+
+// Iterations of the coarsest CG: the largest count at which a test vector
+// reaches coarsest_tol, times 1.25 plus 4 for other right-hand sides; at most
+// COARSEST_CG_MAX (MG_ERR_NOCONV beyond).
 constexpr int COARSEST_CG_MAX = 5000;
 
 void build_coarsest_cg(mg_handle* h) {
   const long long n = h->Nc;
-  std::vector<double2> ones(n, make_double2(1.0, 0.0));
-  ck(h, cudaMemcpyAsync(h->cb, ones.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, h->s),
-     "upload");
-  ck(h, norm2<double>(h->cb, n, 1, h->partials, slot(h, S_T1), h->s), "norm");
-  const double bn = read_scalar(h, S_T1);
-  const double stop = h->p.coarsest_tol * h->p.coarsest_tol * bn;
-  double* rz = slot(h, S_CA);
-  double* rn = slot(h, S_CB);
-  ck(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double2), h->s), "memset");
-  ck(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  ck(h, cudaMemcpyAsync(h->cp, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
-  ck(h, norm2<double>(h->cr, n, 1, h->partials, rz, h->s), "norm");
-  int it = 0;
-  for (; it < COARSEST_CG_MAX; ++it) {
-    apply_level<double>(h, h->L - 1, h->cp, h->cq, 1, W_F64);
-    ck(h, dot<double>(h->cp, h->cq, n, 1, h->partials, slot(h, S_CPQ), h->s), "dot");
-    ck(h, cg_xr<double>(h->cx, h->cr, h->cp, h->cq, rz, slot(h, S_CPQ), nullptr, n, 1,
-                        h->partials, rn, h->s), "cg update");
-    ck(h, cg_p<double>(h->cp, h->cr, rn, rz, nullptr, n, 1, h->s), "cg direction");
-    std::swap(rz, rn);
-    double rr = 0.0;
-    ck(h, cudaMemcpyAsync(&rr, rz, sizeof(double), cudaMemcpyDeviceToHost, h->s), "read");
-    sync(h);
-    if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest CG is not finite");
-    if (rr <= stop) break;
+  int worst = 0;
+  for (int tv = 0; tv < COARSEST_TEST_VECTORS; ++tv) {
+    std::vector<double2> tvec = coarsest_test_vector(n, (uint64_t)tv + 1);
+    ck(h, cudaMemcpyAsync(h->cb, tvec.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, h->s),
+       "upload");
+    ck(h, norm2<double>(h->cb, n, 1, h->partials, slot(h, S_T1), h->s), "norm");
+    const double bn = read_scalar(h, S_T1);
+    const double stop = h->p.coarsest_tol * h->p.coarsest_tol * bn;
+    double* rz = slot(h, S_CA);
+    double* rn = slot(h, S_CB);
+    ck(h, cudaMemsetAsync(h->cx, 0, n * sizeof(double2), h->s), "memset");
+    ck(h, cudaMemcpyAsync(h->cr, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    ck(h, cudaMemcpyAsync(h->cp, h->cb, n * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
+    ck(h, norm2<double>(h->cr, n, 1, h->partials, rz, h->s), "norm");
+    int it = 0;
+    for (; it < COARSEST_CG_MAX; ++it) {
+      apply_level<double>(h, h->L - 1, h->cp, h->cq, 1, W_F64);
+      ck(h, dot<double>(h->cp, h->cq, n, 1, h->partials, slot(h, S_CPQ), h->s), "dot");
+      ck(h, cg_xr<double>(h->cx, h->cr, h->cp, h->cq, rz, slot(h, S_CPQ), nullptr, n, 1,
+                          h->partials, rn, h->s), "cg update");
+      ck(h, cg_p<double>(h->cp, h->cr, rn, rz, nullptr, n, 1, h->s), "cg direction");
+      std::swap(rz, rn);
+      double rr = 0.0;
+      ck(h, cudaMemcpyAsync(&rr, rz, sizeof(double), cudaMemcpyDeviceToHost, h->s), "read");
+      sync(h);
+      if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest CG is not finite");
+      if (rr <= stop) {
+        h->coarsest_test_res = std::max(h->coarsest_test_res, std::sqrt(rr / bn));
+        break;
+      }
+    }
+    if (it == COARSEST_CG_MAX) fail(h, MG_ERR_NOCONV, "coarsest CG did not reach coarsest_tol");
+    worst = std::max(worst, it + 1);
   }
-  if (it == COARSEST_CG_MAX) fail(h, MG_ERR_NOCONV, "coarsest CG did not reach coarsest_tol");
-  h->ccg_iters = std::min(COARSEST_CG_MAX, (it + 1) + (it + 1) / 4 + 4);
+  h->ccg_iters = std::min(COARSEST_CG_MAX, worst + worst / 4 + 4);
 }
 
 void build_coarsest(mg_handle* h) {
+  h->coarsest_test_res = 0.0;
   if (!h->dense) {
     build_coarsest_cg(h);
     return;
@@ -456,29 +492,52 @@ void build_coarsest(mg_handle* h) {
       int e = 0;
       ck(h, cudaMemcpyAsync(&e, gj_err, sizeof(int), cudaMemcpyDeviceToHost, h->s), "read");
       sync(h);
-      if (e) fail(h, MG_ERR_TIMEOUT, "tensor-core Gauss-Jordan update: completion wait ran out");
+      if (e) {
+        // the CTA that gave up may have left tensor-core work in flight: no
+        // later result of this handle can be trusted
+        h->poisoned = true;
+        fail(h, MG_ERR_TIMEOUT, "tensor-core Gauss-Jordan update: completion wait ran out");
+      }
     }
     ck(h, pack_hermitian(h->Binv, h->Bpk, h->ldc, h->s), "pack");
   }
-  // Refinement count: smallest number of FP64 correction steps that brings a
-  // fixed test vector (all ones) to coarsest_tol, plus one.
-  std::vector<double2> ones(h->Nc, make_double2(1.0, 0.0));
-  ck(h, cudaMemcpyAsync(h->cb, ones.data(), sizeof(double2) * h->Nc, cudaMemcpyHostToDevice,
-                        h->s),
-     "upload");
-  ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, slot(h, S_T1), h->s), "norm");
-  const double bn = read_scalar(h, S_T1);
-  int steps = 0;
-  for (; steps <= h->p.coarsest_refine_max; ++steps) {
-    coarsest_solve64(h, h->cb, h->cx, steps, 1);
-    apply_level<double>(h, h->L - 1, h->cx, h->cr, 1, W_F64);
-    ck(h, sub_from<double>(h->cb, h->cr, h->Nc, h->s), "residual");
-    ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, slot(h, S_T0), h->s), "norm");
-    const double rr = read_scalar(h, S_T0);
-    if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest inverse is not finite");
-    if (rr <= h->p.coarsest_tol * h->p.coarsest_tol * bn) break;
+  // Refinement count: the smallest number of FP64 correction steps that brings
+  // every test vector to coarsest_tol, plus one (at most coarsest_refine_max).
+  // If a test vector does not get there within coarsest_refine_max steps the
+  // FP32 inverse is too inaccurate for this operator (condition number near
+  // 1/eps_FP32): MG_ERR_NOCONV, with the residual reached in the message.
+  int worst = 0;
+  for (int tv = 0; tv < COARSEST_TEST_VECTORS; ++tv) {
+    std::vector<double2> tvec = coarsest_test_vector(h->Nc, (uint64_t)tv + 1);
+    ck(h, cudaMemcpyAsync(h->cb, tvec.data(), sizeof(double2) * h->Nc, cudaMemcpyHostToDevice,
+                          h->s),
+       "upload");
+    ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, slot(h, S_T1), h->s), "norm");
+    const double bn = read_scalar(h, S_T1);
+    int steps = 0;
+    double rel = 0.0;
+    for (; steps <= h->p.coarsest_refine_max; ++steps) {
+      coarsest_solve64(h, h->cb, h->cx, steps, 1);
+      apply_level<double>(h, h->L - 1, h->cx, h->cr, 1, W_F64);
+      ck(h, sub_from<double>(h->cb, h->cr, h->Nc, h->s), "residual");
+      ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, slot(h, S_T0), h->s), "norm");
+      const double rr = read_scalar(h, S_T0);
+      if (!(rr == rr)) fail(h, MG_ERR_BREAKDOWN, "coarsest inverse is not finite");
+      rel = std::sqrt(rr / bn);
+      if (rel <= h->p.coarsest_tol) break;
+    }
+    h->coarsest_test_res = std::max(h->coarsest_test_res, rel);
+    if (steps > h->p.coarsest_refine_max) {
+      char msg[200];
+      std::snprintf(msg, sizeof msg,
+                    "coarsest solve: FP64 refinement of the FP32 inverse reached %.3g, not "
+                    "coarsest_tol %.3g, in %d steps (operator too ill-conditioned for FP32)",
+                    rel, h->p.coarsest_tol, h->p.coarsest_refine_max);
+      fail(h, MG_ERR_NOCONV, msg);
+    }
+    worst = std::max(worst, steps);
   }
-  h->n_refine = std::min(steps + 1, h->p.coarsest_refine_max);
+  h->n_refine = std::min(worst + 1, h->p.coarsest_refine_max);
 }
 
 void drop_graphs(mg_handle* h) {
@@ -573,6 +632,10 @@ mg_status validate(const mg_params* p, std::string& msg) {
 
 template <typename F>
 mg_status guarded(mg_handle* h, F&& f) {
+  if (h && h->poisoned) {
+    h->err = "handle unusable: a bounded device-side wait ran out earlier (device state undefined)";
+    return MG_ERR_CUDA;
+  }
   try {
     f();
     return MG_OK;
@@ -1654,6 +1717,17 @@ mg_status mg_set_mass(mg_handle* h, double mass) {
   return guarded(h, [&]() { set_mass_internal(h, mass); });
 }
 
+// Bounded device-side waits of the tensor-core kernels report through a flag;
+// one that ran out leaves the results invalid and the device state undefined.
+void check_device_waits(mg_handle* h) {
+  int flag = 0;
+  ck(h, coarse_tc_take_error(&flag), "read the wait flag");
+  if (flag) {
+    h->poisoned = true;
+    fail(h, MG_ERR_TIMEOUT, "tcgen05 coarse apply: a completion wait ran out (results invalid)");
+  }
+}
+
 mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
                    int solver, mg_solve_info* info) {
   if (!h) return MG_ERR_ARG;
@@ -1674,6 +1748,7 @@ mg_status mg_solve(mg_handle* h, const void* b, void* x, int nrhs, double tol, i
           info[k0 + k].milliseconds = std::chrono::duration<double, std::milli>(t1 - t0).count();
       if (one != MG_OK && worst == MG_OK) worst = one;
     }
+    check_device_waits(h);
   });
   return st != MG_OK ? st : worst;
 }
@@ -1705,7 +1780,17 @@ mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, in
   return guarded(h, [&]() {
     if (precision == MG_PREC_F64) apply_level<double>(h, level - 1, in, out, nrhs, W_F64);
     else apply_level<float>(h, level - 1, in, out, nrhs, precision == MG_PREC_F32 ? W_F32 : W_BF16);
+    if (precision == MG_PREC_BF16) {
+      sync(h);
+      check_device_waits(h);
+    }
   });
+}
+
+mg_status mg_set_coarse_tensor_kernel(int kind) {
+  if (kind != 0 && kind != 1) return MG_ERR_ARG;
+  set_coarse_tensor_kernel(kind);
+  return MG_OK;
 }
 
 mg_status mg_restrict(mg_handle* h, int level, const void* fine_in, void* coarse_out, int nrhs, int precision) {
@@ -1747,6 +1832,14 @@ mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out) {
   return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine, 1); });
 }
 
+mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, double* test_residual) {
+  if (!h || h->L < 2) return MG_ERR_ARG;
+  if (dense) *dense = h->dense ? 1 : 0;
+  if (steps) *steps = h->dense ? h->n_refine : h->ccg_iters;
+  if (test_residual) *test_residual = h->coarsest_test_res;
+  return MG_OK;
+}
+
 mg_status mg_get_level(const mg_handle* h, int level, int* Lx, int* Lt, int* ndof, int* Nv) {
   if (!h || level < 1 || level > h->L) return MG_ERR_ARG;
   const Level& L = h->lv[level - 1];
@@ -1766,7 +1859,9 @@ namespace {
 constexpr int NOALLOC_BLOCKS = 608;
 constexpr int NOALLOC_DOUBLES = 64 + 2 * NOALLOC_BLOCKS;
 constexpr int NOALLOC_MAX_DEVICES = 64;
-double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};   // device address per device
+// device address of the array per device ordinal; threads that make their first
+// call on a device at the same time both look it up and store the same value
+std::atomic<double*> g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 }  // namespace
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
@@ -1776,21 +1871,23 @@ extern "C" mg_status mg_apply_A_dot_noalloc(mg_handle* h, const void* in, void* 
   if (!in || !out || !xAx) { h->err = "invalid arguments"; return MG_ERR_ARG; }
   const Level& F = h->lv[0];
   if (wilson_A_ctas(F.Lx, F.Lt, true) > NOALLOC_BLOCKS) {
-    h->err = "mg_apply_A_dot_noalloc: lattice needs more than " +
-             std::to_string(NOALLOC_BLOCKS) + " thread blocks (limit 155648 sites)";
+    h->err = "mg_apply_A_dot_noalloc: lattice needs " + std::to_string(wilson_A_ctas(F.Lx, F.Lt, true)) +
+             " thread blocks, more than the " + std::to_string(NOALLOC_BLOCKS) +
+             " the library-held scratch holds";
     return MG_ERR_ARG;
   }
   return guarded(h, [&]() {
     int dev = 0;
     ck(h, cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(h, MG_ERR_ARG, "device ordinal out of range");
-    if (!g_noalloc_ptr[dev]) {
+    double* ws = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!ws) {
       // once per device, with that device current: the device address of the array
       void* p = nullptr;
       ck(h, cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-      g_noalloc_ptr[dev] = (double*)p;
+      ws = (double*)p;
+      g_noalloc_ptr[dev].store(ws, std::memory_order_release);
     }
-    double* ws = g_noalloc_ptr[dev];
     // the tickets must start at zero (the last block of a reduction clears them,
     // but a previous kernel may have been interrupted)
     ck(h, cudaMemsetAsync(ws, 0, 64 * sizeof(double), h->s), "clear tickets");

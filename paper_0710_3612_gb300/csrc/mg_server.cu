@@ -81,6 +81,7 @@ struct mg_server {
   long long next_id = 1, tick = 0;
   long long submitted = 0, completed = 0, failed = 0, batches = 0, batched_rhs = 0;
   long long builds = 0, clones = 0, evictions = 0, remasses = 0;
+  int inject_build_failures = 0;   // host-side fault injection (mg_server_inject_build_failures)
   std::vector<double> latencies;
 };
 
@@ -232,10 +233,19 @@ bool choose(mg_server* s, Job* job) {
   return false;
 }
 
-void fail_queue(mg_server* s, Config* c, mg_status st) {
-  std::vector<Request*> all(c->queue.begin(), c->queue.end());
-  c->queue.clear();
-  finish(s, all, st, nullptr);
+// Fails the queued requests of configuration c; mass != nullptr: only those at
+// that mass (a failed build or clone concerns its own group only).
+void fail_queue(mg_server* s, Config* c, mg_status st, const double* mass = nullptr) {
+  std::vector<Request*> out;
+  for (auto it = c->queue.begin(); it != c->queue.end();) {
+    if (!mass || (*it)->mass == *mass) {
+      out.push_back(*it);
+      it = c->queue.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  finish(s, out, st, nullptr);
 }
 
 void worker_main(mg_server* s) {
@@ -258,10 +268,17 @@ void worker_main(mg_server* s) {
     r->busy = true;
     const size_t vb = (size_t)s->max_rhs * c->Lx * c->Lt * 2 * 16;
     if (job.kind == Job::BUILD || job.kind == Job::CLONE) {
+      const bool inject = s->inject_build_failures > 0;
+      if (inject) --s->inject_build_failures;
       lk.unlock();
       mg_status st = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess
                          ? MG_OK : MG_ERR_CUDA;
-      if (st == MG_OK) {
+      if (st == MG_OK && inject) {
+        // stands in for a failing mg_setup / mg_clone, after a while so that
+        // builds of other groups are in flight meanwhile
+        std::this_thread::sleep_for(std::chrono::milliseconds(50));
+        st = MG_ERR_CUDA;
+      } else if (st == MG_OK) {
         if (job.kind == Job::CLONE) {
           st = mg_clone(job.src->h, job.mass, r->stream, &r->h);
         } else {
@@ -282,7 +299,7 @@ void worker_main(mg_server* s) {
         free_hier(r);
         s->resident -= r->bytes;
         erase_hier(c, r);
-        fail_queue(s, c, st);
+        fail_queue(s, c, st, &job.mass);
         s->cv_done.notify_all();
         s->cv_work.notify_all();
         continue;
@@ -302,6 +319,19 @@ void worker_main(mg_server* s) {
         head = q;
         break;
       }
+    if (!head) {                      // nothing left at this mass: release the hierarchy
+      if (job.kind == Job::REMASS) {  // it was re-labelled but never re-massed
+        free_hier(r);
+        s->resident -= r->bytes;
+        erase_hier(c, r);
+      } else {
+        r->busy = false;
+        r->last_used = ++s->tick;
+      }
+      s->cv_done.notify_all();
+      s->cv_work.notify_all();
+      continue;
+    }
     const double tol = head->tol;
     const int solver = head->solver;
     for (auto it = c->queue.begin(); it != c->queue.end();) {
@@ -460,6 +490,13 @@ mg_status mg_server_wait(mg_server* s, long long request_id, mg_solve_info* info
   if (latency_ms) *latency_ms = r->latency_ms;
   s->reqs.erase(it);
   return st;
+}
+
+mg_status mg_server_inject_build_failures(mg_server* s, int count) {
+  if (!s || count < 0) return MG_ERR_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  s->inject_build_failures = count;
+  return MG_OK;
 }
 
 mg_status mg_server_get_stats(mg_server* s, mg_server_stats* out) {

@@ -86,14 +86,17 @@ _SIGS = {
     "mg_get_null_vectors": (_i, [_vp, _i, _vp]),
     "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "mg_get_coarsest_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "mg_apply_A_dot_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mg_set_coarse_tensor_kernel": (_i, [_i]),
     "mg_setup_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "mg_server_create": (_i, [_ll, _i, _i, ctypes.POINTER(_vp)]),
     "mg_server_add_config": (_i, [_vp, _vp, ctypes.POINTER(MgParams), _d, ctypes.POINTER(_i)]),
     "mg_server_submit": (_i, [_vp, _i, _d, _vp, _vp, _i, _d, _i, ctypes.POINTER(_ll)]),
     "mg_server_wait": (_i, [_vp, _ll, _vp, ctypes.POINTER(_d)]),
     "mg_server_get_stats": (_i, [_vp, ctypes.POINTER(MgServerStats)]),
+    "mg_server_inject_build_failures": (_i, [_vp, _i]),
     "mg_server_destroy": (None, [_vp]),
     "mg_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_clone": (_i, [_vp, _d, _vp, ctypes.POINTER(_vp)]),
@@ -343,6 +346,21 @@ def mg_get_smoother(h, level):
     return tuple(buf)
 
 
+COARSE_TC_TCGEN05, COARSE_TC_MMA_SYNC = 0, 1
+
+
+def mg_set_coarse_tensor_kernel(kind):
+    """Process-wide choice of the multi-RHS BF16 coarse-apply kernel (tcgen05 or mma.sync)."""
+    _check(lib().mg_set_coarse_tensor_kernel(int(kind)))
+
+
+def mg_get_coarsest_info(h):
+    """(dense, steps, test_residual) of the coarsest solve fixed at set-up."""
+    dense, steps, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().mg_get_coarsest_info(h, ctypes.byref(dense), ctypes.byref(steps), ctypes.byref(res)), h)
+    return bool(dense.value), steps.value, res.value
+
+
 def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
     import torch
     _check(lib().mg_block_map(Lx, Lt, bx, bt, _ptr(coarse, torch.int32), _ptr(offset, torch.int32),
@@ -473,6 +491,10 @@ class Server:
         st = lib().mg_server_wait(self.s, int(request_id), infos, ctypes.byref(lat))
         self._keep.pop(request_id, None)
         return st, list(infos), lat.value
+
+    def inject_build_failures(self, count):
+        """The next `count` builds or clones fail on the host (test support)."""
+        _check(lib().mg_server_inject_build_failures(self.s, int(count)))
 
     def stats(self) -> MgServerStats:
         out = MgServerStats()

@@ -50,6 +50,51 @@ def check(got, want, mag, tol, what=""):
     assert worst <= 1.0, f"{what}: worst error / bound = {worst:.3g} (max err {err.max():.3e})"
 
 
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def bf16_blocks(M):
+    """The GPU's BF16 copy of FP64 coarse blocks: FP64 -> FP32 -> BF16, each rounded to nearest."""
+    re = bf16_round(M.real.astype(np.float32)).astype(np.float64)
+    im = bf16_round(M.imag.astype(np.float32)).astype(np.float64)
+    return re + 1j * im
+
+
+def gpu_vectors(mg, c, l):
+    """The GPU set-up's own block vectors of level l (0 = finest), [Nv, Lt, Lx, n]."""
+    Lx, Lt, n, Nv = mg.mg_get_level(c.h, l + 1)
+    out = torch.empty((Nv, Lt, Lx, n), dtype=torch.complex128, device=DEV)
+    mg.mg_get_null_vectors(c.h, l + 1, out)
+    return host(out)
+
+
+def gpu_coarse_op(mg, c, l):
+    """The GPU set-up's own FP64 coarse operator of level l >= 1 as an oracle stencil."""
+    op = c.H.levels[l].op
+    out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
+    mg.mg_get_coarse_op(c.h, l + 1, out)
+    return omg.StencilOp(omg.COARSE_DISP, host(out))
+
+
+def abs_normal_stencil(U, m):
+    """|D|^T |D| as a stencil: the sum of magnitudes of the terms of A = D^dagger D."""
+    dd, Md = ow.wilson_stencil(U, m, dagger=True)
+    d_, M = ow.wilson_stencil(U, m, dagger=False)
+    Md, M = np.abs(Md), np.abs(M)
+    acc = {}
+    for e1, (ax, at) in enumerate(dd):
+        Ms = np.roll(M, shift=(-at, -ax), axis=(0, 1))
+        for e2, (bx, bt) in enumerate(d_):
+            key = (ax + bx, at + bt)
+            acc[key] = acc.get(key, 0) + np.einsum("txab,txbc->txac", Md[:, :, e1], Ms[:, :, e2])
+    disp = sorted(acc)
+    return omg.StencilOp(disp, np.stack([acc[k] for k in disp], axis=2))
+
+
 # ---------------------------------------------------------------------------
 # configurations: (Lx, Lt, beta, sweeps, seed, mass, blocks, Nv)
 # ---------------------------------------------------------------------------
@@ -60,6 +105,8 @@ CASES = {
     "3lvl_24x24": (24, 24, 6.0, 40, 2, -1.2, [(4, 4), (2, 2)], [3, 4]),
     # three levels with a coarsest extent of 2 (+1 and -1 neighbours alias)
     "3lvl_16x16_alias": (16, 16, 3.0, 30, 3, -0.4, [(4, 4), (2, 2)], [2, 3]),
+    # the benchmark's coarse shapes: 16 dof (Nv = 8) on 8 x 8, 24 dof (Nv = 12) on 4 x 4
+    "3lvl_32x32_nv8_12": (32, 32, 6.0, 40, 4, -0.9, [(4, 4), (2, 2)], [8, 12]),
 }
 
 
@@ -151,54 +198,90 @@ def test_null_vectors_and_smoother(case, mg):
 
 
 def test_coarse_operators(case, mg):
+    """Two comparisons.  The Galerkin kernels at 1e-12 per element: the GPU's
+    A_{l+1} against the oracle's P^dagger A_l P formed from the GPU's own
+    vectors V_l and its own A_l (level 0: the oracle's A = D^dagger D), the
+    magnitude bound from the same product of absolute values.  The whole
+    set-up at 1e-11 of the row maximum: the GPU's A_{l+1} against the oracle's
+    own set-up (relaxation and Gram-Schmidt on both sides)."""
     H = case.H
     for l in range(1, H.L):
         op = H.levels[l].op
-        out = torch.empty(op.M.shape, dtype=torch.complex128, device=DEV)
-        mg.mg_get_coarse_op(case.h, l + 1, out)
-        got = host(out)
+        got = gpu_coarse_op(mg, case, l).M
         rowmax = np.max(np.abs(op.M), axis=(2, 4), keepdims=True)
-        check(got, op.M, rowmax, 1e-11, f"A_c level {l + 1}")
+        check(got, op.M, rowmax, 1e-11, f"A_c level {l + 1} (set-up)")
+        lv = H.levels[l - 1]
+        V = gpu_vectors(mg, case, l - 1)
+        if l == 1:
+            fine = omg.WilsonNormalOp(case.U, case.m)
+            fine_abs = abs_normal_stencil(case.U, case.m)
+        else:
+            fine = gpu_coarse_op(mg, case, l - 1)
+            fine_abs = omg.StencilOp(fine.disp, np.abs(fine.M))
+        want = omg.galerkin(fine, V, lv.bx, lv.bt).M
+        mag = omg.galerkin(fine_abs, np.abs(V), lv.bx, lv.bt).M.real
+        check(got, want, mag, TOL64, f"A_c level {l + 1} (Galerkin kernels)")
 
 
-@pytest.mark.parametrize("prec,nrhs", [("f64", 2), ("f32", 2), ("bf16", 2), ("bf16", 16),
-                                       ("bf16", 13)])
-def test_apply_coarse(case, mg, prec, nrhs):
+@pytest.mark.parametrize("prec,nrhs,kernel", [("f64", 2, 0), ("f32", 2, 0), ("bf16", 2, 0),
+                                              ("bf16", 16, 0), ("bf16", 13, 0), ("bf16", 64, 0),
+                                              ("bf16", 16, 1), ("bf16", 13, 1), ("bf16", 64, 1)])
+def test_apply_coarse(case, mg, prec, nrhs, kernel):
     """nrhs >= 8 with BF16 blocks runs on the tensor cores (BF16 operands,
-    FP32 accumulation); 13 checks the right-hand-side padding."""
+    FP32 accumulation): kernel 0 = tcgen05 (levels with 16 or 24 dof; others
+    fall back to mma.sync), 1 = mma.sync; 13 checks the right-hand-side
+    padding, 64 the full M tile."""
+    mg.mg_set_coarse_tensor_kernel(kernel)
+    try:
+        _apply_coarse(case, mg, prec, nrhs)
+    finally:
+        mg.mg_set_coarse_tensor_kernel(0)
+
+
+def _apply_coarse(case, mg, prec, nrhs):
     H = case.H
     for l in range(1, H.L):
-        op = H.levels[l].op
+        ora = H.levels[l].op
+        op = gpu_coarse_op(mg, case, l)      # the GPU's own blocks: the kernel alone is compared
         v = W.gaussian_field((nrhs, op.Lt, op.Lx, op.n), 11 + l)
         want = op.apply(v)
         mag = omg.StencilOp(op.disp, np.abs(op.M)).apply(np.abs(v))
+        # the same input through the oracle's own blocks differs only by the set-up's rounding
+        mag_o = omg.StencilOp(ora.disp, np.abs(ora.M)).apply(np.abs(v))
+        check(want, ora.apply(v), mag_o, 1e-11, "coarse blocks (set-up)")
         if prec == "f64":
             out = torch.empty_like(dev(v))
             mg.mg_apply_coarse(case.h, l + 1, dev(v), out, nrhs, mg.PREC_F64)
-            check(host(out), want, mag, 1e-11, "coarse f64")
+            check(host(out), want, mag, TOL64, "coarse f64")
         else:
             inp = dev(v.astype(np.complex64))
             out = torch.empty_like(inp)
             code = mg.PREC_F32 if prec == "f32" else mg.PREC_BF16
             mg.mg_apply_coarse(case.h, l + 1, inp, out, nrhs, code)
-            check(host(out), want, mag, TOL32 if prec == "f32" else TOL16, f"coarse {prec}")
+            got = host(out)
+            check(got, want, mag, TOL32 if prec == "f32" else TOL16, f"coarse {prec}")
+            if prec == "bf16":
+                # with the stored BF16 blocks themselves only the split of X into
+                # two BF16 parts (2^-18 relative) and FP32 accumulation remain
+                want16 = omg.StencilOp(op.disp, bf16_blocks(op.M)).apply(v.astype(np.complex64))
+                check(got, want16, mag, 3e-5, "coarse bf16 (stored blocks)")
 
 
 @pytest.mark.parametrize("prec,nrhs", [("f64", 2), ("f32", 2), ("f64", 9), ("f32", 9)])
 def test_restrict_prolong(case, mg, prec, nrhs):
     """Several right-hand sides per call (one CTA per coarse site)."""
     H = case.H
-    tol = 1e-11 if prec == "f64" else TOL32
+    tol = TOL64 if prec == "f64" else TOL32
     for l in range(H.L - 1):
         lv = H.levels[l]
+        V = gpu_vectors(mg, case, l)         # the GPU's own vectors: the kernels alone are compared
+        check(V, lv.V, np.ones_like(np.abs(lv.V)), 1e-10, "V (set-up)")
         r = W.gaussian_field((nrhs, lv.Lt, lv.Lx, lv.n), 21 + l)
         ec = W.gaussian_field((nrhs, lv.Lt // lv.bt, lv.Lx // lv.bx, 2 * lv.Nv), 31 + l)
-        Pabs = np.abs(omg.prolongator_matrix(lv.V))
-        want_c = omg.restrict(lv.V, lv.bx, lv.bt, r)
-        mag_c = np.stack([omg.restrict(np.abs(lv.V), lv.bx, lv.bt, np.abs(x)) for x in r])
-        want_f = omg.prolong(lv.V, lv.bx, lv.bt, ec)
-        mag_f = np.stack([omg.prolong(np.abs(lv.V), lv.bx, lv.bt, np.abs(x)) for x in ec])
-        del Pabs
+        want_c = omg.restrict(V, lv.bx, lv.bt, r)
+        mag_c = np.stack([omg.restrict(np.abs(V), lv.bx, lv.bt, np.abs(x)) for x in r])
+        want_f = omg.prolong(V, lv.bx, lv.bt, ec)
+        mag_f = np.stack([omg.prolong(np.abs(V), lv.bx, lv.bt, np.abs(x)) for x in ec])
         dt = np.complex128 if prec == "f64" else np.complex64
         code = mg.PREC_F64 if prec == "f64" else mg.PREC_F32
         out_c = torch.empty(want_c.shape, dtype=torch.complex128 if prec == "f64" else torch.complex64, device=DEV)

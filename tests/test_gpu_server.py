@@ -201,3 +201,41 @@ def test_configuration_above_the_budget_fails_cleanly(mg):
         st, _, _ = srv.wait(srv.submit(cid, m0, b, x, 1), 1)
         assert st == 2                                 # MG_ERR_NOMEM
         assert srv.stats().failed == 1
+
+
+def test_failed_clone_fails_its_own_group_only(mg):
+    """Two clones of one configuration built at once, one of them failing (a
+    host-side injected MG_ERR_CUDA in place of mg_clone): the requests at the
+    failed clone's mass fail with that status, the requests at the other mass
+    are solved (true residual recomputed by the oracle), and the server goes on
+    serving the failed mass afterwards with a new clone."""
+    L, beta, sweeps, seed, m0, blocks, Nv, ms = CONFIGS[0]
+    Uh = W.quenched_u1(L, L, beta, sweeps, seed)
+    m1, m2 = ms[1], -1.0
+    with mg.Server(budget_bytes=8 << 30, max_rhs=4, workers=3) as srv:
+        cid = srv.add_config(dev(Uh), mg.make_params(L, L, blocks, Nv), m0,
+                             noise=dev(W.setup_noise(L, L, blocks, Nv, 5)))
+
+        def submit(m, sd):
+            b = dev(ow.apply_D(Uh, m, W.gaussian_field((L, L, 2), sd), dagger=True))
+            x = torch.full_like(b, float("nan"))
+            torch.cuda.synchronize()
+            return srv.submit(cid, m, b, x, 1, TOL, mg.SOLVER_MGCG_MIXED), b, x
+
+        r0, _, _ = submit(m0, 700)
+        assert srv.wait(r0, 1)[0] == 0                 # the set-up is resident
+        srv.inject_build_failures(1)
+        first = [submit(m1, 710), submit(m1, 711)]     # oldest group: its clone takes the failure
+        second = [submit(m2, 720), submit(m2, 721)]
+        for rid, _, _ in first:
+            assert srv.wait(rid, 1)[0] == 3            # MG_ERR_CUDA
+        for rid, b, x in second:
+            st, infos, _ = srv.wait(rid, 1)
+            assert st == 0 and infos[0].true_residual <= TOL
+            res = np.linalg.norm(host(b) - ow.apply_A(Uh, m2, host(x))) / np.linalg.norm(host(b))
+            assert res <= TOL
+        rid, b, x = submit(m1, 730)                    # served again: a new clone
+        st, infos, _ = srv.wait(rid, 1)
+        assert st == 0 and infos[0].true_residual <= TOL
+        stats = srv.stats()
+        assert stats.failed == 2 and stats.completed == 4 and stats.clones == 2
