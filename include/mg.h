@@ -326,12 +326,15 @@ mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, in
 
 /* Tensor-core kernel of the multi-right-hand-side BF16 coarse apply (Eq.
  * Galerkin at every coarse level of the FP32 V-cycle; 8 .. 64 right-hand
- * sides): 0 = tcgen05.mma with the accumulator in tensor memory (coarse
- * levels with 2Nv = 16 or 24 dof per site, the others use 1), 1 = mma.sync
- * (default).  Both
+ * sides): 0 = tcgen05.mma with the accumulator in tensor memory (default;
+ * coarse levels with 2Nv = 16 or 24 dof per site, the others use 1), 1 =
+ * mma.sync (the earlier tensor-core path, kept for comparison).  Both
  * compute with the stored BF16 blocks and X carried as two BF16 parts, FP32
  * accumulation.  Process-wide; takes effect for launches (and CUDA graphs)
- * made after the call.  MG_ERR_ARG for other values. */
+ * made after the call.  The tcgen05 kernel's completion waits are bounded: one
+ * that runs out sets a process-wide flag, and the next mg_solve returns
+ * MG_ERR_TIMEOUT and leaves its handle unusable.  MG_ERR_ARG for other
+ * values. */
 mg_status mg_set_coarse_tensor_kernel(int kind);
 
 /* Restriction P^dagger from level `level` to level+1 (Sec. 2 step 2) and

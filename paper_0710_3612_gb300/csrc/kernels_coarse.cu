@@ -254,7 +254,7 @@ bool coarse_apply_tensor(int weights, int n, int nrhs) {
   return weights == W_BF16 && nrhs >= 8 && n % 8 == 0 && n <= 32 && nrhs <= 64;
 }
 
-static std::atomic<int> g_coarse_tensor_kernel{1};
+static std::atomic<int> g_coarse_tensor_kernel{0};
 
 void set_coarse_tensor_kernel(int kind) { g_coarse_tensor_kernel.store(kind); }
 

@@ -1780,10 +1780,6 @@ mg_status mg_apply_coarse(mg_handle* h, int level, const void* in, void* out, in
   return guarded(h, [&]() {
     if (precision == MG_PREC_F64) apply_level<double>(h, level - 1, in, out, nrhs, W_F64);
     else apply_level<float>(h, level - 1, in, out, nrhs, precision == MG_PREC_F32 ? W_F32 : W_BF16);
-    if (precision == MG_PREC_BF16) {
-      sync(h);
-      check_device_waits(h);
-    }
   });
 }
 
