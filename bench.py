@@ -283,6 +283,17 @@ def gpu_bench(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
+    # gauge fields of the batched workloads, generated on the host meanwhile
+    import multiprocessing as mp
+    cfg_names = [c for c in args.config_legs.split(",") if c]
+    have = critical_table()
+    cfg_gen = [c for c in cfg_names if W.BATCHED_WORKLOADS[c]["critical_key"] in have]
+    cfg_pool = mp.get_context("spawn").Pool(len(cfg_gen)) if cfg_gen else None
+    cfg_theta = {c: cfg_pool.apply_async(_gauge_angles, ((W.BATCHED_WORKLOADS[c]["Lx"],
+                                                            W.BATCHED_WORKLOADS[c]["beta"],
+                                                            W.BATCHED_WORKLOADS[c]["sweeps"],
+                                                            W.BATCHED_WORKLOADS[c]["seed"]),))
+                 for c in cfg_gen}
     wl, crit, U, noise, chi, masses = workload_inputs(args.workload)
     mg.lib()
     stream = torch.cuda.current_stream()
@@ -396,6 +407,18 @@ def gpu_bench(args):
     # adaptive refinement by V-cycles at the near-critical mass
     adaptive = adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world)
 
+    # batched workloads at their near-critical masses (256^2 x 64 RHS, 1024^2 x 16 RHS)
+    config_legs = []
+    for c in cfg_names:
+        if c in cfg_theta:
+            config_legs.append(batched_config_leg(args, mg, torch, dev, stream, c, cfg_theta[c].get(),
+                                                  world))
+        else:
+            config_legs.append({"workload": c, "unavailable": "no near-critical mass from the "
+                                "oracle's finder for this configuration"})
+    if cfg_pool is not None:
+        cfg_pool.close()
+
     # roofline: one profiled step, dominant kernel family by device time
     prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
     roof = roofline(prof, wl, load_peaks())
@@ -434,6 +457,7 @@ def gpu_bench(args):
                            "per_mass": plain["per_mass"]},
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
             "batched": batched,
+            "batched_configs": config_legs,
             "adaptive": adaptive,
             "serving": serving,
             "roofline": roof,
@@ -454,12 +478,21 @@ FAM_NAMES = ["fine_A_f32", "coarse_apply_f32_bf16", "transfer", "coarsest_solve"
              "coarsest_inverse", "galerkin", "fine_A_f64", "coarsest_gemv_tiles", "gj_update",
              "coarse_apply_f64"]
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel source (summaries and commands under profiles/); a kernel changed
-# since its capture has no entry.
-NCU_TRAFFIC = {"gj_update": 71368192 + 13786368,           # profiles/gj_update_L128.md
-               "coarsest_gemv_tiles": 68242688 + 337664,  # profiles/hgemv_warp_L128.md
-               "coarse_apply_bf16": 9581824 + 0}          # profiles/coarse_bf16_L128.md
+def ncu_traffic():
+    """DRAM bytes (read + write) per launch of each roofline candidate from the
+    ncu captures recorded in profiles/ncu_traffic.json, each with the SHA-256
+    of the CUDA source file it was captured from; a candidate whose source has
+    changed since its capture gets None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return {}
+    out = {}
+    for name, rec in json.load(open(p)).items():
+        src = os.path.join(ROOT, rec["source"])
+        ok = os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["source_sha256"]
+        out[name] = rec["dram_bytes_per_launch"] if ok else None
+    return out
 
 
 def roofline(prof, wl, peaks):
@@ -482,6 +515,7 @@ def roofline(prof, wl, peaks):
     ntiles = nt * (nt + 1) // 2
     cand = {8: "gj_update", 7: "coarsest_gemv_tiles", 1: "coarse_apply_bf16", 0: "fine_A_f32",
             6: "fine_A_f64"}
+    traffic = ncu_traffic()
     total = sum(prof[f][0] for f in cand)
 
     def one(fam):
@@ -499,7 +533,7 @@ def roofline(prof, wl, peaks):
                       "peak_note": f"of {peaks['src']}: sustained bf16 x nominal tf32/bf16 1.1/2.25",
                       "tensor_flops_issued_per_launch": 3 * flops,
                       "note": "mma.sync m16n8k8 TF32, three products per FP32-accurate product",
-                      "traffic": NCU_TRAFFIC.get("gj_update")})
+                      "traffic": traffic.get("gj_update")})
         else:
             if fam == 0:
                 byts = 48.0 * V                          # psi in/out + links, FP32
@@ -511,7 +545,7 @@ def roofline(prof, wl, peaks):
                 byts = ntiles * 64 * 64 * 8.0 + ntiles * 2 * 64 * 8.0
             o.update({"bound": "hbm", "achieved": round(byts / per_call_s / 1e9, 1),
                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes_per_launch": int(byts),
-                      "peak_note": f"of {peaks['src']}", "traffic": NCU_TRAFFIC.get(cand[fam])})
+                      "peak_note": f"of {peaks['src']}", "traffic": traffic.get(cand[fam])})
         o["frac"] = round(o["achieved"] / o["peak"], 4)
         o["share_of_candidates"] = round(ms / total, 3) if total else None
         return o
@@ -693,6 +727,137 @@ def adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
                             "unit": UNIT,
                             "speedup": round(beforeB["ms"] / afterB["ms"], 2)},
                 "breakeven_solves": round(refine_ms / max(1e-9, before1["ms"] - after1["ms"]), 1)})
+    return out
+
+
+def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
+    """One batched workload of workloads.BATCHED_WORKLOADS at its near-critical
+    mass (the oracle's finder, workloads/critical_masses.json): nrhs Gaussian
+    sources chi_k (seeds chi_seed + k), b_k = D^dagger chi_k, solved together
+    with the mixed solver.  Reported: set-up time; solves/s over `config_reps`
+    batches and the per-batch latency percentiles; plain FP64 single-RHS MG-CG
+    on b_0 (time-capped: its rate is then iterations done / time); the
+    multi-RHS BF16 coarse apply of level 2 and the fused FP32 fine stencil on
+    nrhs vectors, each over its CUDA-event time, against the HBM roofline."""
+    wl = W.BATCHED_WORKLOADS[name]
+    Lx, Lt, nrhs, tol = wl["Lx"], wl["Lt"], wl["nrhs"], wl["tol"]
+    out = {"workload": name, "lattice": [Lx, Lt], "beta": wl["beta"], "levels": len(wl["blocks"]) + 1,
+           "blocks": wl["blocks"], "Nv": wl["Nv"], "nrhs": nrhs}
+    crit = critical_table().get(wl["critical_key"])
+    if crit is None:
+        out["unavailable"] = "no near-critical mass from the oracle's finder for this configuration"
+        return out
+    if abs(W.mean_plaquette(theta) - crit["plaquette"]) > 1e-12:
+        out["unavailable"] = "regenerated gauge field differs from the one the finder used"
+        return out
+    m = crit["m_nc"]
+    out.update({"mass": m, "m_crit": crit["m_crit"], "lambda_min": crit["lambda_min"]})
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    U_d = torch.from_numpy(W.links_from_angles(theta)).to(dev)
+    noise_d = torch.from_numpy(W.setup_noise(Lx, Lt, wl["blocks"], wl["Nv"], wl["noise_seed"])).to(dev)
+    chi_d = torch.from_numpy(np.stack([W.gaussian_field((Lt, Lx, 2), wl["chi_seed"] + k)
+                                       for k in range(nrhs)])).to(dev)
+    b_d = torch.empty_like(chi_d)
+    x_d = torch.empty_like(chi_d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = mg.Multigrid(U_d, m, wl["blocks"], wl["Nv"], noise_d, stream=stream,
+                     setup_sweeps=wl["setup_sweeps"], max_rhs=nrhs, **wl.get("params", {}))
+    torch.cuda.synchronize()
+    out["setup_ms"] = round((time.perf_counter() - t0) * 1e3, 1)
+    try:
+        dense, steps, tres = mg.mg_get_coarsest_info(s.h)
+        Lc = mg.mg_get_level(s.h, len(wl["blocks"]) + 1)
+        out["coarsest"] = {"unknowns": Lc[0] * Lc[1] * Lc[2], "solver": "fp32 inverse + fp64 refinement"
+                           if dense else "fp64 cg", "steps": steps, "test_residual": tres}
+        out["device_gb"] = round(mg.mg_device_bytes(s.h) / 2 ** 30, 2)
+        mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
+        st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)   # warm-up
+        lat = []
+        for _ in range(max(1, args.config_reps)):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != 0 or max(i.true_residual for i in info) > tol:
+                raise RuntimeError(f"{name}: batched solve failed (status {st})")
+            lat.append(e0.elapsed_time(e1))
+        ms = max_over_ranks(statistics.median(lat), dev)
+        ls = sorted(lat)
+        pct = lambda q: ls[min(len(ls) - 1, int(math.ceil(q * len(ls))) - 1)]   # noqa: E731
+        out.update({"value": round(job_rate(nrhs, world, ms / 1000.0), 3), "unit": UNIT,
+                    "batches": len(lat), "ms_per_batch": round(ms, 2),
+                    "latency_ms": {"p50": round(pct(0.5), 2), "p99": round(pct(0.99), 2),
+                                   "note": f"per batch of {nrhs}, over {len(lat)} batches"},
+                    "iterations_max": max(i.iterations for i in info),
+                    "max_true_residual": max(i.true_residual for i in info)})
+        # where the time of one batched solve goes (eager, CUDA events per kernel family)
+        mg.mg_profile_enable(s.h, 1)
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)
+        out["family_ms_per_solve"] = {FAM_NAMES[f]: round(mg.mg_profile_read(s.h, f)[0], 2)
+                                      for f in range(mg.KF_COUNT)}
+        mg.mg_profile_enable(s.h, 0)
+        # plain FP64 single-RHS MG-CG on b_0, capped in time
+        b0 = b_d[0].contiguous()
+        x0 = torch.empty_like(b0)
+        cap = max(1, args.plain_iter_cap)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        st, info1 = mg.mg_solve(s.h, b0, x0, 1, tol, cap, mg.SOLVER_MGCG_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = e0.elapsed_time(e1)
+        it1 = info1[0].iterations
+        conv = st == 0 and info1[0].true_residual <= tol
+        mixed_iters = max(i.iterations for i in info)
+        plain = {"iterations": it1, "ms": round(t1, 2), "converged": bool(conv),
+                 "true_residual": info1[0].true_residual}
+        if conv:
+            plain["value"] = round(job_rate(1, world, t1 / 1000.0), 4)
+        else:   # the same per-iteration cost over the mixed solver's iteration count (labelled)
+            plain["value_extrapolated"] = round(job_rate(1, world, t1 / 1000.0 * mixed_iters / max(it1, 1)), 4)
+            plain["note"] = (f"stopped at {cap} iterations; rate extrapolated to the mixed batch's "
+                             f"{mixed_iters} iterations at the measured cost per iteration")
+        out["plain_fp64_single_rhs"] = plain
+        pv = plain.get("value", plain.get("value_extrapolated"))
+        out["vs_plain_fp64_single_rhs"] = round(out["value"] / world / pv, 2) if pv else None
+        # level-2 multi-RHS BF16 coarse apply (tcgen05) and fine stencil on nrhs vectors
+        Lx2, Lt2, n2, _ = mg.mg_get_level(s.h, 2)
+        xc = torch.randn((nrhs, Lt2, Lx2, n2), dtype=torch.complex64, device=dev)
+        yc = torch.empty_like(xc)
+        xf = torch.randn((nrhs, Lt, Lx, 2), dtype=torch.complex64, device=dev)
+        yf = torch.empty_like(xf)
+
+        def kernel_us(fn, reps=20):
+            for _ in range(3):
+                fn()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) * 1e3 / reps
+        peaks = load_peaks()
+        us_c = kernel_us(lambda: mg.mg_apply_coarse(s.h, 2, xc, yc, nrhs, mg.PREC_BF16))
+        byt_c = Lx2 * Lt2 * (9 * n2 * n2 * 4.0 + 2 * n2 * nrhs * 8.0)
+        fl_c = 8.0 * 9 * n2 * n2 * nrhs * Lx2 * Lt2
+        out["coarse_apply_level2"] = {
+            "kernel": "tcgen05 multi-RHS BF16 coarse apply", "sites": Lx2 * Lt2, "dof": n2, "nrhs": nrhs,
+            "us": round(us_c, 2), "bytes": int(byt_c), "achieved_gbs": round(byt_c / us_c / 1e3, 1),
+            "frac_hbm": round(byt_c / us_c / 1e3 / peaks["hbm_gbs"], 4),
+            "tflops": round(fl_c / us_c / 1e6, 2), "peak_note": f"of {peaks['src']}",
+            "timing": "20 back-to-back launches between CUDA events on the library stream"}
+        us_f = kernel_us(lambda: mg.mg_apply_A(s.h, xf, yf, nrhs, mg.PREC_F32))
+        byt_f = Lx * Lt * (32.0 * nrhs + 16.0)
+        out["fine_stencil"] = {"precision": "f32", "nrhs": nrhs, "us": round(us_f, 2),
+                               "bytes_per_site": 32 * nrhs + 16, "achieved_gbs": round(byt_f / us_f / 1e3, 1),
+                               "frac_hbm": round(byt_f / us_f / 1e3 / peaks["hbm_gbs"], 4),
+                               "peak_note": f"of {peaks['src']}",
+                               "working_set_mb": round(Lx * Lt * (32.0 * nrhs + 16.0) / 2 ** 20, 1)}
+    finally:
+        s.close()
     return out
 
 
@@ -894,6 +1059,11 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64,
                     help="right-hand sides of the batched leg (0 skips it)")
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--config-legs", default="L256_b10_nc64,L1024_b10_nc16_l5",
+                    help="batched workloads at their near-critical mass ('' skips them)")
+    ap.add_argument("--config-reps", type=int, default=3)
+    ap.add_argument("--plain-iter-cap", type=int, default=400,
+                    help="iteration cap of the plain FP64 single-RHS solve of the batched workloads")
     ap.add_argument("--adaptive-plan", default="112222",
                     help="levels refined by the adaptive passes of the adaptive leg ('' skips it)")
     ap.add_argument("--adaptive-cycles", type=int, default=30)

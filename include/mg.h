@@ -106,7 +106,7 @@ typedef struct {
                                            many unknowns use the dense FP32
                                            inverse with FP64 refinement; larger
                                            ones FP64 CG on the coarsest stencil
-                                           (16384, the largest dense size)      */
+                                           (16384; at most 24576)               */
   int coarsest_gj_tcgen05;              /* rank-64 updates of the dense inverse
                                            on tcgen05 tensor cores (TMEM
                                            accumulator, 1) or with mma.sync

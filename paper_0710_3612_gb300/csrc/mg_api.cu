@@ -105,8 +105,8 @@ struct mg_handle {
 
 namespace {
 
-// Largest coarsest level handled by the dense inverse (FP32 N x N: 2 GiB).
-constexpr long long MG_DENSE_MAX = 16384;
+// Largest coarsest level the dense inverse may take (FP32 N x N: 4.5 GiB).
+constexpr long long MG_DENSE_MAX = 24576;
 
 // scalar slots (each a double2)
 // scalar slots: slot k holds one double2 per right-hand side
@@ -1365,7 +1365,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->vcycle_coarse_bf16 = 1;
   p->max_rhs = 1;
   p->profile = 0;
-  p->coarsest_dense_max = (int)MG_DENSE_MAX;
+  p->coarsest_dense_max = 16384;
   p->coarsest_gj_tcgen05 = 0;
   p->refine_cycles = 30;
   p->autotune = 1;

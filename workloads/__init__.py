@@ -272,3 +272,23 @@ BENCH_WORKLOADS = {
                              Nv=[8, 8], setup_sweeps=8, heavy_masses=[-0.05, 0.0, 0.1],
                              critical_key="L128_b6_s1", noise_seed=7, chi_seed=101, tol=1e-10),
 }
+
+# Batched workloads at the near-critical mass: nrhs Gaussian sources (seeds
+# chi_seed + k), b_k = D^dagger chi_k, all solved in one Krylov loop.
+#   256 x 256, beta = 10 (500 sweeps), 3 levels (4x4, 2x2), Nv = 8, 64 RHS;
+#   1024 x 1024, beta = 10 (500 sweeps), 4 levels (4x4, 2x2, 2x2), Nv = 12, 16 RHS.
+BATCHED_WORKLOADS = {
+    "L256_b10_nc64": dict(Lx=256, Lt=256, beta=10.0, sweeps=500, seed=1, blocks=[(4, 4), (2, 2)],
+                          Nv=[8, 8], setup_sweeps=8, nrhs=64, critical_key="L256_b10_s1",
+                          noise_seed=7, chi_seed=101, tol=1e-10),
+    "L1024_b10_nc16": dict(Lx=1024, Lt=1024, beta=10.0, sweeps=500, seed=1,
+                           blocks=[(4, 4), (2, 2), (2, 2)], Nv=[12, 12, 12], setup_sweeps=8,
+                           nrhs=16, critical_key="L1024_b10_s1", noise_seed=7, chi_seed=101,
+                           tol=1e-10),
+    # the same with a fifth level (2x2 blocks): 24,576 coarsest unknowns instead
+    # of 98,304, inverted densely (FP32 inverse, FP64 refinement)
+    "L1024_b10_nc16_l5": dict(Lx=1024, Lt=1024, beta=10.0, sweeps=500, seed=1,
+                              blocks=[(4, 4), (2, 2), (2, 2), (2, 2)], Nv=[12, 12, 12, 12],
+                              setup_sweeps=8, nrhs=16, critical_key="L1024_b10_s1", noise_seed=7,
+                              chi_seed=101, tol=1e-10, params={"coarsest_dense_max": 24576}),
+}
