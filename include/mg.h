@@ -137,6 +137,20 @@ typedef struct {
                                            combination per level instead of the
                                            Galerkin products; two more FP64
                                            copies of each coarse operator (1)   */
+  double smooth_omega;                  /* smoothed aggregation of the first
+                                           coarsening (Sec. 3): the columns of
+                                           P (fine level -> level 2) become
+                                           P_s = (1 - omega A) P, and level 2 is
+                                           P_s^dagger A P_s.  0: off (default);
+                                           > 0: this omega; < 0: the omega in
+                                           [0, 2 / lambda~max(A)] minimising
+                                           the condition number of level 2
+                                           (two-level hierarchies with a dense
+                                           coarsest level only).  Needs level-1
+                                           blocks of at least 4 x 4 and coarse
+                                           extents of at least 3; excludes
+                                           refine_levels; remass_quadratic is
+                                           ignored (each mass is probed anew) */
 } mg_params;
 
 typedef struct {
@@ -339,7 +353,8 @@ mg_status mg_set_coarse_tensor_kernel(int kind);
 
 /* Restriction P^dagger from level `level` to level+1 (Sec. 2 step 2) and
  * prolongation P from level+1 to `level` (Sec. 2 step 4), 1 <= level < nlevels.
- * precision F64 or F32. */
+ * precision F64 or F32.  On a handle with smoothed aggregation, level 1 uses
+ * P_s = (1 - omega A) P and P_s^dagger (then nrhs <= max_rhs). */
 mg_status mg_restrict(mg_handle* h, int level, const void* fine_in, void* coarse_out, int nrhs,
                       int precision);
 mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_out, int nrhs,
@@ -370,6 +385,13 @@ mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out);
  * or within 5000 CG iterations.  Any output pointer may be NULL; MG_ERR_ARG
  * when h has one level. */
 mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, double* test_residual);
+
+/* Smoothed aggregation of the first coarsening (mg_params.smooth_omega):
+ * *omega the damping in use (0 when off) and *cond the condition number of
+ * the level-2 operator at that omega as the search estimated it (power
+ * iterations on A_2 and on its inverse; 0 when omega was given).  Any output
+ * pointer may be NULL. */
+mg_status mg_get_smoothing(const mg_handle* h, double* omega, double* cond);
 
 /* Level geometry: extents and dof per site; Nv of the blocking below it
  * (0 on the coarsest).  Any output pointer may be NULL. */

@@ -162,6 +162,18 @@ cudaError_t coarse_lincomb(double a, const void* X, double b, const void* Y, dou
 cudaError_t coarse_convert(const void* A64, void* out, int weights, long long count,
                            cudaStream_t s);
 
+// ---- column probing (smoothed Galerkin products) ---------------------------
+// Probe vectors: out[s][j][r] = 1 if r == s and site j has colour (cx, ct) =
+// (x mod Kx, t mod Kt), else 0 (nc vectors of Lxc x Ltc sites, nc dof,
+// complex128).  Scatter: Ac[j][d][r][s] = y[s][j][r] for every site j and
+// displacement d whose neighbour j + d has that colour (Ac complex128
+// [Vc][9][nc][nc]).  With Kx, Kt >= 3 dividing the extents and an operator
+// reaching one block, each entry is written by exactly one colour.
+cudaError_t probe_vectors(void* out, int Lxc, int Ltc, int nc, int Kx, int Kt, int cx, int ct,
+                          cudaStream_t s);
+cudaError_t probe_scatter(const void* y, void* Ac, int Lxc, int Ltc, int nc, int Kx, int Kt, int cx,
+                          int ct, cudaStream_t s);
+
 // ---- transfer ------------------------------------------------------------
 // Vst: [V_f][2][Nv][h] complex (h = n_f / 2), the per-site storage of P.
 template <typename R>

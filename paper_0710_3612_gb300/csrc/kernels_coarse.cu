@@ -335,6 +335,52 @@ cudaError_t coarse_lincomb(double a, const void* X, double b, const void* Y, dou
 }
 
 // ---------------------------------------------------------------------------
+// Column probing of a coarse operator whose couplings reach one block (the
+// Galerkin product of the smoothed prolongator, Sec. 3).  Sites are coloured
+// by (x mod Kx, t mod Kt) with Kx, Kt >= 3 dividing the extents, so that two
+// sites of one colour are never within one block of the same site.
+// ---------------------------------------------------------------------------
+__global__ void k_probe_vectors(double2* __restrict__ out, int Lxc, int Ltc, int nc, int Kx, int Kt,
+                                int cx, int ct) {
+  const long long Vc = (long long)Lxc * Ltc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nc * Vc * nc) return;
+  const int r = (int)(idx % nc), s = (int)(idx / (Vc * nc));
+  const int j = (int)((idx / nc) % Vc), jx = j % Lxc, jt = j / Lxc;
+  const bool on = r == s && jx % Kx == cx && jt % Kt == ct;
+  out[idx] = make_double2(on ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void k_probe_scatter(const double2* __restrict__ y, double2* __restrict__ Ac, int Lxc,
+                                int Ltc, int nc, int Kx, int Kt, int cx, int ct) {
+  const long long Vc = (long long)Lxc * Ltc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Vc * 9 * nc * nc) return;
+  const int sc = (int)(idx % nc), r = (int)((idx / nc) % nc), d = (int)((idx / ((long long)nc * nc)) % 9);
+  const int j = (int)(idx / (9LL * nc * nc)), jx = j % Lxc, jt = j / Lxc;
+  const int xn = (jx + d % 3 - 1 + Lxc) % Lxc, tn = (jt + d / 3 - 1 + Ltc) % Ltc;
+  if (xn % Kx == cx && tn % Kt == ct) Ac[idx] = y[((long long)sc * Vc + j) * nc + r];
+}
+
+cudaError_t probe_vectors(void* out, int Lxc, int Ltc, int nc, int Kx, int Kt, int cx, int ct,
+                          cudaStream_t s) {
+  const long long n = (long long)nc * Lxc * Ltc * nc;
+  k_probe_vectors<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2*)out, Lxc, Ltc, nc, Kx, Kt,
+                                                            cx, ct);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t probe_scatter(const void* y, void* Ac, int Lxc, int Ltc, int nc, int Kx, int Kt, int cx,
+                          int ct, cudaStream_t s) {
+  const long long n = (long long)Lxc * Ltc * 9 * nc * nc;
+  k_probe_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double2*)y, (double2*)Ac, Lxc,
+                                                            Ltc, nc, Kx, Kt, cx, ct);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Restriction and prolongation.  Vst[i][c][k][a]: component c*h + a of vector
 // k at fine site i, orthonormal per (block, chirality).
 // ---------------------------------------------------------------------------

@@ -65,6 +65,8 @@ struct mg_handle {
   bool dense = true;            // dense inverse (else CG on the coarsest stencil)
   int ccg_iters = 0;            // CG iterations of one coarsest solve (fixed at set-up)
   double coarsest_test_res = 0; // worst relative residual of the set-up's test vectors
+  double smooth = 0.0;          // omega of the smoothed first coarsening in use (0: off)
+  double smooth_cond = 0.0;     // condition number of level 2 found by the omega search
   bool poisoned = false;        // a bounded device wait ran out: device state undefined
   double2 *cp = nullptr, *cq = nullptr;                  // coarsest CG vectors
   // CUDA graphs of the Krylov loop (one per preconditioner mode), launched on
@@ -290,22 +292,28 @@ void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
   void* r = w[2];
   // 1. x = R b = c0 b + c1 A b
   apply_level<R>(h, l, b, x, nrhs, weights, ep_lincomb(L.c1, b, L.c0));
-  // 2. r_c = P^dagger (b - A x)
+  // 2. r_c = P^dagger (b - A x); smoothed first coarsening: P_s^dagger r = P^dagger (r - omega A r)
   apply_level<R>(h, l, x, r, nrhs, weights, ep_lincomb(-1.0, b, 1.0));
+  const bool smoothed = l == 0 && h->smooth != 0.0;
+  if (smoothed) apply_level<R>(h, 0, r, w[3], nrhs, weights, ep_lincomb(-h->smooth, r, 1.0));
   const void* Vst = f64 ? (const void*)L.Vst64 : (const void*)L.Vst32;
   {
     ProfScope prof(h, MG_KF_TRANSFER);
-    ck(h, restrict_op<R>(r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s),
+    ck(h, restrict_op<R>(smoothed ? w[3] : r, wc[0], Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv,
+                         nrhs, h->s),
        "restrict");
   }
   // 3. e_c = V_{l+1} r_c
   vcycle<R>(h, l + 1, wc[0], wc[1], nrhs);
-  // 4. x = x + P e_c
+  // 4. x = x + P e_c; smoothed: x = x + p - omega A p with p = P e_c
   {
     ProfScope prof(h, MG_KF_TRANSFER);
-    ck(h, prolong_op<R>(wc[1], x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, true, h->s),
+    ck(h, prolong_op<R>(wc[1], smoothed ? w[3] : x, Vst, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv,
+                        nrhs, !smoothed, h->s),
        "prolong");
   }
+  if (smoothed)
+    apply_level<R>(h, 0, w[3], x, nrhs, weights, ep_lincomb(-h->smooth, w[3], 1.0, x, 1.0));
   // 5. x = x + R (b - A x):  r = b - A x, then x = x + c0 r + c1 A r
   apply_level<R>(h, l, x, r, nrhs, weights, ep_lincomb(-1.0, b, 1.0));
   apply_level<R>(h, l, r, x, nrhs, weights, ep_lincomb(L.c1, r, L.c0, x, 1.0));
@@ -368,6 +376,8 @@ void build_quadratic(mg_handle* h) {
   h->g_built = true;
 }
 
+void galerkin_next(mg_handle* h, int l);
+
 void build_coarse_ops(mg_handle* h) {
   if (h->p.remass_quadratic) {
     if (!h->g_built) build_quadratic(h);
@@ -386,13 +396,7 @@ void build_coarse_ops(mg_handle* h) {
     Level& L = h->lv[l];
     Level& C = h->lv[l + 1];
     ProfScope prof(h, MG_KF_GALERKIN);
-    if (l == 0)
-      ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt,
-                          L.Nv, h->s),
-         "galerkin_fine");
-    else
-      ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s),
-         "galerkin_coarse");
+    galerkin_next(h, l);
     const long long cnt = (long long)C.V * 9 * C.n * C.n;
     ck(h, coarse_convert(C.A64, C.A32, W_F32, cnt, h->s), "convert f32");
     ck(h, coarse_convert(C.A64, C.A16, W_BF16, cnt, h->s), "convert bf16");
@@ -559,6 +563,14 @@ void set_mass_internal(mg_handle* h, double mass) {
 }
 
 // Adaptive passes asked for by p (refine_levels up to the first 0).
+// Parameters as the handle uses them: smoothed aggregation probes every mass
+// anew, so it keeps no quadratic re-mass coefficients.
+mg_params normalized(const mg_params& p) {
+  mg_params q = p;
+  if (q.smooth_omega != 0.0) q.remass_quadratic = 0;
+  return q;
+}
+
 int refine_count(const mg_params* p) {
   int k = 0;
   while (k < MG_MAX_REFINE && p->refine_levels[k] != 0) ++k;
@@ -612,6 +624,24 @@ mg_status validate(const mg_params* p, std::string& msg) {
   if (p->coarsest_dense_max < 0 || p->coarsest_dense_max > MG_DENSE_MAX) {
     msg = "coarsest_dense_max must be in [0, " + std::to_string(MG_DENSE_MAX) + "]";
     return MG_ERR_ARG;
+  }
+  if (p->smooth_omega != 0.0) {
+    if (!std::isfinite(p->smooth_omega) || p->nlevels < 2) {
+      msg = "smooth_omega needs a finite value and nlevels >= 2";
+      return MG_ERR_ARG;
+    }
+    if (p->block[0][0] < 4 || p->block[0][1] < 4 || p->Lx / p->block[0][0] < 3 ||
+        p->Lt / p->block[0][1] < 3) {
+      msg = "smoothed aggregation needs level-1 blocks of at least 4 x 4 and coarse extents of at least 3";
+      return MG_ERR_ARG;
+    }
+    if (refine_count(p)) { msg = "smoothed aggregation excludes refine_levels"; return MG_ERR_ARG; }
+    if (p->smooth_omega < 0.0 &&
+        (p->nlevels != 2 || (long long)(p->Lx / p->block[0][0]) * (p->Lt / p->block[0][1]) * 2 *
+                                    p->Nv[0] > p->coarsest_dense_max)) {
+      msg = "the omega search needs two levels with a dense coarsest level";
+      return MG_ERR_ARG;
+    }
   }
   const int np = refine_count(p);
   if (np) {
@@ -1049,14 +1079,194 @@ long long setup_temp_bytes(const mg_handle* h) {
   long long t = 0;
   for (int l = 0; l + 1 < h->L; ++l)
     t = std::max(t, 2LL * h->lv[l].Nv * h->lv[l].count() * (long long)sizeof(double2));
+  if (h->p.smooth_omega != 0.0 && h->L > 1) {   // column probing of the smoothed level 2
+    const Level& L = h->lv[0];
+    const Level& C = h->lv[1];
+    const long long nc = 2LL * L.Nv;
+    t = std::max(t, (3 * nc * L.count() + 2 * nc * C.count() + 3LL * C.V * 9 * C.n * C.n) *
+                        (long long)sizeof(double2));
+  }
   return t;
+}
+
+// ----- smoothed aggregation of the first coarsening (Sec. 3) ----------------
+// Colour period of the column probing along an axis of `L` coarse sites: the
+// smallest divisor >= 3 (sites of one colour are then at least 3 apart).
+int probe_period(int L) {
+  for (int k = 3; k < L; ++k)
+    if (L % k == 0) return k;
+  return L;
+}
+
+// G_k = P^dagger A^(k+1) P (k = 0, 1, 2) on level 2, by column probing: for
+// each colour, the 2 Nv probe vectors are prolonged, A is applied three times,
+// and the restrictions of A w, A^2 w, A^3 w are scattered into G_0, G_1, G_2.
+// The level-2 operator of P_s = (1 - omega A) P is then
+// P_s^dagger A P_s = G_0 - 2 omega G_1 + omega^2 G_2.
+void smoothed_products(mg_handle* h, double2* G[3]) {
+  Level& L = h->lv[0];
+  Level& C = h->lv[1];
+  const int nc = 2 * L.Nv;
+  const long long c = L.count(), cc = C.count();
+  ProfScope prof(h, MG_KF_GALERKIN);
+  void* W = dalloc(h, (size_t)nc * c * sizeof(double2));
+  void* T1 = dalloc(h, (size_t)nc * c * sizeof(double2));
+  void* T2 = dalloc(h, (size_t)nc * c * sizeof(double2));
+  void* E = dalloc(h, (size_t)nc * cc * sizeof(double2));
+  void* Y = dalloc(h, (size_t)nc * cc * sizeof(double2));
+  const int Kx = probe_period(C.Lx), Kt = probe_period(C.Lt);
+  for (int ct = 0; ct < Kt; ++ct)
+    for (int cx = 0; cx < Kx; ++cx) {
+      ck(h, probe_vectors(E, C.Lx, C.Lt, nc, Kx, Kt, cx, ct, h->s), "probe vectors");
+      ck(h, prolong_op<double>(E, W, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nc, false, h->s),
+         "probe prolong");
+      const void* in = W;
+      void* outs[3] = {T1, T2, T1};
+      for (int k = 0; k < 3; ++k) {
+        apply_level<double>(h, 0, in, outs[k], nc, W_F64);
+        ck(h, restrict_op<double>(outs[k], Y, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nc, h->s),
+           "probe restrict");
+        ck(h, probe_scatter(Y, G[k], C.Lx, C.Lt, nc, Kx, Kt, cx, ct, h->s), "probe scatter");
+        in = outs[k];
+      }
+    }
+  sync(h);
+  for (void* q : {W, T1, T2, E, Y}) {
+    for (auto& a : h->allocs)
+      if (a == q) a = nullptr;
+    cudaFree(q);
+  }
+  h->bytes -= (3LL * nc * c + 2LL * nc * cc) * (long long)sizeof(double2);
+}
+
+void smoothed_combination(mg_handle* h, double2* const G[3], double omega) {
+  Level& C = h->lv[1];
+  ck(h, coarse_lincomb(1.0, G[0], -2.0 * omega, G[1], 0.0, C.A64, C.V, C.n, h->s), "A_c(omega)");
+  ck(h, coarse_lincomb(1.0, C.A64, omega * omega, G[2], 0.0, C.A64, C.V, C.n, h->s), "A_c(omega)");
+}
+
+// Largest eigenvalue of a Hermitian positive operator on n entries by
+// `iters` power iterations from v (overwritten), with w as scratch: the
+// Rayleigh quotient <v, apply(v)> of the last normalised iterate.
+template <typename F>
+double power_rq(mg_handle* h, long long n, void* v, void* w, int iters, F apply) {
+  ck(h, norm2<double>(v, n, 1, h->partials, slot(h, S_T0), h->s), "norm");
+  ck(h, scale_inv_sqrt<double>(v, v, slot(h, S_T0), n, 1, h->s), "scale");
+  for (int it = 0; it < iters; ++it) {
+    apply(v, w);
+    if (it == iters - 1) ck(h, dot<double>(v, w, n, 1, h->partials, slot(h, S_T1), h->s), "dot");
+    ck(h, norm2<double>(w, n, 1, h->partials, slot(h, S_T0), h->s), "norm");
+    ck(h, scale_inv_sqrt<double>(w, v, slot(h, S_T0), n, 1, h->s), "scale");
+  }
+  return read_scalar(h, S_T1);
+}
+
+// Condition number of the two-level hierarchy's level 2 (its coarsest level,
+// with the dense inverse built): lambda_max from power iterations on A_2,
+// lambda_min as 1 / lambda_max(A_2^-1) from power iterations on the coarsest
+// solve, both from fixed Gaussian starts.
+constexpr int SMOOTH_POWER_ITERS = 200;
+
+double coarse_condition(mg_handle* h) {
+  Level& C = h->lv[1];
+  const long long n = C.count();
+  void* v = C.w64[0];
+  void* w = C.w64[1];
+  std::vector<double2> st = coarsest_test_vector(n, 11);
+  ck(h, cudaMemcpyAsync(v, st.data(), n * sizeof(double2), cudaMemcpyHostToDevice, h->s), "upload");
+  const double lmax = power_rq(h, n, v, w, SMOOTH_POWER_ITERS, [&](void* a, void* b) {
+    apply_level<double>(h, 1, a, b, 1, W_F64);
+  });
+  st = coarsest_test_vector(n, 12);
+  ck(h, cudaMemcpyAsync(v, st.data(), n * sizeof(double2), cudaMemcpyHostToDevice, h->s), "upload");
+  const double mu = power_rq(h, n, v, w, SMOOTH_POWER_ITERS, [&](void* a, void* b) {
+    coarsest_solve64(h, (const double2*)a, (double2*)b, h->n_refine, 1);
+  });
+  if (!(lmax > 0.0) || !(mu > 0.0)) return INFINITY;
+  return lmax * mu;
+}
+
+// omega in [0, 2 / lambda~max(A)] minimising the condition number of level 2
+// (Sec. 3: the damping of the smoothing step), the best of an even grid of 41
+// points refined by 40 golden-section steps on the bracket around it.  An omega
+// for which the dense coarsest inverse cannot be refined to coarsest_tol
+// counts as infinitely ill-conditioned.
+double smoothed_search(mg_handle* h, double2* const G[3], double* cond_out) {
+  const double lam = h->lv[0].lambda_max;
+  auto f = [&](double w) {
+    smoothed_combination(h, G, w);
+    try {
+      build_coarsest(h);
+    } catch (const Fail&) {
+      return (double)INFINITY;
+    }
+    return coarse_condition(h);
+  };
+  const int samples = 41, refine = 40;
+  std::vector<double> grid(samples), vals(samples);
+  for (int k = 0; k < samples; ++k) {
+    grid[k] = 2.0 / lam * k / (samples - 1);
+    vals[k] = f(grid[k]);
+  }
+  int kb = 0;
+  for (int k = 1; k < samples; ++k)
+    if (vals[k] < vals[kb]) kb = k;
+  double a = grid[std::max(kb - 1, 0)], b = grid[std::min(kb + 1, samples - 1)];
+  const double g = (std::sqrt(5.0) - 1.0) / 2.0;
+  double c = b - g * (b - a), d = a + g * (b - a);
+  double fc = f(c), fd = f(d);
+  for (int it = 0; it < refine; ++it) {
+    if (fc < fd) {
+      b = d; d = c; fd = fc;
+      c = b - g * (b - a);
+      fc = f(c);
+    } else {
+      a = c; c = d; fc = fd;
+      d = a + g * (b - a);
+      fd = f(d);
+    }
+  }
+  double best = grid[kb], fb = vals[kb];
+  if (fc < fb) { best = c; fb = fc; }
+  if (fd < fb) { best = d; fb = fd; }
+  if (!std::isfinite(fb)) fail(h, MG_ERR_NOCONV, "smoothed aggregation: no omega gives a usable level 2");
+  *cond_out = fb;
+  return best;
+}
+
+// Level 2 from the smoothed prolongator: omega in use, else the given one, else searched.
+void galerkin_smoothed(mg_handle* h) {
+  Level& C = h->lv[1];
+  const size_t ab = (size_t)C.V * 9 * C.n * C.n * sizeof(double2);
+  double2* G[3];
+  for (auto& q : G) q = dalloc<double2>(h, ab);
+  smoothed_products(h, G);
+  if (h->smooth == 0.0) {
+    if (h->p.smooth_omega > 0.0) {
+      h->smooth = h->p.smooth_omega;
+    } else {
+      double cond = 0.0;
+      h->smooth = smoothed_search(h, G, &cond);
+      h->smooth_cond = cond;
+    }
+  }
+  smoothed_combination(h, G, h->smooth);
+  sync(h);
+  for (double2* q : G) {
+    for (auto& a : h->allocs)
+      if (a == q) a = nullptr;
+    cudaFree(q);
+  }
+  h->bytes -= 3LL * (long long)ab;
 }
 
 // Galerkin operator of level l + 1 from the vectors of level l (FP64 master only).
 void galerkin_next(mg_handle* h, int l) {
   Level& L = h->lv[l];
   Level& C = h->lv[l + 1];
-  if (l == 0)
+  if (l == 0 && h->p.smooth_omega != 0.0)
+    galerkin_smoothed(h);
+  else if (l == 0)
     ck(h, galerkin_fine(h->U64, 4.0 + h->mass, L.Vst64, h->Wbuf, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.Nv, h->s), "galerkin_fine");
   else
     ck(h, galerkin_coarse(L.A64, L.Vst64, C.A64, L.Lx, L.Lt, L.bx, L.bt, L.n, L.Nv, h->s), "galerkin_coarse");
@@ -1402,7 +1612,7 @@ mg_status mg_setup(const void* gauge, double mass, const mg_params* params, void
   if (!gauge) { g_last_error = "gauge is NULL"; return MG_ERR_ARG; }
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) { g_last_error = "host allocation failed"; return MG_ERR_NOMEM; }
-  h->p = *params;
+  h->p = normalized(*params);
   h->s = (cudaStream_t)stream;
   h->L = params->nlevels;
   h->R = params->max_rhs;
@@ -1476,7 +1686,7 @@ mg_status mg_setup_bytes(const mg_params* params, long long* resident, long long
     return tmp.bytes;
   };
   long long temp = 0;
-  long long res = dry(after_passes(params, 0), &temp);
+  long long res = dry(normalized(after_passes(params, 0)), &temp);
   long long top = res + temp;
   const int np = refine_count(params);
   for (int k = 0; k < np; ++k) {
@@ -1531,6 +1741,8 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
       L.lambda_max = S.lambda_max;
       L.omega_relax = S.omega_relax;
     }
+    h->smooth = src->smooth;           // the damping found for the source is kept
+    h->smooth_cond = src->smooth_cond;
     if (h->p.remass_quadratic && src->g_built) {
       for (int l = 1; l < h->L; ++l) {
         const size_t ab = (size_t)h->lv[l].V * 9 * h->lv[l].n * h->lv[l].n * sizeof(double2);
@@ -1553,6 +1765,10 @@ mg_status mg_clone(const mg_handle* src, double mass, void* stream, mg_handle** 
 
 mg_status mg_refine(mg_handle* src, int level, const void* e0, int ncycles, const void* noise,
                     void* stream, mg_handle** out, double* rho, void* e_out) {
+  if (src && src->smooth != 0.0) {
+    src->err = "mg_refine: not available with smoothed aggregation";
+    return MG_ERR_ARG;
+  }
   if (!out) { g_last_error = "out is NULL"; return MG_ERR_ARG; }
   *out = nullptr;
   if (!src || !e0 || ncycles < 1 || level < 1 || level >= src->L) {
@@ -1792,24 +2008,45 @@ mg_status mg_set_coarse_tensor_kernel(int kind) {
 mg_status mg_restrict(mg_handle* h, int level, const void* fine_in, void* coarse_out, int nrhs, int precision) {
   if (!h) return MG_ERR_ARG;
   if (level < 1 || level >= h->L || !fine_in || !coarse_out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  const bool sm = level == 1 && h->smooth != 0.0;
+  if (sm && nrhs > h->R) { h->err = "smoothed restriction: nrhs above max_rhs"; return MG_ERR_ARG; }
   return guarded(h, [&]() {
-    const Level& L = h->lv[level - 1];
-    if (precision == MG_PREC_F64)
-      ck(h, restrict_op<double>(fine_in, coarse_out, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
-    else
-      ck(h, restrict_op<float>(fine_in, coarse_out, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
+    Level& L = h->lv[level - 1];
+    const void* in = fine_in;
+    if (precision == MG_PREC_F64) {
+      if (sm) {                        // P_s^dagger r = P^dagger (r - omega A r)
+        apply_level<double>(h, 0, fine_in, L.w64[3], nrhs, W_F64, ep_lincomb(-h->smooth, fine_in, 1.0));
+        in = L.w64[3];
+      }
+      ck(h, restrict_op<double>(in, coarse_out, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
+    } else {
+      if (sm) {
+        apply_level<float>(h, 0, fine_in, L.w32[3], nrhs, W_F32, ep_lincomb(-h->smooth, fine_in, 1.0));
+        in = L.w32[3];
+      }
+      ck(h, restrict_op<float>(in, coarse_out, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, h->s), "restrict");
+    }
   });
 }
 
 mg_status mg_prolong(mg_handle* h, int level, const void* coarse_in, void* fine_out, int nrhs, int precision) {
   if (!h) return MG_ERR_ARG;
   if (level < 1 || level >= h->L || !coarse_in || !fine_out || nrhs < 1 || (precision != MG_PREC_F64 && precision != MG_PREC_F32)) { h->err = "invalid arguments"; return MG_ERR_ARG; }
+  const bool sm = level == 1 && h->smooth != 0.0;
+  if (sm && nrhs > h->R) { h->err = "smoothed prolongation: nrhs above max_rhs"; return MG_ERR_ARG; }
   return guarded(h, [&]() {
-    const Level& L = h->lv[level - 1];
-    if (precision == MG_PREC_F64)
-      ck(h, prolong_op<double>(coarse_in, fine_out, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
-    else
-      ck(h, prolong_op<float>(coarse_in, fine_out, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
+    Level& L = h->lv[level - 1];
+    if (precision == MG_PREC_F64) {
+      void* p = sm ? L.w64[3] : fine_out;
+      ck(h, prolong_op<double>(coarse_in, p, L.Vst64, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
+      if (sm)                          // P_s e = p - omega A p
+        apply_level<double>(h, 0, p, fine_out, nrhs, W_F64, ep_lincomb(-h->smooth, p, 1.0));
+    } else {
+      void* p = sm ? L.w32[3] : fine_out;
+      ck(h, prolong_op<float>(coarse_in, p, L.Vst32, L.Lx, L.Lt, L.bx, L.bt, L.n / 2, L.Nv, nrhs, false, h->s), "prolong");
+      if (sm)
+        apply_level<float>(h, 0, p, fine_out, nrhs, W_F32, ep_lincomb(-h->smooth, p, 1.0));
+    }
   });
 }
 
@@ -1826,6 +2063,13 @@ mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out) {
   if (!h) return MG_ERR_ARG;
   if (!in || !out || h->L < 2) { h->err = "invalid arguments"; return MG_ERR_ARG; }
   return guarded(h, [&]() { coarsest_solve64(h, (const double2*)in, (double2*)out, h->n_refine, 1); });
+}
+
+mg_status mg_get_smoothing(const mg_handle* h, double* omega, double* cond) {
+  if (!h) return MG_ERR_ARG;
+  if (omega) *omega = h->smooth;
+  if (cond) *cond = h->smooth_cond;
+  return MG_OK;
 }
 
 mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, double* test_residual) {

@@ -38,7 +38,8 @@ class MgParams(ctypes.Structure):
                 ("max_rhs", ctypes.c_int), ("profile", ctypes.c_int),
                 ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
                 ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("remass_quadratic", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("remass_quadratic", ctypes.c_int),
+                ("smooth_omega", ctypes.c_double)]
 
 
 class MgStencilTuning(ctypes.Structure):
@@ -87,6 +88,7 @@ _SIGS = {
     "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "mg_get_coarsest_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "mg_get_smoothing": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "mg_apply_A_dot_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mg_set_coarse_tensor_kernel": (_i, [_i]),
@@ -344,6 +346,13 @@ def mg_get_smoother(h, level):
     buf = (ctypes.c_double * 4)()
     _check(lib().mg_get_smoother(h, level, buf), h)
     return tuple(buf)
+
+
+def mg_get_smoothing(h):
+    """(omega, cond) of the smoothed first coarsening (0, 0 when off)."""
+    om, cond = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mg_get_smoothing(h, ctypes.byref(om), ctypes.byref(cond)), h)
+    return om.value, cond.value
 
 
 COARSE_TC_TCGEN05, COARSE_TC_MMA_SYNC = 0, 1
