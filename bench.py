@@ -419,6 +419,9 @@ def gpu_bench(args):
     if cfg_pool is not None:
         cfg_pool.close()
 
+    # smoothed aggregation near the critical mass (NEXT-3)
+    smoothed = smoothed_leg(args, mg, torch, dev, stream) if args.smoothed_leg else None
+
     # roofline: one profiled step, dominant kernel family by device time
     prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
     roof = roofline(prof, wl, load_peaks())
@@ -458,10 +461,12 @@ def gpu_bench(args):
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
             "batched": batched,
             "batched_configs": config_legs,
+            "smoothed_aggregation": smoothed,
             "adaptive": adaptive,
             "serving": serving,
             "roofline": roof,
             "stencil": stencil_gbs(mg, torch, dev, stream),
+            "stencil_multi_rhs": stencil_multi_rhs(mg, torch, dev, stream),
             "autotune": mg.stencil_tunings(),
             "gauge_gen": gauge_gen_leg(mg, torch, dev, stream),
             "e2e": e2e,
@@ -585,6 +590,39 @@ def stencil_gbs(mg, torch, dev, stream):
         return {"lattice": [L, L], "precision": "f32", "median_us": round(med * 1000, 2),
                 "gbs": round(gbs, 1), "frac_hbm": round(gbs / peaks["hbm_gbs"], 4),
                 "bytes_per_site": 48}
+    finally:
+        mg.mg_destroy(h)
+
+
+def stencil_multi_rhs(mg, torch, dev, stream, L=1024, nrhs=16):
+    """Fused FP32 A on nrhs vectors of an L x L lattice (the 1024^2 x 16
+    workload's shape, about 550 MB per launch, above L2): algorithmic
+    32 nrhs + 16 bytes per site over CUDA-event time, median of 20 after 5
+    warm-ups (the autotuned launch shape)."""
+    U = torch.polar(torch.ones(2, L, L, dtype=torch.float64, device=dev),
+                    torch.rand(2, L, L, dtype=torch.float64, device=dev) * 0.5).contiguous()
+    p = mg.make_params(L, L, [], [], max_rhs=nrhs)
+    h = mg.mg_setup(U, 0.1, p, stream)
+    try:
+        x = torch.randn(nrhs * L * L * 2, dtype=torch.complex64, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(5):
+            mg.mg_apply_A(h, x, y, nrhs, mg.PREC_F32)
+        ts = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mg.mg_apply_A(h, x, y, nrhs, mg.PREC_F32)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        med = statistics.median(a.elapsed_time(b) for a, b in ts)
+        byt = (32.0 * nrhs + 16.0) * L * L
+        peaks = load_peaks()
+        return {"lattice": [L, L], "nrhs": nrhs, "precision": "f32", "median_us": round(med * 1000, 2),
+                "gbs": round(byt / (med / 1000.0) / 1e9, 1),
+                "frac_hbm": round(byt / (med / 1000.0) / 1e9 / peaks["hbm_gbs"], 4),
+                "bytes_per_site": 32 * nrhs + 16, "peak_note": f"of {peaks['src']}"}
     finally:
         mg.mg_destroy(h)
 
@@ -861,6 +899,59 @@ def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
     return out
 
 
+def smoothed_leg(args, mg, torch, dev, stream):
+    """Smoothed aggregation (Sec. 3) near the critical mass: 64 x 64, beta = 3
+    (200 sweeps, seed 1) at its near-critical mass (the oracle's finder), 4 x 4
+    blocks, Nv = 8.  omega from the condition-number search on the two-level
+    hierarchy; the same omega on three levels (4 x 4 then 2 x 2 blocks; the
+    first level's vectors are the same, so is the optimal omega).  FP64 and
+    mixed MG-CG iterations and CUDA-event times on one Gaussian source, with
+    the smoothed and with the tentative prolongator."""
+    crit = critical_table().get("L64_b3_s1")
+    L = 64
+    th = W.quenched_u1_angles(L, L, 3.0, 200, 1)
+    if crit is None or abs(W.mean_plaquette(th) - crit["plaquette"]) > 1e-12:
+        return {"unavailable": "no near-critical mass for the 64 x 64 beta 3 configuration"}
+    m = crit["m_nc"]
+    U = torch.from_numpy(W.links_from_angles(th)).to(dev)
+    b = torch.from_numpy(W.gaussian_field((L, L, 2), 303)).to(dev)
+    out = {"lattice": [L, L], "beta": 3.0, "mass": m, "m_crit": crit["m_crit"], "Nv": 8}
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+
+    def run(blocks, Nv, **kw):
+        noise = torch.from_numpy(W.setup_noise(L, L, blocks, Nv, 7)).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with mg.Multigrid(U, m, blocks, Nv, noise, stream=stream, **kw) as s:
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            om, cond = mg.mg_get_smoothing(s.h)
+            bd = torch.empty_like(b)
+            mg.mg_apply_D(s.h, b, bd, 1, 1, mg.PREC_F64)
+            r = {"setup_ms": round(setup_ms, 1), "omega": om}
+            if cond:
+                r["cond_level2"] = round(cond, 3)
+            for name, solver in (("fp64", mg.SOLVER_MGCG_FP64), ("mixed", mg.SOLVER_MGCG_MIXED)):
+                x = torch.empty_like(bd)
+                mg.mg_solve(s.h, bd, x, 1, 1e-10, 100000, solver)
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                st, info = mg.mg_solve(s.h, bd, x, 1, 1e-10, 100000, solver)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if st != 0 or info[0].true_residual > 1e-10:
+                    raise RuntimeError("smoothed leg: solve failed")
+                r[name] = {"iterations": info[0].iterations, "ms": round(e0.elapsed_time(e1), 2)}
+            return r
+    two = [(4, 4)]
+    three = [(4, 4), (2, 2)]
+    sm2 = run(two, [8], smooth_omega=-1.0)
+    out["two_levels"] = {"smoothed": sm2, "tentative": run(two, [8])}
+    out["three_levels"] = {"smoothed": run(three, [8, 8], smooth_omega=sm2["omega"]),
+                           "tentative": run(three, [8, 8])}
+    return out
+
+
 def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, world):
     """Same step through the public API with pinned host buffers copied in and
     the solutions copied out inside the timed region."""
@@ -947,16 +1038,56 @@ def run_oracle_subprocess(name, iters):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def host_cpu():
+    """Model name and logical core count of the host."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
 def cpu_baseline(args):
+    """The oracle on one host core, and the same sample run on every core at
+    once (independent processes, one BLAS thread each: the host's whole-CPU
+    rate for independent solves, the sum of the per-process rates)."""
+    from concurrent.futures import ThreadPoolExecutor
+    model, cores = host_cpu()
     t0 = time.perf_counter()
     s = run_oracle_subprocess(args.workload, args.oracle_iters)
     wall = time.perf_counter() - t0
     step_s, n_nc = scale_oracle(args.workload, s)
-    return {"value": round(4.0 / step_s, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"numpy FP64 oracle, 1 thread: setup at m_nc, {args.oracle_iters} MG-CG "
-                       f"iterations at m_nc, re-mass + full solve at m=0.1; scaled to the 4-mass "
-                       f"step with the oracle's iteration counts (m_nc: {n_nc})"),
-            "sample_wall_s": round(wall, 1), "scaled_step_s": round(step_s, 2)}
+    out = {"value": round(4.0 / step_s, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"numpy FP64 oracle, 1 thread: setup at m_nc, {args.oracle_iters} MG-CG "
+                      f"iterations at m_nc, re-mass + full solve at m=0.1; scaled to the 4-mass "
+                      f"step with the oracle's iteration counts (m_nc: {n_nc})"),
+           "sample_wall_s": round(wall, 1), "scaled_step_s": round(step_s, 2),
+           "host_cpu": model, "host_cores": cores}
+    if args.cpu_all_cores:
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            samples = list(ex.map(lambda _: run_oracle_subprocess(args.workload, args.oracle_iters),
+                                  range(cores)))
+        wall_all = time.perf_counter() - t0
+        rate = sum(4.0 / scale_oracle(args.workload, q)[0] for q in samples)
+        out["all_cores"] = {"value": round(rate, 5), "unit": UNIT, "cores": cores,
+                            "processes": cores, "sample_wall_s": round(wall_all, 1),
+                            "note": "one oracle process per core, each the 1-thread sample above"}
+    return out
 
 
 def reference_arm(args):
@@ -1062,12 +1193,15 @@ def main():
     ap.add_argument("--config-legs", default="L256_b10_nc64,L1024_b10_nc16_l5",
                     help="batched workloads at their near-critical mass ('' skips them)")
     ap.add_argument("--config-reps", type=int, default=3)
+    ap.add_argument("--smoothed-leg", type=int, default=1, help="1: run the smoothed-aggregation leg")
     ap.add_argument("--plain-iter-cap", type=int, default=400,
                     help="iteration cap of the plain FP64 single-RHS solve of the batched workloads")
     ap.add_argument("--adaptive-plan", default="112222",
                     help="levels refined by the adaptive passes of the adaptive leg ('' skips it)")
     ap.add_argument("--adaptive-cycles", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="1: also time the oracle sample on every host core at once")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests in the serving stream (0 skips the serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.7,
