@@ -30,6 +30,16 @@ def _sigma3(n_sites: int) -> sp.dia_matrix:
     return sp.diags(np.tile([1.0, -1.0], n_sites)).astype(np.complex128)
 
 
+def _shift_invert(M: sp.spmatrix) -> spla.LinearOperator:
+    """x -> M^-1 x by a sparse LU of M, for ARPACK's shift-invert mode.  The
+    lattice matrices have a symmetric sparsity pattern, so the fill-reducing
+    ordering is the minimum-degree ordering of M + M^T (far less fill than the
+    column ordering scipy's eigensolvers use by default on 2D lattices)."""
+    lu = spla.splu(M.tocsc(), permc_spec="MMD_AT_PLUS_A",
+                   options=dict(SymmetricMode=True, DiagPivotThresh=0.1))
+    return spla.LinearOperator(M.shape, matvec=lu.solve, dtype=np.complex128)
+
+
 def real_eigenvalues_D0(U: np.ndarray, k: int = 24, shift: float = 1.6, rel_imag: float = 1e-7):
     """Real eigenvalues of D_0 among the k eigenvalues nearest `shift`.
 
@@ -41,8 +51,10 @@ def real_eigenvalues_D0(U: np.ndarray, k: int = 24, shift: float = 1.6, rel_imag
     if n <= 2 * 32 * 32:
         lam = np.linalg.eigvals(D0.toarray())
     else:
+        n0 = D0.shape[0]
         lam = spla.eigs(D0.tocsc(), k=k, sigma=shift, which="LM", return_eigenvectors=False,
-                        tol=1e-12)
+                        tol=1e-12,
+                        OPinv=_shift_invert(D0 - shift * sp.identity(n0, dtype=np.complex128, format="csc")))
     real = np.sort(lam[np.abs(lam.imag) <= rel_imag * np.abs(lam)].real)
     return real, lam
 
@@ -55,7 +67,8 @@ def lambda_min_A(U: np.ndarray, m: float) -> float:
     if n <= 2 * 16 * 16:
         ev = np.linalg.eigvalsh(H.toarray())
     else:
-        ev = spla.eigsh(H, k=2, sigma=0.0, which="LM", return_eigenvectors=False, tol=1e-12)
+        ev = spla.eigsh(H, k=2, sigma=0.0, which="LM", return_eigenvectors=False, tol=1e-12,
+                        OPinv=_shift_invert(H))
     return float(np.min(np.abs(ev)) ** 2)
 
 
@@ -68,7 +81,7 @@ def nearest_eig_H(U: np.ndarray, m: float, D0=None):
     n = D.shape[0]
     s3 = _sigma3(n // 2)
     H = (s3 @ (D + m * sp.identity(n, dtype=np.complex128, format="csr"))).tocsc()
-    ev, vec = spla.eigsh(H, k=1, sigma=0.0, which="LM", tol=1e-13)
+    ev, vec = spla.eigsh(H, k=1, sigma=0.0, which="LM", tol=1e-13, OPinv=_shift_invert(H))
     v = vec[:, 0] / np.linalg.norm(vec[:, 0])
     return float(ev[0]), float(np.real(np.vdot(v, s3 @ v)))
 
