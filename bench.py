@@ -91,19 +91,22 @@ def workload_inputs(name):
 # ---------------------------------------------------------------------------
 # serving workload: Poisson arrivals over 8 configurations
 # ---------------------------------------------------------------------------
-# (key, L, beta, sweeps, seed, blocks, Nv): 64^2 beta 3, 128^2 beta 6, 256^2 and
-# 512^2 beta 10, two seeds each; three levels (four at 512^2, so that the
-# coarsest level keeps 16384 unknowns).
+# (key, L, beta, sweeps, seed, blocks, Nv, plan): 64^2 beta 3, 128^2 beta 6,
+# 256^2 and 512^2 beta 10, two seeds each.  Hierarchies end at a 16 x 16 x 16
+# coarsest level (4096 unknowns): three levels at 64^2 and 128^2, four at
+# 256^2, five at 512^2.  On 256^2 and 512^2 the set-up (at the near-critical
+# mass) adds two adaptive passes (Sec. 3), on levels 1 and 2, 30 V-cycles each.
 SERVING_CONFIGS = [
-    ("L64_b3_s1", 64, 3.0, 200, 1, [(4, 4), (2, 2)], [8, 8]),
-    ("L64_b3_s2", 64, 3.0, 200, 2, [(4, 4), (2, 2)], [8, 8]),
-    ("L128_b6_s1", 128, 6.0, 200, 1, [(4, 4), (2, 2)], [8, 8]),
-    ("L128_b6_s2", 128, 6.0, 200, 2, [(4, 4), (2, 2)], [8, 8]),
-    ("L256_b10_s1", 256, 10.0, 500, 1, [(4, 4), (2, 2)], [8, 8]),
-    ("L256_b10_s2", 256, 10.0, 500, 2, [(4, 4), (2, 2)], [8, 8]),
-    ("L512_b10_s1", 512, 10.0, 500, 1, [(4, 4), (2, 2), (2, 2)], [8, 8, 8]),
-    ("L512_b10_s2", 512, 10.0, 500, 2, [(4, 4), (2, 2), (2, 2)], [8, 8, 8]),
+    ("L64_b3_s1", 64, 3.0, 200, 1, [(4, 4), (2, 2)], [8, 8], ()),
+    ("L64_b3_s2", 64, 3.0, 200, 2, [(4, 4), (2, 2)], [8, 8], ()),
+    ("L128_b6_s1", 128, 6.0, 200, 1, [(4, 4), (2, 2)], [8, 8], ()),
+    ("L128_b6_s2", 128, 6.0, 200, 2, [(4, 4), (2, 2)], [8, 8], ()),
+    ("L256_b10_s1", 256, 10.0, 500, 1, [(4, 4), (2, 2), (2, 2)], [8, 8, 8], (1, 2)),
+    ("L256_b10_s2", 256, 10.0, 500, 2, [(4, 4), (2, 2), (2, 2)], [8, 8, 8], (1, 2)),
+    ("L512_b10_s1", 512, 10.0, 500, 1, [(4, 4), (2, 2), (2, 2), (2, 2)], [8, 8, 8, 8], (1, 2)),
+    ("L512_b10_s2", 512, 10.0, 500, 2, [(4, 4), (2, 2), (2, 2), (2, 2)], [8, 8, 8, 8], (1, 2)),
 ]
+SERVE_CYCLES = 30
 
 
 def _gauge_angles(args):
@@ -120,101 +123,159 @@ def critical_table():
     return out
 
 
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+
 def serving_leg(args, mg, torch, dev):
-    """Requests arrive as a Poisson stream over the 8 configurations (config
-    uniform, mass uniform over {0.05, 0.0, m_nc}, 1-16 Gaussian right-hand
-    sides, tol 1e-10, mixed solver) at a rate set to `--serve-load` times the
-    capacity estimated from a warm-up that builds every (config, mass)
-    hierarchy and then times one 8-right-hand-side request per (config, mass),
-    one at a time (8.5 is the mean request size).  Reported: right-hand
-    sides solved per second over the stream, and the submit-to-completion
-    latency percentiles of its requests."""
+    """Serving stream over the 8 configurations through the serving engine
+    (continuous batching per configuration and mass, 4 workers, max 16
+    right-hand sides per batch).  A request draws its configuration uniformly,
+    its mass uniformly from {0.05, 0.0, m_nc} and 1-16 Gaussian right-hand
+    sides; tol 1e-10, mixed solver.  After a warm-up that builds every
+    (configuration, mass) hierarchy:
+    * one at a time, one right-hand side per (configuration, mass) group with
+      the mixed solver and with plain FP64 MG-CG: the single-RHS service
+      times, from which the single-RHS throughput of each solver on the same
+      request mix follows (right-hand sides / sum of their service times);
+    * the saturation point: all requests of the stream submitted at once; its
+      right-hand sides per second is the capacity;
+    * Poisson points at each fraction of that capacity in --serve-loads.
+    Each point reports right-hand sides per second, submit-to-completion
+    latency p50/p99 and the same split by (configuration, mass) group."""
     import multiprocessing as mp
     crit = critical_table()
     with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
-        thetas = pool.map(_gauge_angles, [(L, beta, sw, seed) for _, L, beta, sw, seed, _, _ in SERVING_CONFIGS])
-    rng = np.random.default_rng(2024)
+        thetas = pool.map(_gauge_angles, [(c[1], c[2], c[3], c[4]) for c in SERVING_CONFIGS])
     gen = torch.Generator(device=dev).manual_seed(2024)
-    masses, missing = [], []
+    masses, missing, labels = [], [], []
+    t_build = time.perf_counter()
     with mg.Server(budget_bytes=args.serve_budget_gb << 30, max_rhs=16, workers=4) as srv:
         ids = []
-        for (key, L, beta, sw, seed, blocks, Nv), th in zip(SERVING_CONFIGS, thetas):
-            ms = [0.05, 0.0]
+        for (key, L, beta, sw, seed, blocks, Nv, plan), th in zip(SERVING_CONFIGS, thetas):
+            ms, lab = [0.05, 0.0], ["0.05", "0.0"]
             if key in crit and abs(W.mean_plaquette(th) - crit[key]["plaquette"]) <= 1e-12:
                 ms.append(crit[key]["m_nc"])
+                lab.append("m_nc")
             else:
                 missing.append(key)
             masses.append(ms)
+            labels.append(lab)
             U = torch.from_numpy(W.links_from_angles(th)).to(dev)
-            noise = torch.from_numpy(W.setup_noise(L, L, blocks, Nv, 7)).to(dev)
-            ids.append(srv.add_config(U, mg.make_params(L, L, blocks, Nv, setup_sweeps=8), min(ms),
-                                      noise=noise))
+            noise = torch.from_numpy(W.setup_noise(L, L, blocks, Nv, 7,
+                                                   refine_levels=[p - 1 for p in plan])).to(dev)
+            kw = dict(setup_sweeps=8)
+            if plan:
+                kw.update(refine_levels=list(plan), refine_cycles=SERVE_CYCLES)
+            ids.append(srv.add_config(U, mg.make_params(L, L, blocks, Nv, **kw), min(ms), noise=noise))
 
         def rhs(c, n):
             L = SERVING_CONFIGS[c][1]
             return torch.randn((n, L, L, 2), dtype=torch.complex128, device=dev, generator=gen)
 
-        # warm-up: every (config, mass) hierarchy built, then one timed solve each
-        def one_each():
-            warm = []
+        def one_at_a_time(solver):
+            out = {}
             for c in range(len(SERVING_CONFIGS)):
-                for m in masses[c]:
+                for m, lab in zip(masses[c], labels[c]):
                     b = rhs(c, 1)
                     x = torch.empty_like(b)
                     torch.cuda.synchronize()
-                    warm.append((srv.submit(ids[c], m, b, x, 1, 1e-10, mg.SOLVER_MGCG_MIXED), b, x))
-            return [srv.wait(r, 1)[2] for r, _, _ in warm]
-        one_each()
-        service = []
-        for c in range(len(SERVING_CONFIGS)):     # one at a time: service time of a mean-size request
-            for m in masses[c]:
-                b = rhs(c, 8)
-                x = torch.empty_like(b)
-                torch.cuda.synchronize()
-                service.append(srv.wait(srv.submit(ids[c], m, b, x, 8, 1e-10, mg.SOLVER_MGCG_MIXED), 8)[2])
-        mean_service_s = statistics.mean(service) / 1000.0
-        rate = args.serve_load / mean_service_s        # requests per second
-        # the stream
-        reqs = []
-        for _ in range(args.serve_requests):
-            c = int(rng.integers(len(SERVING_CONFIGS)))
-            reqs.append((c, masses[c][int(rng.integers(len(masses[c])))], int(rng.integers(1, 17))))
-        gaps = rng.exponential(1.0 / rate, size=len(reqs))
-        bufs = [(rhs(c, n), None) for c, _, n in reqs]
-        bufs = [(b, torch.empty_like(b)) for b, _ in bufs]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        submit_t, rids = [], []
-        for (c, m, n), (b, x), gap in zip(reqs, bufs, gaps):
-            t0 += gap
-            delay = t0 - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            submit_t.append(time.perf_counter())
-            rids.append(srv.submit(ids[c], m, b, x, n, 1e-10, mg.SOLVER_MGCG_MIXED))
-        lat, worst, failed = [], 0.0, 0
-        for r, (c, m, n) in zip(rids, reqs):
-            st, infos, ms = srv.wait(r, n)
-            failed += st != 0
-            lat.append(ms)
-            worst = max([worst] + [i.true_residual for i in infos])
-        end = max(t + l / 1000.0 for t, l in zip(submit_t, lat))
-        wall = end - submit_t[0]
+                    st, infos, ms = srv.wait(srv.submit(ids[c], m, b, x, 1, 1e-10, solver), 1)
+                    if st != 0:
+                        raise RuntimeError(f"serving warm-up solve failed ({st})")
+                    out[(c, lab)] = ms / 1000.0
+            return out
+        one_at_a_time(mg.SOLVER_MGCG_MIXED)          # builds every hierarchy
+        build_s = time.perf_counter() - t_build
+        single_mixed = one_at_a_time(mg.SOLVER_MGCG_MIXED)
+        single_fp64 = one_at_a_time(mg.SOLVER_MGCG_FP64)
+
+        def stream(seed, n_req):
+            rng = np.random.default_rng(seed)
+            reqs = []
+            for _ in range(n_req):
+                c = int(rng.integers(len(SERVING_CONFIGS)))
+                k = int(rng.integers(len(masses[c])))
+                reqs.append((c, k, int(rng.integers(1, 17))))
+            return rng, reqs
+
+        def run_point(seed, rate):
+            rng, reqs = stream(seed, args.serve_requests)
+            gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+            bufs = [rhs(c, n) for c, _, n in reqs]
+            bufs = [(b, torch.empty_like(b)) for b in bufs]
+            s0 = srv.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            submit_t, rids = [], []
+            for (c, k, n), (b, x), gap in zip(reqs, bufs, gaps):
+                t0 += gap
+                delay = t0 - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                submit_t.append(time.perf_counter())
+                rids.append(srv.submit(ids[c], masses[c][k], b, x, n, 1e-10, mg.SOLVER_MGCG_MIXED))
+            lat, worst, failed = [], 0.0, 0
+            for r, (c, k, n) in zip(rids, reqs):
+                st, infos, ms = srv.wait(r, n)
+                failed += st != 0
+                lat.append(ms)
+                worst = max([worst] + [i.true_residual for i in infos])
+            wall = max(t + l / 1000.0 for t, l in zip(submit_t, lat)) - submit_t[0]
+            s1 = srv.stats()
+            total_rhs = sum(n for _, _, n in reqs)
+            groups = {}
+            for (c, k, n), l in zip(reqs, lat):
+                groups.setdefault(f"{SERVING_CONFIGS[c][0]}@{labels[c][k]}", []).append((l, n))
+            by_group = {g: {"requests": len(v), "rhs": sum(n for _, n in v),
+                            "p50_ms": round(_pct([l for l, _ in v], 0.5), 1),
+                            "p99_ms": round(_pct([l for l, _ in v], 0.99), 1)}
+                        for g, v in sorted(groups.items())}
+            p99 = _pct(lat, 0.99)
+            tail = [g for g, v in by_group.items() if v["p99_ms"] >= 0.5 * p99]
+            nb = s1.batches - s0.batches
+            return {"requests": len(reqs), "rhs": total_rhs,
+                    "arrival_rate_per_s": round(rate, 4) if rate else None,
+                    "value": round(total_rhs / wall, 3), "wall_s": round(wall, 2),
+                    "p50_ms": round(_pct(lat, 0.5), 1), "p99_ms": round(p99, 1),
+                    "failed": failed, "max_true_residual": worst,
+                    "mean_batch_rhs": round((s1.batched_rhs - s0.batched_rhs) / max(nb, 1), 2),
+                    "groups_with_p99_above_half_of_overall": tail, "by_group": by_group}
+
+        # saturation, then Poisson points at fractions of the measured capacity
+        sat = run_point(2024, None)
+        mean_rhs = sat["rhs"] / sat["requests"]
+        points = [dict(sat, offered_load="all at once")]
+        for j, load in enumerate(float(v) for v in args.serve_loads.split(",") if v):
+            p = run_point(2025 + j, load * sat["value"] / mean_rhs)
+            points.append(dict(p, offered_load=load))
         stats = srv.stats()
-    lat.sort()
-    pct = lambda q: lat[min(len(lat) - 1, max(0, int(math.ceil(q * len(lat))) - 1))]   # noqa: E731
-    total_rhs = sum(n for _, _, n in reqs)
-    return {"configs": [k for k, *_ in SERVING_CONFIGS], "requests": len(reqs), "rhs": total_rhs,
-            "offered_load": args.serve_load, "arrival_rate_per_s": round(rate, 3),
-            "value": round(total_rhs / wall, 3), "unit": "solves/s (right-hand sides)",
-            "wall_s": round(wall, 3), "p50_ms": round(pct(0.50), 3), "p99_ms": round(pct(0.99), 3),
-            "failed": failed, "max_true_residual": worst,
-            "mean_batch_rhs": round(stats.batched_rhs / max(stats.batches, 1), 2),
+
+    # single-RHS throughput of each solver over the saturation stream's mix
+    _, reqs = stream(2024, args.serve_requests)
+    tot = sum(n for _, _, n in reqs)
+    one = lambda t: round(tot / sum(n * t[(c, labels[c][k])] for c, k, n in reqs), 3)   # noqa: E731
+    fp64_rate, mixed_rate = one(single_fp64), one(single_mixed)
+    return {"configs": [c[0] for c in SERVING_CONFIGS],
+            "hierarchies": {c[0]: {"levels": len(c[5]) + 1, "blocks": c[5], "Nv": c[6],
+                                   "adaptive_passes": list(c[7]), "cycles": SERVE_CYCLES if c[7] else 0}
+                            for c in SERVING_CONFIGS},
+            "unit": "solves/s (right-hand sides)",
+            "value": sat["value"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+            "capacity_rhs_per_s": sat["value"], "points": points,
+            "single_rhs_one_at_a_time": {
+                "plain_fp64_mgcg": fp64_rate, "mixed_mgcg": mixed_rate,
+                "note": "per-(configuration, mass) single-RHS service times on the same resident "
+                        "hierarchies, weighted by the saturation stream's right-hand-side counts"},
+            "capacity_vs_plain_fp64_single_rhs": round(sat["value"] / fp64_rate, 2),
+            "service_ms_single_rhs": {f"{SERVING_CONFIGS[c][0]}@{lab}": {
+                "mixed": round(single_mixed[(c, lab)] * 1e3, 1), "plain_fp64": round(single_fp64[(c, lab)] * 1e3, 1)}
+                for c, lab in sorted(single_mixed)},
+            "build_and_warmup_s": round(build_s, 1),
             "builds": stats.builds, "clones": stats.clones, "evictions": stats.evictions,
-            "remasses": stats.remasses,
-            "peak_resident_gb": round(stats.peak_resident_bytes / 2 ** 30, 2),
-            "budget_gb": args.serve_budget_gb, "masses_without_m_nc": missing,
-            "warmup_mean_service_ms": round(mean_service_s * 1000.0, 3)}
+            "remasses": stats.remasses, "peak_resident_gb": round(stats.peak_resident_bytes / 2 ** 30, 2),
+            "budget_gb": args.serve_budget_gb, "masses_without_m_nc": missing}
 
 
 # ---------------------------------------------------------------------------
@@ -282,6 +343,15 @@ def gpu_bench(args):
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    if args.serving_only:
+        mg.lib()
+        serving = serving_leg(args, mg, torch, dev)
+        if rank == 0:
+            print(json.dumps({"metric": "serving stream: right-hand sides solved per second at "
+                              "saturation, latency p50/p99 per offered load",
+                              "value": serving["value"], "unit": serving["unit"], "n_gpus": world,
+                              "higher_is_better": True, "data": "synthetic", "serving": serving}))
+        return
 
     # gauge fields of the batched workloads, generated on the host meanwhile
     import multiprocessing as mp
@@ -1203,9 +1273,11 @@ def main():
     ap.add_argument("--cpu-all-cores", type=int, default=1,
                     help="1: also time the oracle sample on every host core at once")
     ap.add_argument("--serve-requests", type=int, default=48,
-                    help="requests in the serving stream (0 skips the serving leg)")
-    ap.add_argument("--serve-load", type=float, default=0.7,
-                    help="offered load of the serving stream (fraction of estimated capacity)")
+                    help="requests per point of the serving leg (0 skips the serving leg)")
+    ap.add_argument("--serve-loads", default="0.7",
+                    help="Poisson points of the serving leg, as fractions of the measured capacity")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run the serving leg alone and print it as the JSON line")
     ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the plain-FP64, roofline, stencil and end-to-end legs (profiling runs)")
