@@ -109,6 +109,13 @@ SERVING_CONFIGS = [
 SERVE_CYCLES = 30
 
 
+# Mixed-precision solver of every leg: "reliable" = MG_SOLVER_MGCG_RELIABLE
+# (FP32 Krylov iteration, FP64 reliable updates), "mixed" = MG_SOLVER_MGCG_MIXED
+# (FP64 Krylov recursion); both use the FP32 V-cycle with BF16 coarse blocks.
+SOLVER_CODES = {"mixed": 1, "reliable": 3}
+MIXED_SOLVER = SOLVER_CODES["mixed"]
+
+
 def _gauge_angles(args):
     L, beta, sweeps, seed = args
     return W.quenched_u1_angles(L, L, beta, sweeps, seed)
@@ -186,9 +193,9 @@ def serving_leg(args, mg, torch, dev):
                         raise RuntimeError(f"serving warm-up solve failed ({st})")
                     out[(c, lab)] = ms / 1000.0
             return out
-        one_at_a_time(mg.SOLVER_MGCG_MIXED)          # builds every hierarchy
+        one_at_a_time(MIXED_SOLVER)          # builds every hierarchy
         build_s = time.perf_counter() - t_build
-        single_mixed = one_at_a_time(mg.SOLVER_MGCG_MIXED)
+        single_mixed = one_at_a_time(MIXED_SOLVER)
         single_fp64 = one_at_a_time(mg.SOLVER_MGCG_FP64)
 
         def stream(seed, n_req):
@@ -215,7 +222,7 @@ def serving_leg(args, mg, torch, dev):
                 if delay > 0:
                     time.sleep(delay)
                 submit_t.append(time.perf_counter())
-                rids.append(srv.submit(ids[c], masses[c][k], b, x, n, 1e-10, mg.SOLVER_MGCG_MIXED))
+                rids.append(srv.submit(ids[c], masses[c][k], b, x, n, 1e-10, MIXED_SOLVER))
             lat, worst, failed = [], 0.0, 0
             for r, (c, k, n) in zip(rids, reqs):
                 st, infos, ms = srv.wait(r, n)
@@ -448,11 +455,11 @@ def gpu_bench(args):
 
     # warm-up
     for _ in range(args.warmup):
-        step(mg.SOLVER_MGCG_MIXED)
+        step(MIXED_SOLVER)
     clocks = Clocks(local) if rank == 0 else None
     phases = [] if args.phase_launches else None
     base = mg.mg_kernel_launches()
-    res = timed(mg.SOLVER_MGCG_MIXED, args.steps, clocks, phases)
+    res = timed(MIXED_SOLVER, args.steps, clocks, phases)
     value = job_rate(len(masses) * args.steps, world, res["total_ms"] / 1000.0)
 
     if args.timed_only:
@@ -469,6 +476,13 @@ def gpu_bench(args):
     step(mg.SOLVER_MGCG_FP64)
     plain = timed(mg.SOLVER_MGCG_FP64, kp)
     plain_value = job_rate(len(masses) * kp, world, plain["total_ms"] / 1000.0)
+    # the other mixed-precision variant, same step
+    other = [k for k in SOLVER_CODES if SOLVER_CODES[k] != MIXED_SOLVER][0]
+    step(SOLVER_CODES[other])
+    alt = timed(SOLVER_CODES[other], kp)
+    alt_line = {"solver": other, "value": round(job_rate(len(masses) * kp, world, alt["total_ms"] / 1000.0), 3),
+                "unit": UNIT, "steps": kp, "ms_per_step": round(alt["total_ms"] / kp, 3),
+                "per_mass": alt["per_mass"]}
 
     # batched mixed-precision MG-CG: many right-hand sides of the same
     # configuration at the near-critical mass in one Krylov loop
@@ -493,7 +507,7 @@ def gpu_bench(args):
     smoothed = smoothed_leg(args, mg, torch, dev, stream) if args.smoothed_leg else None
 
     # roofline: one profiled step, dominant kernel family by device time
-    prof = step(mg.SOLVER_MGCG_MIXED, profile=True)
+    prof = step(MIXED_SOLVER, profile=True)
     roof = roofline(prof, wl, load_peaks())
 
     # end-to-end through the public API with host buffers
@@ -513,7 +527,9 @@ def gpu_bench(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(res["total_ms"] / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+bf16 (V-cycle) / f64 (outer, residual, coarsest)",
+            "dtype": ("f32+bf16 (V-cycle), f32 (Krylov iteration) / f64 (reliable updates, solution, "
+                      "true residual, coarsest)" if args.solver == "reliable" else
+                      "f32+bf16 (V-cycle) / f64 (outer, residual, coarsest)"),
             "data": "synthetic: seeded quenched U(1) Metropolis configuration, Gaussian source",
             "config": {"workload": args.workload, "lattice": [wl["Lx"], wl["Lt"]], "beta": wl["beta"],
                        "levels": len(wl["blocks"]) + 1, "blocks": wl["blocks"], "Nv": wl["Nv"],
@@ -529,6 +545,8 @@ def gpu_bench(args):
                            "p50_ms": round(ppct(0.5), 3), "p99_ms": round(ppct(0.99), 3),
                            "per_mass": plain["per_mass"]},
             "mixed_vs_plain_fp64": round(value / plain_value, 3),
+            "solver": args.solver,
+            "other_mixed_solver": alt_line,
             "batched": batched,
             "batched_configs": config_legs,
             "smoothed_aggregation": smoothed,
@@ -736,12 +754,12 @@ def batched_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
     with mg.Multigrid(U_d, masses[0], wl["blocks"], wl["Nv"], noise_d,
                       setup_sweeps=wl["setup_sweeps"], max_rhs=nrhs) as s:
         mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
-        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, mg.SOLVER_MGCG_MIXED)     # warm-up
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, MIXED_SOLVER)     # warm-up
         reps = []
         for _ in range(max(1, args.batch_reps)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, mg.SOLVER_MGCG_MIXED)
+            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 200000, MIXED_SOLVER)
             e1.record(stream)
             torch.cuda.synchronize()
             if st != 0 or max(i.true_residual for i in info) > tol:
@@ -790,12 +808,12 @@ def adaptive_leg(args, mg, torch, dev, stream, wl, U_d, noise_d, masses, world):
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
 
     def timed_solve(h, n):
-        mg.mg_solve(h, b_d, x_d, n, tol, 200000, mg.SOLVER_MGCG_MIXED)       # warm-up
+        mg.mg_solve(h, b_d, x_d, n, tol, 200000, MIXED_SOLVER)       # warm-up
         reps = []
         for _ in range(3):
             e0, e1 = ev(), ev()
             e0.record(stream)
-            st, info = mg.mg_solve(h, b_d, x_d, n, tol, 200000, mg.SOLVER_MGCG_MIXED)
+            st, info = mg.mg_solve(h, b_d, x_d, n, tol, 200000, MIXED_SOLVER)
             e1.record(stream)
             torch.cuda.synchronize()
             if st != 0 or max(i.true_residual for i in info) > tol:
@@ -880,12 +898,12 @@ def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
                            if dense else "fp64 cg", "steps": steps, "test_residual": tres}
         out["device_gb"] = round(mg.mg_device_bytes(s.h) / 2 ** 30, 2)
         mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
-        st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)   # warm-up
+        st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)   # warm-up
         lat = []
         for _ in range(max(1, args.config_reps)):
             e0, e1 = ev(), ev()
             e0.record(stream)
-            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)
+            st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)
             e1.record(stream)
             torch.cuda.synchronize()
             if st != 0 or max(i.true_residual for i in info) > tol:
@@ -902,7 +920,7 @@ def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
                     "max_true_residual": max(i.true_residual for i in info)})
         # where the time of one batched solve goes (eager, CUDA events per kernel family)
         mg.mg_profile_enable(s.h, 1)
-        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, mg.SOLVER_MGCG_MIXED)
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)
         out["family_ms_per_solve"] = {FAM_NAMES[f]: round(mg.mg_profile_read(s.h, f)[0], 2)
                                       for f in range(mg.KF_COUNT)}
         mg.mg_profile_enable(s.h, 0)
@@ -1001,7 +1019,7 @@ def smoothed_leg(args, mg, torch, dev, stream):
             r = {"setup_ms": round(setup_ms, 1), "omega": om}
             if cond:
                 r["cond_level2"] = round(cond, 3)
-            for name, solver in (("fp64", mg.SOLVER_MGCG_FP64), ("mixed", mg.SOLVER_MGCG_MIXED)):
+            for name, solver in (("fp64", mg.SOLVER_MGCG_FP64), ("mixed", MIXED_SOLVER)):
                 x = torch.empty_like(bd)
                 mg.mg_solve(s.h, bd, x, 1, 1e-10, 100000, solver)
                 e0, e1 = ev(), ev()
@@ -1043,7 +1061,7 @@ def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, wor
                 if m != masses[0]:
                     s.set_mass(m)
                 mg.mg_apply_D(s.h, cd, b, 1, 1, mg.PREC_F64)
-                x, info = s.solve(b, tol=wl["tol"], maxiter=200000, solver=mg.SOLVER_MGCG_MIXED)
+                x, info = s.solve(b, tol=wl["tol"], maxiter=200000, solver=MIXED_SOLVER)
                 xh.copy_(x, non_blocking=True)
                 torch.cuda.synchronize()
                 if not info[0].true_residual <= wl["tol"]:
@@ -1253,6 +1271,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solver", default="mixed", choices=list(SOLVER_CODES),
+                    help="mixed-precision MG-CG variant of every leg")
     ap.add_argument("--workload", default="L128_b6_massweep", choices=list(W.BENCH_WORKLOADS))
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -1290,6 +1310,8 @@ def main():
                                            "setup"],
                     help="run a small kernel case for an ncu capture and exit")
     args = ap.parse_args()
+    global MIXED_SOLVER
+    MIXED_SOLVER = SOLVER_CODES[args.solver]
     if args.ncu_case:
         ncu_case(args)
     elif args.impl == "reference":

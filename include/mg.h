@@ -73,7 +73,20 @@ typedef enum {
                                V-cycle: FP32 smoother, restriction, prolongation
                                and coarse applies (coarse blocks FP32, or BF16
                                with FP32 accumulation), coarsest solve in FP64 */
-  MG_SOLVER_CG_FP64 = 2     /* plain CG on A, FP64 (the paper's baseline)        */
+  MG_SOLVER_CG_FP64 = 2,    /* plain CG on A, FP64 (the paper's baseline)        */
+  MG_SOLVER_MGCG_RELIABLE = 3 /* flexible CG preconditioned by the same FP32
+                               V-cycle, with the iteration itself in FP32 (A p
+                               by the FP32 stencil, residual, search direction
+                               and solution increment in FP32; inner products
+                               summed in FP64 across thread blocks) and FP64
+                               reliable updates: when the iterated |r| falls
+                               below reliable_delta times its largest value
+                               since the last update, the increment is added
+                               to the FP64 solution and r = b - A x is
+                               recomputed with the FP64 stencil.  The solution
+                               and the final true residual are FP64 as in
+                               MG_SOLVER_MGCG_MIXED; per iteration no FP64
+                               arithmetic runs on fine-lattice vectors        */
 } mg_solver;
 
 typedef struct {
@@ -151,6 +164,9 @@ typedef struct {
                                            extents of at least 3; excludes
                                            refine_levels; remass_quadratic is
                                            ignored (each mass is probed anew) */
+  double reliable_delta;                /* MG_SOLVER_MGCG_RELIABLE: residual
+                                           reduction between FP64 reliable
+                                           updates, in (0, 1); default 0.1   */
 } mg_params;
 
 typedef struct {

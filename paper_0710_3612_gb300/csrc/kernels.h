@@ -66,6 +66,27 @@ cudaError_t dot2_zq_rz(const void* z32, const void* q, const void* r, long long 
                        double* ws, double* zr, cudaStream_t s);
 cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq, double* rz,
                     const int* frozen, long long count, int nrhs, cudaStream_t s);
+// Reliable-update flexible CG: every vector of the iteration in FP32 (per-
+// thread FP32 partial sums, FP64 across blocks); the solution increment x32
+// and the true residual are carried over to FP64 by ru_fold / ru_residual.
+cudaError_t rdot(const void* a, const void* b, long long count, int nrhs, double* ws, double* out,
+                 cudaStream_t s);
+cudaError_t rcg_xr(void* x32, void* r32, const void* p32, const void* q32, const double* rz,
+                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
+                   double* rr, cudaStream_t s);
+cudaError_t rdot2_zq_rz(const void* z32, const void* q32, const void* r32, long long count,
+                        int nrhs, double* ws, double* zr, cudaStream_t s);
+cudaError_t rcg_p(void* p32, const void* z32, const double* zr, const double* pq, double* rz,
+                  const int* frozen, long long count, int nrhs, cudaStream_t s);
+// rmax = max(rmax, rr) over running right-hand sides; *due = some rr < delta2 rmax
+// (then ++*count); with cond_set the IF condition of the graph node follows *due.
+cudaError_t ru_check(const double* rr, double* rmax, const int* ctrl, double delta2, int* due,
+                     int* count, cudaGraphConditionalHandle cond, bool cond_set, cudaStream_t s);
+// x64 += x32 and x32 = 0 over count entries.
+cudaError_t ru_fold(void* x64, void* x32, long long count, cudaStream_t s);
+// r32 = (float) r64, rr = |r64|^2 per rhs, and rmax = rr when rmax is given.
+cudaError_t ru_residual(const void* r64, void* r32, long long count, int nrhs, double* ws,
+                        double* rr, double* rmax, cudaStream_t s);
 // out(FP32) = in(FP64) * (1/sqrt(nrm[rhs].x)) ; in==0 norm -> 0.
 cudaError_t f64_to_f32_scaled(const void* in, void* out, const double* nrm, long long count,
                               int nrhs, cudaStream_t s);

@@ -307,6 +307,208 @@ cudaError_t cg_p_pr(void* p, const void* z32, const double* zr, const double* pq
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Reliable-update flexible CG (FP32 iteration, FP64 solution and true
+// residual).  Per-thread partial sums are kept in FP32 (a thread covers a few
+// entries) and the blocks are combined in FP64 by the deterministic
+// single-pass reduction, so no FP64 arithmetic runs per entry.
+// ---------------------------------------------------------------------------
+
+// ab[rhs] = <a, b> of FP32 vectors.
+__global__ void __launch_bounds__(RT) k_rdot(const float2* __restrict__ a,
+                                             const float2* __restrict__ b, long long count,
+                                             double* ws, double* out) {
+  __shared__ double sh[2 * RT / 32];
+  const long long base = (long long)blockIdx.y * count;
+  float re = 0.f, im = 0.f;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const float2 u = a[base + i], v = b[base + i];
+    re = fmaf(u.x, v.x, fmaf(u.y, v.y, re));
+    im = fmaf(u.x, v.y, fmaf(-u.y, v.x, im));
+  }
+  finish_reduction((double)re, (double)im, ws, out, sh);
+}
+
+cudaError_t rdot(const void* a, const void* b, long long count, int nrhs, double* ws, double* out,
+                 cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  k_rdot<<<dim3(reduce_blocks(count), nrhs), RT, 0, s>>>((const float2*)a, (const float2*)b,
+                                                         count, ws, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; rr = |r|^2 (FP32 vectors, alpha
+// rounded to FP32 once per right-hand side); frozen right-hand sides keep x
+// and r and report their |r|^2.
+__global__ void __launch_bounds__(RT) k_rcg_xr(float2* __restrict__ x, float2* __restrict__ r,
+                                               const float2* __restrict__ p,
+                                               const float2* __restrict__ q, const double* rz,
+                                               const double* pq, const int* frozen,
+                                               long long count, double* ws, double* rr) {
+  __shared__ double sh[2 * RT / 32];
+  const int rhs = blockIdx.y;
+  const bool skip = frozen && frozen[rhs];
+  const double d = pq[2 * rhs];
+  const float alpha = (d != 0.0 && !skip) ? (float)(rz[2 * rhs] / d) : 0.f;
+  float acc = 0.f;
+  const long long base = (long long)rhs * count;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const long long k = base + i;
+    float2 rv = r[k];
+    if (!skip) {
+      const float2 xv = x[k], pv = p[k], qv = q[k];
+      x[k] = make_float2(fmaf(alpha, pv.x, xv.x), fmaf(alpha, pv.y, xv.y));
+      rv = make_float2(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y));
+      r[k] = rv;
+    }
+    acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, acc));
+  }
+  finish_reduction((double)acc, 0.0, ws, rr, sh);
+}
+
+cudaError_t rcg_xr(void* x32, void* r32, const void* p32, const void* q32, const double* rz,
+                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
+                   double* rr, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  k_rcg_xr<<<dim3(reduce_blocks(count), nrhs), RT, 0, s>>>(
+      (float2*)x32, (float2*)r32, (const float2*)p32, (const float2*)q32, rz, pq, frozen, count,
+      ws, rr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// zr[rhs] = {Re<z, q>, Re<r, z>} of FP32 vectors.
+__global__ void __launch_bounds__(RT) k_rdot2_zq_rz(const float2* __restrict__ z,
+                                                    const float2* __restrict__ q,
+                                                    const float2* __restrict__ r, long long count,
+                                                    double* ws, double* zr) {
+  __shared__ double sh[2 * RT / 32];
+  const long long base = (long long)blockIdx.y * count;
+  float a = 0.f, b = 0.f;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const float2 zv = z[base + i], qv = q[base + i], rv = r[base + i];
+    a = fmaf(zv.x, qv.x, fmaf(zv.y, qv.y, a));
+    b = fmaf(rv.x, zv.x, fmaf(rv.y, zv.y, b));
+  }
+  finish_reduction((double)a, (double)b, ws, zr, sh);
+}
+
+cudaError_t rdot2_zq_rz(const void* z32, const void* q32, const void* r32, long long count,
+                        int nrhs, double* ws, double* zr, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  k_rdot2_zq_rz<<<dim3(reduce_blocks(count), nrhs), RT, 0, s>>>(
+      (const float2*)z32, (const float2*)q32, (const float2*)r32, count, ws, zr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// beta = -zr[0] / Re(pq); p = z + beta p (FP32); rz <- {zr[1], 0}.
+__global__ void k_rcg_p(float2* __restrict__ p, const float2* __restrict__ z, const double* zr,
+                        const double* pq, double* rz, const int* frozen, long long count) {
+  const int rhs = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (frozen && frozen[rhs]) return;
+  if (i == 0) {
+    rz[2 * rhs] = zr[2 * rhs + 1];
+    rz[2 * rhs + 1] = 0.0;
+  }
+  if (i >= count) return;
+  const double d = pq[2 * rhs];
+  const float beta = d != 0.0 ? (float)(-zr[2 * rhs] / d) : 0.f;
+  const long long k = (long long)rhs * count + i;
+  const float2 pv = p[k], zv = z[k];
+  p[k] = make_float2(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y));
+}
+
+cudaError_t rcg_p(void* p32, const void* z32, const double* zr, const double* pq, double* rz,
+                  const int* frozen, long long count, int nrhs, cudaStream_t s) {
+  k_rcg_p<<<grid1(count, nrhs), RT, 0, s>>>((float2*)p32, (const float2*)z32, zr, pq, rz, frozen,
+                                             count);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Reliable-update test, one thread: for every running right-hand side,
+// rmax = max(rmax, rr); an update is due when some rr < delta^2 rmax.  Sets
+// *due (and the IF condition of the enclosing graph node when cond_set).
+__global__ void k_ru_check(const double* rr, double* rmax, const int* ctrl, double delta2,
+                           int* due, int* count, cudaGraphConditionalHandle cond, int cond_set) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int nrhs = ctrl[3];
+  const int* frozen = ctrl + 4;
+  int any = 0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (frozen[k]) continue;
+    const double r = rr[2 * k];
+    if (r > rmax[2 * k]) rmax[2 * k] = r;
+    if (r < delta2 * rmax[2 * k]) any = 1;
+  }
+  *due = any;
+  if (any) *count += 1;
+  if (cond_set) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+cudaError_t ru_check(const double* rr, double* rmax, const int* ctrl, double delta2, int* due,
+                     int* count, cudaGraphConditionalHandle cond, bool cond_set, cudaStream_t s) {
+  k_ru_check<<<1, 32, 0, s>>>(rr, rmax, ctrl, delta2, due, count, cond, cond_set ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// x64 += x32, x32 = 0 (the FP32 increment folded into the FP64 solution).
+__global__ void k_ru_fold(double2* __restrict__ x, float2* __restrict__ x32, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float2 v = x32[i];
+  const double2 xv = x[i];
+  x[i] = make_double2(xv.x + (double)v.x, xv.y + (double)v.y);
+  x32[i] = make_float2(0.f, 0.f);
+}
+
+cudaError_t ru_fold(void* x64, void* x32, long long count, cudaStream_t s) {
+  k_ru_fold<<<grid1(count, 1), RT, 0, s>>>((double2*)x64, (float2*)x32, count);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// r32 = (float) r64 and rr = rmax = |r64|^2 (FP64) per right-hand side.
+__global__ void __launch_bounds__(RT) k_ru_residual(const double2* __restrict__ r,
+                                                    float2* __restrict__ r32, long long count,
+                                                    double* ws, double* rr) {
+  __shared__ double sh[2 * RT / 32];
+  const long long base = (long long)blockIdx.y * count;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < count;
+       i += (long long)gridDim.x * RT) {
+    const double2 v = r[base + i];
+    r32[base + i] = make_float2((float)v.x, (float)v.y);
+    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+  }
+  finish_reduction(acc, 0.0, ws, rr, sh);
+}
+
+__global__ void k_copy_slots(const double* src, double* dst, int n2) {
+  const int i = threadIdx.x;
+  if (i < n2) dst[i] = src[i];
+}
+
+cudaError_t ru_residual(const void* r64, void* r32, long long count, int nrhs, double* ws,
+                        double* rr, double* rmax, cudaStream_t s) {
+  if (nrhs > 64) return cudaErrorInvalidValue;
+  k_ru_residual<<<dim3(reduce_blocks(count), nrhs), RT, 0, s>>>((const double2*)r64, (float2*)r32,
+                                                                count, ws, rr);
+  count_launch();
+  if (rmax) {
+    k_copy_slots<<<1, 128, 0, s>>>(rr, rmax, 2 * nrhs);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
 __global__ void k_f64_to_f32_scaled(const double2* __restrict__ in, float2* __restrict__ out,
                                     const double* nrm, long long count) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   const R ca = (R)ep.ca, cu = (R)ep.cu, cw = (R)ep.cw;
   const C* EU = (const C*)ep.U;
   const C* EW = (const C*)ep.W;
-  double dre = 0.0, dim = 0.0;
+  R dre = (R)0, dim = (R)0;     // per-thread partials in the stencil's precision
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int lt = tid / TX + TY * k;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
     if (ep.dot_out) {
       C p0, p1;
       split(sp[(lt + 2) * PW + (lx + 2)], p0, p1);
-      dre += (double)p0.x * y0.x + (double)p0.y * y0.y + (double)p1.x * y1.x + (double)p1.y * y1.y;
-      dim += (double)p0.x * y0.y - (double)p0.y * y0.x + (double)p1.x * y1.y - (double)p1.y * y1.x;
+      dre += p0.x * y0.x + p0.y * y0.y + p1.x * y1.x + p1.y * y1.y;
+      dim += p0.x * y0.y - p0.y * y0.x + p1.x * y1.y - p1.y * y1.x;
     }
     y0 = mk(ca * y0.x, ca * y0.y);
     y1 = mk(ca * y1.x, ca * y1.y);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   }
   if (ep.dot_out) {
     __shared__ double sh[64];
-    finish_reduction_g(dre, dim, ep.dot_ws, ep.dot_out, sh, blockIdx.z,
+    finish_reduction_g((double)dre, (double)dim, ep.dot_ws, ep.dot_out, sh, blockIdx.z,
                        blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
   }
 }

@@ -74,8 +74,10 @@ struct mg_handle {
   cudaStream_t gs = nullptr;
   cudaEvent_t fence[2] = {nullptr, nullptr};
   static constexpr int MAXR = 64;
-  cudaGraphExec_t loop_exec[3 * MAXR] = {};     // per (preconditioner mode, nrhs)
-  long long loop_kernels[3] = {0, 0, 0};      // kernels per loop-body iteration
+  cudaGraphExec_t loop_exec[4 * MAXR] = {};     // per (preconditioner mode, nrhs)
+  long long loop_kernels[4] = {0, 0, 0, 0};   // kernels per loop-body iteration
+  long long ru_kernels = 0;                   // kernels of one reliable update
+  int* ru = nullptr;            // reliable updates: {due, count since the loop started}
   int* dctrl = nullptr;         // loop control (see k_cg_control)
   int* hctrl = nullptr;         // pinned host mirror of dctrl
   int R = 1;                    // right-hand sides per batch (max_rhs)
@@ -112,7 +114,8 @@ constexpr long long MG_DENSE_MAX = 24576;
 
 // scalar slots (each a double2)
 // scalar slots: slot k holds one double2 per right-hand side
-enum { S_RZ = 0, S_RZN, S_PQ, S_RR, S_T0, S_T1, S_BN, S_NR, S_STOP, S_CA, S_CB, S_CPQ, S_COUNT };
+enum { S_RZ = 0, S_RZN, S_PQ, S_RR, S_T0, S_T1, S_BN, S_NR, S_STOP, S_CA, S_CB, S_CPQ, S_RMAX,
+       S_COUNT };
 
 struct Fail {
   mg_status st;
@@ -620,6 +623,10 @@ mg_status validate(const mg_params* p, std::string& msg) {
   }
   if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
   if (p->max_rhs < 1 || p->max_rhs > 64) { msg = "max_rhs must be in [1, 64]"; return MG_ERR_ARG; }
+  if (!(p->reliable_delta > 0.0 && p->reliable_delta < 1.0)) {
+    msg = "reliable_delta must be in (0, 1)";
+    return MG_ERR_ARG;
+  }
   if (p->nlevels > 1 && !p->setup_noise) { msg = "setup_noise is NULL"; return MG_ERR_ARG; }
   if (p->coarsest_dense_max < 0 || p->coarsest_dense_max > MG_DENSE_MAX) {
     msg = "coarsest_dense_max must be in [0, " + std::to_string(MG_DENSE_MAX) + "]";
@@ -710,10 +717,21 @@ void free_all(mg_handle* h) {
 int* frozen_of(mg_handle* h) { return h->dctrl + 4; }
 
 // q = A p and <p, q> per rhs (fused when the kernel's block count allows it).
-void apply_pq(mg_handle* h, int nrhs) {
+// pmode 3: p, q and the product in FP32 (sv32[0], sv32[2]).
+void apply_pq(mg_handle* h, int nrhs, int pmode) {
   const long long n = h->lv[0].count();
   const Level& F = h->lv[0];
   Epilogue ep;
+  if (pmode == 3) {
+    if (wilson_A_ctas(F.Lx, F.Lt, false) <= 608) {
+      ep.dot_ws = h->partials;
+      ep.dot_out = slot(h, S_PQ);
+    }
+    apply_level<float>(h, 0, h->sv32[0], h->sv32[2], nrhs, W_F32, ep);
+    if (!ep.dot_out)
+      ck(h, rdot(h->sv32[0], h->sv32[2], n, nrhs, h->partials, slot(h, S_PQ), h->s), "dot");
+    return;
+  }
   if (wilson_A_ctas(F.Lx, F.Lt, true) <= 608) {
     ep.dot_ws = h->partials;
     ep.dot_out = slot(h, S_PQ);
@@ -726,6 +744,12 @@ void apply_pq(mg_handle* h, int nrhs) {
 // x += alpha p, r -= alpha q, |r|^2 (and the FP32 copy of r for pmode 2).
 void pcg_update(mg_handle* h, void* x, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
+  if (pmode == 3) {           // x32 += alpha p32, r32 -= alpha q32, |r32|^2
+    ck(h, rcg_xr(h->sv32[3], h->sv32[1], h->sv32[0], h->sv32[2], slot(h, S_RZ), slot(h, S_PQ),
+                 frozen_of(h), n, nrhs, h->partials, slot(h, S_RR), h->s),
+       "cg_xr");
+    return;
+  }
   ck(h, cg_xr<double>(x, h->sv64[1], h->sv64[2], h->sv64[3], slot(h, S_RZ), slot(h, S_PQ),
                       frozen_of(h), n, nrhs, h->partials, slot(h, S_RR), h->s,
                       pmode == 2 ? h->sv32[1] : nullptr),
@@ -740,7 +764,13 @@ void pcg_direction(mg_handle* h, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
   void *r = h->sv64[1], *p = h->sv64[2], *q = h->sv64[3], *z = h->sv64[4];
   const size_t sb = 2 * sizeof(double) * nrhs;
-  if (pmode == 2) {
+  if (pmode == 3) {
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
+    ck(h, rdot2_zq_rz(h->sv32[4], h->sv32[2], h->sv32[1], n, nrhs, h->partials, slot(h, S_T0),
+                      h->s), "dot2");
+    ck(h, rcg_p(h->sv32[0], h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h),
+                n, nrhs, h->s), "cg_p");
+  } else if (pmode == 2) {
     vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
     ck(h, dot2_zq_rz(h->sv32[4], q, r, n, nrhs, h->partials, slot(h, S_T0), h->s), "dot2");
     ck(h, cg_p_pr(p, h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h), n,
@@ -760,6 +790,16 @@ void pcg_direction(mg_handle* h, int pmode, int nrhs) {
 void pcg_start(mg_handle* h, int pmode, int nrhs) {
   const long long n = h->lv[0].count();
   void *r = h->sv64[1], *p = h->sv64[2], *z = h->sv64[4];
+  if (pmode == 3) {           // r32 = r, rmax = |r|^2, x32 = 0, p32 = z32 = V r32, rz = <r32, z32>
+    ck(h, ru_residual(r, h->sv32[1], n, nrhs, h->partials, slot(h, S_RR), slot(h, S_RMAX), h->s),
+       "residual");
+    ck(h, cudaMemsetAsync(h->sv32[3], 0, n * nrhs * sizeof(float2), h->s), "memset");
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
+    ck(h, cudaMemcpyAsync(h->sv32[0], h->sv32[4], n * nrhs * sizeof(float2),
+                          cudaMemcpyDeviceToDevice, h->s), "copy");
+    ck(h, rdot(h->sv32[1], h->sv32[4], n, nrhs, h->partials, slot(h, S_RZ), h->s), "dot");
+    return;
+  }
   if (pmode == 2) {
     ck(h, convert_f64_f32(r, h->sv32[1], n * nrhs, h->s), "to f32");
     vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
@@ -773,10 +813,26 @@ void pcg_start(mg_handle* h, int pmode, int nrhs) {
   ck(h, dot<double>(r, p, n, nrhs, h->partials, slot(h, S_RZ), h->s), "dot");
 }
 
+// Reliable update (pmode 3): the FP32 increment joins the FP64 solution and
+// the residual is recomputed from it in FP64: x += x32, x32 = 0,
+// r = b - A x (FP64 stencil), r32 = r, rr = rmax = |r|^2.
+void ru_update(mg_handle* h, const void* b, void* x, int nrhs) {
+  const long long n = h->lv[0].count();
+  void* r = h->sv64[1];
+  ck(h, ru_fold(x, h->sv32[3], n * nrhs, h->s), "fold");
+  apply_level<double>(h, 0, x, r, nrhs, W_F64, ep_lincomb(-1.0, b, 1.0));
+  ck(h, ru_residual(r, h->sv32[1], n, nrhs, h->partials, slot(h, S_RR), slot(h, S_RMAX), h->s),
+     "residual");
+}
+
+double ru_delta2(const mg_handle* h) { return h->p.reliable_delta * h->p.reliable_delta; }
+
 // Captures the CG loop body into the body of a conditional WHILE node: the
 // control kernel at the end of each iteration decides on the device whether
-// to run another iteration, so the whole loop is one graph launch.
-cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode, int nrhs) {
+// to run another iteration, so the whole loop is one graph launch.  pmode 3
+// adds a conditional IF node after the residual update whose body is the
+// reliable update; the test kernel before it sets its condition.
+cudaGraphExec_t build_loop_graph(mg_handle* h, const void* b, void* x, int pmode, int nrhs) {
   const unsigned long long launches0 = launch_count();
   cudaGraph_t g = nullptr;
   ck(h, cudaGraphCreate(&g, 0), "graph create");
@@ -791,13 +847,48 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode, int nrhs) {
   cudaGraphNode_t node;
   ck(h, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np), "conditional node");
   cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle ifc{};
+  if (pmode == 3)
+    ck(h, cudaGraphConditionalHandleCreate(&ifc, body, 0, cudaGraphCondAssignDefault),
+       "conditional handle");
   cudaStream_t saved = h->s;
   h->s = h->gs;
   ck(h, cudaStreamBeginCaptureToGraph(h->gs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal), "begin capture");
+  long long ru_kern = 0;
   try {
-    apply_pq(h, nrhs);
+    apply_pq(h, nrhs, pmode);
     pcg_update(h, x, pmode, nrhs);
+    if (pmode == 3) {
+      ck(h, ru_check(slot(h, S_RR), slot(h, S_RMAX), h->dctrl, ru_delta2(h), h->ru, h->ru + 1, ifc,
+                     true, h->s), "reliable-update test");
+      // close this segment, add the IF node after its last node, capture the
+      // update into the IF body, then continue the loop body after the IF node
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      ck(h, cudaStreamGetCaptureInfo(h->gs, &cs, nullptr, nullptr, &deps, nullptr, &nd),
+         "capture info");
+      std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+      cudaGraph_t seg;
+      ck(h, cudaStreamEndCapture(h->gs, &seg), "end capture");
+      alignas(cudaGraphNodeParams) unsigned char raw_if[sizeof(cudaGraphNodeParams)] = {};
+      cudaGraphNodeParams& ip = *reinterpret_cast<cudaGraphNodeParams*>(raw_if);
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = ifc;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t ifnode;
+      ck(h, cudaGraphAddNode(&ifnode, body, dv.data(), nullptr, dv.size(), &ip), "IF node");
+      ck(h, cudaStreamBeginCaptureToGraph(h->gs, ip.conditional.phGraph_out[0], nullptr, nullptr,
+                                          0, cudaStreamCaptureModeThreadLocal), "begin capture");
+      const unsigned long long u0 = launch_count();
+      ru_update(h, b, x, nrhs);
+      ru_kern = (long long)(launch_count() - u0);
+      ck(h, cudaStreamEndCapture(h->gs, &seg), "end capture");
+      ck(h, cudaStreamBeginCaptureToGraph(h->gs, body, &ifnode, nullptr, 1,
+                                          cudaStreamCaptureModeThreadLocal), "begin capture");
+    }
     pcg_direction(h, pmode, nrhs);
     ck(h, cg_control(slot(h, S_RR), slot(h, S_PQ), slot(h, S_STOP), h->dctrl, cond, h->s), "control");
   } catch (...) {
@@ -815,7 +906,8 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, void* x, int pmode, int nrhs) {
   cudaGraphExec_t exec = nullptr;
   ck(h, cudaGraphInstantiate(&exec, g, 0), "graph instantiate");
   cudaGraphDestroy(g);
-  h->loop_kernels[pmode] = kern;
+  h->loop_kernels[pmode] = kern - ru_kern;
+  if (pmode == 3) h->ru_kernels = ru_kern;
   return exec;
 }
 
@@ -840,6 +932,7 @@ int pcg(mg_handle* h, const void* b, void* x, double tol2, int maxiter, int pmod
   ck(h, cudaMemsetAsync(x, 0, n * nrhs * sizeof(double2), h->s), "memset");
   ck(h, cudaMemcpyAsync(r, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, h->s), "copy");
   ck(h, set_control(h->dctrl, maxiter, nrhs, slot(h, S_BN), tol2, slot(h, S_STOP), h->s), "control init");
+  if (pmode == 3) ck(h, cudaMemsetAsync(h->ru, 0, 2 * sizeof(int), h->s), "memset");
   pcg_start(h, pmode, nrhs);
   if (pmode) {
     h->vcycles++;
@@ -847,16 +940,19 @@ int pcg(mg_handle* h, const void* b, void* x, double tol2, int maxiter, int pmod
   }
   const int per_it_fine = 1 + (pmode ? 4 : 0);
   int it = 0, status = 0;
+  int hru[2] = {0, 0};
   if (h->use_graphs && !h->prof_on) {
-    const int key = pmode + 3 * (nrhs - 1);
+    const int key = pmode + 4 * (nrhs - 1);
     auto& exec = h->loop_exec[key];
-    if (!exec) exec = build_loop_graph(h, x, pmode, nrhs);
+    if (!exec) exec = build_loop_graph(h, b, x, pmode, nrhs);
     ck(h, cudaEventRecord(h->fence[0], h->s), "event");
     ck(h, cudaStreamWaitEvent(h->gs, h->fence[0], 0), "wait");
     ck(h, cudaGraphLaunch(exec, h->gs), "graph launch");
     ck(h, cudaEventRecord(h->fence[1], h->gs), "event");
     ck(h, cudaStreamWaitEvent(h->s, h->fence[1], 0), "wait");
     ck(h, cudaMemcpyAsync(h->hctrl, h->dctrl, (4 + 2 * nrhs) * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+    if (pmode == 3)
+      ck(h, cudaMemcpyAsync(hru, h->ru, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
     sync(h);
     it = h->hctrl[0];
     status = h->hctrl[1];
@@ -873,9 +969,16 @@ int pcg(mg_handle* h, const void* b, void* x, double tol2, int maxiter, int pmod
     sync(h);
     status = 0;
     while (status == 0) {
-      apply_pq(h, nrhs);
+      apply_pq(h, nrhs, pmode);
       h->fine_applies++;
       pcg_update(h, x, pmode, nrhs);
+      if (pmode == 3) {         // the reliable-update test of the graph, decided on the host
+        ck(h, ru_check(slot(h, S_RR), slot(h, S_RMAX), h->dctrl, ru_delta2(h), h->ru, h->ru + 1,
+                       cudaGraphConditionalHandle{}, false, h->s), "reliable-update test");
+        ck(h, cudaMemcpyAsync(hru, h->ru, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->s), "rb");
+        sync(h);
+        if (hru[0]) ru_update(h, b, x, nrhs);
+      }
       ck(h, cudaMemcpyAsync(pq.data(), slot(h, S_PQ), pq.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
       ck(h, cudaMemcpyAsync(rr.data(), slot(h, S_RR), rr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s), "rb");
       sync(h);
@@ -905,6 +1008,11 @@ int pcg(mg_handle* h, const void* b, void* x, double tol2, int maxiter, int pmod
     }
     std::memcpy(h->hctrl, ctrl.data(), ctrl.size() * sizeof(int));
   }
+  if (pmode == 3) {             // updates made in the loop, then the last FP32 increment
+    if (h->use_graphs && !h->prof_on) add_launches((long long)hru[1] * h->ru_kernels);
+    h->fine_applies += hru[1];
+    ck(h, ru_fold(x, h->sv32[3], n * nrhs, h->s), "fold");
+  }
   for (int k = 0; k < nrhs; ++k) iters[k] += h->hctrl[4 + nrhs + k];
   if (status == 2) {
     st = MG_ERR_BREAKDOWN;
@@ -929,8 +1037,10 @@ void true_residuals(mg_handle* h, const void* b, const void* x, void* r, int nrh
 mg_status solve_batch(mg_handle* h, const void* b, void* x, int nrhs, double tol, int maxiter,
                       int solver, mg_solve_info* info) {
   const long long n = h->lv[0].count();
-  const int pmode = solver == MG_SOLVER_MGCG_FP64 ? 1 : solver == MG_SOLVER_MGCG_MIXED ? 2 : 0;
-  if (solver != MG_SOLVER_MGCG_FP64 && solver != MG_SOLVER_CG_FP64 && solver != MG_SOLVER_MGCG_MIXED)
+  const int pmode = solver == MG_SOLVER_MGCG_FP64 ? 1 : solver == MG_SOLVER_MGCG_MIXED ? 2
+                    : solver == MG_SOLVER_MGCG_RELIABLE ? 3 : 0;
+  if (solver != MG_SOLVER_MGCG_FP64 && solver != MG_SOLVER_CG_FP64 && solver != MG_SOLVER_MGCG_MIXED &&
+      solver != MG_SOLVER_MGCG_RELIABLE)
     fail(h, MG_ERR_ARG, "unknown solver");
   h->fine_applies = 0;
   h->vcycles = 0;
@@ -1001,6 +1111,7 @@ void allocate_storage(mg_handle* h) {
   h->scal = dalloc<double>(h, (size_t)S_COUNT * 2 * h->R * sizeof(double));
   h->dflag = dalloc<int>(h, sizeof(int));
   h->dctrl = dalloc<int>(h, (4 + 2 * h->R) * sizeof(int));
+  h->ru = dalloc<int>(h, 2 * sizeof(int));
   int max_nv = h->R;
   for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
   ensure_partials(h, max_nv);
@@ -1574,6 +1685,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->inner_coarsest_refine = 1;
   p->vcycle_coarse_bf16 = 1;
   p->max_rhs = 1;
+  p->reliable_delta = 0.1;
   p->profile = 0;
   p->coarsest_dense_max = 16384;
   p->coarsest_gj_tcgen05 = 0;

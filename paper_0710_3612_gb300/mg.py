@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmg.so")
 MG_MAX_LEVELS = 5
 MG_MAX_REFINE = 16
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
-SOLVER_MGCG_FP64, SOLVER_MGCG_MIXED, SOLVER_CG_FP64 = 0, 1, 2
+SOLVER_MGCG_FP64, SOLVER_MGCG_MIXED, SOLVER_CG_FP64, SOLVER_MGCG_RELIABLE = 0, 1, 2, 3
 STATUS = {0: "MG_OK", 1: "MG_ERR_ARG", 2: "MG_ERR_NOMEM", 3: "MG_ERR_CUDA", 4: "MG_ERR_NOCONV",
           5: "MG_ERR_BREAKDOWN", 6: "MG_ERR_TIMEOUT"}
 
@@ -39,7 +39,7 @@ class MgParams(ctypes.Structure):
                 ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
                 ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("remass_quadratic", ctypes.c_int),
-                ("smooth_omega", ctypes.c_double)]
+                ("smooth_omega", ctypes.c_double), ("reliable_delta", ctypes.c_double)]
 
 
 class MgStencilTuning(ctypes.Structure):

@@ -325,14 +325,14 @@ def test_vcycle_f32_is_close(case, mg):
     assert np.vdot(r, got).real > 0
 
 
-@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "cg_fp64"])
+@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "reliable", "cg_fp64"])
 def test_solve_matches_oracle(case, mg, solver):
     chi = W.gaussian_field((case.Lt, case.Lx, 2), 61)
     b = ow.apply_D(case.U, case.m, chi, dagger=True)
     tol = 1e-10
     x_ora, it_ora, info_ora = okr.mgcg(case.H, b, 1e-12)
     code = {"mgcg_fp64": mg.SOLVER_MGCG_FP64, "mixed": mg.SOLVER_MGCG_MIXED,
-            "cg_fp64": mg.SOLVER_CG_FP64}[solver]
+            "reliable": mg.SOLVER_MGCG_RELIABLE, "cg_fp64": mg.SOLVER_CG_FP64}[solver]
     x, infos = case.solver.solve(dev(b), tol=tol, maxiter=20000, solver=code)
     got = host(x).reshape(b.shape)
     A = case.H.levels[0].op
@@ -360,12 +360,13 @@ def test_zero_rhs_and_repeatability(case, mg):
     assert np.array_equal(x1, host(x2))     # fixed reduction order: identical bits
 
 
-@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "cg_fp64"])
+@pytest.mark.parametrize("solver", ["mgcg_fp64", "mixed", "reliable", "cg_fp64"])
 def test_graph_loop_matches_eager_loop(case, mg, solver):
-    """The Krylov loop runs as one CUDA graph with a device-side WHILE condition;
-    with per-kernel profiling on it runs eagerly.  Both give identical bits."""
+    """The Krylov loop runs as one CUDA graph with a device-side WHILE condition
+    (and, for the reliable-update solver, an IF node for the update); with
+    per-kernel profiling on it runs eagerly.  Both give identical bits."""
     code = {"mgcg_fp64": mg.SOLVER_MGCG_FP64, "mixed": mg.SOLVER_MGCG_MIXED,
-            "cg_fp64": mg.SOLVER_CG_FP64}[solver]
+            "reliable": mg.SOLVER_MGCG_RELIABLE, "cg_fp64": mg.SOLVER_CG_FP64}[solver]
     chi = W.gaussian_field((case.Lt, case.Lx, 2), 81)
     b = dev(ow.apply_D(case.U, case.m, chi, dagger=True))
     xg, ig = case.solver.solve(b, tol=1e-10, maxiter=20000, solver=code)
@@ -428,16 +429,18 @@ def test_batched_tensor_core_vcycle_solve(mg):
         c.solver.close()
 
 
-def test_batched_graph_matches_eager(mg):
+@pytest.mark.parametrize("solver", ["mixed", "reliable"])
+def test_batched_graph_matches_eager(mg, solver):
     c = Case(mg, "2lvl_24x16")
+    code = mg.SOLVER_MGCG_MIXED if solver == "mixed" else mg.SOLVER_MGCG_RELIABLE
     try:
         chis = W.gaussian_field((3, c.Lt, c.Lx, 2), 7)
         b = dev(np.stack([ow.apply_D(c.U, c.m, x, dagger=True) for x in chis]))
         with mg.Multigrid(c.Ug, c.m, c.blocks, c.Nv, c.noise_g, max_rhs=3) as sb:
-            xg, ig = sb.solve(b, tol=1e-10, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+            xg, ig = sb.solve(b, tol=1e-10, maxiter=20000, solver=code)
             xg = host(xg)
             mg.mg_profile_enable(sb.h, True)
-            xe, ie = sb.solve(b, tol=1e-10, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+            xe, ie = sb.solve(b, tol=1e-10, maxiter=20000, solver=code)
             xe = host(xe)
         assert [i.iterations for i in ig] == [i.iterations for i in ie]
         assert np.array_equal(xg, xe)
