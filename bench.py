@@ -898,9 +898,9 @@ def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
                            if dense else "fp64 cg", "steps": steps, "test_residual": tres}
         out["device_gb"] = round(mg.mg_device_bytes(s.h) / 2 ** 30, 2)
         mg.mg_apply_D(s.h, chi_d, b_d, nrhs, 1, mg.PREC_F64)
-        st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)   # warm-up
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 30, MIXED_SOLVER)   # warm-up: graphs built
         lat = []
-        for _ in range(max(1, args.config_reps)):
+        for _ in range(max(1, min(args.config_reps, wl.get("reps", args.config_reps)))):
             e0, e1 = ev(), ev()
             e0.record(stream)
             st, info = mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)
@@ -918,11 +918,12 @@ def batched_config_leg(args, mg, torch, dev, stream, name, theta, world):
                                    "note": f"per batch of {nrhs}, over {len(lat)} batches"},
                     "iterations_max": max(i.iterations for i in info),
                     "max_true_residual": max(i.true_residual for i in info)})
-        # where the time of one batched solve goes (eager, CUDA events per kernel family)
+        # where the time of an iteration goes (50 eager iterations, CUDA events
+        # per kernel family; eager launches add a few microseconds per kernel)
         mg.mg_profile_enable(s.h, 1)
-        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 100000, MIXED_SOLVER)
-        out["family_ms_per_solve"] = {FAM_NAMES[f]: round(mg.mg_profile_read(s.h, f)[0], 2)
-                                      for f in range(mg.KF_COUNT)}
+        mg.mg_solve(s.h, b_d, x_d, nrhs, tol, 50, MIXED_SOLVER)
+        out["family_ms_per_iteration"] = {FAM_NAMES[f]: round(mg.mg_profile_read(s.h, f)[0] / 50, 3)
+                                          for f in range(mg.KF_COUNT)}
         mg.mg_profile_enable(s.h, 0)
         # plain FP64 single-RHS MG-CG on b_0, capped in time
         b0 = b_d[0].contiguous()

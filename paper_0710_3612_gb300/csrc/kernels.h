@@ -254,6 +254,12 @@ cudaError_t hermitian_gemv_f32(const void* P, const void* x, void* y, int N, int
 // products run on tensor cores from an FP32 copy of x held there.
 cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, int nrhs,
                                  void* part, cudaStream_t s, void* xscratch = nullptr);
+// hermitian_gemv_tiles for 1 to 4 vectors given in FP32 (x32, complex64
+// [nrhs][N]); the diagonal tiles also write the exact FP64 copy of x32 into
+// x64 (complex128 [nrhs][N]).
+bool hermitian_gemv_f32in_ok(int nrhs);
+cudaError_t hermitian_gemv_tiles_f32in(const void* P, const void* x32, int N, int ld, int nrhs,
+                                       void* part, void* x64, cudaStream_t s);
 // y32 (optional, complex64 [nrhs][N]) receives an FP32 copy of y.
 cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int nrhs,
                                   bool accumulate, cudaStream_t s, void* y32 = nullptr);

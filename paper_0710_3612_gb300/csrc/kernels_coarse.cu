@@ -1616,6 +1616,7 @@ cudaError_t dense_gemv_f32(const void* B, const void* x, void* y, int N, int ld,
 // buffer and a second kernel sums them per row in a fixed order.
 static constexpr int HT = 64;
 
+
 __global__ void k_pack_hermitian(const float2* __restrict__ M, float2* __restrict__ P, int ld) {
   const int k = blockIdx.x;
   int I = (int)((sqrtf(8.f * k + 1.f) - 1.f) * 0.5f);
@@ -1841,11 +1842,18 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-template <int NR>
+__device__ __forceinline__ float2 ld_x32(const double2* p) {
+  const double2 v = *p;
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ float2 ld_x32(const float2* p) { return *p; }
+
+template <int NR, typename XT = double2>
 __global__ void __launch_bounds__(64) k_hgemv_warp(const float2* __restrict__ P,
-                                                   const double2* __restrict__ x, int N,
+                                                   const XT* __restrict__ x, int N,
                                                    int ntiles, int nrhs,
-                                                   float2* __restrict__ part) {
+                                                   float2* __restrict__ part,
+                                                   double2* __restrict__ x64) {
   __shared__ float4 colsum[NR][32];                      // column partials of warp 1
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k = blockIdx.x;                              // one tile, rows split by warp
@@ -1860,12 +1868,17 @@ __global__ void __launch_bounds__(64) k_hgemv_warp(const float2* __restrict__ P,
     for (int q = 0; q < NR; ++q) {
       xj0[q] = xj1[q] = xi0[q] = xi1[q] = ac0[q] = ac1[q] = make_float2(0.f, 0.f);
       if (q0 + q < nrhs) {
-        const double2* xr = x + (long long)(q0 + q) * N;
+        const XT* xr = x + (long long)(q0 + q) * N;
         const int cj = J * HT + 2 * lane, ri = I * HT + lane;
-        if (cj < N) xj0[q] = make_float2((float)xr[cj].x, (float)xr[cj].y);
-        if (cj + 1 < N) xj1[q] = make_float2((float)xr[cj + 1].x, (float)xr[cj + 1].y);
-        if (ri < N) xi0[q] = make_float2((float)xr[ri].x, (float)xr[ri].y);
-        if (ri + 32 < N) xi1[q] = make_float2((float)xr[ri + 32].x, (float)xr[ri + 32].y);
+        if (cj < N) xj0[q] = ld_x32(xr + cj);
+        if (cj + 1 < N) xj1[q] = ld_x32(xr + cj + 1);
+        if (ri < N) xi0[q] = ld_x32(xr + ri);
+        if (ri + 32 < N) xi1[q] = ld_x32(xr + ri + 32);
+        if (x64 && I == J && w == 0) {         // the FP64 copy of x, once per row block
+          double2* xo = x64 + (long long)(q0 + q) * N;
+          if (ri < N) xo[ri] = make_double2(xi0[q].x, xi0[q].y);
+          if (ri + 32 < N) xo[ri + 32] = make_double2(xi1[q].x, xi1[q].y);
+        }
       }
     }
 #pragma unroll(NR == 1 ? 2 : 1)
@@ -1983,13 +1996,13 @@ cudaError_t hermitian_gemv_tiles(const void* P, const void* x, int N, int ld, in
     const dim3 grid(ntiles);
     if (nrhs == 1)
       k_hgemv_warp<1><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
-                                           (float2*)part);
+                                           (float2*)part, nullptr);
     else if (nrhs == 2)
       k_hgemv_warp<2><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
-                                           (float2*)part);
+                                           (float2*)part, nullptr);
     else
       k_hgemv_warp<4><<<grid, 64, 0, s>>>((const float2*)P, (const double2*)x, N, ntiles, nrhs,
-                                           (float2*)part);
+                                           (float2*)part, nullptr);
   } else {
     k_hgemv_tiles<<<ntiles, 256, 0, s>>>((const float2*)P, (const double2*)x, N, nrhs,
                                          (float2*)part);
@@ -2004,6 +2017,26 @@ cudaError_t hermitian_gemv_reduce(const void* part, void* y, int N, int ld, int 
   const int nt = ld / HT;
   k_hgemv_reduce<<<dim3(nt, nrhs), 256, 0, s>>>((const float2*)part, (double2*)y, N, nt,
                                                 accumulate, (float2*)y32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool hermitian_gemv_f32in_ok(int nrhs) { return nrhs >= 1 && nrhs <= 4; }
+
+cudaError_t hermitian_gemv_tiles_f32in(const void* P, const void* x32, int N, int ld, int nrhs,
+                                       void* part, void* x64, cudaStream_t s) {
+  if (ld % HT || ld < N || !hermitian_gemv_f32in_ok(nrhs)) return cudaErrorInvalidValue;
+  const int nt = ld / HT, ntiles = nt * (nt + 1) / 2;
+  const dim3 grid(ntiles);
+  if (nrhs == 1)
+    k_hgemv_warp<1, float2><<<grid, 64, 0, s>>>((const float2*)P, (const float2*)x32, N, ntiles,
+                                                 nrhs, (float2*)part, (double2*)x64);
+  else if (nrhs == 2)
+    k_hgemv_warp<2, float2><<<grid, 64, 0, s>>>((const float2*)P, (const float2*)x32, N, ntiles,
+                                                 nrhs, (float2*)part, (double2*)x64);
+  else
+    k_hgemv_warp<4, float2><<<grid, 64, 0, s>>>((const float2*)P, (const float2*)x32, N, ntiles,
+                                                 nrhs, (float2*)part, (double2*)x64);
   count_launch();
   return cudaGetLastError();
 }

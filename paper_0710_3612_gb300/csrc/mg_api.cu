@@ -248,19 +248,28 @@ void coarsest_cg(mg_handle* h, const double2* b, double2* x, int iters, int nrhs
 // Dense path: FP32 explicit inverse refined in FP64.  x = B b; then `steps`
 // times: r = b - A_L x (FP64 stencil), x += B r; for nrhs vectors [nrhs][N].
 // x32 (optional): an FP32 copy of the result, written by the last step.
+// b32 (optional): the right-hand side in FP32; b then receives its FP64 copy
+// (for 1 to 4 vectors written by the first GEMV's tile kernel itself).
 void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int nrhs,
-                      void* x32 = nullptr) {
+                      void* x32 = nullptr, const float2* b32 = nullptr) {
   ProfScope prof(h, MG_KF_COARSEST);
+  const long long c = (long long)h->Nc * nrhs;
+  const bool in32 = b32 && h->dense && hermitian_gemv_f32in_ok(nrhs);
+  if (b32 && !in32) ck(h, convert_f32_f64(b32, (void*)b, c, h->s), "coarsest in");
   if (!h->dense) {
     coarsest_cg(h, b, x, h->ccg_iters, nrhs);
-    if (x32) ck(h, convert_f64_f32(x, x32, (long long)h->Nc * nrhs, h->s), "coarsest out");
+    if (x32) ck(h, convert_f64_f32(x, x32, c, h->s), "coarsest out");
     return;
   }
   auto gemv = [&](const double2* in, bool accumulate, void* out32) {
     {
       ProfScope pd(h, MG_KF_DENSE);
-      ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s, h->gemv_x),
-         "coarsest gemv");
+      if (in32 && in == b)
+        ck(h, hermitian_gemv_tiles_f32in(h->Bpk, b32, h->Nc, h->ldc, nrhs, h->gemv_part, (void*)b,
+                                         h->s), "coarsest gemv");
+      else
+        ck(h, hermitian_gemv_tiles(h->Bpk, in, h->Nc, h->ldc, nrhs, h->gemv_part, h->s, h->gemv_x),
+           "coarsest gemv");
     }
     ck(h, hermitian_gemv_reduce(h->gemv_part, x, h->Nc, h->ldc, nrhs, accumulate, h->s, out32),
        "coarsest gemv reduce");
@@ -282,9 +291,7 @@ void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
     if (f64) {
       coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine, nrhs);
     } else {
-      const long long c = (long long)h->Nc * nrhs;
-      ck(h, convert_f32_f64(b, h->cb, c, h->s), "coarsest in");
-      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs, x);
+      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs, x, (const float2*)b);
     }
     return;
   }

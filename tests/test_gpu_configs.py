@@ -10,6 +10,10 @@
   so it checks what holds at any size: D^dagger on sampled right-hand sides
   element by element, and every solution's true FP64 residual, recomputed
   with the oracle's own operator.
+* 1024 x 1024, beta = 10, at the oracle's near-critical mass: 16 right-hand
+  sides in one batched mixed solve on the five-level hierarchy of the
+  benchmark (D^dagger sampled, every true residual recomputed), and at
+  m = -1.9 on the configured four levels.
 """
 import json
 import os
@@ -145,7 +149,47 @@ def test_cfg_128x128_mass_sweep(mg):
                 assert abs(infos[0].iterations - it10) <= 1
 
 
-def test_cfg_1024x1024_four_level_16_rhs(mg):
+@pytest.fixture(scope="module")
+def field_1024():
+    """The 1024 x 1024 beta = 10 field of the oracle's finder (seed 1, 500 sweeps)."""
+    crit = json.load(open(os.path.join(ROOT, "workloads", "critical_masses.json")))["L1024_b10_s1"]
+    th = W.quenched_u1_angles(1024, 1024, crit["beta"], crit["sweeps"], crit["seed"])
+    assert W.mean_plaquette(th) == pytest.approx(crit["plaquette"], abs=1e-12)
+    return W.links_from_angles(th), crit
+
+
+def test_cfg_1024x1024_near_critical_16_rhs(mg, field_1024):
+    """1024 x 1024 at the oracle's near-critical mass (m_crit + 0.002,
+    lambda_min(A) = 3.4e-6): 16 Gaussian right-hand sides b = D^dagger chi in
+    one batched mixed solve, on the five-level hierarchy the benchmark runs
+    (4x4, 2x2, 2x2, 2x2 blocks, Nv = 12; 32 x 32 x 24 = 24576 coarsest
+    unknowns, FP32 inverse with FP64 refinement).  The oracle checks D^dagger
+    per element on two right-hand sides and recomputes every solution's true
+    residual with its own operator."""
+    U, crit = field_1024
+    wl = W.BATCHED_WORKLOADS["L1024_b10_nc16_l5"]
+    L, m, nrhs = 1024, crit["m_nc"], wl["nrhs"]
+    noise = W.setup_noise(L, L, wl["blocks"], wl["Nv"], wl["noise_seed"])
+    chis = np.stack([W.gaussian_field((L, L, 2), 1201 + k) for k in range(nrhs)])
+    with mg.Multigrid(dev(U), m, wl["blocks"], wl["Nv"], dev(noise), setup_sweeps=wl["setup_sweeps"],
+                      max_rhs=nrhs, **wl["params"]) as s:
+        dense, _, res0 = mg.mg_get_coarsest_info(s.h)
+        assert dense and 0 < res0 <= s.params.coarsest_tol
+        b_d = torch.empty((nrhs, L, L, 2), dtype=torch.complex128, device=DEV)
+        mg.mg_apply_D(s.h, dev(chis), b_d, nrhs, 1, mg.PREC_F64)
+        b = host(b_d)
+        for k in (0, nrhs - 1):
+            want = ow.apply_D(U, m, chis[k], dagger=True)
+            assert np.max(np.abs(b[k] - want)) <= 1e-12 * np.max(np.abs(want))
+        x, infos = s.solve(b_d, tol=TOL, maxiter=20000, solver=mg.SOLVER_MGCG_MIXED)
+        got = host(x).reshape(b.shape)
+    for k in range(nrhs):
+        res = np.linalg.norm(b[k] - ow.apply_A(U, m, got[k])) / np.linalg.norm(b[k])
+        assert res <= TOL and infos[k].true_residual <= TOL
+        assert abs(infos[k].true_residual - res) <= 1e-3 * TOL
+
+
+def test_cfg_1024x1024_four_level_16_rhs(mg, field_1024):
     """1024 x 1024, beta = 10 (500 checkerboard sweeps), four levels (4x4, 2x2,
     2x2), Nv = 12, 16 right-hand sides in one batched mixed solve; the
     coarsest level (64 x 64 x 24 = 98304 unknowns) is solved by FP64 CG.  At
@@ -154,7 +198,7 @@ def test_cfg_1024x1024_four_level_16_rhs(mg):
     for a test).  The oracle checks D^dagger per element on two right-hand
     sides and every solution's true residual."""
     L, blocks, Nv, nrhs, m = 1024, [(4, 4), (2, 2), (2, 2)], [12, 12, 12], 16, -1.9
-    U = W.quenched_u1(L, L, 10.0, 500, 1)
+    U = field_1024[0]
     noise = W.setup_noise(L, L, blocks, Nv, 7)
     chis = np.stack([W.gaussian_field((L, L, 2), 1101 + k) for k in range(nrhs)])
     with mg.Multigrid(dev(U), m, blocks, Nv, dev(noise), setup_sweeps=8, max_rhs=nrhs) as s:

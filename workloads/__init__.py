@@ -290,5 +290,6 @@ BATCHED_WORKLOADS = {
     "L1024_b10_nc16_l5": dict(Lx=1024, Lt=1024, beta=10.0, sweeps=500, seed=1,
                               blocks=[(4, 4), (2, 2), (2, 2), (2, 2)], Nv=[12, 12, 12, 12],
                               setup_sweeps=8, nrhs=16, critical_key="L1024_b10_s1", noise_seed=7,
-                              chi_seed=101, tol=1e-10, params={"coarsest_dense_max": 24576}),
+                              chi_seed=101, tol=1e-10, params={"coarsest_dense_max": 24576},
+                              reps=1),
 }
