@@ -1644,6 +1644,75 @@ cudaError_t pack_hermitian(const void* M, void* P, int ld, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One work item of k_hgemv_mma: rows 16 mt0 .. 16 (mt0 + MT) - 1 of the tile
+// product (pass 0: T X_J, pass 1: T^H X_I) for right-hand sides 16 ng .. 16 ng + 15.
+template <int MT>
+__device__ __forceinline__ void hgemv_mma_item(const float2* sT, const float2* sXJ,
+                                               const float2* sXI, int pass, int mt0, int ng,
+                                               int k, int ntiles, int nrhs,
+                                               float2* __restrict__ part) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  const float2* sX = pass ? sXI : sXJ;
+  const float* sTf = (const float*)sT;
+  float acc[MT][4][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][n][e] = 0.f;
+#pragma unroll 2
+  for (int kk = 0; kk < 2 * HT / 8; ++kk) {
+    uint32_t ah[MT][4], al[MT][4], bh[4][2], bl[4][2];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int m = 16 * (mt0 + mt) + g;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int mm = m + 8 * (f & 1), kr = 8 * kk + tq + 4 * (f >> 1);
+        float a;
+        if (pass == 0) {
+          a = sTf[mm * 2 * GJC + kr];                      // T[m][kr/2], (re, im) along K
+        } else {
+          const float2 t = sT[(kr >> 1) * GJC + mm];       // conj(T[kr/2][m])
+          a = (kr & 1) ? -t.y : t.x;
+        }
+        split_tf32(a, ah[mt][f], al[mt][f]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int j = 16 * ng + 4 * n + (g >> 1), d = g & 1;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int kr = 8 * kk + tq + 4 * hh;
+        const float2 v = sX[(kr >> 1) * GJR + j];
+        const float x = (kr & 1) ? (d ? v.x : -v.y) : (d ? v.y : v.x);
+        split_tf32(x, bh[n][hh], bl[n][hh]);
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        mma_tf32(acc[mt][n], al[mt], bh[n]);
+        mma_tf32(acc[mt][n], ah[mt], bl[n]);
+        mma_tf32(acc[mt][n], ah[mt], bh[n]);
+      }
+  }
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int m = 16 * (mt0 + mt) + g + 8 * hh, r = 16 * ng + 4 * n + tq;
+        if (r < nrhs)
+          part[(long long)r * ntiles * 2 * HT + (2LL * k + pass) * HT + m] =
+              make_float2(acc[mt][n][2 * hh], acc[mt][n][2 * hh + 1]);
+      }
+}
+
 // Tensor-core variant for 16..64 right-hand sides: per stored tile T (64 x 64
 // complex) the row products T X_J and, off the diagonal, the column products
 // T^H X_I, as realified GEMMs on mma.sync m16n8k8 TF32 with three products per
@@ -1688,69 +1757,20 @@ __global__ void __launch_bounds__(256) k_hgemv_mma(const float2* __restrict__ P,
     sXI[kk * GJR + r] = xi;
   }
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
-  const int wm = warp >> 2, wn = warp & 3;
-  const bool active = 16 * wn < nrhs;                    // warp-uniform: its 16 RHS exist
-  const float* sTf = (const float*)sT;
-  for (int pass = 0; pass < (I == J ? 1 : 2) && active; ++pass) {  // 0: T X_J, 1: T^H X_I
-    const float2* sX = pass ? sXI : sXJ;
-    float acc[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[mt][n][e] = 0.f;
-#pragma unroll 2
-    for (int kk = 0; kk < 2 * HT / 8; ++kk) {
-      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int m = 32 * wm + 16 * mt + g;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int mm = m + 8 * (f & 1), kr = 8 * kk + tq + 4 * (f >> 1);
-          float a;
-          if (pass == 0) {
-            a = sTf[mm * 2 * GJC + kr];                      // T[m][kr/2], (re, im) along K
-          } else {
-            const float2 t = sT[(kr >> 1) * GJC + mm];       // conj(T[kr/2][m])
-            a = (kr & 1) ? -t.y : t.x;
-          }
-          split_tf32(a, ah[mt][f], al[mt][f]);
-        }
-      }
-#pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        const int j = 16 * wn + 4 * n + (g >> 1), d = g & 1;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int kr = 8 * kk + tq + 4 * hh;
-          const float2 v = sX[(kr >> 1) * GJR + j];
-          const float x = (kr & 1) ? (d ? v.x : -v.y) : (d ? v.y : v.x);
-          split_tf32(x, bh[n][hh], bl[n][hh]);
-        }
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          mma_tf32(acc[mt][n], al[mt], bh[n]);
-          mma_tf32(acc[mt][n], ah[mt], bl[n]);
-          mma_tf32(acc[mt][n], ah[mt], bh[n]);
-        }
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int m = 32 * wm + 16 * mt + g + 8 * hh, r = 16 * wn + 4 * n + tq;
-          if (r < nrhs)
-            part[(long long)r * ntiles * 2 * HT + (2LL * k + pass) * HT + m] =
-                make_float2(acc[mt][n][2 * hh], acc[mt][n][2 * hh + 1]);
-        }
+  // Work items (product, MT 16-row tiles, 16 right-hand sides) are spread
+  // over the 8 warps: one row tile per item up to 32 right-hand sides (so
+  // that 16 right-hand sides still occupy every warp), two beyond (the A
+  // fragments are then shared by two row tiles).
+  const int warp = tid >> 5;
+  const int NG = (nrhs + 15) / 16, npass = I == J ? 1 : 2;
+  if (NG <= 2) {
+    for (int item = warp; item < npass * 4 * NG; item += 8)
+      hgemv_mma_item<1>(sT, sXJ, sXI, item / (4 * NG), (item / NG) % 4, item % NG, k, ntiles, nrhs,
+                        part);
+  } else {
+    for (int item = warp; item < npass * 2 * NG; item += 8)
+      hgemv_mma_item<2>(sT, sXJ, sXI, item / (2 * NG), 2 * ((item / NG) % 2), item % NG, k, ntiles,
+                        nrhs, part);
   }
 }
 
