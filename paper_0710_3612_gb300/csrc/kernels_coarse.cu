@@ -449,13 +449,14 @@ __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restr
   using C = cplx_t<R>;
   extern __shared__ unsigned char smraw[];
   const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, T = b2 * h, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
+  const int TP = T | 1;                                 // odd row stride: conflict-free row reads
   C* sv = (C*)smraw;
-  C* sr = sv + 2 * Nv * T;
+  C* sr = sv + 2 * Nv * TP;
   const int j = blockIdx.x, V = Lx * Lt;
   for (int q = threadIdx.x; q < b2 * 2 * Nv * h; q += blockDim.x) {
     const int o = q / (2 * Nv * h), rest = q % (2 * Nv * h);
     const int ck = rest / h, a = rest % h;                // ck = c Nv + k
-    sv[ck * T + o * h + a] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
+    sv[ck * TP + o * h + a] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
   }
   for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
     const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restr
     C acc = mk((R)0, (R)0);
     if (q < nout) {
       const int sidx = q % nc, rhs = q / nc, c = sidx / Nv;
-      const C* v = sv + sidx * T;
+      const C* v = sv + sidx * TP;
       const C* r = sr + (rhs * 2 + c) * T;
       for (int t = g; t < T; t += G) cfmac(acc, v[t], r[t]);
     }
@@ -490,12 +491,14 @@ __global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restri
   using C = cplx_t<R>;
   extern __shared__ unsigned char smraw[];
   const int b2 = bx * bt, nf = 2 * h, nc = 2 * Nv, Lxc = Lx / bx, Vc = Lxc * (Lt / bt);
-  C* sv = (C*)smraw;                                 // [b2][2][Nv][h]
-  C* se = sv + b2 * 2 * Nv * h;                      // [nrhs][nc]
+  const int RS = (Nv * h) | 1;                       // odd row stride: conflict-free row reads
+  C* sv = (C*)smraw;                                 // [b2][2] rows of [Nv][h], stride RS
+  C* se = sv + b2 * 2 * RS;                          // [nrhs][nc]
   const int j = blockIdx.x, V = Lx * Lt;
   for (int q = threadIdx.x; q < b2 * 2 * Nv * h; q += blockDim.x) {
     const int o = q / (2 * Nv * h), rest = q % (2 * Nv * h);
-    sv[q] = Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
+    sv[(o * 2 + rest / (Nv * h)) * RS + rest % (Nv * h)] =
+        Vst[(long long)block_site(j, o, Lxc, Lx, bx, bt) * 2 * Nv * h + rest];
   }
   for (int q = threadIdx.x; q < nrhs * nc; q += blockDim.x)
     se[q] = coarse[((long long)(q / nc) * Vc + j) * nc + q % nc];
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(256) k_prolong_multi(const cplx_t<R>* __restri
       rhs = q / (nf * b2);
       const int c = comp / h, a = comp % h;
       for (int k = g; k < Nv; k += G)
-        cfma(acc, sv[((o * 2 + c) * Nv + k) * h + a], se[rhs * nc + c * Nv + k]);
+        cfma(acc, sv[(o * 2 + c) * RS + k * h + a], se[rhs * nc + c * Nv + k]);
     }
     acc = group_sum(acc, G);
     if (q < nout && g == 0) {
@@ -531,7 +534,8 @@ static int transfer_group(int outputs, int terms) {
 
 static size_t transfer_multi_smem(int bx, int bt, int h, int Nv, int nrhs, size_t csz, bool restr) {
   const size_t b2 = (size_t)bx * bt;
-  return csz * (b2 * 2 * Nv * h + (restr ? (size_t)nrhs * b2 * 2 * h : (size_t)nrhs * 2 * Nv));
+  const size_t vrows = restr ? (size_t)2 * Nv * ((b2 * h) | 1) : b2 * 2 * (((size_t)Nv * h) | 1);
+  return csz * (vrows + (restr ? (size_t)nrhs * b2 * 2 * h : (size_t)nrhs * 2 * Nv));
 }
 
 template <typename R>
