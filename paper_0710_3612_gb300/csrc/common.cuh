@@ -100,7 +100,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
 // the last block to finish (found with an atomic ticket) adds the partials in
 // a fixed order and resets the ticket.  ws = [64 tickets (as doubles)][partials].
 // rhs selects the output and ticket; blk in [0, G) is this block's slot.
-__device__ __forceinline__ void finish_reduction_g(double re, double im, double* ws, double* out,
+// Returns true in the block that wrote the sum (all its threads).
+__device__ __forceinline__ bool finish_reduction_g(double re, double im, double* ws, double* out,
                                                    double* sh, int rhs, int blk, int G) {
   unsigned* tickets = (unsigned*)ws;
   double* partials = ws + 64;
@@ -113,7 +114,7 @@ __device__ __forceinline__ void finish_reduction_g(double re, double im, double*
     last = atomicAdd(&tickets[rhs], 1u) == (unsigned)(G - 1);
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   re = 0.0;
   im = 0.0;
@@ -128,11 +129,12 @@ __device__ __forceinline__ void finish_reduction_g(double re, double im, double*
     out[2 * rhs + 1] = im;
     tickets[rhs] = 0u;
   }
+  return true;
 }
 
-__device__ __forceinline__ void finish_reduction(double re, double im, double* ws, double* out,
+__device__ __forceinline__ bool finish_reduction(double re, double im, double* ws, double* out,
                                                  double* sh) {
-  finish_reduction_g(re, im, ws, out, sh, blockIdx.y, blockIdx.x, gridDim.x);
+  return finish_reduction_g(re, im, ws, out, sh, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // Block map of the geometric blocking S_j: coarse site and in-block offset.

@@ -40,13 +40,23 @@ cudaError_t axpby(double a, const void* x, double b, void* y, long long count, i
 template <typename R>
 cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long count, int nrhs,
                            cudaStream_t s);
+// Loop control of k_cg_control run by cg_xr itself (graph loops): the block
+// that completes the last right-hand side's |r|^2 takes the decisions; tick is
+// one unsigned, zero between launches.
+struct CgControl {
+  int* ctrl = nullptr;
+  const double* stop = nullptr;
+  unsigned* tick = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+};
 // CG step on per-RHS device scalars (double2 arrays, real part used):
 //   alpha = rz / pq (0 when frozen[rhs]); x += alpha p; r -= alpha q;
-//   rr[rhs] = |r|^2 (one launch, reduction workspace ws).
+//   rr[rhs] = |r|^2 (one launch, reduction workspace ws); cc: see CgControl.
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
-                  double* rr, cudaStream_t s, void* r32 = nullptr);
+                  double* rr, cudaStream_t s, void* r32 = nullptr,
+                  const CgControl* cc = nullptr);
 //   beta = rz_new / rz_old; p = z + beta p; then rz_old <- rz_new is done by the caller.
 template <typename R>
 cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_old,
@@ -114,7 +124,11 @@ struct Epilogue {
   const void* U = nullptr;
   const void* W = nullptr;
   double* dot_ws = nullptr;
-  double* dot_out = nullptr;
+  double* dot_out = nullptr;     // <in, out> per rhs (fine stencil; needs <= 608 blocks)
+  // with dot_out, instead of <in, out>: {Re<out, zq_q>, Re<zq_r, out>} per rhs,
+  // zq_q and zq_r complex128 vectors shaped like out (the flexible-CG pair)
+  const void* zq_q = nullptr;
+  const void* zq_r = nullptr;
 };
 
 // ---- fine Wilson operator ------------------------------------------------

@@ -113,13 +113,16 @@ cudaError_t scale_inv_sqrt(const void* x, void* y, const double* nrm, long long 
   return cudaGetLastError();
 }
 
+__device__ void cg_control_step(const double* rr, const double* pq, const double* stop, int* ctrl,
+                                cudaGraphConditionalHandle cond);
+
 template <typename R>
 __global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<R>* __restrict__ r,
                                               const cplx_t<R>* __restrict__ p,
                                               const cplx_t<R>* __restrict__ q, const double* rz,
                                               const double* pq, const int* frozen,
                                               long long count, double* ws, double* rr,
-                                              float2* __restrict__ r32) {
+                                              float2* __restrict__ r32, CgControl cc) {
   __shared__ double sh[2 * RT / 32];
   const int rhs = blockIdx.y;
   const bool skip = frozen && frozen[rhs];
@@ -141,18 +144,27 @@ __global__ void __launch_bounds__(RT) k_cg_xr(cplx_t<R>* __restrict__ x, cplx_t<
     acc = fma((double)rv.x, (double)rv.x, acc);
     acc = fma((double)rv.y, (double)rv.y, acc);
   }
-  finish_reduction(acc, 0.0, ws, rr, sh);
+  const bool done = finish_reduction(acc, 0.0, ws, rr, sh);
+  // loop control in the block that completes the last right-hand side's sum
+  if (cc.ctrl && done && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(cc.tick, 1u) == gridDim.y - 1) {
+      __threadfence();
+      *cc.tick = 0u;
+      cg_control_step(rr, pq, cc.stop, cc.ctrl, cc.cond);
+    }
+  }
 }
 
 template <typename R>
 cudaError_t cg_xr(void* x, void* r, const void* p, const void* q, const double* rz,
                   const double* pq, const int* frozen, long long count, int nrhs, double* ws,
-                  double* rr, cudaStream_t s, void* r32) {
+                  double* rr, cudaStream_t s, void* r32, const CgControl* cc) {
   if (nrhs > 64) return cudaErrorInvalidValue;
   int g = reduce_blocks(count);
   k_cg_xr<R><<<dim3(g, nrhs), RT, 0, s>>>((cplx_t<R>*)x, (cplx_t<R>*)r, (const cplx_t<R>*)p,
                                           (const cplx_t<R>*)q, rz, pq, frozen, count, ws, rr,
-                                          (float2*)r32);
+                                          (float2*)r32, cc ? *cc : CgControl{});
   count_launch();
   return cudaGetLastError();
 }
@@ -185,9 +197,8 @@ cudaError_t cg_p(void* p, const void* z, const double* rz_new, const double* rz_
 // it_done[rhs] (ctrl + 4 + nrhs) records its iteration count.  status: 0
 // running, 1 all converged, 2 a breakdown, 3 limit reached.  Sets the WHILE
 // condition of the enclosing graph node.
-__global__ void k_cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
-                             cudaGraphConditionalHandle cond) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void cg_control_step(const double* rr, const double* pq, const double* stop, int* ctrl,
+                                cudaGraphConditionalHandle cond) {
   const int it = ctrl[0] + 1;
   const int nrhs = ctrl[3];
   int* frozen = ctrl + 4;
@@ -196,7 +207,7 @@ __global__ void k_cg_control(const double* rr, const double* pq, const double* s
   int running = 0, broken = 0;
   for (int k = 0; k < nrhs; ++k) {
     if (frozen[k]) continue;
-    const double r = rr[2 * k], d = pq[2 * k];
+    const double r = __ldcg(rr + 2 * k), d = __ldcg(pq + 2 * k);
     if (!(d > 0.0) || !(r == r)) {
       frozen[k] = 2;
       it_done[k] = it;
@@ -216,6 +227,12 @@ __global__ void k_cg_control(const double* rr, const double* pq, const double* s
       if (!frozen[k]) it_done[k] = it;
   ctrl[1] = status;
   cudaGraphSetConditional(cond, status == 0 ? 1u : 0u);
+}
+
+__global__ void k_cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
+                             cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cg_control_step(rr, pq, stop, ctrl, cond);
 }
 
 cudaError_t cg_control(const double* rr, const double* pq, const double* stop, int* ctrl,
@@ -610,7 +627,7 @@ cudaError_t sub_from(const void* b, void* r, long long count, cudaStream_t s) {
                                          cudaStream_t);                                      \
   template cudaError_t cg_xr<R>(void*, void*, const void*, const void*, const double*,       \
                                 const double*, const int*, long long, int, double*, double*, \
-                                cudaStream_t, void*);                                        \
+                                cudaStream_t, void*, const CgControl*);                      \
   template cudaError_t cg_p<R>(void*, const void*, const double*, const double*, const int*, \
                                long long, int, cudaStream_t);                                \
   template cudaError_t sub_from<R>(const void*, void*, long long, cudaStream_t);             \

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
   const C* EU = (const C*)ep.U;
   const C* EW = (const C*)ep.W;
   R dre = (R)0, dim = (R)0;     // per-thread partials in the stencil's precision
+  double zq = 0.0, rz = 0.0;     // the flexible-CG pair (FP64 operands)
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int lt = tid / TX + TY * k;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
     C y0 = mk(diag * f0.x - (R)0.5 * a0.x, diag * f0.y - (R)0.5 * a0.y);
     C y1 = mk(diag * f1.x - (R)0.5 * a1.x, diag * f1.y - (R)0.5 * a1.y);
     const long long g = off + 2LL * (gx + Lx * gt);
-    if (ep.dot_out) {
+    if (ep.dot_out && !ep.zq_q) {
       C p0, p1;
       split(sp[(lt + 2) * PW + (lx + 2)], p0, p1);
       dre += p0.x * y0.x + p0.y * y0.y + p1.x * y1.x + p1.y * y1.y;
@@ -208,10 +209,22 @@ __global__ void __launch_bounds__(TX* TY) k_wilson_A(const cplx_t<R>* __restrict
       y0 = mk(y0.x + cw * w0.x, y0.y + cw * w0.y);
       y1 = mk(y1.x + cw * w1.x, y1.y + cw * w1.y);
     }
+    if (ep.zq_q) {
+      const double2* Q = (const double2*)ep.zq_q + g;
+      const double2* Rv = (const double2*)ep.zq_r + g;
+      const double2 q0 = Q[0], q1 = Q[1], r0 = Rv[0], r1 = Rv[1];
+      zq += (double)y0.x * q0.x + (double)y0.y * q0.y + (double)y1.x * q1.x + (double)y1.y * q1.y;
+      rz += r0.x * (double)y0.x + r0.y * (double)y0.y + r1.x * (double)y1.x + r1.y * (double)y1.y;
+    }
     st_spinor(out + g, join(y0, y1));
   }
   if (ep.dot_out) {
     __shared__ double sh[64];
+    if (ep.zq_q) {
+      finish_reduction_g(zq, rz, ep.dot_ws, ep.dot_out, sh, blockIdx.z,
+                         blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+      return;
+    }
     finish_reduction_g((double)dre, (double)dim, ep.dot_ws, ep.dot_out, sh, blockIdx.z,
                        blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
   }

@@ -78,6 +78,7 @@ struct mg_handle {
   long long loop_kernels[4] = {0, 0, 0, 0};   // kernels per loop-body iteration
   long long ru_kernels = 0;                   // kernels of one reliable update
   int* ru = nullptr;            // reliable updates: {due, count since the loop started}
+  unsigned* cg_tick = nullptr;  // ticket of the loop control fused into cg_xr
   int* dctrl = nullptr;         // loop control (see k_cg_control)
   int* hctrl = nullptr;         // pinned host mirror of dctrl
   int R = 1;                    // right-hand sides per batch (max_rhs)
@@ -283,8 +284,11 @@ void coarsest_solve64(mg_handle* h, const double2* b, double2* x, int steps, int
 
 // ----- V-cycle (Sec. 2, five steps), recursive ------------------------------
 // Reads b, writes x (both level-l vectors of precision R, nrhs of them).
+// tail (optional, level 0): reductions fused into the cycle's last stencil
+// application (the flexible-CG pair of Epilogue::zq_q / zq_r).
 template <typename R>
-void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
+void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1,
+            const Epilogue* tail = nullptr) {
   const bool f64 = sizeof(R) == 8;
   const int weights = f64 ? W_F64 : (h->p.vcycle_coarse_bf16 ? W_BF16 : W_F32);
   if (l == h->L - 1) {
@@ -326,7 +330,14 @@ void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1) {
     apply_level<R>(h, 0, w[3], x, nrhs, weights, ep_lincomb(-h->smooth, w[3], 1.0, x, 1.0));
   // 5. x = x + R (b - A x):  r = b - A x, then x = x + c0 r + c1 A r
   apply_level<R>(h, l, x, r, nrhs, weights, ep_lincomb(-1.0, b, 1.0));
-  apply_level<R>(h, l, r, x, nrhs, weights, ep_lincomb(L.c1, r, L.c0, x, 1.0));
+  Epilogue e5 = ep_lincomb(L.c1, r, L.c0, x, 1.0);
+  if (tail && l == 0) {
+    e5.dot_ws = tail->dot_ws;
+    e5.dot_out = tail->dot_out;
+    e5.zq_q = tail->zq_q;
+    e5.zq_r = tail->zq_r;
+  }
+  apply_level<R>(h, l, r, x, nrhs, weights, e5);
 }
 
 // ----- setup pieces ---------------------------------------------------------
@@ -748,8 +759,9 @@ void apply_pq(mg_handle* h, int nrhs, int pmode) {
     ck(h, dot<double>(h->sv64[2], h->sv64[3], n, nrhs, h->partials, slot(h, S_PQ), h->s), "dot");
 }
 
-// x += alpha p, r -= alpha q, |r|^2 (and the FP32 copy of r for pmode 2).
-void pcg_update(mg_handle* h, void* x, int pmode, int nrhs) {
+// x += alpha p, r -= alpha q, |r|^2 (and the FP32 copy of r for pmode 2);
+// cc: the loop control taken in the same kernel (graph loops, pmode 0-2).
+void pcg_update(mg_handle* h, void* x, int pmode, int nrhs, const CgControl* cc = nullptr) {
   const long long n = h->lv[0].count();
   if (pmode == 3) {           // x32 += alpha p32, r32 -= alpha q32, |r32|^2
     ck(h, rcg_xr(h->sv32[3], h->sv32[1], h->sv32[0], h->sv32[2], slot(h, S_RZ), slot(h, S_PQ),
@@ -759,7 +771,7 @@ void pcg_update(mg_handle* h, void* x, int pmode, int nrhs) {
   }
   ck(h, cg_xr<double>(x, h->sv64[1], h->sv64[2], h->sv64[3], slot(h, S_RZ), slot(h, S_PQ),
                       frozen_of(h), n, nrhs, h->partials, slot(h, S_RR), h->s,
-                      pmode == 2 ? h->sv32[1] : nullptr),
+                      pmode == 2 ? h->sv32[1] : nullptr, cc),
      "cg_xr");
 }
 
@@ -778,8 +790,17 @@ void pcg_direction(mg_handle* h, int pmode, int nrhs) {
     ck(h, rcg_p(h->sv32[0], h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h),
                 n, nrhs, h->s), "cg_p");
   } else if (pmode == 2) {
-    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs);
-    ck(h, dot2_zq_rz(h->sv32[4], q, r, n, nrhs, h->partials, slot(h, S_T0), h->s), "dot2");
+    // {Re<z, q>, Re<r, z>} in the V-cycle's last fine stencil when its block count allows
+    const Level& F = h->lv[0];
+    Epilogue tail;
+    tail.dot_ws = h->partials;
+    tail.dot_out = slot(h, S_T0);
+    tail.zq_q = q;
+    tail.zq_r = r;
+    const bool fused = wilson_A_ctas(F.Lx, F.Lt, false) <= 608;
+    vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs, fused ? &tail : nullptr);
+    if (!fused)
+      ck(h, dot2_zq_rz(h->sv32[4], q, r, n, nrhs, h->partials, slot(h, S_T0), h->s), "dot2");
     ck(h, cg_p_pr(p, h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h), n,
                   nrhs, h->s), "cg_p");
   } else if (pmode == 1) {
@@ -865,7 +886,12 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, const void* b, void* x, int pmode
   long long ru_kern = 0;
   try {
     apply_pq(h, nrhs, pmode);
-    pcg_update(h, x, pmode, nrhs);
+    CgControl cc;
+    cc.ctrl = h->dctrl;
+    cc.stop = slot(h, S_STOP);
+    cc.tick = h->cg_tick;
+    cc.cond = cond;
+    pcg_update(h, x, pmode, nrhs, pmode == 3 ? nullptr : &cc);
     if (pmode == 3) {
       ck(h, ru_check(slot(h, S_RR), slot(h, S_RMAX), h->dctrl, ru_delta2(h), h->ru, h->ru + 1, ifc,
                      true, h->s), "reliable-update test");
@@ -897,7 +923,9 @@ cudaGraphExec_t build_loop_graph(mg_handle* h, const void* b, void* x, int pmode
                                           cudaStreamCaptureModeThreadLocal), "begin capture");
     }
     pcg_direction(h, pmode, nrhs);
-    ck(h, cg_control(slot(h, S_RR), slot(h, S_PQ), slot(h, S_STOP), h->dctrl, cond, h->s), "control");
+    if (pmode == 3)
+      ck(h, cg_control(slot(h, S_RR), slot(h, S_PQ), slot(h, S_STOP), h->dctrl, cond, h->s),
+         "control");
   } catch (...) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(h->gs, &dummy);
@@ -1119,6 +1147,8 @@ void allocate_storage(mg_handle* h) {
   h->dflag = dalloc<int>(h, sizeof(int));
   h->dctrl = dalloc<int>(h, (4 + 2 * h->R) * sizeof(int));
   h->ru = dalloc<int>(h, 2 * sizeof(int));
+  h->cg_tick = dalloc<unsigned>(h, sizeof(unsigned));
+  if (!h->dry) ck(h, cudaMemsetAsync(h->cg_tick, 0, sizeof(unsigned), h->s), "memset ticket");
   int max_nv = h->R;
   for (int l = 0; l + 1 < h->L; ++l) max_nv = std::max(max_nv, h->lv[l].Nv);
   ensure_partials(h, max_nv);
