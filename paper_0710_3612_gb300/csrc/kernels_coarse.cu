@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restr
   for (int q = threadIdx.x; q < nrhs * b2 * nf; q += blockDim.x) {
     const int comp = q % nf, o = (q / nf) % b2, rhs = q / (nf * b2);
     const int c = comp / h, a = comp % h;
-    sr[(rhs * 2 + c) * T + o * h + a] =
+    sr[(rhs * 2 + c) * TP + o * h + a] =
         fine[((long long)rhs * V + block_site(j, o, Lxc, Lx, bx, bt)) * nf + comp];
   }
   __syncthreads();
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_restrict_multi(const cplx_t<R>* __restr
     if (q < nout) {
       const int sidx = q % nc, rhs = q / nc, c = sidx / Nv;
       const C* v = sv + sidx * TP;
-      const C* r = sr + (rhs * 2 + c) * T;
+      const C* r = sr + (rhs * 2 + c) * TP;
       for (int t = g; t < T; t += G) cfmac(acc, v[t], r[t]);
     }
     acc = group_sum(acc, G);
@@ -535,7 +535,7 @@ static int transfer_group(int outputs, int terms) {
 static size_t transfer_multi_smem(int bx, int bt, int h, int Nv, int nrhs, size_t csz, bool restr) {
   const size_t b2 = (size_t)bx * bt;
   const size_t vrows = restr ? (size_t)2 * Nv * ((b2 * h) | 1) : b2 * 2 * (((size_t)Nv * h) | 1);
-  return csz * (vrows + (restr ? (size_t)nrhs * b2 * 2 * h : (size_t)nrhs * 2 * Nv));
+  return csz * (vrows + (restr ? (size_t)nrhs * 2 * ((b2 * h) | 1) : (size_t)nrhs * 2 * Nv));
 }
 
 template <typename R>
