@@ -1295,7 +1295,7 @@ def main():
                     help="1: also time the oracle sample on every host core at once")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests per point of the serving leg (0 skips the serving leg)")
-    ap.add_argument("--serve-loads", default="0.5",
+    ap.add_argument("--serve-loads", default="0.3",
                     help="Poisson points of the serving leg, as fractions of the measured capacity")
     ap.add_argument("--serving-only", action="store_true",
                     help="run the serving leg alone and print it as the JSON line")

@@ -790,14 +790,16 @@ void pcg_direction(mg_handle* h, int pmode, int nrhs) {
     ck(h, rcg_p(h->sv32[0], h->sv32[4], slot(h, S_T0), slot(h, S_PQ), slot(h, S_RZ), frozen_of(h),
                 n, nrhs, h->s), "cg_p");
   } else if (pmode == 2) {
-    // {Re<z, q>, Re<r, z>} in the V-cycle's last fine stencil when its block count allows
+    // {Re<z, q>, Re<r, z>} in the V-cycle's last fine stencil for batches (when its
+    // block count allows); one right-hand side keeps the separate reduction, which
+    // measured as fast and leaves the stencil without FP64 operands
     const Level& F = h->lv[0];
     Epilogue tail;
     tail.dot_ws = h->partials;
     tail.dot_out = slot(h, S_T0);
     tail.zq_q = q;
     tail.zq_r = r;
-    const bool fused = wilson_A_ctas(F.Lx, F.Lt, false) <= 608;
+    const bool fused = nrhs > 1 && wilson_A_ctas(F.Lx, F.Lt, false) <= 608;
     vcycle<float>(h, 0, h->sv32[1], h->sv32[4], nrhs, fused ? &tail : nullptr);
     if (!fused)
       ck(h, dot2_zq_rz(h->sv32[4], q, r, n, nrhs, h->partials, slot(h, S_T0), h->s), "dot2");
