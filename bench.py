@@ -382,7 +382,7 @@ def gpu_bench(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
     tol = wl["tol"]
     params = mg.make_params(wl["Lx"], wl["Lt"], wl["blocks"], wl["Nv"], noise_d,
-                            setup_sweeps=wl["setup_sweeps"])
+                            setup_sweeps=wl["setup_sweeps"], coarsest_reuse=args.coarsest_reuse)
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
 
     def step(solver, record=None, profile=False, phases=None):
@@ -536,6 +536,7 @@ def gpu_bench(args):
                        "masses": [round(m, 12) for m in masses], "m_crit": crit["m_crit"],
                        "tol": wl["tol"], "rhs_per_solve": 1, "solves_per_step": len(masses),
                        "step": "setup at m_nc + 4 x (re-Galerkin/coarsest inverse, b = D^dag chi, solve)",
+                       "coarsest_reuse": args.coarsest_reuse,
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "latency_ms": {"p50": round(pct(0.5), 3), "p99": round(pct(0.99), 3),
@@ -1056,7 +1057,7 @@ def e2e_leg(args, mg, torch, dev, stream, wl, U, noise, chi, masses, params, wor
         nd = nh.to(dev, non_blocking=True)
         cd = ch.to(dev, non_blocking=True)
         with mg.Multigrid(Ud, masses[0], wl["blocks"], wl["Nv"], nd,
-                          setup_sweeps=wl["setup_sweeps"]) as s:
+                          setup_sweeps=wl["setup_sweeps"], coarsest_reuse=args.coarsest_reuse) as s:
             b = torch.empty_like(cd)
             for m in masses:
                 if m != masses[0]:
@@ -1272,6 +1273,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--coarsest-reuse", type=int, default=12,
+                    help="mg_params.coarsest_reuse of the mass-sweep step (0: invert at every mass)")
     ap.add_argument("--solver", default="mixed", choices=list(SOLVER_CODES),
                     help="mixed-precision MG-CG variant of every leg")
     ap.add_argument("--workload", default="L128_b6_massweep", choices=list(W.BENCH_WORKLOADS))

@@ -167,6 +167,19 @@ typedef struct {
   double reliable_delta;                /* MG_SOLVER_MGCG_RELIABLE: residual
                                            reduction between FP64 reliable
                                            updates, in (0, 1); default 0.1   */
+  int coarsest_reuse;                   /* mg_set_mass with a dense coarsest
+                                           level: 0 (default) inverts the new
+                                           coarsest operator; k > 0 first tries
+                                           the FP32 inverse of the previous
+                                           mass inside the FP64 refinement and
+                                           keeps it when both test vectors reach
+                                           coarsest_tol within
+                                           min(k, coarsest_refine_max - 1)
+                                           steps (the coarsest solve stays exact
+                                           to coarsest_tol; the refinement count
+                                           grows instead of a new inversion);
+                                           the FP32 V-cycle then refines until
+                                           the test vectors reach 1e-6 */
 } mg_params;
 
 typedef struct {
@@ -401,6 +414,11 @@ mg_status mg_coarsest_solve(mg_handle* h, const void* in, void* out);
  * or within 5000 CG iterations.  Any output pointer may be NULL; MG_ERR_ARG
  * when h has one level. */
 mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, double* test_residual);
+
+/* Dense coarsest level: *inner = FP64 refinement steps of the FP32 V-cycle's
+ * coarsest solve, *reuses = re-masses of this handle that kept the previous
+ * FP32 inverse (mg_params.coarsest_reuse).  Any output pointer may be NULL. */
+mg_status mg_get_coarsest_reuse(const mg_handle* h, int* inner, int* reuses);
 
 /* Smoothed aggregation of the first coarsening (mg_params.smooth_omega):
  * *omega the damping in use (0 when off) and *cond the condition number of

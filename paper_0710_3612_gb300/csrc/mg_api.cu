@@ -61,6 +61,9 @@ struct mg_handle {
   float2* Bpk = nullptr;        // packed Hermitian tiles of the inverse
   float2* gemv_part = nullptr;  // partial products of the packed GEMV
   int n_refine = 0;
+  int n_inner = 1;              // refinement steps of the FP32 V-cycle's coarsest solve
+  bool inverse_ok = false;      // Binv / Bpk hold an FP32 inverse (of some mass)
+  int inverse_reuses = 0;       // re-masses that kept the previous inverse
   double2 *cb = nullptr, *cx = nullptr, *cr = nullptr;   // coarsest FP64 scratch
   bool dense = true;            // dense inverse (else CG on the coarsest stencil)
   int ccg_iters = 0;            // CG iterations of one coarsest solve (fixed at set-up)
@@ -295,7 +298,7 @@ void vcycle(mg_handle* h, int l, const void* b, void* x, int nrhs = 1,
     if (f64) {
       coarsest_solve64(h, (const double2*)b, (double2*)x, h->n_refine, nrhs);
     } else {
-      coarsest_solve64(h, h->cb, h->cx, h->p.inner_coarsest_refine, nrhs, x, (const float2*)b);
+      coarsest_solve64(h, h->cb, h->cx, h->n_inner, nrhs, x, (const float2*)b);
     }
     return;
   }
@@ -493,12 +496,65 @@ void build_coarsest_cg(mg_handle* h) {
   h->ccg_iters = std::min(COARSEST_CG_MAX, worst + worst / 4 + 4);
 }
 
-void build_coarsest(mg_handle* h) {
+// Refinement with the FP32 inverse in hand on the current coarsest operator,
+// one step at a time: x = B b, then x += B (b - A x) until every test vector
+// reaches coarsest_tol within kmax steps.  On success *steps and *inner are the
+// largest step counts that reached coarsest_tol and 1e-6.
+bool refinement_test(mg_handle* h, int kmax, int* steps, int* inner, double* worst_rel) {
+  *steps = 0;
+  *inner = 0;
+  *worst_rel = 0.0;
+  for (int tv = 0; tv < COARSEST_TEST_VECTORS; ++tv) {
+    std::vector<double2> tvec = coarsest_test_vector(h->Nc, (uint64_t)tv + 1);
+    ck(h, cudaMemcpyAsync(h->cb, tvec.data(), sizeof(double2) * h->Nc, cudaMemcpyHostToDevice,
+                          h->s),
+       "upload");
+    ck(h, norm2<double>(h->cb, h->Nc, 1, h->partials, slot(h, S_T1), h->s), "norm");
+    const double bn = read_scalar(h, S_T1);
+    ck(h, hermitian_gemv_tiles(h->Bpk, h->cb, h->Nc, h->ldc, 1, h->gemv_part, h->s), "gemv");
+    ck(h, hermitian_gemv_reduce(h->gemv_part, h->cx, h->Nc, h->ldc, 1, false, h->s), "gemv");
+    int s = 0, s6 = -1;
+    double rel = 0.0;
+    for (;; ++s) {
+      apply_level<double>(h, h->L - 1, h->cx, h->cr, 1, W_F64, ep_lincomb(-1.0, h->cb, 1.0));
+      ck(h, norm2<double>(h->cr, h->Nc, 1, h->partials, slot(h, S_T0), h->s), "norm");
+      const double rr = read_scalar(h, S_T0);
+      if (!(rr == rr)) return false;
+      rel = std::sqrt(rr / bn);
+      if (s6 < 0 && rel <= 1e-6) s6 = s;
+      if (rel <= h->p.coarsest_tol) break;
+      if (s == kmax) return false;
+      ck(h, hermitian_gemv_tiles(h->Bpk, h->cr, h->Nc, h->ldc, 1, h->gemv_part, h->s), "gemv");
+      ck(h, hermitian_gemv_reduce(h->gemv_part, h->cx, h->Nc, h->ldc, 1, true, h->s), "gemv");
+    }
+    *steps = std::max(*steps, s);
+    *inner = std::max(*inner, s6);
+    *worst_rel = std::max(*worst_rel, rel);
+  }
+  return true;
+}
+
+// remass: called for a new mass of an existing hierarchy (mg_set_mass).
+void build_coarsest(mg_handle* h, bool remass = false) {
   h->coarsest_test_res = 0.0;
   if (!h->dense) {
     build_coarsest_cg(h);
     return;
   }
+  if (remass && h->inverse_ok && h->p.coarsest_reuse > 0) {
+    int steps = 0, inner = 0;
+    double rel = 0.0;
+    const int kmax = std::min(h->p.coarsest_reuse, h->p.coarsest_refine_max - 1);
+    if (refinement_test(h, kmax, &steps, &inner, &rel)) {
+      h->coarsest_test_res = rel;
+      h->n_refine = std::min(steps + 1, h->p.coarsest_refine_max);
+      h->n_inner = std::max(h->p.inner_coarsest_refine, inner);
+      ++h->inverse_reuses;
+      return;
+    }
+    h->coarsest_test_res = 0.0;
+  }
+  h->inverse_ok = false;
   Level& L = h->lv[h->L - 1];
   ck(h, coarse_to_dense_f32(L.A64, h->Binv, L.Lx, L.Lt, L.n, h->ldc, h->s), "dense");
   {
@@ -563,6 +619,8 @@ void build_coarsest(mg_handle* h) {
     worst = std::max(worst, steps);
   }
   h->n_refine = std::min(worst + 1, h->p.coarsest_refine_max);
+  h->n_inner = h->p.inner_coarsest_refine;
+  h->inverse_ok = true;
 }
 
 void drop_graphs(mg_handle* h) {
@@ -579,7 +637,7 @@ void set_mass_internal(mg_handle* h, double mass) {
   build_coarse_ops(h);
   for (int l = 0; l + 1 < h->L; ++l)
     smoother_coefficients(h, l, h->lv[l].w64[3], h->lv[l].w64[2]);
-  if (h->L > 1) build_coarsest(h);
+  if (h->L > 1) build_coarsest(h, true);
   sync(h);
 }
 
@@ -641,6 +699,10 @@ mg_status validate(const mg_params* p, std::string& msg) {
   }
   if (p->setup_sweeps < 0 || p->power_iters < 1) { msg = "setup_sweeps >= 0 and power_iters >= 1 required"; return MG_ERR_ARG; }
   if (p->max_rhs < 1 || p->max_rhs > 64) { msg = "max_rhs must be in [1, 64]"; return MG_ERR_ARG; }
+  if (p->coarsest_reuse < 0) {
+    msg = "coarsest_reuse must be >= 0";
+    return MG_ERR_ARG;
+  }
   if (!(p->reliable_delta > 0.0 && p->reliable_delta < 1.0)) {
     msg = "reliable_delta must be in (0, 1)";
     return MG_ERR_ARG;
@@ -1725,6 +1787,7 @@ mg_status mg_params_default(mg_params* p, int Lx, int Lt) {
   p->vcycle_coarse_bf16 = 1;
   p->max_rhs = 1;
   p->reliable_delta = 0.1;
+  p->coarsest_reuse = 0;
   p->profile = 0;
   p->coarsest_dense_max = 16384;
   p->coarsest_gj_tcgen05 = 0;
@@ -2228,6 +2291,13 @@ mg_status mg_get_coarsest_info(const mg_handle* h, int* dense, int* steps, doubl
   if (dense) *dense = h->dense ? 1 : 0;
   if (steps) *steps = h->dense ? h->n_refine : h->ccg_iters;
   if (test_residual) *test_residual = h->coarsest_test_res;
+  return MG_OK;
+}
+
+mg_status mg_get_coarsest_reuse(const mg_handle* h, int* inner, int* reuses) {
+  if (!h || h->L < 2) return MG_ERR_ARG;
+  if (inner) *inner = h->n_inner;
+  if (reuses) *reuses = h->inverse_reuses;
   return MG_OK;
 }
 

@@ -39,7 +39,8 @@ class MgParams(ctypes.Structure):
                 ("coarsest_dense_max", ctypes.c_int), ("coarsest_gj_tcgen05", ctypes.c_int),
                 ("refine_levels", ctypes.c_int * MG_MAX_REFINE), ("refine_cycles", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("remass_quadratic", ctypes.c_int),
-                ("smooth_omega", ctypes.c_double), ("reliable_delta", ctypes.c_double)]
+                ("smooth_omega", ctypes.c_double), ("reliable_delta", ctypes.c_double),
+                ("coarsest_reuse", ctypes.c_int)]
 
 
 class MgStencilTuning(ctypes.Structure):
@@ -88,6 +89,7 @@ _SIGS = {
     "mg_get_coarse_op": (_i, [_vp, _i, _vp]),
     "mg_get_smoother": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "mg_get_coarsest_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "mg_get_coarsest_reuse": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mg_get_smoothing": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "mg_block_map": (_i, [_i, _i, _i, _i, _vp, _vp, _vp]),
     "mg_apply_A_dot_noalloc": (_i, [_vp, _vp, _vp, _vp]),
@@ -368,6 +370,13 @@ def mg_get_coarsest_info(h):
     dense, steps, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().mg_get_coarsest_info(h, ctypes.byref(dense), ctypes.byref(steps), ctypes.byref(res)), h)
     return bool(dense.value), steps.value, res.value
+
+
+def mg_get_coarsest_reuse(h):
+    """(FP32 V-cycle refinement steps, re-masses that kept the previous inverse)."""
+    inner, reuses = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mg_get_coarsest_reuse(h, ctypes.byref(inner), ctypes.byref(reuses)), h)
+    return inner.value, reuses.value
 
 
 def mg_block_map(Lx, Lt, bx, bt, coarse, offset, stream=None):
