@@ -115,3 +115,24 @@ def test_new_entry_points_reject_arguments_on_the_host(lib_path):
     rr = (ctypes.c_double * 4)()
     n = ctypes.c_int()
     assert L.mg_get_refine_rho(None, rr, 4, ctypes.byref(n)) == 1
+
+
+def test_solver_parameters_on_the_host(lib_path):
+    """reliable_delta and coarsest_reuse: their defaults, their checks in the
+    size-only pass (no GPU needed), and the sizes they leave unchanged."""
+    from paper_0710_3612_gb300 import mg
+    p = mg.make_params(64, 64, [(4, 4), (2, 2)], [8, 8])
+    assert p.reliable_delta == 0.1 and p.coarsest_reuse == 0
+    p.setup_noise = 1
+    res = mg.mg_setup_bytes(p)[0]
+    ok = mg.make_params(64, 64, [(4, 4), (2, 2)], [8, 8], reliable_delta=0.5, coarsest_reuse=12)
+    ok.setup_noise = 1
+    assert mg.mg_setup_bytes(ok)[0] == res
+    for kw in (dict(reliable_delta=0.0), dict(reliable_delta=1.0), dict(reliable_delta=float("nan")),
+               dict(coarsest_reuse=-1)):
+        q = mg.make_params(64, 64, [(4, 4), (2, 2)], [8, 8], **kw)
+        q.setup_noise = 1
+        with pytest.raises(mg.MgError) as e:
+            mg.mg_setup_bytes(q)
+        assert e.value.status == 1 and next(iter(kw)) in str(e.value)
+    assert mg.SOLVER_MGCG_RELIABLE == 3
